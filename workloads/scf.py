@@ -1,0 +1,156 @@
+"""Closed-shell RHF, MO transform and occupied/virtual pairing.
+
+The paper takes its orbitals and integrals from external programs (Implementation
+section); this module is the synthetic stand-in: canonical RHF orbitals with a
+deterministic phase, dense chemists'-notation MO integrals (pq|rs), and the
+pairing of Fig. 1 -- the k-th highest occupied orbital with the k-th lowest
+virtual (hole indices reversed).
+"""
+from dataclasses import dataclass, field
+import numpy as np
+
+from .ppp import polyene_geometry, acene_geometry, ppp_site_hamiltonian
+from .hchain import hchain_ao_integrals
+
+
+@dataclass
+class Hamiltonian:
+    """One active-space Hamiltonian in the MO basis (Hartree, chemists' notation)."""
+    name: str
+    h: np.ndarray            # [n, n] one-electron integrals
+    eri: np.ndarray          # [n, n, n, n] (pq|rs)
+    e_const: float           # constant energy (core-core / nuclear repulsion)
+    occ_of_pair: np.ndarray  # [N] MO index of the occupied orbital of each pair
+    vir_of_pair: np.ndarray  # [N] MO index of the virtual orbital of each pair
+    mo_energy: np.ndarray = field(default=None)
+    e_rhf: float = 0.0
+
+    @property
+    def n_orb(self):
+        return self.h.shape[0]
+
+    @property
+    def n_pairs(self):
+        return len(self.occ_of_pair)
+
+    def min_orbital_gap(self):
+        e = np.sort(self.mo_energy)
+        return float(np.min(np.diff(e))) if len(e) > 1 else 0.0
+
+
+def _fix_phase(C):
+    C = C.copy()
+    for k in range(C.shape[1]):
+        i = int(np.argmax(np.abs(C[:, k]) + 1e-9 * np.arange(C.shape[0])[::-1]))
+        if C[i, k] < 0:
+            C[:, k] = -C[:, k]
+    return C
+
+
+def rhf(S, h, n_occ, jk, max_iter=500, tol=1e-11, diis_dim=8):
+    """Closed-shell RHF with Pulay DIIS.  jk(P) returns (J, K) for the AO
+    density P = 2 C_occ C_occ^T.  Returns (mo_energy, C, e_elec)."""
+    s, U = np.linalg.eigh(S)
+    X = U @ np.diag(s ** -0.5) @ U.T
+    e, Cp = np.linalg.eigh(X.T @ h @ X)
+    C = X @ Cp
+    fs, es = [], []
+    e_old = 0.0
+    for it in range(max_iter):
+        Co = C[:, :n_occ]
+        P = 2.0 * Co @ Co.T
+        J, K = jk(P)
+        F = h + J - 0.5 * K
+        e_elec = 0.5 * np.sum(P * (h + F))
+        err = X.T @ (F @ P @ S - S @ P @ F) @ X
+        fs.append(F); es.append(err)
+        fs, es = fs[-diis_dim:], es[-diis_dim:]
+        if len(fs) > 1:
+            m = len(fs)
+            B = -np.ones((m + 1, m + 1)); B[m, m] = 0.0
+            for i in range(m):
+                for j in range(m):
+                    B[i, j] = np.sum(es[i] * es[j])
+            rhs = np.zeros(m + 1); rhs[m] = -1.0
+            coef = np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
+            F = sum(c * f for c, f in zip(coef, fs))
+        e, Cp = np.linalg.eigh(X.T @ F @ X)
+        C = X @ Cp
+        if np.max(np.abs(err)) < tol and abs(e_elec - e_old) < tol:
+            break
+        e_old = e_elec
+    Co = C[:, :n_occ]
+    P = 2.0 * Co @ Co.T
+    J, K = jk(P)
+    F = h + J - 0.5 * K
+    e, Cp = np.linalg.eigh(X.T @ F @ X)
+    C = _fix_phase(X @ Cp)
+    e_elec = 0.5 * np.sum(P * (h + F))
+    return e, C, e_elec
+
+
+def mo_integrals(C, h_ao, eri_ao=None, gamma_zdo=None):
+    """(h_mo, eri_mo).  Either a dense AO ERI or a ZDO gamma matrix."""
+    h_mo = C.T @ h_ao @ C
+    if gamma_zdo is not None:
+        n = C.shape[1]
+        D = (C[:, :, None] * C[:, None, :]).reshape(C.shape[0], n * n)
+        eri = (D.T @ gamma_zdo @ D).reshape(n, n, n, n)
+    else:
+        eri = np.einsum('pqrs,pi,qj,rk,sl->ijkl', eri_ao, C, C, C, C, optimize=True)
+    return h_mo, eri
+
+
+def pair_orbitals(n_occ, n_pairs=None):
+    """Fig. 1 pairing on energy-ordered MOs: pair k couples occupied orbital
+    n_occ-1-k (k-th highest) with virtual n_occ+k (k-th lowest)."""
+    N = n_occ if n_pairs is None else n_pairs
+    occ = np.array([n_occ - 1 - k for k in range(N)], dtype=np.int32)
+    vir = np.array([n_occ + k for k in range(N)], dtype=np.int32)
+    return occ, vir
+
+
+def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True):
+    """kind 'polyene' (size = number of sites) or 'acene' (size = rings)."""
+    if kind == 'polyene':
+        xyz, bonds = polyene_geometry(size)
+        name = f"PPP C{size}H{size + 2}"
+    elif kind == 'acene':
+        xyz, bonds = acene_geometry(size)
+        name = f"PPP {size}-acene"
+    else:
+        raise ValueError(kind)
+    h, gamma, e_const = ppp_site_hamiltonian(xyz, bonds, beta_ev, u_ev)
+    n = h.shape[0]
+    assert n % 2 == 0
+    nocc = n // 2
+
+    def jk(P):
+        J = np.diag(gamma @ np.diag(P))
+        K = P * gamma
+        return J, K
+    e, C, e_elec = rhf(np.eye(n), h, nocc, jk)
+    occ, vir = pair_orbitals(nocc)
+    if with_eri:
+        h_mo, eri = mo_integrals(C, h, gamma_zdo=gamma)
+    else:
+        h_mo, eri = C.T @ h @ C, None
+    H = Hamiltonian(name, h_mo, eri, e_const, occ, vir, e, e_elec + e_const)
+    H.C = C
+    H.gamma_site = gamma
+    return H
+
+
+def build_hchain(n_atoms, spacing_angstrom):
+    S, h, eri, e_nuc = hchain_ao_integrals(n_atoms, spacing_angstrom)
+    nocc = n_atoms // 2
+
+    def jk(P):
+        J = np.einsum('mnls,ls->mn', eri, P)
+        K = np.einsum('mlns,ls->mn', eri, P)
+        return J, K
+    e, C, e_elec = rhf(S, h, nocc, jk)
+    occ, vir = pair_orbitals(nocc)
+    h_mo, eri_mo = mo_integrals(C, h, eri_ao=eri)
+    return Hamiltonian(f"H{n_atoms} d={spacing_angstrom:.3f}A", h_mo, eri_mo,
+                       e_nuc, occ, vir, e, e_elec + e_nuc)
