@@ -236,6 +236,11 @@ def diis_extrapolate(ts, es):
     for i in range(m):
         for j in range(m):
             B[i, j] = np.dot(es[i], es[j])
+    # scaling the error block leaves c unchanged (the multiplier absorbs it)
+    # but keeps lstsq from treating a block of tiny dot products as zero
+    sc = np.max(np.abs(np.diag(B[:m, :m])))
+    if sc > 0.0:
+        B[:m, :m] /= sc
     B[m, :] = -1.0; B[:, m] = -1.0; B[m, m] = 0.0
     rhs = np.zeros(m + 1); rhs[m] = -1.0
     c = np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
