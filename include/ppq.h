@@ -1,0 +1,119 @@
+/*
+ * ppq.h -- C ABI of the GB300 PQ amplitude solver (perfect quadruples model).
+ *
+ * The method (Theory section of the paper): coupled-cluster theory truncated
+ * to amplitudes whose holes and particles carry at most K = 2 pairing labels
+ * (CCSDTQ truncated to two pairs, Eq. decompose and Tables I-II), each label
+ * P being the quartet of alpha/beta occupied orbital occ_of_pair[P] and
+ * alpha/beta virtual orbital vir_of_pair[P] (Fig. 1: the k-th highest occupied
+ * orbital paired with the k-th lowest virtual).  Two-electron integrals are
+ * kept for at most two labels (Table I: v has rank-1 and rank-2 subtensors
+ * only in PQ); the Fock matrix is the full one.  The projected equations
+ * R_mu = <mu| exp(-T) H_N exp(T) |Phi> = 0 are evaluated exactly and solved
+ * by Jacobi steps with orbital-energy denominators and DIIS (Implementation
+ * section); the energy follows Eq. Ec.
+ *
+ * Amplitude layout (length ppq_amp_count):
+ *   t1[P][k]     k = 0..2   single-pair excitations, P = 0..N-1
+ *   t2[P][Q][k]  k = 0..28  two-pair excitations, stored for both orders of
+ *                           the pair, t2[Q][P][swap(k)] = sign(k) t2[P][Q][k],
+ *                           zero when P == Q (the paper's vanishing-diagonal
+ *                           convention).
+ * offset of t2 = 3N; ppq_amp_layout describes the excitation of each channel.
+ *
+ * Conventions of every entry point
+ *   - return 0 on success; < 0 on invalid arguments (nothing written, message
+ *     in ppq_last_error); > 0 numerical status (1 not converged within
+ *     max_iter, 2 diverged, 3 non-finite input) with outputs written;
+ *   - n_pairs >= 2; occ_of_pair / vir_of_pair are HOST int32 arrays of length
+ *     n_pairs that together list every one of the 2 n_pairs active orbitals
+ *     exactly once;
+ *   - h (n_orb^2) and eri (n_orb^4, chemists' notation (pq|rs), 8-fold
+ *     symmetric, row-major) are FP64 and may be host or device pointers
+ *     (detected); they are read, never written, and stay caller-owned;
+ *   - amplitude / residual buffers are FP64 and may be host or device
+ *     pointers (detected);
+ *   - work runs on `stream` (a cudaStream_t, 0 = legacy default stream); the
+ *     call returns after the stream has finished the work;
+ *   - the library keeps a per-device workspace between calls (released by
+ *     ppq_release); calls on one device are serialised by a mutex.
+ */
+#ifndef PPQ_H
+#define PPQ_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int K;              /* amplitude truncation: 2 = PQ (set by pq_solve)        */
+  int K_H;            /* integral truncation in labels: 0 = same as K; only 2  */
+  int precision;      /* 0 = FP64 throughout; 1 = mixed: FP32 residual until   */
+                      /*     ||R|| <= switch_tol or stagnation, then FP64      */
+  double switch_tol;  /* 1e-5                                                  */
+  double r_tol;       /* converged when ||R||_2 <= r_tol ...  (1e-10)           */
+  double e_tol;       /* ... and |dE| <= e_tol (1e-12)                          */
+  int max_iter;       /* 200                                                   */
+  int diis_dim;       /* 8 (0 disables DIIS)                                    */
+  int diis_start;     /* 3                                                     */
+  double level_shift; /* added to |denominator| (0)                             */
+  int guess;          /* 0 = zero amplitudes, 1 = start from t_in               */
+} ppq_opts;
+
+typedef struct {
+  int status;          /* as the return value                                  */
+  int iters;           /* residual evaluations                                 */
+  int polish_iters;    /* of which in FP64 after the switch (mixed)            */
+  int switched_at;     /* iteration of the precision switch (-1 none)          */
+  double res_norm;     /* ||R||_2 over unique amplitudes at the returned t     */
+  double e_corr;       /* correlation energy (Eh)                              */
+  double e_total;      /* e_corr + reference energy + e_const (Eh)             */
+  double t_residual_ms;/* device time in residual evaluations                  */
+  double t_total_ms;   /* wall time of the call                                */
+  double residual_flops; /* algorithmic FLOPs of one residual evaluation       */
+} ppq_info;
+
+/* Fill *o with the defaults listed above.  Returns 0. */
+int ppq_default_opts(ppq_opts* o);
+
+/* Number of amplitudes of the layout above for n_pairs pairs: 3N + 29N^2.
+   Returns 0, or -1 if K != 2 or n_pairs < 1. */
+int ppq_amp_count(int K, int n_pairs, size_t* n_amp);
+
+/* Describe the 32 channels (3 single-pair then 29 two-pair): desc[3*c+0] =
+   number of pairs (1 or 2), desc[3*c+1], desc[3*c+2] = 4-bit monomial masks of
+   the first and second pair: bit 0 annihilates the alpha occupied orbital,
+   bit 1 the beta occupied, bit 2 creates the alpha virtual, bit 3 the beta
+   virtual.  The excitation operator of t1[P][k] is E_P^{m}; that of
+   t2[P][Q][k] is E_P^{a} E_Q^{b}, with E^m = (a+_{v,alpha})^{b2}
+   (a+_{v,beta})^{b3} (a_{o,beta})^{b1} (a_{o,alpha})^{b0} on one pair.
+   desc must hold 96 ints.  Returns 0, -1 for K != 2. */
+int ppq_amp_layout(int K, int* desc);
+
+/* One residual evaluation R(T) and correlation energy at amplitudes t (both
+   in the layout above): the operation of the Theory section, Eq. decompose
+   inserted into the projected CC equations.  precision 0 = FP64, 1 = FP32
+   contractions (energy sums in FP64). */
+int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                const double* h, const double* eri, const double* t,
+                double* r, double* e_corr, int precision, void* stream);
+
+/* Solve the PQ amplitude equations.  t_in (nullable unless guess == 1) and
+   t_out use the layout above; e_corr / e_total / info are host pointers
+   (nullable).  e_total = e_corr + E_ref + e_const with
+   E_ref = sum_i (h_ii + f_ii) over the occupied orbitals. */
+int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+             const double* h, const double* eri, double e_const,
+             const ppq_opts* opts, const double* t_in, double* t_out,
+             double* e_corr, double* e_total, ppq_info* info, void* stream);
+
+/* Free the cached workspace of the current device.  Returns 0. */
+int ppq_release(void);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* ppq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,166 @@
+"""GB300 PQ amplitude solver: Python binding of the C ABI in include/ppq.h.
+
+The binding only marshals arguments (pointers, sizes, the CUDA stream); every
+step of the residual, the energy and the Jacobi/DIIS update runs in the CUDA
+kernels of libppq.so.  There is no CPU fallback: importing the binding without
+the compiled library raises.  Build it with ``python -m
+paper_1609_00077_gb300.build`` (or ``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libppq.so")
+
+N_CHANNELS_1 = 3
+N_CHANNELS_2 = 29
+
+
+class PPQError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("K_H", ctypes.c_int), ("precision", ctypes.c_int),
+                ("switch_tol", ctypes.c_double), ("r_tol", ctypes.c_double),
+                ("e_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("diis_dim", ctypes.c_int), ("diis_start", ctypes.c_int),
+                ("level_shift", ctypes.c_double), ("guess", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("polish_iters", ctypes.c_int), ("switched_at", ctypes.c_int),
+                ("res_norm", ctypes.c_double), ("e_corr", ctypes.c_double),
+                ("e_total", ctypes.c_double), ("t_residual_ms", ctypes.c_double),
+                ("t_total_ms", ctypes.c_double), ("residual_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libppq.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PPQError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -m paper_1609_00077_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        L.ppq_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.ppq_amp_count.argtypes = [I, I, ctypes.POINTER(S)]
+        L.ppq_amp_layout.argtypes = [I, P]
+        L.pq_residual.argtypes = [I, P, P, P, P, P, P, P, I, P]
+        L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
+                               ctypes.POINTER(Info), P]
+        L.ppq_last_error.restype = ctypes.c_char_p
+        for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
+                  L.pq_solve, L.ppq_release):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
+            "pq_solve", "ppq_release", "ppq_last_error"]
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags['C_CONTIGUOUS']
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise PPQError(f"{what} failed ({rc}): {lib().ppq_last_error().decode()}")
+    return rc
+
+
+def amp_count(n_pairs):
+    n = ctypes.c_size_t()
+    _check(lib().ppq_amp_count(2, n_pairs, ctypes.byref(n)), "ppq_amp_count")
+    return n.value
+
+
+def amp_layout():
+    """(kind, first monomial, second monomial) for the 32 channels."""
+    d = np.zeros(96, dtype=np.int32)
+    _check(lib().ppq_amp_layout(2, d.ctypes.data), "ppq_amp_layout")
+    return d.reshape(32, 3)
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().ppq_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _pairs(occ, vir):
+    occ = np.ascontiguousarray(occ, dtype=np.int32)
+    vir = np.ascontiguousarray(vir, dtype=np.int32)
+    return occ, vir
+
+
+def pq_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, stream=None):
+    """R(T) and E_c at amplitudes t (layout of include/ppq.h).  h, eri, t, r may
+    be torch CUDA tensors or numpy arrays (FP64, contiguous).  Returns (r, e_corr)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    if r is None:
+        r = np.zeros(amp_count(N)) if isinstance(t, np.ndarray) else t.new_zeros(amp_count(N))
+    e = ctypes.c_double()
+    rc = lib().pq_residual(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t),
+                           _ptr(r), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p),
+                           precision, _stream(stream))
+    _check(rc, "pq_residual")
+    return r, e.value
+
+
+def pq_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=None,
+             stream=None, **opts):
+    """Solve the PQ equations.  Returns (status, e_total, t_out, info dict)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    o = default_opts(**opts)
+    if t_in is not None and 'guess' not in opts:
+        o.guess = 1
+    if t_out is None:
+        t_out = np.zeros(amp_count(N))
+    ec, et = ctypes.c_double(), ctypes.c_double()
+    info = Info()
+    rc = lib().pq_solve(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), float(e_const),
+                        ctypes.byref(o), _ptr(t_in), _ptr(t_out),
+                        ctypes.cast(ctypes.pointer(ec), ctypes.c_void_p),
+                        ctypes.cast(ctypes.pointer(et), ctypes.c_void_p),
+                        ctypes.byref(info), _stream(stream))
+    _check(rc, "pq_solve")
+    return rc, et.value, t_out, info.as_dict()
+
+
+def release():
+    return lib().ppq_release()

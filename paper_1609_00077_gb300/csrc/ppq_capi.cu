@@ -1,0 +1,550 @@
+// ppq_capi.cu -- C ABI of the PQ solver (see include/ppq.h): argument checks,
+// input staging, the per-device workspace, the residual pipeline and the
+// Jacobi/DIIS solve loop (Implementation section: denominators, DIIS).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <type_traits>
+#include <utility>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ppq.h"
+#include "ppq_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(-100, "CUDA error %s at %s:%d", cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                       \
+  } while (0)
+
+constexpr int kDiisMax = 16;
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+
+// Per-device workspace, grown on demand and kept between calls.
+struct Workspace {
+  int N = 0;       // capacity in pairs
+  size_t eri_cap = 0;
+  int diis_cap = 0;
+  // staged inputs
+  double *h = nullptr, *eri = nullptr;  // only when the caller passes host pointers
+  int *occ = nullptr, *vir = nullptr, *lab = nullptr;
+  double *f = nullptr, *hp = nullptr, *fo = nullptr, *fv = nullptr;
+  double *g1d = nullptr, *g2d = nullptr;
+  float *g1f = nullptr, *g2f = nullptr;
+  // amplitudes, residual
+  double *t = nullptr, *r = nullptr, *dir = nullptr, *abuf = nullptr;
+  // residual scratch (sized for double, reused as float)
+  void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
+  double *esite = nullptr, *epair = nullptr;
+  // reductions
+  double *part = nullptr, *scal = nullptr, *coef = nullptr;
+  int* ok = nullptr;
+  int* order = nullptr;
+  double* host = nullptr;  // pinned host scalars
+  // DIIS ring: slots of t_new and of e
+  double *slot_t = nullptr, *slot_e = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+std::mutex g_mu;
+std::map<int, Workspace*> g_ws;
+
+size_t amp_len(int N) { return (size_t)3 * N + (size_t)PPQ_NA2 * N * N; }
+
+void free_ws(Workspace* w) {
+  void* ps[] = {w->h, w->eri, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
+                w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
+                w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (w->host) cudaFreeHost(w->host);
+  if (w->ev0) cudaEventDestroy(w->ev0);
+  if (w->ev1) cudaEventDestroy(w->ev1);
+  *w = Workspace();
+}
+
+int grow(Workspace* w, int N, int diis) {
+  if (N <= w->N && diis <= w->diis_cap && w->host) return 0;
+  int n = 2 * N;
+  int Nc = N > w->N ? N : w->N;
+  int dc = diis > w->diis_cap ? diis : w->diis_cap;
+  free_ws(w);
+  size_t NN = (size_t)Nc * Nc, L = amp_len(Nc);
+  n = 2 * Nc;
+#define AL(ptr, bytes) CK(cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 8))
+  AL(w->h, sizeof(double) * n * n);
+  AL(w->occ, sizeof(int) * Nc); AL(w->vir, sizeof(int) * Nc); AL(w->lab, sizeof(int) * n);
+  AL(w->f, sizeof(double) * n * n); AL(w->hp, sizeof(double) * n * n);
+  AL(w->fo, sizeof(double) * Nc); AL(w->fv, sizeof(double) * Nc);
+  AL(w->g1d, sizeof(double) * Nc * PPQ_NG1); AL(w->g2d, sizeof(double) * NN * PPQ_NG2);
+  AL(w->g1f, sizeof(float) * Nc * PPQ_NG1); AL(w->g2f, sizeof(float) * NN * PPQ_NG2);
+  AL(w->t, sizeof(double) * L); AL(w->r, sizeof(double) * L);
+  AL(w->dir, sizeof(double) * NN * PPQ_NA2); AL(w->abuf, sizeof(double) * NN * PPQ_NA2);
+  AL(w->cl, sizeof(double) * NN * PPQ_NS36); AL(w->hs, sizeof(double) * Nc * 256);
+  AL(w->pg, sizeof(double) * NN * PPQ_NS36); AL(w->pt7, sizeof(double) * NN * PPQ_NT7E);
+  AL(w->pc0, sizeof(double) * NN * PPQ_NCOL0);
+  AL(w->esite, sizeof(double) * Nc); AL(w->epair, sizeof(double) * NN);
+  AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
+  AL(w->scal, sizeof(double) * (kDiisMax + 4)); AL(w->coef, sizeof(double) * kDiisMax);
+  AL(w->ok, sizeof(int)); AL(w->order, sizeof(int) * kDiisMax);
+  if (dc > 0) {
+    AL(w->slot_t, sizeof(double) * L * dc);
+    AL(w->slot_e, sizeof(double) * L * dc);
+  }
+#undef AL
+  CK(cudaMallocHost((void**)&w->host, sizeof(double) * 64));
+  CK(cudaEventCreate(&w->ev0));
+  CK(cudaEventCreate(&w->ev1));
+  w->N = Nc;
+  w->diis_cap = dc;
+  return 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// validate the pairing: a bijection onto 0..2N-1
+int check_pairing(int N, const int* occ, const int* vir, std::vector<int>& lab) {
+  if (N < 2) return fail(-1, "n_pairs must be >= 2 (got %d)", N);
+  if (!occ || !vir) return fail(-2, "occ_of_pair / vir_of_pair must be non-null host arrays");
+  int n = 2 * N;
+  lab.assign(n, -1);
+  for (int k = 0; k < N; ++k) {
+    int o = occ[k], v = vir[k];
+    if (o < 0 || o >= n || v < 0 || v >= n)
+      return fail(-3, "orbital index out of range in pair %d", k);
+    if (lab[o] >= 0 || lab[v] >= 0 || o == v)
+      return fail(-3, "orbital listed twice in the pairing (pair %d)", k);
+    lab[o] = k;
+    lab[v] = k;
+  }
+  return 0;
+}
+
+__global__ void k_count_nonfinite(size_t L, const double* __restrict__ x, int* __restrict__ bad) {
+  int b = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) b = 1;
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+__global__ void k_fdiag(int N, int n, const double* __restrict__ f, const int* __restrict__ occ,
+                        const int* __restrict__ vir, double* __restrict__ fo, double* __restrict__ fv) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  fo[k] = f[(size_t)occ[k] * n + occ[k]];
+  fv[k] = f[(size_t)vir[k] * n + vir[k]];
+}
+
+__global__ void k_eref(int N, int n, const double* __restrict__ h, const double* __restrict__ f,
+                       const int* __restrict__ occ, double* __restrict__ out) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int k = 0; k < N; ++k) s += h[(size_t)occ[k] * n + occ[k]] + f[(size_t)occ[k] * n + occ[k]];
+  out[0] = s;
+}
+
+// multi-dot: row 0 = weighted norm^2 of x0; rows 1..m = <e_slot[order[j]], e_new>
+__global__ void k_multidot(size_t L, int N, const double* __restrict__ x0, int m,
+                           const double* __restrict__ slots, size_t ld, const int* __restrict__ order,
+                           int inew, double* __restrict__ part) {
+  __shared__ double red[32];
+  int row = blockIdx.y;
+  const double* a;
+  const double* b;
+  if (row == 0) { a = x0; b = x0; }
+  else { a = slots + (size_t)order[row - 1] * ld; b = slots + (size_t)inew * ld; }
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
+    s += ppq::amp_weight(i, N) * a[i] * b[i];
+  s = ppq::block_sum(s, red);
+  if (threadIdx.x == 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_rowsum(int nb, int rows, const double* __restrict__ part, int N,
+                         const double* __restrict__ esite, const double* __restrict__ epair,
+                         double* __restrict__ out) {
+  __shared__ double red[32];
+  for (int r = 0; r < rows; ++r) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[(size_t)r * nb + i];
+    s = ppq::block_sum(s, red);
+    if (threadIdx.x == 0) out[r] = s;
+  }
+  double e = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) e += esite[i];
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) e += 0.5 * epair[i];
+  e = ppq::block_sum(e, red);
+  if (threadIdx.x == 0) out[rows] = e;
+}
+
+struct Problem {
+  int N, n;
+  const double* h;    // device
+  const double* eri;  // device
+};
+
+// stage integrals: Fock, h', gathers, denominators
+int stage(Workspace* w, const Problem& P, cudaStream_t s) {
+  int N = P.N, n = P.n;
+  ppq::k_fock<<<(n * n + 127) / 128, 128, 0, s>>>(n, N, P.h, P.eri, w->occ, w->lab, w->f, w->hp);
+  k_fdiag<<<1, 256, 0, s>>>(N, n, w->f, w->occ, w->vir, w->fo, w->fv);
+  size_t tot = (size_t)N * N * PPQ_NG2 + (size_t)N * PPQ_NG1;
+  unsigned nb = (unsigned)((tot + 255) / 256);
+  ppq::k_gather<double><<<nb, 256, 0, s>>>(n, N, w->hp, P.eri, w->occ, w->vir, w->g1d, w->g2d);
+  ppq::k_gather<float><<<nb, 256, 0, s>>>(n, N, w->hp, P.eri, w->occ, w->vir, w->g1f, w->g2f);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+// one residual evaluation at w->t into w->r; energy pieces into esite/epair
+template <typename R>
+int residual(Workspace* w, int N, cudaStream_t s) {
+  const R* g1 = std::is_same<R, double>::value ? (const R*)w->g1d : (const R*)w->g1f;
+  const R* g2 = std::is_same<R, double>::value ? (const R*)w->g2d : (const R*)w->g2f;
+  const double* t1 = w->t;
+  const double* t2 = w->t + 3 * N;
+  R* cl = (R*)w->cl;
+  R* hs = (R*)w->hs;
+  R* pg = (R*)w->pg;
+  R* pt7 = (R*)w->pt7;
+  R* pc0 = (R*)w->pc0;
+  int NN = N * N;
+  ppq::k_links<R><<<(NN + 63) / 64, 64, 0, s>>>(N, t2, cl);
+  ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
+  ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair);
+  ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
+  ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, pt7, pg, cl, t2, w->dir, w->abuf);
+  size_t L2 = (size_t)NN * PPQ_NA2;
+  ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->r + 3 * N);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
+  return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+}
+
+double residual_flops(int N) {
+  double n = N, pairs = n * (n - 1);
+  double fma = 0.0;
+  fma += pairs * PPQ_NSOP;                                                  // links
+  fma += n * (PPQ_H1_NEL + 2 * 3 * 16 * 3);                                 // site closures (approx)
+  fma += pairs * (17792.0 + PPQ_PR_N + PPQ_PL_N);                           // pair closures
+  fma += n * ((n - 1) * PPQ_NT3 + (n - 1) * (n - 2) * PPQ_NT8);             // r1
+  fma += pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 +         // r2
+                  (n - 2) * ((n - 3) * PPQ_NQ9 + PPQ_NC9) + PPQ_NSOP);
+  return 2.0 * fma;
+}
+
+// common entry preparation: workspace, pairing, staged inputs
+int prepare(int N, const int* occ, const int* vir, const double* h, const double* eri, int diis,
+            cudaStream_t s, Workspace** pw, Problem* P) {
+  std::vector<int> lab;
+  int rc = check_pairing(N, occ, vir, lab);
+  if (rc) return rc;
+  if (!h || !eri) return fail(-2, "h and eri must be non-null");
+  int dev;
+  CK(cudaGetDevice(&dev));
+  Workspace*& w = g_ws[dev];
+  if (!w) w = new Workspace();
+  if ((rc = grow(w, N, diis))) return rc;
+  int n = 2 * N;
+  CK(cudaMemcpyAsync(w->occ, occ, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->vir, vir, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->lab, lab.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  P->N = N;
+  P->n = n;
+  size_t n4 = (size_t)n * n * n * n;
+  if (is_device_ptr(h)) P->h = h;
+  else {
+    CK(cudaMemcpyAsync(w->h, h, sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
+    P->h = w->h;
+  }
+  if (is_device_ptr(eri)) P->eri = eri;
+  else {
+    if (w->eri_cap < n4) {
+      if (w->eri) cudaFree(w->eri);
+      w->eri = nullptr;
+      CK(cudaMalloc((void**)&w->eri, sizeof(double) * n4));
+      w->eri_cap = n4;
+    }
+    CK(cudaMemcpyAsync(w->eri, eri, sizeof(double) * n4, cudaMemcpyHostToDevice, s));
+    P->eri = w->eri;
+  }
+  // non-finite screen
+  CK(cudaMemsetAsync(w->ok, 0, sizeof(int), s));
+  k_count_nonfinite<<<kRedBlocks, 256, 0, s>>>((size_t)n * n, P->h, w->ok);
+  k_count_nonfinite<<<kRedBlocks * 4, 256, 0, s>>>(n4, P->eri, w->ok);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, w->ok, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return 3;
+  if ((rc = stage(w, *P, s))) return rc;
+  *pw = w;
+  return 0;
+}
+
+int copy_amps(double* dst, const double* src, size_t L, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, sizeof(double) * L, cudaMemcpyDefault, s));
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppq_default_opts(ppq_opts* o) {
+  if (!o) return fail(-2, "null opts");
+  o->K = 2; o->K_H = 0; o->precision = 0;
+  o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-12;
+  o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
+  o->level_shift = 0.0; o->guess = 0;
+  return 0;
+}
+
+int ppq_amp_count(int K, int n_pairs, size_t* n_amp) {
+  if (K != 2 || n_pairs < 1 || !n_amp) return fail(-1, "ppq_amp_count: K must be 2 and n_pairs >= 1");
+  *n_amp = amp_len(n_pairs);
+  return 0;
+}
+
+int ppq_amp_layout(int K, int* desc) {
+  if (K != 2 || !desc) return fail(-1, "ppq_amp_layout: K must be 2");
+  for (int i = 0; i < 96; ++i) desc[i] = ppq_layout_desc[i];
+  return 0;
+}
+
+int ppq_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  auto it = g_ws.find(dev);
+  if (it != g_ws.end() && it->second) {
+    free_ws(it->second);
+    delete it->second;
+    g_ws.erase(it);
+  }
+  return 0;
+}
+
+const char* ppq_last_error(void) { return g_err.c_str(); }
+
+int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                const double* eri, const double* t, double* r, double* e_corr, int precision,
+                void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!t || !r) return fail(-2, "t and r must be non-null");
+  if (precision != 0 && precision != 1) return fail(-4, "precision must be 0 or 1");
+  Workspace* w = nullptr;
+  Problem P;
+  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 0, s, &w, &P);
+  if (rc) return rc;
+  int N = n_pairs;
+  size_t L = amp_len(N);
+  if ((rc = copy_amps(w->t, t, L, s))) return rc;
+  if ((rc = run_residual(w, N, precision, s))) return rc;
+  k_rowsum<<<1, 256, 0, s>>>(1, 0, w->part, N, w->esite, w->epair, w->scal);
+  if ((rc = copy_amps(r, w->r, L, s))) return rc;
+  CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e_corr) *e_corr = w->host[0];
+  return 0;
+}
+
+int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
+             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  if (o.K != 2) return fail(-4, "pq_solve: K must be 2 (PQ)");
+  if (o.K_H != 0 && o.K_H != 2) return fail(-4, "pq_solve: only the two-label integral truncation (K_H = 2) is built");
+  if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
+  if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
+    return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
+  if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
+  Workspace* w = nullptr;
+  Problem P;
+  int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
+  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, m_max, s, &w, &P);
+  if (rc) {
+    if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
+    return rc;
+  }
+  int N = n_pairs, n = 2 * N;
+  size_t L = amp_len(N);
+  if (o.guess == 1) { if ((rc = copy_amps(w->t, t_in, L, s))) return rc; }
+  else CK(cudaMemsetAsync(w->t, 0, sizeof(double) * L, s));
+  k_eref<<<1, 1, 0, s>>>(N, n, P.h, w->f, w->occ, w->scal + kDiisMax + 2);
+  CK(cudaMemcpyAsync(w->host + 40, w->scal + kDiisMax + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+
+  int prec = o.precision;
+  int switched_at = prec ? -1 : 0, polish = 0;
+  double e_old = 0.0, res = 0.0, e = 0.0, t_res_ms = 0.0;
+  bool have_old = false;
+  int status = 1, it = 0;
+  std::vector<double> B(kDiisMax * kDiisMax, 0.0);
+  std::vector<int> ring;  // slot ids, oldest first
+  std::vector<double> hist;
+  unsigned lb = (unsigned)((L + 255) / 256);
+  for (it = 1; it <= o.max_iter; ++it) {
+    CK(cudaEventRecord(w->ev0, s));
+    if ((rc = run_residual(w, N, prec, s))) return rc;
+    CK(cudaEventRecord(w->ev1, s));
+    // Jacobi step into the next DIIS slot
+    int slot;
+    if ((int)ring.size() < m_max) slot = (int)ring.size();
+    else slot = ring.front();
+    double* st = w->slot_t + (size_t)slot * L;
+    double* se = w->slot_e + (size_t)slot * L;
+    ppq::k_jacobi<<<lb, 256, 0, s>>>(L, N, w->t, w->r, w->fo, w->fv, o.level_shift, st, se);
+    // order of the slots that will be active after this step
+    std::vector<int> act;
+    for (int id : ring) if (id != slot) act.push_back(id);
+    if ((int)act.size() >= m_max) act.erase(act.begin());
+    act.push_back(slot);
+    int m = (int)act.size();
+    memcpy(w->host + 48, act.data(), sizeof(int) * m);
+    CK(cudaMemcpyAsync(w->order, w->host + 48, sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    dim3 g(kRedBlocks, 1 + m);
+    k_multidot<<<g, 256, 0, s>>>(L, N, w->r, m, w->slot_e, L, w->order, slot, w->part);
+    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
+    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, w->ev0, w->ev1);
+    t_res_ms += ms;
+    res = sqrt(w->host[0]);
+    e = w->host[m + 1];
+    if (prec == 0 && switched_at >= 0) polish++;
+    hist.push_back(res);
+    if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
+    if (prec == 0 && have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
+    // precision switch: reached switch_tol, or stagnation (< 10 % decrease over 3 iterations)
+    if (prec == 1) {
+      size_t k = hist.size();
+      bool stagnant = k >= 4 && res < 1e-3 && hist[k - 1] > 0.9 * hist[k - 4];
+      if (res <= o.switch_tol || stagnant) {
+        prec = 0;
+        switched_at = it;
+        have_old = false;
+        ring.clear();  // restart DIIS with FP64 residuals
+        continue;      // re-evaluate the residual at the same t in FP64
+      }
+    }
+    e_old = e;
+    have_old = true;
+    // new row/column of the DIIS matrix, indexed by slot id
+    ring = act;
+    for (int i = 0; i < m; ++i) {
+      double d = w->host[1 + i];
+      B[act[i] * kDiisMax + slot] = d;
+      B[slot * kDiisMax + act[i]] = d;
+    }
+    bool extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
+    if (extrap) {
+      // solve [B -1; -1 0] [c; l] = [0; -1] on the host (m <= 16)
+      int nn = m + 1;
+      std::vector<double> A((size_t)nn * (nn + 1), 0.0);
+      double sc = 0.0;
+      for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(B[act[i] * kDiisMax + act[i]]));
+      if (sc <= 0.0) sc = 1.0;
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) A[i * (nn + 1) + j] = B[act[i] * kDiisMax + act[j]] / sc;
+        A[i * (nn + 1) + m] = -1.0;
+      }
+      for (int j = 0; j < m; ++j) A[m * (nn + 1) + j] = -1.0;
+      A[m * (nn + 1) + nn] = -1.0;
+      bool ok = true;
+      for (int c = 0; c < nn && ok; ++c) {
+        int piv = c;
+        for (int r2 = c + 1; r2 < nn; ++r2)
+          if (fabs(A[r2 * (nn + 1) + c]) > fabs(A[piv * (nn + 1) + c])) piv = r2;
+        if (fabs(A[piv * (nn + 1) + c]) < 1e-300) { ok = false; break; }
+        if (piv != c)
+          for (int k = 0; k <= nn; ++k) std::swap(A[c * (nn + 1) + k], A[piv * (nn + 1) + k]);
+        for (int r2 = c + 1; r2 < nn; ++r2) {
+          double f = A[r2 * (nn + 1) + c] / A[c * (nn + 1) + c];
+          for (int k = c; k <= nn; ++k) A[r2 * (nn + 1) + k] -= f * A[c * (nn + 1) + k];
+        }
+      }
+      std::vector<double> x(nn, 0.0);
+      if (ok) {
+        for (int r2 = nn - 1; r2 >= 0; --r2) {
+          double sum = A[r2 * (nn + 1) + nn];
+          for (int k = r2 + 1; k < nn; ++k) sum -= A[r2 * (nn + 1) + k] * x[k];
+          x[r2] = sum / A[r2 * (nn + 1) + r2];
+        }
+        for (int i = 0; i < m; ++i) w->host[8 + i] = x[i];
+      } else {
+        for (int i = 0; i < m; ++i) w->host[8 + i] = (i == m - 1) ? 1.0 : 0.0;
+      }
+    } else {
+      for (int i = 0; i < m; ++i) w->host[8 + i] = (i == m - 1) ? 1.0 : 0.0;
+    }
+    int one = 1;
+    memcpy(w->host + 32, &one, sizeof(int));
+    CK(cudaMemcpyAsync(w->coef, w->host + 8, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
+    ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, w->t);
+    CK(cudaGetLastError());
+  }
+  if (it > o.max_iter) it = o.max_iter;
+  if (t_out) { if ((rc = copy_amps(t_out, w->t, L, s))) return rc; }
+  CK(cudaStreamSynchronize(s));
+  double e_ref = w->host[40];
+  if (e_corr) *e_corr = e;
+  if (e_total) *e_total = e + e_ref + e_const;
+  if (info) {
+    info->status = status;
+    info->iters = it;
+    info->polish_iters = o.precision ? polish : 0;
+    info->switched_at = o.precision ? switched_at : -1;
+    info->res_norm = res;
+    info->e_corr = e;
+    info->e_total = e + e_ref + e_const;
+    info->t_residual_ms = t_res_ms;
+    info->t_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    info->residual_flops = residual_flops(N);
+  }
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,488 @@
+// ppq_kernels.cuh -- CUDA kernels of the PQ residual, energy and update.
+//
+// The residual R(T) of the PQ model (Theory section: the block decomposition
+// of Eq. decompose inserted into the projected CC equations, exact, two-label
+// integrals, full Fock matrix) is evaluated in a site formulation: every pair
+// label P is a site with a 16-state local Fock space, T and H are written as
+// graded products of per-site monomials, and the linked residual
+// <mu| exp(-T) H exp(T) |Phi> is summed over the Hamiltonian pieces H_S
+// (one- or two-site S).  For each piece only clusters touching S contribute;
+// internal clusters are absorbed into the closure Ht_S = exp(-I_S) H_S exp(I_S)
+// and the clusters linking S to the output sites enter through the link
+// coefficients Cl[X,Y] = components of exp(T_XY)|ref>.  Nine topologies
+// (output sites inside or outside S, zero to two summed sites) give the
+// residual; the quartic one (two summed sites) is the paper's O(N^4)
+// three-label-intermediate class (Table V, kernels o(x,y,z) <- sum_w ...).
+// All coefficient tables come from tables.py (ppq_tables.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "ppq_tables.h"
+
+namespace ppq {
+
+__device__ __forceinline__ int unpack_t(int32_t e) { return e >> 17; }
+__device__ __forceinline__ int unpack_s(int32_t e) { return (e >> 1) & 0xFFFF; }
+template <typename R>
+__device__ __forceinline__ R unpack_sign(int32_t e) { return (e & 1) ? R(-1) : R(1); }
+
+// ---------------------------------------------------------------- a1: staging
+// f_pq = h_pq + sum_i [2 (pq|ii) - (pi|iq)];  h'_pq keeps the mean field of the
+// occupied orbitals whose label lies outside {L(p), L(q)} (those integrals are
+// three-label ones, dropped by the two-label truncation).
+__global__ void k_fock(int n, int N, const double* __restrict__ h, const double* __restrict__ eri,
+                       const int* __restrict__ occ, const int* __restrict__ lab,
+                       double* __restrict__ f, double* __restrict__ hp) {
+  int pq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= n * n) return;
+  int p = pq / n, q = pq % n;
+  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  double mf = 0.0, mfl = 0.0;
+  int lp = lab[p], lq = lab[q];
+  for (int k = 0; k < N; ++k) {
+    size_t i = occ[k];
+    double v = 2.0 * eri[p * n3 + q * n2 + i * n1 + i] - eri[p * n3 + i * n2 + i * n1 + q];
+    mf += v;
+    if (k == lp || k == lq) mfl += v;
+  }
+  f[pq] = h[pq] + mf;
+  hp[pq] = (lp == lq) ? h[pq] : h[pq] + mf - mfl;
+}
+
+// gather the per-site (20) and per-ordered-pair (232) integrals
+template <typename R>
+__global__ void k_gather(int n, int N, const double* __restrict__ hp, const double* __restrict__ eri,
+                         const int* __restrict__ occ, const int* __restrict__ vir,
+                         R* __restrict__ g1, R* __restrict__ g2) {
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  size_t tot2 = (size_t)N * N * PPQ_NG2;
+  if (tid < tot2) {
+    int j = tid % PPQ_NG2;
+    int XW = tid / PPQ_NG2;
+    int X = XW / N, W = XW % N;
+    if (X == W) { g2[tid] = R(0); return; }
+    const int8_t* k = ppq_g2key + 5 * j;
+    int o[4] = {occ[X], vir[X], occ[W], vir[W]};
+    double v;
+    if (k[0] == 0) v = hp[o[k[1]] * n1 + o[k[2]]];
+    else v = eri[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]];
+    g2[tid] = R(v);
+    return;
+  }
+  tid -= tot2;
+  if (tid < (size_t)N * PPQ_NG1) {
+    int j = tid % PPQ_NG1, X = tid / PPQ_NG1;
+    const int8_t* k = ppq_g1key + 5 * j;
+    int o[2] = {occ[X], vir[X]};
+    double v;
+    if (k[0] == 0) v = hp[o[k[1]] * n1 + o[k[2]]];
+    else v = eri[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]];
+    g1[tid] = R(v);
+  }
+}
+
+// ---------------------------------------------------------------- links
+// Cl[X,Y][c] = <c| exp(T_XY) |ref> on the 36-state zero-charge sector
+// (c = 0..29 nonzero), exp(T_XY) = prod_k (1 + t_k O_k).
+template <typename R>
+__global__ void k_links(int N, const double* __restrict__ t2, R* __restrict__ cl) {
+  int XY = blockIdx.x * blockDim.x + threadIdx.x;
+  if (XY >= N * N) return;
+  int X = XY / N, Y = XY % N;
+  R v[PPQ_NS36];
+#pragma unroll
+  for (int c = 0; c < PPQ_NS36; ++c) v[c] = R(0);
+  if (X != Y) {
+    v[0] = R(1);
+    const double* t = t2 + (size_t)XY * PPQ_NA2;
+    for (int k = 0; k < PPQ_NA2; ++k) {
+      R tk = R(t[k]);
+      for (int e = ppq_sop_ptr[k]; e < ppq_sop_ptr[k + 1]; ++e) {
+        int32_t w = ppq_sop[e];
+        v[unpack_t(w)] += tk * unpack_sign<R>(w) * v[unpack_s(w)];
+      }
+    }
+  }
+  R* o = cl + (size_t)XY * PPQ_NS36;
+#pragma unroll
+  for (int c = 0; c < PPQ_NS36; ++c) o[c] = v[c];
+}
+
+// ---------------------------------------------------------------- closures
+// one-site closure Ht_X = exp(-T_X) H_X exp(T_X), full 16x16
+template <typename R>
+__global__ void k_site_closure(int N, const R* __restrict__ g1, const double* __restrict__ t1,
+                               R* __restrict__ hs, double* __restrict__ esite) {
+  __shared__ R M[256];
+  __shared__ R h00;
+  int X = blockIdx.x;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) M[i] = R(0);
+  __syncthreads();
+  const R* g = g1 + (size_t)X * PPQ_NG1;
+  for (int el = threadIdx.x; el < PPQ_H1_NEL; el += blockDim.x) {
+    R s = R(0);
+    for (int p = ppq_h1_ptr[el]; p < ppq_h1_ptr[el + 1]; ++p) s += R(ppq_h1_c[p]) * g[ppq_h1_j[p]];
+    M[ppq_h1_el[el]] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) h00 = M[0];
+  for (int k = 0; k < 3; ++k) {
+    R tk = R(t1[X * 3 + k]);
+    for (int e = ppq_s_rptr[k] + threadIdx.x; e < ppq_s_rptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_right[e];
+      M[unpack_t(w)] += tk * unpack_sign<R>(w) * M[unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < 3; ++k) {
+    R tk = R(t1[X * 3 + k]);
+    for (int e = ppq_s_lptr[k] + threadIdx.x; e < ppq_s_lptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_left[e];
+      M[unpack_t(w)] -= tk * unpack_sign<R>(w) * M[unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hs[(size_t)X * 256 + i] = M[i];
+  if (threadIdx.x == 0) esite[X] = double(M[0]) - double(h00);
+}
+
+// two-site closure Ht_XW = exp(-I) H_XW exp(I), I = T_X + T_W + T_XW, on the
+// charge/S_z block layout (4900 entries); writes the entries the topologies use
+template <typename R>
+__global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict__ g2,
+    const double* __restrict__ t1, const double* __restrict__ t2, R* __restrict__ pg,
+    R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair) {
+  extern __shared__ unsigned char smem_raw[];
+  R* M = reinterpret_cast<R*>(smem_raw);
+  __shared__ R h00;
+  __shared__ double tops[35];
+  int XW = blockIdx.x;
+  int X = XW / N, W = XW % N;
+  if (X == W) {
+    for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = R(0);
+    for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) pt7[(size_t)XW * PPQ_NT7E + i] = R(0);
+    for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = R(0);
+    if (threadIdx.x == 0) epair[XW] = 0.0;
+    return;
+  }
+  if (threadIdx.x < 35) {
+    int o = threadIdx.x;
+    tops[o] = o < 3 ? t1[X * 3 + o] : (o < 6 ? t1[W * 3 + o - 3] : t2[(size_t)XW * PPQ_NA2 + o - 6]);
+  }
+  for (int i = threadIdx.x; i < PPQ_BLK; i += blockDim.x) M[i] = R(0);
+  __syncthreads();
+  const R* g = g2 + (size_t)XW * PPQ_NG2;
+  for (int el = threadIdx.x; el < PPQ_H2_NEL; el += blockDim.x) {
+    R s = R(0);
+    for (int p = ppq_h2_ptr[el]; p < ppq_h2_ptr[el + 1]; ++p) s += R(ppq_h2_c[p]) * g[ppq_h2_j[p]];
+    M[ppq_h2_el[el]] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) h00 = M[PPQ_EL00];
+  for (int o = 0; o < 35; ++o) {
+    R to = R(tops[o]);
+    if (to != R(0)) {
+      for (int e = ppq_p_rptr[o] + threadIdx.x; e < ppq_p_rptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_right[e];
+        M[unpack_t(w)] += to * unpack_sign<R>(w) * M[unpack_s(w)];
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = 0; o < 35; ++o) {
+    R to = R(tops[o]);
+    if (to != R(0)) {
+      for (int e = ppq_p_lptr[o] + threadIdx.x; e < ppq_p_lptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_left[e];
+        M[unpack_t(w)] -= to * unpack_sign<R>(w) * M[unpack_s(w)];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = M[ppq_g_el[i]];
+  for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) pt7[(size_t)XW * PPQ_NT7E + i] = M[ppq_t7_el[i]];
+  for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = M[ppq_col0_el[i]];
+  if (threadIdx.x == 0) epair[XW] = double(M[PPQ_EL00]) - double(h00);
+}
+
+// ---------------------------------------------------------------- contractions
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  R s = R(0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+// r1[Y]: topologies T1 (Ht_Y), T6 (pair pieces on Y,W), T3 (one-site piece on
+// X linked to Y), T8 (pair piece on X,W, both linked to Y)
+template <typename R>
+__global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
+                     const R* __restrict__ cl, const R* __restrict__ pg, double* __restrict__ r1) {
+  __shared__ R red[32];
+  int Y = blockIdx.x;
+  R acc[3] = {R(0), R(0), R(0)};
+  for (int X = threadIdx.x; X < N; X += blockDim.x) {
+    if (X == Y) continue;
+    const R* c = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    const R* h0 = hs + (size_t)X * 256;  // row 0 of Ht_X
+    for (int k = 0; k < 3; ++k)
+      for (int e = ppq_t3p[k]; e < ppq_t3p[k + 1]; ++e)
+        acc[k] += h0[ppq_t3[3 * e + 1]] * c[ppq_t3[3 * e]];
+    const R* p0 = pc0 + ((size_t)Y * N + X) * PPQ_NCOL0;
+    for (int k = 0; k < 3; ++k) acc[k] += p0[29 + k];
+  }
+  for (int XW = threadIdx.x; XW < N * N; XW += blockDim.x) {
+    int X = XW / N, W = XW % N;
+    if (X == W || X == Y || W == Y) continue;
+    const R* cx = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    const R* cw = cl + ((size_t)W * N + Y) * PPQ_NS36;
+    const R* g = pg + (size_t)XW * PPQ_NS36;
+    for (int k = 0; k < 3; ++k)
+      for (int e = ppq_t8p[k]; e < ppq_t8p[k + 1]; ++e) {
+        const int16_t* q = ppq_t8 + 5 * e;
+        acc[k] += R(0.5) * R(q[4]) * cx[q[0]] * cw[q[1]] * g[q[2]];
+      }
+  }
+  for (int k = 0; k < 3; ++k) {
+    R s = block_sum(acc[k], red);
+    if (threadIdx.x == 0) r1[Y * 3 + k] = double(s) + double(hs[(size_t)Y * 256 + ppq_A1[k] * 16]);
+  }
+}
+
+// r2 for ordered (Y,Z): T5, T4, T9 directly (dir) and T2+T7 through the
+// exp(-T_YZ) transform (abuf, mirrored later)
+template <typename R>
+__global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
+    const R* __restrict__ pt7, const R* __restrict__ pg, const R* __restrict__ cl,
+    const double* __restrict__ t2, double* __restrict__ dir, double* __restrict__ abuf) {
+  __shared__ R B[PPQ_NQ9];
+  __shared__ R U[PPQ_NS36];
+  __shared__ R outs[PPQ_NA2];
+  int YZ = blockIdx.x;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) {
+    for (int k = threadIdx.x; k < PPQ_NA2; k += blockDim.x) {
+      dir[(size_t)YZ * PPQ_NA2 + k] = 0.0;
+      abuf[(size_t)YZ * PPQ_NA2 + k] = 0.0;
+    }
+    return;
+  }
+  const R* clYZ = cl + (size_t)YZ * PPQ_NS36;
+  // T5 + T4 (thread per output channel, deterministic order)
+  if (threadIdx.x < PPQ_NA2) {
+    int o = threadIdx.x;
+    R acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
+    for (int X = 0; X < N; ++X) {
+      if (X == Y || X == Z) continue;
+      const R* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
+      const R* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
+      const R* h0 = hs + (size_t)X * 256;
+      for (int e = ppq_t4p[o]; e < ppq_t4p[o + 1]; ++e) {
+        const int16_t* q = ppq_t4 + 5 * e;
+        acc += R(q[4]) * cy[q[0]] * cz[q[1]] * h0[q[2]];
+      }
+    }
+    outs[o] = acc;
+  }
+  // T2 + T7 into U
+  if (threadIdx.x >= 64 && threadIdx.x < 64 + PPQ_NS36) {
+    int nu = threadIdx.x - 64;
+    R acc = R(0);
+    const R* hY = hs + (size_t)Y * 256;
+    for (int e = ppq_t2p[nu]; e < ppq_t2p[nu + 1]; ++e) {
+      const int16_t* q = ppq_t2 + 4 * e;
+      acc += clYZ[q[0]] * hY[q[1] * 16 + q[2]];
+    }
+    for (int W = 0; W < N; ++W) {
+      if (W == Y || W == Z) continue;
+      const R* cw = cl + ((size_t)W * N + Z) * PPQ_NS36;
+      const R* p7 = pt7 + ((size_t)Y * N + W) * PPQ_NT7E;
+      for (int e = ppq_t7p[nu]; e < ppq_t7p[nu + 1]; ++e) {
+        const int16_t* q = ppq_t7 + 5 * e;
+        acc += R(q[4]) * clYZ[q[0]] * cw[q[1]] * p7[q[2]];
+      }
+    }
+    U[nu] = acc;
+  }
+  __syncthreads();
+  // T9: for each W, B[q] = sum_X Cl[X,Y][p.c1] Cl[X,Z][p.c2] G[X,W][g]
+  R acc9 = R(0);
+  for (int W = 0; W < N; ++W) {
+    if (W == Y || W == Z) continue;
+    for (int q = threadIdx.x; q < PPQ_NQ9; q += blockDim.x) {
+      int p = ppq_q9[2 * q], gi = ppq_q9[2 * q + 1];
+      int c1 = ppq_p9[2 * p], c2 = ppq_p9[2 * p + 1];
+      R s = R(0);
+      for (int X = 0; X < N; ++X) {
+        if (X == Y || X == Z || X == W) continue;
+        s += cl[((size_t)X * N + Y) * PPQ_NS36 + c1] * cl[((size_t)X * N + Z) * PPQ_NS36 + c2] *
+             pg[((size_t)X * N + W) * PPQ_NS36 + gi];
+      }
+      B[q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < PPQ_NA2) {
+      int o = threadIdx.x;
+      const R* cy = cl + ((size_t)W * N + Y) * PPQ_NS36;
+      const R* cz = cl + ((size_t)W * N + Z) * PPQ_NS36;
+      for (int e = ppq_c9p[o]; e < ppq_c9p[o + 1]; ++e) {
+        const int16_t* q = ppq_c9 + 5 * e;
+        acc9 += R(q[4]) * B[q[0]] * cy[q[1]] * cz[q[2]];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < PPQ_NA2) outs[threadIdx.x] += R(0.5) * acc9;
+  // exp(-T_YZ) on U (sequential over the commuting factors)
+  const double* t = t2 + (size_t)YZ * PPQ_NA2;
+  for (int k = 0; k < PPQ_NA2; ++k) {
+    R tk = R(t[k]);
+    int e = ppq_sop_ptr[k] + threadIdx.x;
+    if (e < ppq_sop_ptr[k + 1]) {
+      int32_t w = ppq_sop[e];
+      U[unpack_t(w)] -= tk * unpack_sign<R>(w) * U[unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < PPQ_NA2; k += blockDim.x) {
+    dir[(size_t)YZ * PPQ_NA2 + k] = double(outs[k]);
+    abuf[(size_t)YZ * PPQ_NA2 + k] = double(U[1 + k]);
+  }
+}
+
+// r2[Y,Z] = dir[Y,Z] + abuf[Y,Z] + mirror(abuf[Z,Y])
+__global__ void k_assemble(int N, const double* __restrict__ dir, const double* __restrict__ abuf,
+                           double* __restrict__ r2) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * N * PPQ_NA2) return;
+  int k = i % PPQ_NA2;
+  int YZ = i / PPQ_NA2;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) { r2[i] = 0.0; return; }
+  size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + ppq_a2_swap[k];
+  r2[i] = dir[i] + abuf[i] + double(ppq_a2_swsg[k]) * abuf[j];
+}
+
+// ---------------------------------------------------------------- reductions / update
+// weight of amplitude i in norms and DIIS dots: 1 for t1, 1/2 for each stored
+// copy of a two-pair amplitude (so sums run over unique amplitudes)
+__device__ __forceinline__ double amp_weight(size_t i, int N) { return i < (size_t)3 * N ? 1.0 : 0.5; }
+
+__device__ __forceinline__ double denom(size_t i, int N, const double* fo, const double* fv, double shift) {
+  double d;
+  if (i < (size_t)3 * N) {
+    int X = i / 3, m = ppq_A1[i % 3];
+    d = ppq_nhole[m] * fo[X] - ppq_npart[m] * fv[X];
+  } else {
+    size_t j = i - 3 * N;
+    int k = j % PPQ_NA2;
+    int XY = j / PPQ_NA2;
+    int X = XY / N, Y = XY % N;
+    int a = ppq_A2[2 * k], b = ppq_A2[2 * k + 1];
+    d = ppq_nhole[a] * fo[X] - ppq_npart[a] * fv[X] + ppq_nhole[b] * fo[Y] - ppq_npart[b] * fv[Y];
+  }
+  return d - shift;
+}
+
+// partial sums over blocks of sum_i w_i x_i y_i (x == y for norms)
+__global__ void k_wdot(size_t L, int N, const double* __restrict__ x, const double* __restrict__ y,
+                       double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
+    s += amp_weight(i, N) * x[i] * y[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// final reduction of block partials and of the energy pieces, in FP64
+__global__ void k_finalize(int nb, const double* __restrict__ part, int N, const double* __restrict__ esite,
+                           const double* __restrict__ epair, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0, e = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) e += esite[i];
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) e += 0.5 * epair[i];
+  s = block_sum(s, red);
+  double es = block_sum(e, red);
+  if (threadIdx.x == 0) { out[0] = s; out[1] = es; }
+}
+
+// Jacobi step: tn = t + r / D, e = tn - t; written to DIIS slot
+__global__ void k_jacobi(size_t L, int N, const double* __restrict__ t, const double* __restrict__ r,
+                         const double* __restrict__ fo, const double* __restrict__ fv, double shift,
+                         double* __restrict__ tn, double* __restrict__ en) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double d = denom(i, N, fo, fv, shift);
+  double e = (d != 0.0) ? r[i] / d : 0.0;
+  if (i >= (size_t)3 * N) {
+    size_t j = i - 3 * N;
+    int XY = j / PPQ_NA2;
+    if (XY / N == XY % N) e = 0.0;
+  }
+  tn[i] = t[i] + e;
+  en[i] = e;
+}
+
+// DIIS: B[i][j] = <e_i, e_j> (weighted); solve [B -1; -1 0][c; l] = [0; -1]
+// by Gaussian elimination with partial pivoting (FP64, one thread).
+__global__ void k_diis_solve(int m, const double* __restrict__ bmat, int ld, double* __restrict__ coef,
+                             int* __restrict__ ok) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double A[17][18];
+  int n = m + 1;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i][j] = bmat[i * ld + j];
+    A[i][m] = -1.0;
+    A[i][n] = 0.0;
+  }
+  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
+  A[m][m] = 0.0;
+  A[m][n] = -1.0;
+  // scale the error block for conditioning (solution for c is unchanged)
+  double sc = 0.0;
+  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(A[i][i]));
+  if (sc > 0.0)
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) A[i][j] /= sc;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (fabs(A[piv][c]) < 1e-300) { *ok = 0; return; }
+    if (piv != c)
+      for (int k = 0; k <= n; ++k) { double tmp = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = tmp; }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  double x[17];
+  for (int r = n - 1; r >= 0; --r) {
+    double s = A[r][n];
+    for (int k = r + 1; k < n; ++k) s -= A[r][k] * x[k];
+    x[r] = s / A[r][r];
+  }
+  for (int i = 0; i < m; ++i) coef[i] = x[i];
+  *ok = 1;
+}
+
+__global__ void k_extrapolate(size_t L, int m, const double* __restrict__ coef, const int* __restrict__ ok,
+                              const double* __restrict__ slots, size_t ld, const int* __restrict__ order,
+                              double* __restrict__ t) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L || !*ok) return;
+  double s = 0.0;
+  for (int k = 0; k < m; ++k) s += coef[k] * slots[order[k] * ld + i];
+  t[i] = s;
+}
+
+}  // namespace ppq

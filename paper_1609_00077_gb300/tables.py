@@ -1,0 +1,630 @@
+"""Build-time generator of the site-algebra tables used by the CUDA kernels.
+
+Each pairing label P (a quartet: alpha/beta occupied orbital, alpha/beta
+virtual orbital -- Theory section) is treated as a site with a 16-state local
+Fock space.  Local spin orbitals: 0 = o_up, 1 = o_dn, 2 = v_up, 3 = v_dn.
+
+Every excitation is a product of per-site *monomials* E^m: m is a 4-bit mask,
+bits 0/1 annihilate the occupied up/down orbital and bits 2/3 create the
+virtual up/down orbital, E^m = a+_{v_up}^{b2} a+_{v_dn}^{b3} a_{o_dn}^{b1} a_{o_up}^{b0}.
+Applied to the site reference (both occupied orbitals filled) the 16 monomials
+give the 16 local states, so local states are labelled by monomials:
+|m> := E^m |ref>.  Multi-site states are |m0, m1, ...> := E_0^{m0} E_1^{m1} ... |ref>
+(a graded tensor product; odd monomials on different sites anticommute).
+
+The amplitude manifold of PQ is, in this language (Eq. decompose and Table II):
+  A1 = the 3 non-identity single-site monomials that conserve charge and S_z,
+  A2 = the 29 pairs (a, b) of non-identity monomials on two sites whose charge
+       and S_z changes cancel.
+So T = sum_P sum_{m in A1} t1[P,m] E_P^m
+     + 1/2 sum_{P != Q} sum_{(a,b) in A2} t2[P,Q,(a,b)] E_P^a E_Q^b,
+with t2[Q,P,(b,a)] = (-1)^{|a||b|} t2[P,Q,(a,b)] and zero diagonal (the
+paper's vanishing-diagonal convention).
+
+The Hamiltonian (two-electron integrals truncated to two labels, full Fock
+matrix -- Table I and the Implementation section) is written as one-site
+pieces H_P and two-site pieces H_{PQ} whose matrices are linear maps of
+integrals gathered per site (20 numbers) and per ordered pair (232 numbers).
+
+Signs are computed here by explicit Jordan-Wigner evaluation (sites in order,
+four spin orbitals per site), never by hand.
+"""
+import itertools
+import numpy as np
+
+REF = 0b0011
+NS = 16
+
+
+# ---------------------------------------------------------------- JW helpers
+def _apply(state, ops):
+    """ops: list of (spin orbital, dagger) applied right to left."""
+    sign = 1
+    for p, dag in reversed(ops):
+        occ = (state >> p) & 1
+        if dag == occ:
+            return None, 0
+        if bin(state & ((1 << p) - 1)).count("1") & 1:
+            sign = -sign
+        state ^= 1 << p
+    return state, sign
+
+
+def mono_ops(m, site=0):
+    o = 4 * site
+    ops = []
+    if m & 4: ops.append((o + 2, 1))
+    if m & 8: ops.append((o + 3, 1))
+    if m & 2: ops.append((o + 1, 0))
+    if m & 1: ops.append((o + 0, 0))
+    return ops
+
+
+def parity(m):
+    return bin(m).count("1") & 1
+
+
+def qn(m):
+    """(charge change, 2*S_z change) of monomial m."""
+    dn = bin(m & 12).count("1") - bin(m & 3).count("1")
+    ds = ((m >> 2) & 1) - ((m >> 3) & 1) - ((m & 1) - ((m >> 1) & 1))
+    return dn, ds
+
+
+class Space:
+    """k-site space in the monomial basis, with its map to JW determinants."""
+
+    def __init__(self, k):
+        self.k = k
+        self.ref = sum(REF << (4 * j) for j in range(k))
+        self.tuples = list(itertools.product(range(NS), repeat=k))
+        self.jw = {}
+        self.inv = {}
+        for tup in self.tuples:
+            ops = []
+            for j, m in enumerate(tup):
+                ops += mono_ops(m, j)
+            st, sg = _apply(self.ref, ops)
+            assert st is not None
+            self.jw[tup] = (st, sg)
+            self.inv[st] = (tup, sg)
+
+    def index(self, tup):
+        idx = 0
+        for m in tup:
+            idx = idx * NS + m
+        return idx
+
+    def op_matrix_terms(self, terms):
+        """terms: list of (key, coef, ops).  Returns dict (row, col) -> {key: coef}
+        for the operator sum coef*ops in the monomial basis."""
+        out = {}
+        for tup in self.tuples:
+            st, sg = self.jw[tup]
+            for key, coef, ops in terms:
+                st2, sg2 = _apply(st, ops)
+                if st2 is None or st2 not in self.inv:
+                    continue
+                tup2, sg3 = self.inv[st2]
+                r, c = self.index(tup2), self.index(tup)
+                d = out.setdefault((r, c), {})
+                d[key] = d.get(key, 0.0) + coef * sg * sg2 * sg3
+        return out
+
+    def apply_monomials(self, tup_ops, tup):
+        """Apply the product prod_j E_{site_j}^{m_j} (left to right as given in
+        tup_ops = [(site, m), ...]) to the basis state tup: (tup', sign) or None."""
+        st, sg = self.jw[tup]
+        ops = []
+        for site, m in tup_ops:
+            ops += mono_ops(m, site)
+        st2, sg2 = _apply(st, ops)
+        if st2 is None:
+            return None
+        tup2, sg3 = self.inv[st2]
+        return tup2, sg * sg2 * sg3
+
+
+# ---------------------------------------------------------------- tables
+def local_product_table():
+    """prod_sign[a, m] = s with E^a E^m = s E^{a|m} (0 if a & m != 0)."""
+    S1 = Space(1)
+    tab = np.zeros((NS, NS), dtype=np.int64)
+    for a in range(NS):
+        for m in range(NS):
+            r = S1.apply_monomials([(0, a)], (m,))
+            if r is None:
+                continue
+            (m2,), s = r
+            assert m2 == a | m and (a & m) == 0
+            tab[a, m] = s
+    return tab
+
+
+def amplitude_channels():
+    A1 = [m for m in range(1, NS) if qn(m) == (0, 0)]
+    A2 = [(a, b) for a in range(1, NS) for b in range(1, NS)
+          if qn(a)[0] + qn(b)[0] == 0 and qn(a)[1] + qn(b)[1] == 0]
+    return A1, A2
+
+
+def _spin_orbital(site, x, sigma):
+    return 4 * site + 2 * x + sigma
+
+
+def site_integral_keys():
+    """20 per-site integrals: 4 one-body h'[x,x'] then 16 (x x'|x'' x''')."""
+    keys = [("h", x, y) for x in range(2) for y in range(2)]
+    keys += [("v", p, q, r, s) for p in range(2) for q in range(2)
+             for r in range(2) for s in range(2)]
+    return keys
+
+
+def pair_integral_keys():
+    """232 per-ordered-pair integrals over the 4 spatial orbitals
+    0 = X_o, 1 = X_v, 2 = W_o, 3 = W_v: 8 cross one-body h'[p,q] and the 224
+    (pq|rs) whose orbitals touch both sites."""
+    keys = [("h", p, q) for p in range(4) for q in range(4) if (p // 2) != (q // 2)]
+    keys += [("v", p, q, r, s) for p in range(4) for q in range(4) for r in range(4)
+             for s in range(4) if len({p // 2, q // 2, r // 2, s // 2}) == 2]
+    assert len(keys) == 232
+    return keys
+
+
+def _hamiltonian_terms(keys):
+    """Second-quantised terms of sum h[p,q] a+_{p s} a_{q s}
+    + 1/2 sum (pq|rs) a+_{p s} a+_{r t} a_{s t} a_{q s} for the given keys;
+    spatial orbital p lives on site p // 2 with local spatial index p % 2."""
+    terms = []
+    for j, key in enumerate(keys):
+        if key[0] == "h":
+            _, p, q = key
+            for s in range(2):
+                terms.append((j, 1.0, [(_spin_orbital(p // 2, p % 2, s), 1),
+                                       (_spin_orbital(q // 2, q % 2, s), 0)]))
+        else:
+            _, p, q, r, s_ = key
+            for s1 in range(2):
+                for s2 in range(2):
+                    terms.append((j, 0.5, [(_spin_orbital(p // 2, p % 2, s1), 1),
+                                           (_spin_orbital(r // 2, r % 2, s2), 1),
+                                           (_spin_orbital(s_ // 2, s_ % 2, s2), 0),
+                                           (_spin_orbital(q // 2, q % 2, s1), 0)]))
+    return terms
+
+
+def hamiltonian_structure(k):
+    """Sparse linear map integrals -> matrix of the k-site piece (k = 1, 2) in
+    the monomial basis: arrays (row, col, key_index, coef)."""
+    keys = site_integral_keys() if k == 1 else pair_integral_keys()
+    S = Space(k)
+    mat = S.op_matrix_terms(_hamiltonian_terms(keys))
+    rows, cols, js, cs = [], [], [], []
+    for (r, c), d in sorted(mat.items()):
+        for j, coef in sorted(d.items()):
+            if abs(coef) > 1e-14:
+                rows.append(r); cols.append(c); js.append(j); cs.append(coef)
+    return (np.array(rows), np.array(cols), np.array(js), np.array(cs), keys)
+
+
+def pair_op_table(A2):
+    """For each (a,b) in A2 the action of E_X^a E_Y^b on 2-site basis states:
+    arrays (k, src, dst, sign) with src/dst = 16*mX + mY."""
+    S2 = Space(2)
+    out = []
+    for k, (a, b) in enumerate(A2):
+        for tup in S2.tuples:
+            r = S2.apply_monomials([(0, a), (1, b)], tup)
+            if r is not None:
+                out.append((k, S2.index(tup), S2.index(r[0]), r[1]))
+    return np.array(out, dtype=np.int64)
+
+
+def site_op_tables(A1):
+    """Action of E^m (m in A1) on site 0 and on site 1 of the 2-site space,
+    and on the 1-site space: arrays (k, src, dst, sign)."""
+    S1, S2 = Space(1), Space(2)
+    one, s0, s1 = [], [], []
+    for k, m in enumerate(A1):
+        for tup in S1.tuples:
+            r = S1.apply_monomials([(0, m)], tup)
+            if r is not None:
+                one.append((k, tup[0], r[0][0], r[1]))
+        for tup in S2.tuples:
+            r = S2.apply_monomials([(0, m)], tup)
+            if r is not None:
+                s0.append((k, S2.index(tup), S2.index(r[0]), r[1]))
+            r = S2.apply_monomials([(1, m)], tup)
+            if r is not None:
+                s1.append((k, S2.index(tup), S2.index(r[0]), r[1]))
+    return (np.array(one, dtype=np.int64), np.array(s0, dtype=np.int64),
+            np.array(s1, dtype=np.int64))
+
+
+def graded_sign_checks(prod):
+    """Check the graded rules used by the contraction formulas against JW:
+    E_X^a E_Y^b E_X^c = (-1)^{|b||c|} E_X^a E_X^c E_Y^b on 2 sites."""
+    S2 = Space(2)
+    ref = (0, 0)
+    for a in range(NS):
+        for b in range(NS):
+            for c in range(NS):
+                lhs = S2.apply_monomials([(0, a), (1, b), (0, c)], ref)
+                if (a & c) != 0:
+                    assert lhs is None
+                    continue
+                sgn = (-1) ** (parity(b) * parity(c)) * prod[a, c]
+                assert lhs == ((a | c, b), sgn), (a, b, c, lhs, sgn)
+    return True
+
+
+class Tables:
+    """All generated tables, as numpy arrays."""
+
+    def __init__(self):
+        self.prod = local_product_table()
+        graded_sign_checks(self.prod)
+        self.A1, self.A2 = amplitude_channels()
+        assert len(self.A1) == 3 and len(self.A2) == 29
+        self.par = np.array([parity(m) for m in range(NS)], dtype=np.int64)
+        self.qn = np.array([qn(m) for m in range(NS)], dtype=np.int64)
+        self.h1 = hamiltonian_structure(1)
+        self.h2 = hamiltonian_structure(2)
+        self.pair_ops = pair_op_table(self.A2)
+        self.site_ops1, self.site_ops2a, self.site_ops2b = site_op_tables(self.A1)
+        # index of each A2 channel by (a, b); 30 "cluster states" = ref + A2
+        self.a2_index = {ab: k for k, ab in enumerate(self.A2)}
+        self.a1_index = {m: k for k, m in enumerate(self.A1)}
+        self.sector36 = sector36(self.A1, self.A2)
+
+
+# ---------------------------------------------------------------- sector / channel lists
+def sector36(A1, A2):
+    """The 36 two-site states with zero total charge and S_z change, in the
+    order: ref, A2 (29), (A1, ref) (3), (ref, A1) (3).  Index c; the link
+    coefficients of exp(T_XY)|ref> live on c = 0..29."""
+    st = [(0, 0)] + list(A2) + [(m, 0) for m in A1] + [(0, m) for m in A1]
+    assert len(st) == 36
+    return st
+
+
+def _p(m):
+    return bin(m).count("1") & 1
+
+
+def t9_channels(T):
+    """Quartic topology (Hamiltonian piece on X,W; outputs on Y,Z linked by
+    exp(T_XY) exp(T_XZ) exp(T_WY) exp(T_WZ)): entries
+    (c_xy, c_xz, c_wy, c_wz, g, out, sign) with
+    r2[Y,Z][out] += 1/2 sum_{X != W} sign Cl[X,Y][c_xy] Cl[X,Z][c_xz]
+                     Cl[W,Y][c_wy] Cl[W,Z][c_wz] G[X,W][g]."""
+    st = T.sector36
+    idx = {s: i for i, s in enumerate(st)}
+    links = st[:30]
+    prod = T.prod
+    out = []
+    for c1, (a1, b1) in enumerate(links):
+        for c2, (a2, e1) in enumerate(links):
+            if a1 & a2:
+                continue
+            s12 = prod[a1, a2] * (-1) ** (_p(a2) * _p(b1))
+            m = a1 | a2
+            for c3, (d1, b2) in enumerate(links):
+                if b1 & b2:
+                    continue
+                for c4, (d2, e2) in enumerate(links):
+                    if d1 & d2 or e1 & e2:
+                        continue
+                    n = d1 | d2
+                    if (m, n) not in idx:
+                        continue
+                    b, c = b1 | b2, e1 | e2
+                    if b == 0 or c == 0:
+                        continue
+                    sg = (s12 * prod[d1, d2] * prod[b1, b2] * prod[e1, e2]
+                          * (-1) ** (_p(d1) * (_p(e1) + _p(b1)))
+                          * (-1) ** (_p(d2) * (_p(b2) + _p(e1) + _p(b1)))
+                          * (-1) ** (_p(b2) * _p(e1)))
+                    out.append((c1, c2, c3, c4, idx[(m, n)], T.a2_index[(b, c)], sg))
+    return np.array(out, dtype=np.int64)
+
+
+def t8_channels(T):
+    """r1[Y][k] += 1/2 sum_{X != W} sign Cl[X,Y][c_xy] Cl[W,Y][c_wy] G[X,W][g]."""
+    st = T.sector36
+    idx = {s: i for i, s in enumerate(st)}
+    out = []
+    for c1, (a, b1) in enumerate(st[:30]):
+        for c2, (d, b2) in enumerate(st[:30]):
+            if b1 & b2 or (a, d) not in idx:
+                continue
+            b = b1 | b2
+            if b not in T.a1_index:
+                continue
+            sg = T.prod[b1, b2] * (-1) ** (_p(b1) * _p(d))
+            out.append((c1, c2, idx[(a, d)], T.a1_index[b], sg))
+    return np.array(out, dtype=np.int64)
+
+
+def t4_channels(T):
+    """r2[Y,Z][out] += sum_X sign Cl[X,Y][c_xy] Cl[X,Z][c_xz] Ht_X[0, m]."""
+    st = T.sector36
+    out = []
+    for c1, (a1, b) in enumerate(st[1:30], start=1):
+        for c2, (a2, c) in enumerate(st[1:30], start=1):
+            if a1 & a2:
+                continue
+            m = a1 | a2
+            if tuple(T.qn[m]) != (0, 0):
+                continue
+            sg = T.prod[a1, a2] * (-1) ** (_p(b) * _p(a2))
+            out.append((c1, c2, m, T.a2_index[(b, c)], sg))
+    return np.array(out, dtype=np.int64)
+
+
+def t3_channels(T):
+    """r1[Y][k] += sum_X Ht_X[0, a] Cl[X,Y][c_xy] with c_xy = (a, A1[k])."""
+    st = T.sector36
+    idx = {s: i for i, s in enumerate(st)}
+    out = []
+    for k, m in enumerate(T.A1):
+        for a in range(NS):
+            if (a, m) in idx and idx[(a, m)] < 30:
+                out.append((idx[(a, m)], a, k))
+    return np.array(out, dtype=np.int64)
+
+
+def t2_channels(T):
+    """U[nu] += sum_a Cl[X,Y][c_xy] Ht_X[nu_X, a] with c_xy = (a, nu_Y):
+    entries (c_xy, nu_X, a, nu)."""
+    st = T.sector36
+    idx = {s: i for i, s in enumerate(st)}
+    out = []
+    for nu, (nx, ny) in enumerate(st):
+        for a in range(NS):
+            if (a, ny) in idx and idx[(a, ny)] < 30:
+                out.append((idx[(a, ny)], nx, a, nu))
+    return np.array(out, dtype=np.int64)
+
+
+def t7_channels(T):
+    """U[nu] += sum_W sign Cl[X,Y][c_xy] Cl[W,Y][c_wy] Ht_XW[(nu_X,0),(a,d)]:
+    entries (c_xy, c_wy, row, col, nu, sign), row/col 2-site indices 16*mX+mW."""
+    st = T.sector36
+    idx = {s: i for i, s in enumerate(st)}
+    out = []
+    for nu, (nx, ny) in enumerate(st):
+        for c1, (a, b1) in enumerate(st[:30]):
+            for c2, (d, b2) in enumerate(st[:30]):
+                if b1 & b2 or (b1 | b2) != ny:
+                    continue
+                # charge/S_z of column must match the row (nu_X, 0)
+                if tuple(T.qn[a] + T.qn[d]) != tuple(T.qn[nx]):
+                    continue
+                sg = T.prod[b1, b2] * (-1) ** (_p(b1) * _p(d))
+                out.append((c1, c2, 16 * nx, 16 * a + d, nu, sg))
+    return np.array(out, dtype=np.int64)
+
+
+def sector_pair_ops(T):
+    """Pair excitation operators restricted to the 36-state sector:
+    (k, src, dst, sign) with src/dst sector indices."""
+    st = T.sector36
+    idx = {16 * a + b: i for i, (a, b) in enumerate(st)}
+    out = []
+    for k, s, d, g in T.pair_ops:
+        if s in idx and d in idx:
+            out.append((k, idx[s], idx[d], g))
+    return np.array(out, dtype=np.int64)
+
+
+# ---------------------------------------------------------------- 2-site block layout
+class BlockLayout:
+    """Dense charge/S_z sector blocks of the 256-state 2-site space: element
+    (r, c) with both states in sector q is stored at base[q] + pos[r]*dim[q] + pos[c]."""
+
+    def __init__(self, T):
+        secs = {}
+        for s in range(256):
+            m, n = divmod(s, 16)
+            q = tuple(T.qn[m] + T.qn[n])
+            secs.setdefault(q, []).append(s)
+        self.sectors = [secs[q] for q in sorted(secs)]
+        self.sec_of = np.zeros(256, dtype=np.int64)
+        self.pos = np.zeros(256, dtype=np.int64)
+        self.base = []
+        off = 0
+        for i, ss in enumerate(self.sectors):
+            self.base.append(off)
+            for p, s in enumerate(ss):
+                self.sec_of[s] = i; self.pos[s] = p
+            off += len(ss) ** 2
+        self.size = off
+        self.dim = [len(ss) for ss in self.sectors]
+
+    def elem(self, r, c):
+        q = self.sec_of[r]
+        if self.sec_of[c] != q:
+            return -1
+        return self.base[q] + self.pos[r] * self.dim[q] + self.pos[c]
+
+
+def _pack(t, s, g):
+    return (int(t) << 17) | (int(s) << 1) | (1 if g < 0 else 0)
+
+
+def pair_transform_lists(T, L):
+    """Work lists for M <- M exp(I) (right) and M <- exp(-I) M (left) on the
+    block layout, I = T_X (ops 0-2) + T_W (3-5) + T_XW (6-34).  Entries pack
+    (target element, source element, sign bit)."""
+    ops = []
+    for k in range(3):
+        ops.append(T.site_ops2a[T.site_ops2a[:, 0] == k])
+    for k in range(3):
+        ops.append(T.site_ops2b[T.site_ops2b[:, 0] == k])
+    for k in range(29):
+        ops.append(T.pair_ops[T.pair_ops[:, 0] == k])
+    right, left, rptr, lptr = [], [], [0], [0]
+    for tab in ops:
+        for _, src, dst, sg in tab:
+            # right: O|src> = sg|dst>  =>  M[r, src] += t sg M[r, dst]
+            q = L.sec_of[src]
+            for r in L.sectors[q]:
+                right.append(_pack(L.elem(r, src), L.elem(r, dst), sg))
+            # left: M[dst, c] -= t sg M[src, c]
+            for c in L.sectors[q]:
+                left.append(_pack(L.elem(dst, c), L.elem(src, c), sg))
+        rptr.append(len(right)); lptr.append(len(left))
+    return (np.array(right, dtype=np.int64), np.array(rptr, dtype=np.int64),
+            np.array(left, dtype=np.int64), np.array(lptr, dtype=np.int64))
+
+
+def site_transform_lists(T):
+    right, left, rptr, lptr = [], [], [0], [0]
+    for k in range(3):
+        tab = T.site_ops1[T.site_ops1[:, 0] == k]
+        for _, src, dst, sg in tab:
+            for r in range(NS):
+                right.append(_pack(16 * r + src, 16 * r + dst, sg))
+            for c in range(NS):
+                left.append(_pack(16 * dst + c, 16 * src + c, sg))
+        rptr.append(len(right)); lptr.append(len(left))
+    return (np.array(right, dtype=np.int64), np.array(rptr, dtype=np.int64),
+            np.array(left, dtype=np.int64), np.array(lptr, dtype=np.int64))
+
+
+def csr_from_structure(struct, elem_of):
+    r, c, j, coef, _ = struct
+    ent = {}
+    for ri, ci, ji, co in zip(r, c, j, coef):
+        e = elem_of(int(ri), int(ci))
+        assert e >= 0
+        ent.setdefault(e, []).append((int(ji), float(co)))
+    els = sorted(ent)
+    ptr, js, cs = [0], [], []
+    for e in els:
+        for ji, co in ent[e]:
+            js.append(ji); cs.append(co)
+        ptr.append(len(js))
+    return (np.array(els, dtype=np.int64), np.array(ptr, dtype=np.int64),
+            np.array(js, dtype=np.int64), np.array(cs))
+
+
+def _c_array(name, ctype, arr, per_line=16):
+    arr = np.asarray(arr).ravel()
+    body = []
+    for i in range(0, len(arr), per_line):
+        if ctype in ("float", "double"):
+            body.append(", ".join(repr(float(x)) + ("f" if ctype == "float" else "") for x in arr[i:i + per_line]))
+        else:
+            body.append(", ".join(str(int(x)) for x in arr[i:i + per_line]))
+    return f"static __device__ const {ctype} {name}[{max(len(arr), 1)}] = {{\n  " + ",\n  ".join(body or ["0"]) + "\n};\n"
+
+
+def emit_header(path):
+    """Write the generated tables as a CUDA header."""
+    T = Tables()
+    L = BlockLayout(T)
+    st = T.sector36
+    sidx = {s: i for i, s in enumerate(st)}
+    out = ["/* Generated by paper_1609_00077_gb300/tables.py -- do not edit. */",
+           "#pragma once", "#include <stdint.h>", ""]
+    defs = dict(PPQ_NA1=3, PPQ_NA2=29, PPQ_NG1=20, PPQ_NG2=232, PPQ_NS36=36,
+                PPQ_BLK=L.size, PPQ_NLINK=30)
+    for k, v in defs.items():
+        out.append(f"#define {k} {v}")
+    out.append("")
+    out.append(_c_array("ppq_A1", "int8_t", T.A1))
+    out.append(_c_array("ppq_A2", "int8_t", np.array(T.A2)))
+    out.append(_c_array("ppq_S36", "int8_t", np.array(st)))
+    out.append(_c_array("ppq_par", "int8_t", T.par))
+    # monomial hole / particle counts (for denominators)
+    nh = [bin(m & 3).count("1") for m in range(16)]
+    npart = [bin(m & 12).count("1") for m in range(16)]
+    out.append(_c_array("ppq_nhole", "int8_t", nh))
+    out.append(_c_array("ppq_npart", "int8_t", npart))
+    # 1-site Hamiltonian CSR (dense 16x16 element index) and transforms
+    e1, p1, j1, c1 = csr_from_structure(T.h1, lambda r, c: 16 * r + c)
+    out += [f"#define PPQ_H1_NEL {len(e1)}", _c_array("ppq_h1_el", "int16_t", e1),
+            _c_array("ppq_h1_ptr", "int16_t", p1), _c_array("ppq_h1_j", "uint8_t", j1),
+            _c_array("ppq_h1_c", "float", c1)]
+    sr, srp, sl, slp = site_transform_lists(T)
+    out += [_c_array("ppq_s_right", "int32_t", sr), _c_array("ppq_s_rptr", "int16_t", srp),
+            _c_array("ppq_s_left", "int32_t", sl), _c_array("ppq_s_lptr", "int16_t", slp)]
+    # 2-site Hamiltonian CSR on the block layout and transforms
+    e2, p2, j2, c2 = csr_from_structure(T.h2, L.elem)
+    out += [f"#define PPQ_H2_NEL {len(e2)}", _c_array("ppq_h2_el", "int16_t", e2),
+            _c_array("ppq_h2_ptr", "int32_t", p2), _c_array("ppq_h2_j", "uint8_t", j2),
+            _c_array("ppq_h2_c", "float", c2)]
+    pr, prp, pl, plp = pair_transform_lists(T, L)
+    out += [f"#define PPQ_PR_N {len(pr)}", f"#define PPQ_PL_N {len(pl)}",
+            _c_array("ppq_p_right", "int32_t", pr), _c_array("ppq_p_rptr", "int32_t", prp),
+            _c_array("ppq_p_left", "int32_t", pl), _c_array("ppq_p_lptr", "int32_t", plp)]
+    # outputs of the pair closure: G row, T7 entries, column-0 entries, element (0,0)
+    g_el = [L.elem(0, 16 * a + b) for a, b in st]
+    t7 = t7_channels(T)
+    t7rc = sorted(set((int(r), int(c)) for r, c in t7[:, [2, 3]]))
+    t7e = {rc: i for i, rc in enumerate(t7rc)}
+    t7_el = [L.elem(r, c) for r, c in t7rc]
+    col0 = [L.elem(16 * a + b, 0) for a, b in T.A2] + [L.elem(16 * m, 0) for m in T.A1]
+    out += [f"#define PPQ_NT7E {len(t7rc)}", f"#define PPQ_NCOL0 {len(col0)}",
+            f"#define PPQ_EL00 {L.elem(0, 0)}",
+            _c_array("ppq_g_el", "int16_t", g_el), _c_array("ppq_t7_el", "int16_t", t7_el),
+            _c_array("ppq_col0_el", "int16_t", col0)]
+    # link / transform operators on the 36-state sector
+    sop = sector_pair_ops(T)
+    sptr = [0]
+    for k in range(29):
+        sptr.append(int(np.sum(sop[:, 0] <= k)))
+    out += [f"#define PPQ_NSOP {len(sop)}",
+            _c_array("ppq_sop", "int32_t", [_pack(d, s, g) for _, s, d, g in sop]),
+            _c_array("ppq_sop_ptr", "int16_t", sptr)]
+    # topology channel lists
+    def by_out(arr, col, nout):
+        arr = np.asarray(arr)
+        order = np.argsort(arr[:, col], kind="stable")
+        arr = arr[order]
+        ptr = [int(np.sum(arr[:, col] < o)) for o in range(nout + 1)]
+        return arr, ptr
+    t2, t2p = by_out(t2_channels(T), 3, 36)
+    t3, t3p = by_out(t3_channels(T), 2, 3)
+    t4, t4p = by_out(t4_channels(T), 3, 29)
+    t8, t8p = by_out(t8_channels(T), 3, 3)
+    out += [f"#define PPQ_NT2 {len(t2)}", _c_array("ppq_t2", "int16_t", t2), _c_array("ppq_t2p", "int16_t", t2p),
+            f"#define PPQ_NT3 {len(t3)}", _c_array("ppq_t3", "int16_t", t3), _c_array("ppq_t3p", "int16_t", t3p),
+            f"#define PPQ_NT4 {len(t4)}", _c_array("ppq_t4", "int16_t", t4), _c_array("ppq_t4p", "int16_t", t4p),
+            f"#define PPQ_NT8 {len(t8)}", _c_array("ppq_t8", "int16_t", t8), _c_array("ppq_t8p", "int16_t", t8p)]
+    t7c, t7p = by_out(np.array([(c1, c2, t7e[(int(r), int(c))], nu, s) for c1, c2, r, c, nu, s in t7]), 3, 36)
+    out += [f"#define PPQ_NT7 {len(t7c)}", _c_array("ppq_t7", "int16_t", t7c), _c_array("ppq_t7p", "int16_t", t7p)]
+    swap = [T.a2_index[(b, a)] for a, b in T.A2]
+    swsg = [(-1) ** (_p(a) * _p(b)) for a, b in T.A2]
+    out += [_c_array("ppq_a2_swap", "int8_t", swap), _c_array("ppq_a2_swsg", "int8_t", swsg)]
+    t9 = t9_channels(T)
+    p9 = sorted(set((int(a), int(b)) for a, b in t9[:, [0, 1]]))
+    p9i = {p: i for i, p in enumerate(p9)}
+    q9 = sorted(set((p9i[(int(a), int(b))], int(g)) for a, b, g in t9[:, [0, 1, 4]]))
+    q9i = {q: i for i, q in enumerate(q9)}
+    ch9 = [(q9i[(p9i[(int(r[0]), int(r[1]))], int(r[4]))], int(r[2]), int(r[3]), int(r[5]), int(r[6]))
+           for r in t9]
+    ch9, c9p = by_out(np.array(ch9), 3, 29)
+    out.append(_c_array("ppq_c9p", "int16_t", c9p))
+    out += [f"#define PPQ_NP9 {len(p9)}", f"#define PPQ_NQ9 {len(q9)}", f"#define PPQ_NC9 {len(ch9)}",
+            _c_array("ppq_p9", "int8_t", np.array(p9)), _c_array("ppq_q9", "int16_t", np.array(q9)),
+            _c_array("ppq_c9", "int16_t", np.array(ch9))]
+    # integral gather keys
+    k1 = site_integral_keys(); k2 = pair_integral_keys()
+    enc1 = [(0, k[1], k[2], 0, 0) if k[0] == "h" else (1,) + k[1:] for k in k1]
+    enc2 = [(0, k[1], k[2], 0, 0) if k[0] == "h" else (1,) + k[1:] for k in k2]
+    out += [_c_array("ppq_g1key", "int8_t", np.array(enc1)), _c_array("ppq_g2key", "int8_t", np.array(enc2))]
+    # amplitude layout descriptor for the C-ABI: kind, first monomial, second
+    desc = [(1, m, 0) for m in T.A1] + [(2, a, b) for a, b in T.A2]
+    out.append(_c_array("ppq_layout_desc", "int8_t", np.array(desc)).replace("static __device__ const", "static const"))
+    text = "\n".join(out) + "\n"
+    with open(path, "w") as fh:
+        fh.write(text)
+    return dict(blk=L.size, right=len(pr), left=len(pl), h2=len(j2), t7e=len(t7rc))
+
+
+if __name__ == "__main__":
+    import sys
+    print(emit_header(sys.argv[1]))

@@ -1,0 +1,145 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Residuals are compared element by element at seeded random amplitudes
+(uniform +-0.1, zero diagonals), energies to 1e-9 Eh after convergence
+(FP64 path) and 1e-8 Eh for the mixed path.  Tolerances:
+  FP64 residual: 1e-11 absolute -- the kernels and the oracle sum the same
+    terms in different orders; with |terms| <= ~1 and <= ~10^4 terms per
+    element the rounding difference is < 1e-12.
+  FP32 residual: 2e-5 * max|R| -- unit roundoff 6e-8 times the same growth
+    factor (sums of up to ~10^4 products of O(1) factors, random-walk
+    accumulation) plus the FP32 rounding of the integrals themselves.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1609_00077_gb300 as ppq
+from workloads import build_ppp, build_hchain, random_pair_amplitude_seed
+from oracle.detcc import Problem, enumerate_manifold
+from oracle.loccc import LocalAssembly
+from oracle.fci import fci_energy
+from tests.layout import LayoutMap
+
+SYSTEMS = {
+    "H4": lambda: build_hchain(4, 1.5),
+    "C6H8": lambda: build_ppp('polyene', 6),
+    "C8H10": lambda: build_ppp('polyene', 8),
+    "H10": lambda: build_hchain(10, 1.9),
+    "H12": lambda: build_hchain(12, 1.6),
+    "C16H18": lambda: build_ppp('polyene', 16),
+    "H20": lambda: build_hchain(20, 2.0),
+}
+ORACLE_DET = {"H4", "C6H8", "C8H10", "H10"}
+_cache = {}
+
+
+def system(name):
+    if name not in _cache:
+        H = SYSTEMS[name]()
+        if name in ORACLE_DET:
+            P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2)
+            res, man = P.residual, P.cc.manifold
+        else:
+            P = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2)
+            res, man = P.residual, P.manifold
+        lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+        _cache[name] = (H, res, lm, len(man))
+    return _cache[name]
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_parity_random_amplitudes(name, precision):
+    H, res, lm, n_amp = system(name)
+    rng = np.random.default_rng(random_pair_amplitude_seed(H.n_pairs))
+    t = rng.uniform(-0.1, 0.1, n_amp)
+    R_ref, e_ref = res(t)
+    tl = lm.to_layout(t)
+    r, e = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), dev(tl),
+                           precision=precision)
+    r = r.cpu().numpy()
+    assert lm.mirror_error(r) < (1e-12 if precision == 0 else 1e-6)
+    R = lm.from_layout(r)
+    if precision == 0:
+        assert np.abs(R - R_ref).max() < 1e-11
+        assert abs(e - e_ref) < 1e-11
+    else:
+        scale = np.abs(R_ref).max()
+        assert np.abs(R - R_ref).max() < 2e-5 * scale
+        assert abs(e - e_ref) < 2e-5 * max(1.0, abs(e_ref))
+
+
+def test_residual_host_and_device_inputs_agree():
+    H, res, lm, n_amp = system("C8H10")
+    t = lm.to_layout(np.random.default_rng(5).uniform(-0.1, 0.1, n_amp))
+    r_dev, e_dev = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), dev(t))
+    r_host, e_host = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, np.ascontiguousarray(H.h),
+                                     np.ascontiguousarray(H.eri), t)
+    assert np.array_equal(r_dev.cpu().numpy(), r_host) and e_dev == e_host
+
+
+def test_zero_amplitudes_residual_is_mp2_like_first_order():
+    """At T = 0 the residual is <mu|H_N|Phi>: for doubles the antisymmetrised
+    integrals, for singles f_ia (zero for canonical RHF orbitals)."""
+    H, res, lm, n_amp = system("H10")
+    r, e = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri),
+                           dev(np.zeros(lm.n_amp)))
+    R = lm.from_layout(r.cpu().numpy())
+    R_ref, _ = res(np.zeros(n_amp))
+    assert np.abs(R - R_ref).max() < 1e-12 and abs(e) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["H4", "C8H10", "H10"])
+def test_solve_matches_oracle_energy(name):
+    H, res, lm, n_amp = system(name)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, e_const=H.e_const)
+    ro = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    assert ro['converged']
+    e_oracle = ro['e_corr'] + P.e_ref
+    rc, e, t, info = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const,
+                                  r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    assert rc == 0 and info['status'] == 0
+    assert abs(e - e_oracle) < 1e-9
+    assert np.abs(lm.from_layout(t) - ro['t']).max() < 1e-7
+    if H.n_pairs == 2:
+        assert abs(e - fci_energy(H.h, H.eri, 2, H.e_const)) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["C8H10", "H10", "C16H18"])
+def test_mixed_precision_matches_fp64(name):
+    H = SYSTEMS[name]()
+    kw = dict(r_tol=1e-10, e_tol=1e-12, max_iter=400)
+    rc0, e0, _, i0 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const,
+                                  precision=0, **kw)
+    rc1, e1, _, i1 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const,
+                                  precision=1, **kw)
+    assert rc0 == 0 and rc1 == 0
+    assert i1['switched_at'] > 0 and i1['polish_iters'] > 0
+    assert abs(e1 - e0) < 1e-8
+
+
+def test_status_codes():
+    H = SYSTEMS["C8H10"]()
+    rc, e, t, info = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), max_iter=2)
+    assert rc == 1 and info['status'] == 1 and info['iters'] == 2
+    eri = H.eri.copy(); eri[0, 1, 2, 3] = np.nan
+    rc, e, t, info = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(eri))
+    assert rc == 3 and info['status'] == 3
+
+
+def test_warm_start_from_converged_amplitudes():
+    H = SYSTEMS["H10"]()
+    rc, e, t, info = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const)
+    rc2, e2, t2, info2 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri),
+                                      H.e_const, t_in=t)
+    assert rc2 == 0 and info2['iters'] <= 3 and abs(e2 - e) < 1e-10
