@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark: PQ time to solution on the PPP pi space of C140H142.
+
+Workload (140 electrons in 140 orbitals, 70 pairs): all-trans zigzag chain,
+bonds 1.35/1.46 A, beta = -2.4 eV, U = 11.26 eV, Ohno gamma, RHF orbitals
+Boys-localised in the occupied and the virtual space, each occupied orbital
+paired with the nearest virtual (the paper's localised-orbital pairing; with
+delocalised canonical orbitals the Jacobi/DIIS iteration of this 140-site
+chain does not converge); dense FP64 MO integrals (pq|rs) of 140^4 entries
+(3.07 GB) built on the device.
+
+A step is one complete mixed-precision PQ solve (FP32 residual until
+||R|| <= 1e-5 or stagnation, then FP64 polish to ||R|| <= 1e-10 and
+|dE| <= 1e-12): integral staging, every residual evaluation, energy, Jacobi
+update and DIIS.  `value` is the time to solution in seconds (device time,
+CUDA events, inputs resident in HBM).  The FP64-only solve is timed beside it
+and |dE| between the two is reported.  `e2e` repeats the mixed solve through
+the C ABI with host (pinned) integrals and host output amplitudes.
+
+`--impl reference` times the CPU oracle (local inclusion-exclusion over
+determinant-space problems) on a bounded sample of the same workload and
+extrapolates to the same metric.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sites", type=int, default=140, help="polyene sites (2 x pairs)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-only comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def workload(sites):
+    from workloads import build_ppp
+    H = build_ppp('polyene', sites, with_eri=False, orbitals="local")
+    return H
+
+
+def device_eri(H, torch):
+    C = torch.from_numpy(H.C).cuda()
+    g = torch.from_numpy(H.gamma_site).cuda()
+    n = C.shape[1]
+    D = (C[:, :, None] * C[:, None, :]).reshape(C.shape[0], n * n)
+    eri = (D.T @ g @ D).reshape(n, n, n, n).contiguous()
+    del D
+    return eri
+
+
+def cpu_baseline(sites, seconds, iters, seed=0):
+    """Time the oracle (O-loc) on a bounded random sample of the local
+    label-subset problems of one residual evaluation of this workload and scale
+    to a full solve: per-size mean time x number of subsets x iterations."""
+    from math import comb
+    from workloads import build_ppp
+    from oracle.loccc import LocalAssembly
+    H = build_ppp('polyene', sites, orbitals="local")
+    N = H.n_pairs
+    rng = np.random.default_rng(seed)
+    per_size = {}
+    t_start = time.perf_counter()
+    budget = {1: 0.05, 2: 0.15, 3: 0.3, 4: 0.5}
+    counts = {}
+    for k in (1, 2, 3, 4):
+        subs = [tuple(sorted(rng.choice(N, k, replace=False))) for _ in range(4096)]
+        L = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, subsets=subs[:1])
+        t = rng.uniform(-0.05, 0.05, len(L.manifold))
+        done, spent = 0, 0.0
+        for s in subs:
+            loc = L._local(s)
+            tl = loc['sgn'] * t[loc['glob']]
+            t0 = time.perf_counter()
+            loc['cc'].residual(tl, loc['h'], loc['v'])
+            spent += time.perf_counter() - t0
+            done += 1
+            if spent > seconds * budget[k]:
+                break
+        per_size[k] = spent / done
+        counts[k] = done
+    per_residual = sum(per_size[k] * comb(N, k) for k in per_size)
+    return {
+        "value": per_residual * iters, "unit": "s", "cores": 1, "kind": "oracle",
+        "sample": (f"O-loc local problems of one residual of PPP C{sites}H{sites + 2}: "
+                   + ", ".join(f"{counts[k]} of C({N},{k})={comb(N, k)} {k}-label" for k in counts)
+                   + f"; mean time per problem x count x {iters} iterations (extrapolated)"),
+        "per_residual_s": per_residual,
+        "sample_wall_s": time.perf_counter() - t_start,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    iters = 40
+    times = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.sites, args.cpu_seconds / 3, iters, seed=k)
+        if k >= args.warmup:
+            times.append(cb["value"])
+    v = float(np.mean(times))
+    out = {"impl": "reference", "metric": "PQ time to solution, PPP C140H142 (70 pairs)",
+           "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"PQ PPP C{args.sites}H{args.sites + 2} pi space, {args.sites // 2} pairs",
+                      "global_batch": 1, "precision": "oracle FP64"},
+           "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1609_00077_gb300 as ppq
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    H = workload(args.sites)
+    eri = device_eri(H, torch)
+    h = torch.from_numpy(H.h).cuda()
+    N = H.n_pairs
+    L = ppq.amp_count(N)
+    t_out = torch.zeros(L, dtype=torch.float64, device="cuda")
+    kw = dict(r_tol=1e-10, e_tol=1e-12, max_iter=300)
+
+    def solve(precision, profile=0):
+        return ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, t_out=t_out,
+                            precision=precision, profile=profile, stream=stream.cuda_stream, **kw)
+
+    for _ in range(args.warmup):
+        solve(1)
+    torch.cuda.synchronize()
+    infos = []
+    with Clocks(local) as clk:
+        if dist: dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rc, e_mixed, _, info = solve(1, profile=1)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist: dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    info = infos[-1]
+    # FP64-only solve beside it
+    fp64 = None
+    if not args.no_fp64:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc64, e64, _, info64 = solve(0, profile=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"seconds": e0.elapsed_time(e1) / 1e3, "status": rc64, "iters": info64["iters"],
+                "e_total": e64, "residual_tflops": info64["residual_flops"] * info64["iters"]
+                / (info64["t_residual_ms"] * 1e-3) / 1e12,
+                "abs_dE_mixed_vs_fp64": abs(e_mixed - e64)}
+    # end to end through the C ABI with host buffers
+    h_host = torch.from_numpy(H.h).pin_memory()
+    eri_host = eri.cpu().pin_memory()
+    t_host = torch.zeros(L, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc_e, e_e2e, _, info_e = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h_host.numpy(),
+                                              eri_host.numpy(), H.e_const, t_out=t_host.numpy(),
+                                              precision=1, stream=stream.cuda_stream, **kw)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - w0) / args.steps
+    # roofline of the dominant kernel (the quartic contraction, FP32 in the bulk)
+    pk = peaks()
+    t_q = info["t_quartic_ms"] / max(info["n_quartic"], 1)
+    achieved = info["quartic_flops"] / (t_q * 1e-3) / 1e12
+    # SIMT peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 x clock
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    n_launch = info["n_launches"]
+    res_tflops = info["residual_flops"] * info["iters"] / (info["t_residual_ms"] * 1e-3) / 1e12
+    out = {
+        "metric": "PQ time to solution, PPP C140H142 (70 pairs), mixed FP32/FP64",
+        "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"PQ PPP C{args.sites}H{args.sites + 2} pi space, {N} pairs, "
+                               f"dense FP64 (pq|rs) {args.sites}^4",
+                   "global_batch": world, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (3.07 GB integrals re-read by staging each step)",
+                   "precision": "FP32 residual to ||R||<=1e-5 or stagnation, FP64 polish to 1e-10"},
+        "status": info["status"], "iters": info["iters"], "polish_iters": info["polish_iters"],
+        "switched_at": info["switched_at"], "e_total": e_mixed,
+        "residual_tflops": res_tflops,
+        "fp64": fp64,
+        "gpu_launches": n_launch * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_r2 (quartic contraction, FP32 launches dominate)",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_note": "FP32 SIMT peak from 152 SMs x 128 lanes x 2 FLOP x 2070 MHz "
+                                  "(MEASURED_PEAKS.json has no FP32 SIMT figure)"},
+        "e2e": {"value": e2e_s, "unit": "s",
+                "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),
+                "d2h_bytes_per_step": int(L * 8 + 16)},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args.sites, args.cpu_seconds, info["iters"])
+        out["cpu_baseline"]["cores"] = 1
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

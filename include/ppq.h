@@ -58,6 +58,8 @@ typedef struct {
   int diis_start;     /* 3                                                     */
   double level_shift; /* added to |denominator| (0)                             */
   int guess;          /* 0 = zero amplitudes, 1 = start from t_in               */
+  int profile;        /* 1 = time the quartic contraction kernel with CUDA      */
+                      /*     events on `stream` (fields t_quartic_ms, ... )     */
 } ppq_opts;
 
 typedef struct {
@@ -71,6 +73,11 @@ typedef struct {
   double t_residual_ms;/* device time in residual evaluations                  */
   double t_total_ms;   /* wall time of the call                                */
   double residual_flops; /* algorithmic FLOPs of one residual evaluation       */
+  double quartic_flops;  /* algorithmic FLOPs of one launch of the quartic      */
+                         /* (two-summed-label) contraction kernel              */
+  double t_quartic_ms;   /* device time of those launches (profile = 1)        */
+  int n_quartic;         /* number of those launches                           */
+  int n_launches;        /* kernels launched by the call                       */
 } ppq_info;
 
 /* Fill *o with the defaults listed above.  Returns 0. */

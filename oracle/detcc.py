@@ -47,17 +47,13 @@ def truncated_hamiltonian(h, eri, occ_of_pair, vir_of_pair, K_H):
     if K_H < 0:
         vt = eri.copy()
     else:
-        L = lab
-        nl = np.zeros((n, n, n, n), dtype=np.int64)
-        # number of distinct labels of each index quadruple
-        for p in range(n):
-            for q in range(n):
-                base = {L[p], L[q]}
-                for r in range(n):
-                    b2 = base | {L[r]}
-                    for s in range(n):
-                        nl[p, q, r, s] = len(b2 | {L[s]})
+        # number of distinct labels of each index quadruple (p, q, r, s)
+        La = lab[:, None, None, None]; Lb = lab[None, :, None, None]
+        Lc = lab[None, None, :, None]; Ld = lab[None, None, None, :]
+        nl = (1 + (Lb != La).astype(np.int8) + ((Lc != La) & (Lc != Lb)).astype(np.int8)
+              + ((Ld != La) & (Ld != Lb) & (Ld != Lc)).astype(np.int8))
         vt = np.where(nl <= K_H, eri, 0.0)
+        del nl
     f = h + 2.0 * eri[:, :, occ, occ].sum(-1) - eri[:, occ, occ, :].sum(1)
     hp = f - 2.0 * vt[:, :, occ, occ].sum(-1) + vt[:, occ, occ, :].sum(1)
     e_ref = float(np.sum(h[occ, occ]) + np.sum(f[occ, occ]))

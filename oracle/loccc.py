@@ -36,7 +36,10 @@ def _moebius_coeff(N, k, kmax):
 class LocalAssembly:
     """Residual and energy of a PQ/PH problem by local inclusion-exclusion."""
 
-    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0):
+    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0, subsets=None):
+        """subsets: optional list of label subsets; when given, only those local
+        problems are built and residual() returns their partial sum (used to
+        time a bounded sample of a large problem)."""
         self.K = K
         self.K_H = K if K_H == 0 else K_H
         self.occ = np.asarray(occ_of_pair); self.vir = np.asarray(vir_of_pair)
@@ -50,9 +53,20 @@ class LocalAssembly:
         kmax = K + self.K_H
         self.kmax = kmax
         self.locals = []
+        if subsets is not None:
+            for Lset in subsets:
+                self.locals.append(self._local(tuple(sorted(Lset))))
+            return
         for m in range(1, min(kmax, self.N) + 1):
             for Lset in combinations(range(self.N), m):
                 self.locals.append(self._local(Lset))
+
+    def _labels(self, d):
+        if not hasattr(self, "_lab"):
+            self._lab = {}
+            for k, (i, a) in enumerate(zip(self.occ, self.vir)):
+                self._lab[int(i)] = k; self._lab[int(a)] = k
+        return {self._lab[x] for x in d[0] + d[1] + d[2] + d[3]}
 
     def _local(self, Lset):
         orbs = sorted([int(self.occ[k]) for k in Lset] + [int(self.vir[k]) for k in Lset])
@@ -69,16 +83,19 @@ class LocalAssembly:
                  + vt[np.ix_(o, occL, occL, o)].diagonal(axis1=1, axis2=2).sum(-1))
         v_loc = vt[np.ix_(o, o, o, o)]
         # local manifold = global excitations whose labels lie in Lset
-        Lc = set(Lset)
+        if not hasattr(self, "_by_labels"):
+            self._by_labels = {}
+            for d in self.manifold:
+                self._by_labels.setdefault(frozenset(self._labels(d)), []).append(d)
         glob, locm = [], []
-        for d in self.manifold:
-            ah, ap, bh, bp = d
-            labs = set()
-            for x in ah + ap + bh + bp:
-                labs.add(int(np.where((self.occ == x) | (self.vir == x))[0][0]))
-            if labs <= Lc:
-                glob.append(self.index[d])
-                locm.append(tuple(tuple(pos[x] for x in part) for part in d))
+        for m in range(1, len(Lset) + 1):
+            for sub in combinations(Lset, m):
+                for d in self._by_labels.get(frozenset(sub), []):
+                    glob.append(self.index[d])
+                    locm.append(tuple(tuple(pos[x] for x in part) for part in d))
+        order = np.argsort(glob, kind="stable")
+        glob = [glob[i] for i in order]
+        locm = [locm[i] for i in order]
         cc = DetCC(len(orbs), locc, lvir, self.K, manifold=locm)
         # sign between the global and local operator conventions
         lref = sum(1 << i for i in locc)

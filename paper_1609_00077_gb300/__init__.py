@@ -27,7 +27,8 @@ class Opts(ctypes.Structure):
                 ("switch_tol", ctypes.c_double), ("r_tol", ctypes.c_double),
                 ("e_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_dim", ctypes.c_int), ("diis_start", ctypes.c_int),
-                ("level_shift", ctypes.c_double), ("guess", ctypes.c_int)]
+                ("level_shift", ctypes.c_double), ("guess", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -35,7 +36,9 @@ class Info(ctypes.Structure):
                 ("polish_iters", ctypes.c_int), ("switched_at", ctypes.c_int),
                 ("res_norm", ctypes.c_double), ("e_corr", ctypes.c_double),
                 ("e_total", ctypes.c_double), ("t_residual_ms", ctypes.c_double),
-                ("t_total_ms", ctypes.c_double), ("residual_flops", ctypes.c_double)]
+                ("t_total_ms", ctypes.c_double), ("residual_flops", ctypes.c_double),
+                ("quartic_flops", ctypes.c_double), ("t_quartic_ms", ctypes.c_double),
+                ("n_quartic", ctypes.c_int), ("n_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

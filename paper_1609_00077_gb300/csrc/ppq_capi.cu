@@ -67,7 +67,12 @@ struct Workspace {
   double* host = nullptr;  // pinned host scalars
   // DIIS ring: slots of t_new and of e
   double *slot_t = nullptr, *slot_e = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evq0 = nullptr, evq1 = nullptr;
+  // optional timing of the quartic kernel (opts.profile)
+  bool profile = false;
+  double t_quartic_ms = 0.0;
+  int n_quartic = 0;
+  int n_launches = 0;
 };
 
 std::mutex g_mu;
@@ -84,6 +89,8 @@ void free_ws(Workspace* w) {
   if (w->host) cudaFreeHost(w->host);
   if (w->ev0) cudaEventDestroy(w->ev0);
   if (w->ev1) cudaEventDestroy(w->ev1);
+  if (w->evq0) cudaEventDestroy(w->evq0);
+  if (w->evq1) cudaEventDestroy(w->evq1);
   *w = Workspace();
 }
 
@@ -119,6 +126,8 @@ int grow(Workspace* w, int N, int diis) {
   CK(cudaMallocHost((void**)&w->host, sizeof(double) * 64));
   CK(cudaEventCreate(&w->ev0));
   CK(cudaEventCreate(&w->ev1));
+  CK(cudaEventCreate(&w->evq0));
+  CK(cudaEventCreate(&w->evq1));
   w->N = Nc;
   w->diis_cap = dc;
   return 0;
@@ -244,15 +253,25 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
   ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair);
   ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
+  if (w->profile) CK(cudaEventRecord(w->evq0, s));
   ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, pt7, pg, cl, t2, w->dir, w->abuf);
+  if (w->profile) CK(cudaEventRecord(w->evq1, s));
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->r + 3 * N);
   CK(cudaGetLastError());
+  w->n_launches += 6;
   return 0;
 }
 
 int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+}
+
+// algorithmic FLOPs of one k_r2 launch (topologies T4, T5, T2+T7, T9)
+double quartic_flops(int N) {
+  double n = N, pairs = n * (n - 1);
+  return 2.0 * pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 +
+                        (n - 2) * ((n - 3) * PPQ_NQ9 + PPQ_NC9) + PPQ_NSOP);
 }
 
 double residual_flops(int N) {
@@ -329,7 +348,7 @@ int ppq_default_opts(ppq_opts* o) {
   o->K = 2; o->K_H = 0; o->precision = 0;
   o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-12;
   o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
-  o->level_shift = 0.0; o->guess = 0;
+  o->level_shift = 0.0; o->guess = 0; o->profile = 0;
   return 0;
 }
 
@@ -409,8 +428,17 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   }
   int N = n_pairs, n = 2 * N;
   size_t L = amp_len(N);
-  if (o.guess == 1) { if ((rc = copy_amps(w->t, t_in, L, s))) return rc; }
-  else CK(cudaMemsetAsync(w->t, 0, sizeof(double) * L, s));
+  w->profile = o.profile != 0;
+  w->t_quartic_ms = 0.0;
+  w->n_quartic = 0;
+  w->n_launches = 0;
+  if (o.guess == 1) {
+    if ((rc = copy_amps(w->t, t_in, L, s))) return rc;
+    size_t L2 = (size_t)N * N * PPQ_NA2;
+    ppq::k_symmetrize<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->t + 3 * N);
+  } else {
+    CK(cudaMemsetAsync(w->t, 0, sizeof(double) * L, s));
+  }
   k_eref<<<1, 1, 0, s>>>(N, n, P.h, w->f, w->occ, w->scal + kDiisMax + 2);
   CK(cudaMemcpyAsync(w->host + 40, w->scal + kDiisMax + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
 
@@ -434,6 +462,7 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     double* st = w->slot_t + (size_t)slot * L;
     double* se = w->slot_e + (size_t)slot * L;
     ppq::k_jacobi<<<lb, 256, 0, s>>>(L, N, w->t, w->r, w->fo, w->fv, o.level_shift, st, se);
+    w->n_launches += 3;
     // order of the slots that will be active after this step
     std::vector<int> act;
     for (int id : ring) if (id != slot) act.push_back(id);
@@ -450,6 +479,12 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, w->ev0, w->ev1);
     t_res_ms += ms;
+    if (w->profile) {
+      float mq = 0.f;
+      cudaEventElapsedTime(&mq, w->evq0, w->evq1);
+      w->t_quartic_ms += mq;
+      w->n_quartic++;
+    }
     res = sqrt(w->host[0]);
     e = w->host[m + 1];
     if (prec == 0 && switched_at >= 0) polish++;
@@ -523,6 +558,7 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     CK(cudaMemcpyAsync(w->coef, w->host + 8, sizeof(double) * m, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
     ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, w->t);
+    w->n_launches += 1;
     CK(cudaGetLastError());
   }
   if (it > o.max_iter) it = o.max_iter;
@@ -543,6 +579,10 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     info->t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     info->residual_flops = residual_flops(N);
+    info->quartic_flops = quartic_flops(N);
+    info->t_quartic_ms = w->t_quartic_ms;
+    info->n_quartic = w->n_quartic;
+    info->n_launches = w->n_launches + 7;  // + staging kernels
   }
   return status;
 }

@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
   }
 }
 
-// r2[Y,Z] = dir[Y,Z] + abuf[Y,Z] + mirror(abuf[Z,Y])
+// r2[Y,Z] = dir[Y,Z] + abuf[Y,Z] + mirror(abuf[Z,Y]).  Both stored
+// orientations of a pair get the average of the two evaluations, so the two
+// copies of every amplitude stay exactly consistent under the update.
 __global__ void k_assemble(int N, const double* __restrict__ dir, const double* __restrict__ abuf,
                            double* __restrict__ r2) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,8 +368,29 @@ __global__ void k_assemble(int N, const double* __restrict__ dir, const double* 
   int YZ = i / PPQ_NA2;
   int Y = YZ / N, Z = YZ % N;
   if (Y == Z) { r2[i] = 0.0; return; }
+  if (Y > Z) return;  // written by the (Z,Y) thread's partner below
+  int k2 = ppq_a2_swap[k];
+  double sg = double(ppq_a2_swsg[k]);
+  size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + k2;
+  double v = dir[i] + abuf[i] + sg * abuf[j];
+  double w = dir[j] + abuf[j] + sg * abuf[i];  // (Z,Y) orientation, channel k2
+  double a = 0.5 * (v + sg * w);
+  r2[i] = a;
+  r2[j] = sg * a;
+}
+
+// make the two stored copies of every two-pair amplitude consistent (upper
+// triangle wins) and zero the diagonal
+__global__ void k_symmetrize(int N, double* __restrict__ t2) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * N * PPQ_NA2) return;
+  int k = i % PPQ_NA2;
+  int YZ = i / PPQ_NA2;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) { t2[i] = 0.0; return; }
+  if (Y > Z) return;
   size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + ppq_a2_swap[k];
-  r2[i] = dir[i] + abuf[i] + double(ppq_a2_swsg[k]) * abuf[j];
+  t2[j] = double(ppq_a2_swsg[k]) * t2[i];
 }
 
 // ---------------------------------------------------------------- reductions / update

@@ -110,8 +110,10 @@ def pair_orbitals(n_occ, n_pairs=None):
     return occ, vir
 
 
-def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True):
-    """kind 'polyene' (size = number of sites) or 'acene' (size = rings)."""
+def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True, orbitals="canonical"):
+    """kind 'polyene' (size = number of sites) or 'acene' (size = rings).
+    orbitals: 'canonical' (RHF, Fig. 1 energy pairing) or 'local' (Boys
+    localised occupied and virtual orbitals, nearest-centroid pairing)."""
     if kind == 'polyene':
         xyz, bonds = polyene_geometry(size)
         name = f"PPP C{size}H{size + 2}"
@@ -131,6 +133,15 @@ def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True):
         return J, K
     e, C, e_elec = rhf(np.eye(n), h, nocc, jk)
     occ, vir = pair_orbitals(nocc)
+    if orbitals == "local":
+        from .localize import localized_pairs
+        C, occ, vir = localized_pairs(C, np.asarray(xyz), nocc)
+        name += " (Boys-localised pairs)"
+        P = 2.0 * C[:, occ] @ C[:, occ].T
+        J, K = jk(P)
+        e = np.diag(C.T @ (h + J - 0.5 * K) @ C)
+    elif orbitals != "canonical":
+        raise ValueError(orbitals)
     if with_eri:
         h_mo, eri = mo_integrals(C, h, gamma_zdo=gamma)
     else:
