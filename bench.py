@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-only comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer C-ABI leg")
+    ap.add_argument("--mode", default="solve", choices=["solve", "residual"],
+                    help="'residual': only --steps residual evaluations (for ncu captures)")
+    ap.add_argument("--precision", type=int, default=1, help="residual mode: 0 FP64, 1 FP32")
     return ap.parse_args()
 
 
@@ -179,10 +183,31 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def residual_mode(args):
+    """A few residual evaluations at the converged-scale amplitudes of a short
+    mixed solve (the small case used for ncu captures)."""
+    import torch
+    import paper_1609_00077_gb300 as ppq
+    H = workload(args.sites)
+    eri = device_eri(H, torch)
+    h = torch.from_numpy(H.h).cuda()
+    t = torch.zeros(ppq.amp_count(H.n_pairs), dtype=torch.float64, device="cuda")
+    ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, t_out=t, precision=1,
+                 max_iter=8)
+    r = torch.zeros_like(t)
+    for _ in range(args.steps):
+        ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, h, eri, t, r, precision=args.precision)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "residual", "sites": args.sites, "steps": args.steps,
+                      "norm": float(r.norm())}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "residual":
+        return residual_mode(args)
     import torch
     import paper_1609_00077_gb300 as ppq
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -240,17 +265,18 @@ def main():
                 / (info64["t_residual_ms"] * 1e-3) / 1e12,
                 "abs_dE_mixed_vs_fp64": abs(e_mixed - e64)}
     # end to end through the C ABI with host buffers
+    e2e_s = None
     h_host = torch.from_numpy(H.h).pin_memory()
     eri_host = eri.cpu().pin_memory()
     t_host = torch.zeros(L, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(args.steps):
-        rc_e, e_e2e, _, info_e = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h_host.numpy(),
-                                              eri_host.numpy(), H.e_const, t_out=t_host.numpy(),
-                                              precision=1, stream=stream.cuda_stream, **kw)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - w0) / args.steps
+    if not args.no_e2e:
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h_host.numpy(), eri_host.numpy(), H.e_const,
+                         t_out=t_host.numpy(), precision=1, stream=stream.cuda_stream, **kw)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - w0) / args.steps
     # roofline of the dominant kernel (the quartic contraction, FP32 in the bulk)
     pk = peaks()
     t_q = info["t_quartic_ms"] / max(info["n_quartic"], 1)
