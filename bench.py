@@ -192,8 +192,8 @@ def residual_mode(args):
     eri = device_eri(H, torch)
     h = torch.from_numpy(H.h).cuda()
     t = torch.zeros(ppq.amp_count(H.n_pairs), dtype=torch.float64, device="cuda")
-    ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, t_out=t, precision=1,
-                 max_iter=8)
+    ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, t_out=t,
+                 precision=args.precision, max_iter=8)
     r = torch.zeros_like(t)
     for _ in range(args.steps):
         ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, h, eri, t, r, precision=args.precision)

@@ -59,6 +59,10 @@ struct Workspace {
   double *t = nullptr, *r = nullptr, *dir = nullptr, *abuf = nullptr;
   // residual scratch (sized for double, reused as float)
   void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
+  void *clT = nullptr, *gT = nullptr, *B9 = nullptr;  // quartic GEMM operands / output
+  double* t9 = nullptr;
+  int* work9 = nullptr;
+  int n_work9 = 0;
   double *esite = nullptr, *epair = nullptr;
   // reductions
   double *part = nullptr, *scal = nullptr, *coef = nullptr;
@@ -83,7 +87,8 @@ size_t amp_len(int N) { return (size_t)3 * N + (size_t)PPQ_NA2 * N * N; }
 void free_ws(Workspace* w) {
   void* ps[] = {w->h, w->eri, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
-                w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e};
+                w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
+                w->clT, w->gT, w->B9, w->t9, w->work9};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -114,6 +119,19 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->cl, sizeof(double) * NN * PPQ_NS36); AL(w->hs, sizeof(double) * Nc * 256);
   AL(w->pg, sizeof(double) * NN * PPQ_NS36); AL(w->pt7, sizeof(double) * NN * PPQ_NT7E);
   AL(w->pc0, sizeof(double) * NN * PPQ_NCOL0);
+  AL(w->clT, sizeof(double) * NN * PPQ_NS36); AL(w->gT, sizeof(double) * NN * PPQ_NS36);
+  AL(w->B9, sizeof(double) * NN * Nc * PPQ_NQ9); AL(w->t9, sizeof(double) * NN * PPQ_NA2);
+  {
+    // quartic GEMM work items: chunks of at most 4 (c1, g) entries of one c2
+    std::vector<int> wk;
+    for (int c2 = 0; c2 < 30; ++c2)
+      for (int a = ppq_q9cptr_h[c2]; a < ppq_q9cptr_h[c2 + 1]; a += 4) {
+        wk.push_back(c2); wk.push_back(a); wk.push_back(std::min(a + 4, (int)ppq_q9cptr_h[c2 + 1]));
+      }
+    w->n_work9 = (int)wk.size() / 3;
+    AL(w->work9, sizeof(int) * wk.size());
+    CK(cudaMemcpy(w->work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice));
+  }
   AL(w->esite, sizeof(double) * Nc); AL(w->epair, sizeof(double) * NN);
   AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
   AL(w->scal, sizeof(double) * (kDiisMax + 4)); AL(w->coef, sizeof(double) * kDiisMax);
@@ -236,9 +254,37 @@ int stage(Workspace* w, const Problem& P, cudaStream_t s) {
   return 0;
 }
 
+template <typename R, int MT>
+int launch_t9_mt(Workspace* w, int N, cudaStream_t s) {
+  int T = (N + MT - 1) / MT;           // thread grid T x T, micro-tile MT x MT
+  int nth = ((T * T + 31) / 32) * 32;
+  size_t smem = 2 * 16 * (size_t)T * MT * sizeof(R);
+  dim3 grid(w->n_work9, N);
+  ppq::k_t9_gemm<R, MT><<<grid, nth, smem, s>>>(N, T, (const R*)w->clT, (const R*)w->gT, w->work9,
+                                                 (R*)w->B9);
+  return 0;
+}
+
+template <typename R>
+int launch_t9_gemm(Workspace* w, int N, cudaStream_t s) {
+  int mt = (N + 15) / 16;
+  switch (mt) {
+    case 1: return launch_t9_mt<R, 1>(w, N, s);
+    case 2: return launch_t9_mt<R, 2>(w, N, s);
+    case 3: return launch_t9_mt<R, 3>(w, N, s);
+    case 4: return launch_t9_mt<R, 4>(w, N, s);
+    case 5: return launch_t9_mt<R, 5>(w, N, s);
+    case 6: return launch_t9_mt<R, 6>(w, N, s);
+    case 7: return launch_t9_mt<R, 7>(w, N, s);
+    case 8: return launch_t9_mt<R, 8>(w, N, s);
+    default: return fail(-5, "n_pairs > 128 is not supported by the quartic kernel");
+  }
+}
+
 // one residual evaluation at w->t into w->r; energy pieces into esite/epair
 template <typename R>
 int residual(Workspace* w, int N, cudaStream_t s) {
+  int rc = 0;
   const R* g1 = std::is_same<R, double>::value ? (const R*)w->g1d : (const R*)w->g1f;
   const R* g2 = std::is_same<R, double>::value ? (const R*)w->g2d : (const R*)w->g2f;
   const double* t1 = w->t;
@@ -253,13 +299,22 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
   ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair);
   ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
-  if (w->profile) CK(cudaEventRecord(w->evq0, s));
   ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, pt7, pg, cl, t2, w->dir, w->abuf);
+  // quartic term: transposed operands, GEMM, W-contraction
+  size_t T36 = (size_t)NN * PPQ_NS36;
+  ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl, (R*)w->clT);
+  ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
+  if (w->profile) CK(cudaEventRecord(w->evq0, s));
+  if ((rc = launch_t9_gemm<R>(w, N, s))) return rc;
   if (w->profile) CK(cudaEventRecord(w->evq1, s));
+  size_t epi_smem = 2 * sizeof(R) * N * PPQ_NS36;
+  if (epi_smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(ppq::k_t9_epi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
+  ppq::k_t9_epi<R><<<NN, 256, epi_smem, s>>>(N, (const R*)w->B9, cl, w->t9);
   size_t L2 = (size_t)NN * PPQ_NA2;
-  ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->r + 3 * N);
+  ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
   CK(cudaGetLastError());
-  w->n_launches += 6;
+  w->n_launches += 10;
   return 0;
 }
 
@@ -267,11 +322,11 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
 }
 
-// algorithmic FLOPs of one k_r2 launch (topologies T4, T5, T2+T7, T9)
+// algorithmic FLOPs of one k_t9_gemm launch: for each unordered pair Y < Z and
+// each of the NQ9 (c1, c2, g) combinations, sum over X (N) for every W (N)
 double quartic_flops(int N) {
-  double n = N, pairs = n * (n - 1);
-  return 2.0 * pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 +
-                        (n - 2) * ((n - 3) * PPQ_NQ9 + PPQ_NC9) + PPQ_NSOP);
+  double n = N;
+  return 2.0 * (n * (n - 1) / 2) * PPQ_NQ9 * n * n;
 }
 
 double residual_flops(int N) {
@@ -281,8 +336,8 @@ double residual_flops(int N) {
   fma += n * (PPQ_H1_NEL + 2 * 3 * 16 * 3);                                 // site closures (approx)
   fma += pairs * (17792.0 + PPQ_PR_N + PPQ_PL_N);                           // pair closures
   fma += n * ((n - 1) * PPQ_NT3 + (n - 1) * (n - 2) * PPQ_NT8);             // r1
-  fma += pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 +         // r2
-                  (n - 2) * ((n - 3) * PPQ_NQ9 + PPQ_NC9) + PPQ_NSOP);
+  fma += pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 + PPQ_NSOP);  // r2
+  fma += (pairs / 2) * (n * n * PPQ_NQ9 + n * PPQ_NC9);                      // quartic
   return 2.0 * fma;
 }
 

@@ -256,13 +256,12 @@ __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
   }
 }
 
-// r2 for ordered (Y,Z): T5, T4, T9 directly (dir) and T2+T7 through the
-// exp(-T_YZ) transform (abuf, mirrored later)
+// r2 for ordered (Y,Z): T5, T4 directly (dir) and T2+T7 through the
+// exp(-T_YZ) transform (abuf, mirrored later); T9 is k_t9_gemm + k_t9_epi
 template <typename R>
 __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
     const R* __restrict__ pt7, const R* __restrict__ pg, const R* __restrict__ cl,
     const double* __restrict__ t2, double* __restrict__ dir, double* __restrict__ abuf) {
-  __shared__ R B[PPQ_NQ9];
   __shared__ R U[PPQ_NS36];
   __shared__ R outs[PPQ_NA2];
   int YZ = blockIdx.x;
@@ -275,11 +274,14 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
     return;
   }
   const R* clYZ = cl + (size_t)YZ * PPQ_NS36;
-  // T5 + T4 (thread per output channel, deterministic order)
-  if (threadIdx.x < PPQ_NA2) {
-    int o = threadIdx.x;
-    R acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
-    for (int X = 0; X < N; ++X) {
+  constexpr int S4 = 8, S7 = 7;
+  __shared__ R part4[PPQ_NA2][S4];
+  __shared__ R part7[PPQ_NS36][S7];
+  // T4: thread (o, s) sums X = s, s + S4, ...
+  if (threadIdx.x < PPQ_NA2 * S4) {
+    int o = threadIdx.x / S4, sl = threadIdx.x % S4;
+    R acc = R(0);
+    for (int X = sl; X < N; X += S4) {
       if (X == Y || X == Z) continue;
       const R* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
       const R* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
@@ -289,18 +291,13 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
         acc += R(q[4]) * cy[q[0]] * cz[q[1]] * h0[q[2]];
       }
     }
-    outs[o] = acc;
+    part4[o][sl] = acc;
   }
-  // T2 + T7 into U
-  if (threadIdx.x >= 64 && threadIdx.x < 64 + PPQ_NS36) {
-    int nu = threadIdx.x - 64;
+  // T7: thread (nu, s) sums W = s, s + S7, ...
+  if (threadIdx.x < PPQ_NS36 * S7) {
+    int nu = threadIdx.x / S7, sl = threadIdx.x % S7;
     R acc = R(0);
-    const R* hY = hs + (size_t)Y * 256;
-    for (int e = ppq_t2p[nu]; e < ppq_t2p[nu + 1]; ++e) {
-      const int16_t* q = ppq_t2 + 4 * e;
-      acc += clYZ[q[0]] * hY[q[1] * 16 + q[2]];
-    }
-    for (int W = 0; W < N; ++W) {
+    for (int W = sl; W < N; W += S7) {
       if (W == Y || W == Z) continue;
       const R* cw = cl + ((size_t)W * N + Z) * PPQ_NS36;
       const R* p7 = pt7 + ((size_t)Y * N + W) * PPQ_NT7E;
@@ -309,37 +306,27 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
         acc += R(q[4]) * clYZ[q[0]] * cw[q[1]] * p7[q[2]];
       }
     }
+    part7[nu][sl] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < PPQ_NA2) {
+    int o = threadIdx.x;
+    R acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
+    for (int sl = 0; sl < S4; ++sl) acc += part4[o][sl];
+    outs[o] = acc;
+  }
+  if (threadIdx.x >= 64 && threadIdx.x < 64 + PPQ_NS36) {
+    int nu = threadIdx.x - 64;
+    R acc = R(0);
+    const R* hY = hs + (size_t)Y * 256;
+    for (int e = ppq_t2p[nu]; e < ppq_t2p[nu + 1]; ++e) {
+      const int16_t* q = ppq_t2 + 4 * e;
+      acc += clYZ[q[0]] * hY[q[1] * 16 + q[2]];
+    }
+    for (int sl = 0; sl < S7; ++sl) acc += part7[nu][sl];
     U[nu] = acc;
   }
   __syncthreads();
-  // T9: for each W, B[q] = sum_X Cl[X,Y][p.c1] Cl[X,Z][p.c2] G[X,W][g]
-  R acc9 = R(0);
-  for (int W = 0; W < N; ++W) {
-    if (W == Y || W == Z) continue;
-    for (int q = threadIdx.x; q < PPQ_NQ9; q += blockDim.x) {
-      int p = ppq_q9[2 * q], gi = ppq_q9[2 * q + 1];
-      int c1 = ppq_p9[2 * p], c2 = ppq_p9[2 * p + 1];
-      R s = R(0);
-      for (int X = 0; X < N; ++X) {
-        if (X == Y || X == Z || X == W) continue;
-        s += cl[((size_t)X * N + Y) * PPQ_NS36 + c1] * cl[((size_t)X * N + Z) * PPQ_NS36 + c2] *
-             pg[((size_t)X * N + W) * PPQ_NS36 + gi];
-      }
-      B[q] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < PPQ_NA2) {
-      int o = threadIdx.x;
-      const R* cy = cl + ((size_t)W * N + Y) * PPQ_NS36;
-      const R* cz = cl + ((size_t)W * N + Z) * PPQ_NS36;
-      for (int e = ppq_c9p[o]; e < ppq_c9p[o + 1]; ++e) {
-        const int16_t* q = ppq_c9 + 5 * e;
-        acc9 += R(q[4]) * B[q[0]] * cy[q[1]] * cz[q[2]];
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < PPQ_NA2) outs[threadIdx.x] += R(0.5) * acc9;
   // exp(-T_YZ) on U (sequential over the commuting factors)
   const double* t = t2 + (size_t)YZ * PPQ_NA2;
   for (int k = 0; k < PPQ_NA2; ++k) {
@@ -361,7 +348,7 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
 // orientations of a pair get the average of the two evaluations, so the two
 // copies of every amplitude stay exactly consistent under the update.
 __global__ void k_assemble(int N, const double* __restrict__ dir, const double* __restrict__ abuf,
-                           double* __restrict__ r2) {
+                           const double* __restrict__ t9, double* __restrict__ r2) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)N * N * PPQ_NA2) return;
   int k = i % PPQ_NA2;
@@ -372,9 +359,9 @@ __global__ void k_assemble(int N, const double* __restrict__ dir, const double* 
   int k2 = ppq_a2_swap[k];
   double sg = double(ppq_a2_swsg[k]);
   size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + k2;
-  double v = dir[i] + abuf[i] + sg * abuf[j];
-  double w = dir[j] + abuf[j] + sg * abuf[i];  // (Z,Y) orientation, channel k2
-  double a = 0.5 * (v + sg * w);
+  // direct terms evaluated in both orientations are averaged; the quartic
+  // term (Y < Z only) and the two transformed pieces add
+  double a = 0.5 * (dir[i] + sg * dir[j]) + t9[i] + abuf[i] + sg * abuf[j];
   r2[i] = a;
   r2[j] = sg * a;
 }
@@ -506,6 +493,147 @@ __global__ void k_extrapolate(size_t L, int m, const double* __restrict__ coef, 
   double s = 0.0;
   for (int k = 0; k < m; ++k) s += coef[k] * slots[order[k] * ld + i];
   t[i] = s;
+}
+
+}  // namespace ppq
+
+namespace ppq {
+
+// ---------------------------------------------------------------- quartic term (T9) as GEMMs
+// out[Y,Z][o] = 1/2 sum_{X,W} sum_ch s Cl[X,Y][c1] Cl[X,Z][c2] G[X,W][g] Cl[W,Y][c3] Cl[W,Z][c4]
+// Stage 1 (this kernel): for each (c2, Y) and each (c1, g) of the channel list
+//   B[Y][q][Z][W] = sum_X clT[c2][X][Z] * (clT[c1][X][Y] * gT[g][X][W])
+// a GEMM with M = Z, N = W, K = X: rows Z <= Y are skipped (Y < Z symmetry).
+// Thread (tz, tw) of a 16x16 grid owns rows tz + 16 i and columns tw + 16 j.
+template <typename R, int MT>
+__global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restrict__ clT,
+    const R* __restrict__ gT, const int* __restrict__ work, R* __restrict__ B) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int KC = 16;
+  const int NPD = T * MT;                       // padded row length (zeros beyond N)
+  R* As = reinterpret_cast<R*>(smem_raw);      // [KC][NPD]
+  R* Bs = As + KC * NPD;                        // [KC][NPD]
+  int c2 = work[3 * blockIdx.x], q0 = work[3 * blockIdx.x + 1], q1 = work[3 * blockIdx.x + 2];
+  int Y = blockIdx.y;
+  int tz = threadIdx.x / T, tw = threadIdx.x % T;
+  bool active = tz < T;
+  size_t NN = (size_t)N * N;
+  const R* a_src = clT + (size_t)c2 * NN;      // [X][Z]
+  int i0 = (Y + 1) / T;                        // first micro-row that can hold Z > Y
+  int nth = blockDim.x;
+  for (int qq = q0; qq < q1; ++qq) {
+    int c1 = ppq_q9c[3 * qq], g = ppq_q9c[3 * qq + 1], q = ppq_q9c[3 * qq + 2];
+    const R* ys = clT + (size_t)c1 * NN;       // [X][Y]
+    const R* gs = gT + (size_t)g * NN;         // [X][W]
+    R acc[MT][MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < MT; ++j) acc[i][j] = R(0);
+    for (int k0 = 0; k0 < N; k0 += KC) {
+      int kc = min(KC, N - k0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kc * NPD; e += nth) {
+        int kk = e / NPD, z = e - kk * NPD, X = k0 + kk;
+        R av = R(0), bv = R(0);
+        if (z < N) {
+          av = a_src[(size_t)X * N + z];
+          bv = ys[(size_t)X * N + Y] * gs[(size_t)X * N + z];
+        }
+        As[e] = av;
+        Bs[e] = bv;
+      }
+      __syncthreads();
+      if (active) {
+        const R* ap = As + tz;
+        const R* bp = Bs + tw;
+        for (int kk = 0; kk < kc; ++kk) {
+          R a[MT], b[MT];
+#pragma unroll
+          for (int i = 0; i < MT; ++i) a[i] = ap[T * i];
+#pragma unroll
+          for (int j = 0; j < MT; ++j) b[j] = bp[T * j];
+#pragma unroll
+          for (int i = 0; i < MT; ++i) {
+            if (i < i0) continue;
+#pragma unroll
+            for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          }
+          ap += NPD;
+          bp += NPD;
+        }
+      }
+    }
+    if (active) {
+      R* out = B + (((size_t)Y * PPQ_NQ9 + q) * N) * N;
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        int Z = tz + T * i;
+        if (Z <= Y || Z >= N) continue;
+#pragma unroll
+        for (int j = 0; j < MT; ++j) {
+          int W = tw + T * j;
+          if (W < N) out[(size_t)Z * N + W] = acc[i][j];
+        }
+      }
+    }
+  }
+}
+
+// Stage 2: t9[Y,Z][o] = 1/2 sum_W sum_{ch -> o} s B[Y][q][Z][W] Cl[W,Y][c3] Cl[W,Z][c4], Y < Z
+template <typename R>
+__global__ void __launch_bounds__(256) k_t9_epi(int N, const R* __restrict__ B, const R* __restrict__ cl,
+                                                double* __restrict__ t9) {
+  extern __shared__ unsigned char smem_raw[];
+  R* cy = reinterpret_cast<R*>(smem_raw);
+  R* cz = cy + N * PPQ_NS36;
+  int YZ = blockIdx.x;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y >= Z) return;
+  for (int e = threadIdx.x; e < N * PPQ_NS36; e += blockDim.x) {
+    int W = e / PPQ_NS36, c = e % PPQ_NS36;
+    cy[e] = cl[((size_t)W * N + Y) * PPQ_NS36 + c];
+    cz[e] = cl[((size_t)W * N + Z) * PPQ_NS36 + c];
+  }
+  __syncthreads();
+  const R* bb = B + ((size_t)Y * PPQ_NQ9 * N + Z) * N;   // + q * N * N + W
+  size_t qs = (size_t)N * N;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int o = warp; o < PPQ_NA2; o += nw) {
+    R acc = R(0);
+    for (int e = ppq_c9p[o]; e < ppq_c9p[o + 1]; ++e) {
+      const int16_t* c = ppq_c9 + 5 * e;
+      const R* bq = bb + c[0] * qs;
+      R sg = R(c[4]);
+      int c3 = c[1], c4 = c[2];
+      for (int W = lane; W < N; W += 32) acc += sg * bq[W] * cy[W * PPQ_NS36 + c3] * cz[W * PPQ_NS36 + c4];
+    }
+    double v = double(acc);
+    for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
+    if (lane == 0) t9[(size_t)YZ * PPQ_NA2 + o] = 0.5 * v;
+  }
+}
+
+// transposed link coefficients clT[c][X][Y] = Cl[X,Y][c]
+template <typename R>
+__global__ void k_transpose_cl(int N, const R* __restrict__ cl, R* __restrict__ clT) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t NN = (size_t)N * N;
+  if (i >= NN * PPQ_NS36) return;
+  int c = i / NN;
+  size_t XY = i % NN;
+  clT[i] = cl[XY * PPQ_NS36 + c];
+}
+
+// transposed closure row gT[g][X][W] = G[X,W][g]
+template <typename R>
+__global__ void k_transpose_g(int N, const R* __restrict__ pg, R* __restrict__ gT) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t NN = (size_t)N * N;
+  if (i >= NN * PPQ_NS36) return;
+  int g = i / NN;
+  size_t XW = i % NN;
+  gT[i] = pg[XW * PPQ_NS36 + g];
 }
 
 }  // namespace ppq

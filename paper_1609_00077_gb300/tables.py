@@ -606,7 +606,16 @@ def emit_header(path):
     q9i = {q: i for i, q in enumerate(q9)}
     ch9 = [(q9i[(p9i[(int(r[0]), int(r[1]))], int(r[4]))], int(r[2]), int(r[3]), int(r[5]), int(r[6]))
            for r in t9]
-    ch9, c9p = by_out(np.array(ch9), 3, 29)
+    # GEMM form of the quartic topology: for each c2 the list of (c1, g, q)
+    c2list = sorted(((int(p9[p][1]), int(p9[p][0]), int(g), qi) for qi, (p, g) in enumerate(q9)))
+    g2ptr = [0]
+    for c2 in range(30):
+        g2ptr.append(sum(1 for e in c2list if e[0] <= c2))
+    out += [_c_array("ppq_q9c", "int16_t", np.array([(c1, g, qi) for _, c1, g, qi in c2list])),
+            _c_array("ppq_q9cptr", "int16_t", g2ptr),
+            _c_array("ppq_q9cptr_h", "int16_t", g2ptr).replace("static __device__ const", "static const")]
+    ch9arr = np.array(ch9)
+    ch9, c9p = by_out(ch9arr, 3, 29)
     out.append(_c_array("ppq_c9p", "int16_t", c9p))
     out += [f"#define PPQ_NP9 {len(p9)}", f"#define PPQ_NQ9 {len(q9)}", f"#define PPQ_NC9 {len(ch9)}",
             _c_array("ppq_p9", "int8_t", np.array(p9)), _c_array("ppq_q9", "int16_t", np.array(q9)),
