@@ -114,6 +114,26 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);
 
+/* pq_residual without any device allocation.  The paper has no counterpart:
+   this entry point exists for callers that cannot call cudaMalloc.  Examples
+   are code running inside another framework's memory pool or under a fixed
+   device-memory budget, or code on a path where cudaMalloc's implicit device
+   synchronisation is not acceptable.  Every intermediate lives in one
+   file-scope device array of 16 MiB.  Each GPU that loads the library holds
+   that array until the process exits, so the call is limited to
+   n_pairs <= 12; larger sizes return -6 with a message.
+   h, eri, t and r must be device pointers (else -7); occ_of_pair / vir_of_pair
+   are host arrays; e_corr is a host pointer (nullable).  Like pq_residual, the
+   call returns after `stream` has finished the work.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) while that device is current; make that first call
+   before any stream capture.  All calls share the one array, and each call
+   clears the part it uses before use.  Calls that overlap on the GPU (from
+   several host threads or streams) race on the array, so serialise them. */
+int pq_residual_static(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                       const double* h, const double* eri, const double* t,
+                       double* r, double* e_corr, int precision, void* stream);
+
 /* Free the cached workspace of the current device.  Returns 0. */
 int ppq_release(void);
 

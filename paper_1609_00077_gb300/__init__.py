@@ -60,18 +60,19 @@ def lib():
         L.ppq_amp_count.argtypes = [I, I, ctypes.POINTER(S)]
         L.ppq_amp_layout.argtypes = [I, P]
         L.pq_residual.argtypes = [I, P, P, P, P, P, P, P, I, P]
+        L.pq_residual_static.argtypes = [I, P, P, P, P, P, P, P, I, P]
         L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
                                ctypes.POINTER(Info), P]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
-                  L.pq_solve, L.ppq_release):
+                  L.pq_residual_static, L.pq_solve, L.ppq_release):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
-            "pq_solve", "ppq_release", "ppq_last_error"]
+            "pq_residual_static", "pq_solve", "ppq_release", "ppq_last_error"]
 
 
 def _ptr(x):
@@ -142,6 +143,19 @@ def pq_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, stream
                            precision, _stream(stream))
     _check(rc, "pq_residual")
     return r, e.value
+
+
+def pq_residual_static(occ_of_pair, vir_of_pair, h, eri, t, r, precision=0, stream=None):
+    """pq_residual without device allocation (scratch in a fixed 16 MiB device
+    array, n_pairs <= 12).  For callers that cannot call cudaMalloc: h, eri, t
+    and r must already be device tensors (torch CUDA).  Returns e_corr."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    e = ctypes.c_double()
+    rc = lib().pq_residual_static(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
+                                  _ptr(t), _ptr(r), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p),
+                                  precision, _stream(stream))
+    _check(rc, "pq_residual_static")
+    return e.value
 
 
 def pq_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=None,

@@ -643,3 +643,109 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free residual
+// pq_residual_static: the residual evaluation of pq_residual with every
+// intermediate placed in one file-scope device array instead of the cached
+// workspace, for callers that must not allocate device memory.
+namespace {
+
+constexpr int kStaticMaxPairs = 12;
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+std::map<int, unsigned char*> g_static_addr;  // device address of g_static_scratch, per device
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side symbol is only a handle, never a device address).
+int static_scratch_address(unsigned char** out) {
+  int dev;
+  CK(cudaGetDevice(&dev));
+  auto it = g_static_addr.find(dev);
+  if (it == g_static_addr.end()) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(-100, "cudaGetSymbolAddress(g_static_scratch) failed: %s", cudaGetErrorString(e));
+    it = g_static_addr.emplace(dev, static_cast<unsigned char*>(p)).first;
+  }
+  *out = it->second;
+  return 0;
+}
+
+struct Carver {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * (count > 0 ? count : 1);
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                                  const double* h, const double* eri, const double* t, double* r,
+                                  double* e_corr, int precision, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs > kStaticMaxPairs)
+    return fail(-6, "pq_residual_static: n_pairs = %d exceeds the static scratch limit of %d pairs",
+                n_pairs, kStaticMaxPairs);
+  std::vector<int> lab;
+  int rc = check_pairing(n_pairs, occ_of_pair, vir_of_pair, lab);
+  if (rc) return rc;
+  if (precision != 0 && precision != 1) return fail(-4, "precision must be 0 or 1");
+  if (!h || !eri || !t || !r) return fail(-2, "h, eri, t and r must be non-null");
+  if (!is_device_ptr(h) || !is_device_ptr(eri) || !is_device_ptr(t) || !is_device_ptr(r))
+    return fail(-7, "pq_residual_static needs device pointers for h, eri, t and r");
+  unsigned char* base = nullptr;
+  if ((rc = static_scratch_address(&base))) return rc;
+  int N = n_pairs, n = 2 * N;
+  size_t NN = (size_t)N * N;
+  Carver cv{base};
+  Workspace w;  // pointers into the static array; nothing is allocated
+  w.occ = cv.take<int>(N); w.vir = cv.take<int>(N); w.lab = cv.take<int>(n);
+  w.f = cv.take<double>((size_t)n * n); w.hp = cv.take<double>((size_t)n * n);
+  w.fo = cv.take<double>(N); w.fv = cv.take<double>(N);
+  w.g1d = cv.take<double>((size_t)N * PPQ_NG1); w.g2d = cv.take<double>(NN * PPQ_NG2);
+  w.g1f = cv.take<float>((size_t)N * PPQ_NG1); w.g2f = cv.take<float>(NN * PPQ_NG2);
+  w.dir = cv.take<double>(NN * PPQ_NA2); w.abuf = cv.take<double>(NN * PPQ_NA2);
+  w.cl = cv.take<double>(NN * PPQ_NS36); w.hs = cv.take<double>((size_t)N * 256);
+  w.pg = cv.take<double>(NN * PPQ_NS36); w.pt7 = cv.take<double>(NN * PPQ_NT7E);
+  w.pc0 = cv.take<double>(NN * PPQ_NCOL0);
+  w.clT = cv.take<double>(NN * PPQ_NS36); w.gT = cv.take<double>(NN * PPQ_NS36);
+  w.B9 = cv.take<double>(NN * N * PPQ_NQ9); w.t9 = cv.take<double>(NN * PPQ_NA2);
+  w.esite = cv.take<double>(N); w.epair = cv.take<double>(NN);
+  w.part = cv.take<double>(kRedBlocks); w.scal = cv.take<double>(4);
+  std::vector<int> wk;
+  for (int c2 = 0; c2 < 30; ++c2)
+    for (int a = ppq_q9cptr_h[c2]; a < ppq_q9cptr_h[c2 + 1]; a += 4) {
+      wk.push_back(c2); wk.push_back(a); wk.push_back(std::min(a + 4, (int)ppq_q9cptr_h[c2 + 1]));
+    }
+  w.n_work9 = (int)wk.size() / 3;
+  w.work9 = cv.take<int>(wk.size());
+  if (cv.off > kStaticScratchBytes)
+    return fail(-6, "pq_residual_static: %zu bytes of scratch needed, %zu available", cv.off,
+                kStaticScratchBytes);
+  // the array keeps the previous call's contents: clear the part this call uses
+  CK(cudaMemsetAsync(base, 0, cv.off, s));
+  CK(cudaMemcpyAsync(w.occ, occ_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.vir, vir_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.lab, lab.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice, s));
+  Problem P{N, n, h, eri};
+  if ((rc = stage(&w, P, s))) return rc;
+  w.t = const_cast<double*>(t);  // read only by the residual kernels
+  w.r = r;
+  if ((rc = run_residual(&w, N, precision, s))) return rc;
+  k_rowsum<<<1, 256, 0, s>>>(1, 0, w.part, N, w.esite, w.epair, w.scal);
+  double e = 0.0;
+  CK(cudaMemcpyAsync(&e, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e_corr) *e_corr = e;
+  return 0;
+}
