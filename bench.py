@@ -277,12 +277,17 @@ def main():
                          t_out=t_host.numpy(), precision=1, stream=stream.cuda_stream, **kw)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - w0) / args.steps
-    # roofline of the dominant kernel (the quartic contraction, FP32 in the bulk)
+    # roofline of the dominant kernel: the quartic GEMM, split by precision
     pk = peaks()
-    t_q = info["t_quartic_ms"] / max(info["n_quartic"], 1)
-    achieved = info["quartic_flops"] / (t_q * 1e-3) / 1e12
-    # SIMT peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 x clock
+    n32 = info["n_quartic32"]; n64 = info["n_quartic"] - n32
+    t32 = info["t_quartic32_ms"]; t64 = info["t_quartic_ms"] - t32
+    ach32 = info["quartic_flops"] / (t32 / max(n32, 1) * 1e-3) / 1e12 if n32 else None
+    ach64 = info["quartic_flops"] / (t64 / max(n64, 1) * 1e-3) / 1e12 if n64 else None
+    # SIMT peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 x clock; FP64 measured DGEMM
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    fp64_peak = 1.05
+    dominant64 = t64 > t32
+    achieved = ach64 if dominant64 else ach32
     n_launch = info["n_launches"]
     res_tflops = info["residual_flops"] * info["iters"] / (info["t_residual_ms"] * 1e-3) / 1e12
     out = {
@@ -300,11 +305,21 @@ def main():
         "residual_tflops": res_tflops,
         "fp64": fp64,
         "gpu_launches": n_launch * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_r2 (quartic contraction, FP32 launches dominate)",
-                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_note": "FP32 SIMT peak from 152 SMs x 128 lanes x 2 FLOP x 2070 MHz "
-                                  "(MEASURED_PEAKS.json has no FP32 SIMT figure)"},
+        "roofline": {"bound": "alu",
+                     "kernel": "k_t9_gemm<%s> (quartic GEMM, largest share of device time)"
+                               % ("double" if dominant64 else "float"),
+                     "achieved": achieved, "peak": fp64_peak if dominant64 else fp32_peak,
+                     "unit": "TFLOP/s",
+                     "frac": achieved / (fp64_peak if dominant64 else fp32_peak), "traffic": None,
+                     "peak_note": ("measured cuBLAS DGEMM 1.05 TFLOP/s (not in MEASURED_PEAKS.json)"
+                                   if dominant64 else
+                                   "FP32 SIMT peak from 152 SMs x 128 lanes x 2 FLOP x 2070 MHz "
+                                   "(MEASURED_PEAKS.json has no FP32 SIMT figure)"),
+                     "fp32_launches": {"n": n32, "ms_total": t32, "tflops": ach32,
+                                       "frac_of_simt_peak": ach32 / fp32_peak if ach32 else None},
+                     "fp64_launches": {"n": n64, "ms_total": t64, "tflops": ach64,
+                                       "frac_of_dgemm": ach64 / fp64_peak if ach64 else None}},
+        "evals": {"fp32": info["evals_fp32"], "fp64": info["evals_fp64"]},
         "e2e": {"value": e2e_s, "unit": "s",
                 "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),
                 "d2h_bytes_per_step": int(L * 8 + 16)},

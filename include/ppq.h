@@ -60,12 +60,17 @@ typedef struct {
   int guess;          /* 0 = zero amplitudes, 1 = start from t_in               */
   int profile;        /* 1 = time the quartic contraction kernel with CUDA      */
                       /*     events on `stream` (fields t_quartic_ms, ... )     */
+  int polish;         /* after the switch (precision = 1): 0 = plain FP64       */
+                      /*     Jacobi/DIIS iterations; 1 = FP64 defect correction:*/
+                      /*     each outer step evaluates R in FP64 (norm, energy, */
+                      /*     convergence test) and solves J d = -R with FP32    */
+                      /*     finite-difference Jacobian products (default 1)    */
 } ppq_opts;
 
 typedef struct {
   int status;          /* as the return value                                  */
-  int iters;           /* residual evaluations                                 */
-  int polish_iters;    /* of which in FP64 after the switch (mixed)            */
+  int iters;           /* residual evaluations (FP32 + FP64)                    */
+  int polish_iters;    /* FP64 evaluations after the switch (mixed)            */
   int switched_at;     /* iteration of the precision switch (-1 none)          */
   double res_norm;     /* ||R||_2 over unique amplitudes at the returned t     */
   double e_corr;       /* correlation energy (Eh)                              */
@@ -78,6 +83,10 @@ typedef struct {
   double t_quartic_ms;   /* device time of those launches (profile = 1)        */
   int n_quartic;         /* number of those launches                           */
   int n_launches;        /* kernels launched by the call                       */
+  int evals_fp32;        /* residual evaluations in FP32                        */
+  int evals_fp64;        /* residual evaluations in FP64                        */
+  double t_quartic32_ms; /* part of t_quartic_ms spent in FP32 launches         */
+  int n_quartic32;       /* number of FP32 launches among n_quartic             */
 } ppq_info;
 
 /* Fill *o with the defaults listed above.  Returns 0. */

@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
                 ("e_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_dim", ctypes.c_int), ("diis_start", ctypes.c_int),
                 ("level_shift", ctypes.c_double), ("guess", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("polish", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -38,7 +38,9 @@ class Info(ctypes.Structure):
                 ("e_total", ctypes.c_double), ("t_residual_ms", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double), ("residual_flops", ctypes.c_double),
                 ("quartic_flops", ctypes.c_double), ("t_quartic_ms", ctypes.c_double),
-                ("n_quartic", ctypes.c_int), ("n_launches", ctypes.c_int)]
+                ("n_quartic", ctypes.c_int), ("n_launches", ctypes.c_int),
+                ("evals_fp32", ctypes.c_int), ("evals_fp64", ctypes.c_int),
+                ("t_quartic32_ms", ctypes.c_double), ("n_quartic32", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -42,6 +43,17 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr int kDiisMax = 16;
+
+// PPQ_TRACE=1 in the environment prints one line per residual evaluation
+// (phase, precision, ||R||, E_c) to stderr.
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("PPQ_TRACE");
+    on = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
 // Per-device workspace, grown on demand and kept between calls.
@@ -61,6 +73,8 @@ struct Workspace {
   void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
   void *clT = nullptr, *gT = nullptr, *B9 = nullptr;  // quartic GEMM operands / output
   double* t9 = nullptr;
+  double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;
+  unsigned long long* amax = nullptr;
   int* work9 = nullptr;
   int n_work9 = 0;
   double *esite = nullptr, *epair = nullptr;
@@ -76,6 +90,8 @@ struct Workspace {
   bool profile = false;
   double t_quartic_ms = 0.0;
   int n_quartic = 0;
+  double t_quartic32_ms = 0.0;  // FP32 launches only
+  int n_quartic32 = 0;
   int n_launches = 0;
 };
 
@@ -88,7 +104,8 @@ void free_ws(Workspace* w) {
   void* ps[] = {w->h, w->eri, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
                 w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
-                w->clT, w->gT, w->B9, w->t9, w->work9};
+                w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
+                w->amax};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -120,6 +137,9 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->pg, sizeof(double) * NN * PPQ_NS36); AL(w->pt7, sizeof(double) * NN * PPQ_NT7E);
   AL(w->pc0, sizeof(double) * NN * PPQ_NCOL0);
   AL(w->clT, sizeof(double) * NN * PPQ_NS36); AL(w->gT, sizeof(double) * NN * PPQ_NS36);
+  AL(w->tb, sizeof(double) * L); AL(w->r64, sizeof(double) * L); AL(w->rb, sizeof(double) * L);
+  AL(w->del, sizeof(double) * L); AL(w->rho, sizeof(double) * L);
+  AL(w->amax, sizeof(unsigned long long));
   AL(w->B9, sizeof(double) * NN * Nc * PPQ_NQ9); AL(w->t9, sizeof(double) * NN * PPQ_NA2);
   {
     // quartic GEMM work items: chunks of at most 4 (c1, g) entries of one c2
@@ -396,6 +416,241 @@ int copy_amps(double* dst, const double* src, size_t L, cudaStream_t s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- solver pieces
+__global__ void k_absmax(size_t L, const double* __restrict__ x, unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// t = tb + (eta / max|x|) x
+__global__ void k_fd_point(size_t L, const double* __restrict__ tb, const double* __restrict__ x,
+                           const unsigned long long* __restrict__ amax, double eta, double* __restrict__ t) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double m = __longlong_as_double((long long)*amax);
+  t[i] = tb[i] + (m > 0.0 ? eta / m : 0.0) * x[i];
+}
+
+// rho = r64 + (r - rb) * max|x| / eta   (r64 + J x by a forward difference)
+__global__ void k_fd_rho(size_t L, const double* __restrict__ r64, const double* __restrict__ r,
+                         const double* __restrict__ rb, const unsigned long long* __restrict__ amax,
+                         double eta, double* __restrict__ rho) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double m = __longlong_as_double((long long)*amax);
+  rho[i] = r64[i] + (m > 0.0 ? (r[i] - rb[i]) * (m / eta) : 0.0);
+}
+
+__global__ void k_axpy_to(size_t L, const double* __restrict__ a, const double* __restrict__ b,
+                          double* __restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) out[i] = a[i] + b[i];
+}
+
+// Pulay DIIS state: slot ids (oldest first) and the error-dot matrix by slot id
+struct Diis {
+  int m_max;
+  std::vector<int> ring;
+  std::vector<double> B;
+  explicit Diis(int m) : m_max(m), B(kDiisMax * kDiisMax, 0.0) {}
+  void reset() { ring.clear(); }
+};
+
+// Solve the bordered DIIS system [B -1; -1 0][c; l] = [0; -1] (FP64, host);
+// the error block is scaled by its largest diagonal (c is unchanged).
+bool diis_coefficients(const Diis& d, const std::vector<int>& act, std::vector<double>& c) {
+  int m = (int)act.size(), nn = m + 1;
+  std::vector<double> A((size_t)nn * (nn + 1), 0.0);
+  double sc = 0.0;
+  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(d.B[act[i] * kDiisMax + act[i]]));
+  if (sc <= 0.0) sc = 1.0;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i * (nn + 1) + j] = d.B[act[i] * kDiisMax + act[j]] / sc;
+    A[i * (nn + 1) + m] = -1.0;
+  }
+  for (int j = 0; j < m; ++j) A[m * (nn + 1) + j] = -1.0;
+  A[m * (nn + 1) + nn] = -1.0;
+  for (int col = 0; col < nn; ++col) {
+    int piv = col;
+    for (int r2 = col + 1; r2 < nn; ++r2)
+      if (fabs(A[r2 * (nn + 1) + col]) > fabs(A[piv * (nn + 1) + col])) piv = r2;
+    if (fabs(A[piv * (nn + 1) + col]) < 1e-300) return false;
+    if (piv != col)
+      for (int k = 0; k <= nn; ++k) std::swap(A[col * (nn + 1) + k], A[piv * (nn + 1) + k]);
+    for (int r2 = col + 1; r2 < nn; ++r2) {
+      double f = A[r2 * (nn + 1) + col] / A[col * (nn + 1) + col];
+      for (int k = col; k <= nn; ++k) A[r2 * (nn + 1) + k] -= f * A[col * (nn + 1) + k];
+    }
+  }
+  std::vector<double> x(nn, 0.0);
+  for (int r2 = nn - 1; r2 >= 0; --r2) {
+    double sum = A[r2 * (nn + 1) + nn];
+    for (int k = r2 + 1; k < nn; ++k) sum -= A[r2 * (nn + 1) + k] * x[k];
+    x[r2] = sum / A[r2 * (nn + 1) + r2];
+  }
+  c.assign(x.begin(), x.begin() + m);
+  return true;
+}
+
+// The iteration machinery of pq_solve around the residual pipeline.
+struct Solver {
+  Workspace* w;
+  int N;
+  size_t L;
+  ppq_opts o;
+  cudaStream_t s;
+  unsigned lb;
+  int evals = 0, evals32 = 0, polish_evals = 0;
+  double t_res_ms = 0.0;
+  double last_outer = 0.0;
+  double last_norm2 = 0.0;
+  Solver(Workspace* w_, int N_, size_t L_, const ppq_opts& o_, cudaStream_t s_)
+      : w(w_), N(N_), L(L_), o(o_), s(s_), lb((unsigned)((L_ + 255) / 256)) {}
+
+  int cur_prec = 0;
+  // residual at w->t (precision prec) into w->r; ||R|| and E_c to the host
+  int eval(int prec, double* res, double* e) {
+    cur_prec = prec;
+    CK(cudaEventRecord(w->ev0, s));
+    int rc = run_residual(w, N, prec, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(w->ev1, s));
+    dim3 g(kRedBlocks, 1);
+    k_multidot<<<g, 256, 0, s>>>(L, N, w->r, 0, w->slot_e, L, w->order, 0, w->part);
+    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    w->n_launches += 2;
+    account();
+    evals++;
+    if (prec) evals32++;
+    last_norm2 = w->host[0];
+    *res = sqrt(w->host[0]);
+    *e = w->host[1];
+    if (trace_on())
+      fprintf(stderr, "ppq eval %4d %s |R| %.3e E_c %.12f\n", evals, prec ? "fp32" : "fp64", *res, *e);
+    return 0;
+  }
+
+  void account() {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, w->ev0, w->ev1);
+    t_res_ms += ms;
+    if (w->profile) {
+      float mq = 0.f;
+      cudaEventElapsedTime(&mq, w->evq0, w->evq1);
+      w->t_quartic_ms += mq;
+      w->n_quartic++;
+      if (cur_prec) {
+        w->t_quartic32_ms += mq;
+        w->n_quartic32++;
+      }
+    }
+  }
+
+  // Jacobi step x <- x + res / D with DIIS over the slots; `it` counts steps
+  int diis_step(Diis& d, double* x, const double* res, int it) {
+    int slot = (int)d.ring.size() < d.m_max ? (int)d.ring.size() : d.ring.front();
+    double* st = w->slot_t + (size_t)slot * L;
+    double* se = w->slot_e + (size_t)slot * L;
+    ppq::k_jacobi<<<lb, 256, 0, s>>>(L, N, x, res, w->fo, w->fv, o.level_shift, st, se);
+    std::vector<int> act;
+    for (int id : d.ring) if (id != slot) act.push_back(id);
+    if ((int)act.size() >= d.m_max) act.erase(act.begin());
+    act.push_back(slot);
+    int m = (int)act.size();
+    memcpy(w->host + 48, act.data(), sizeof(int) * m);
+    CK(cudaMemcpyAsync(w->order, w->host + 48, sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    dim3 g(kRedBlocks, 1 + m);
+    k_multidot<<<g, 256, 0, s>>>(L, N, res, m, w->slot_e, L, w->order, slot, w->part);
+    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
+    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    d.ring = act;
+    for (int i = 0; i < m; ++i) {
+      double dd = w->host[1 + i];
+      d.B[act[i] * kDiisMax + slot] = dd;
+      d.B[slot * kDiisMax + act[i]] = dd;
+    }
+    std::vector<double> c;
+    bool extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
+    if (!extrap || !diis_coefficients(d, act, c)) {
+      c.assign(m, 0.0);
+      c[m - 1] = 1.0;
+    }
+    for (int i = 0; i < m; ++i) w->host[8 + i] = c[i];
+    int one = 1;
+    memcpy(w->host + 32, &one, sizeof(int));
+    CK(cudaMemcpyAsync(w->coef, w->host + 8, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
+    ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, x);
+    w->n_launches += 4;
+    CK(cudaGetLastError());
+    return 0;
+  }
+
+  int step_plain(Diis& d, int it) { return diis_step(d, w->t, w->r, it); }
+
+  // FP64 defect correction: w->r holds R_64(t) on entry.  Solves
+  // r + J delta = 0 to a relative accuracy of ~3e-4 with forward-difference
+  // Jacobian products of FP32 residuals (perturbation eta = 3e-4 in max norm,
+  // far above the FP32 resolution of t), then t <- t + delta.
+  int defect_correction(int* inner_out, int* it_io) {
+    const double eta = 1e-3, tol = 3e-4;
+    double* tb = w->tb;
+    double* r64 = w->r64;
+    double* rb = w->rb;
+    double* del = w->del;
+    double* rho = w->rho;
+    CK(cudaMemcpyAsync(tb, w->t, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(r64, w->r, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    double r0 = sqrt(last_norm2), rn, ed;
+    // FP32 residual at the base point
+    int rc = eval(1, &rn, &ed);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(rb, w->r, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(del, 0, sizeof(double) * L, s));
+    CK(cudaMemcpyAsync(rho, r64, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    Diis d(w->diis_cap);
+    int inner = 0;
+    std::vector<double> hist;
+    for (; inner < 30 && *it_io < o.max_iter; ++inner) {
+      if ((rc = diis_step(d, del, rho, inner + 1))) return rc;
+      // rho = r64 + J del by a forward difference at tb
+      CK(cudaMemsetAsync(w->amax, 0, sizeof(unsigned long long), s));
+      k_absmax<<<kRedBlocks, 256, 0, s>>>(L, del, w->amax);
+      k_fd_point<<<lb, 256, 0, s>>>(L, tb, del, w->amax, eta, w->t);
+      if ((rc = eval(1, &rn, &ed))) return rc;
+      k_fd_rho<<<lb, 256, 0, s>>>(L, r64, w->r, rb, w->amax, eta, rho);
+      w->n_launches += 3;
+      (*it_io)++;
+      // weighted norm of rho
+      dim3 g(kRedBlocks, 1);
+      k_multidot<<<g, 256, 0, s>>>(L, N, rho, 0, w->slot_e, L, w->order, 0, w->part);
+      k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+      CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      w->n_launches += 2;
+      double rr = sqrt(w->host[0]);
+      if (trace_on()) fprintf(stderr, "ppq   inner %2d |r + J d| %.3e (target %.3e)\n", inner, rr, tol * r0);
+      if (!isfinite(rr)) break;
+      if (rr <= tol * r0) { inner++; break; }
+      // stop at the finite-difference noise floor (< 10 % gain over 3 steps)
+      hist.push_back(rr);
+      size_t k = hist.size();
+      if (k >= 4 && hist[k - 1] > 0.9 * hist[k - 4]) { inner++; break; }
+    }
+    k_axpy_to<<<lb, 256, 0, s>>>(L, tb, del, w->t);
+    w->n_launches += 1;
+    CK(cudaGetLastError());
+    *inner_out = inner;
+    return 0;
+  }
+};
+
 extern "C" {
 
 int ppq_default_opts(ppq_opts* o) {
@@ -403,7 +658,7 @@ int ppq_default_opts(ppq_opts* o) {
   o->K = 2; o->K_H = 0; o->precision = 0;
   o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-12;
   o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
-  o->level_shift = 0.0; o->guess = 0; o->profile = 0;
+  o->level_shift = 0.0; o->guess = 0; o->profile = 0; o->polish = 1;
   return 0;
 }
 
@@ -470,13 +725,15 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   if (o.K != 2) return fail(-4, "pq_solve: K must be 2 (PQ)");
   if (o.K_H != 0 && o.K_H != 2) return fail(-4, "pq_solve: only the two-label integral truncation (K_H = 2) is built");
   if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
+  if (o.polish != 0 && o.polish != 1) return fail(-4, "polish must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
   if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
   Workspace* w = nullptr;
   Problem P;
   int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
-  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, m_max, s, &w, &P);
+  int slots = (o.precision == 1 && o.polish == 1) ? kDiisMax : m_max;
+  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, slots, s, &w, &P);
   if (rc) {
     if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
     return rc;
@@ -486,6 +743,8 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   w->profile = o.profile != 0;
   w->t_quartic_ms = 0.0;
   w->n_quartic = 0;
+  w->t_quartic32_ms = 0.0;
+  w->n_quartic32 = 0;
   w->n_launches = 0;
   if (o.guess == 1) {
     if ((rc = copy_amps(w->t, t_in, L, s))) return rc;
@@ -497,56 +756,45 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   k_eref<<<1, 1, 0, s>>>(N, n, P.h, w->f, w->occ, w->scal + kDiisMax + 2);
   CK(cudaMemcpyAsync(w->host + 40, w->scal + kDiisMax + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
 
+  Solver S(w, N, L, o, s);
   int prec = o.precision;
-  int switched_at = prec ? -1 : 0, polish = 0;
-  double e_old = 0.0, res = 0.0, e = 0.0, t_res_ms = 0.0;
+  int switched_at = prec ? -1 : 0;
+  double e_old = 0.0, res = 0.0, e = 0.0;
   bool have_old = false;
   int status = 1, it = 0;
-  std::vector<double> B(kDiisMax * kDiisMax, 0.0);
-  std::vector<int> ring;  // slot ids, oldest first
+  Diis D(m_max);
   std::vector<double> hist;
-  unsigned lb = (unsigned)((L + 255) / 256);
+  bool defect = false;  // FP64 defect-correction polish active
   for (it = 1; it <= o.max_iter; ++it) {
-    CK(cudaEventRecord(w->ev0, s));
-    if ((rc = run_residual(w, N, prec, s))) return rc;
-    CK(cudaEventRecord(w->ev1, s));
-    // Jacobi step into the next DIIS slot
-    int slot;
-    if ((int)ring.size() < m_max) slot = (int)ring.size();
-    else slot = ring.front();
-    double* st = w->slot_t + (size_t)slot * L;
-    double* se = w->slot_e + (size_t)slot * L;
-    ppq::k_jacobi<<<lb, 256, 0, s>>>(L, N, w->t, w->r, w->fo, w->fv, o.level_shift, st, se);
-    w->n_launches += 3;
-    // order of the slots that will be active after this step
-    std::vector<int> act;
-    for (int id : ring) if (id != slot) act.push_back(id);
-    if ((int)act.size() >= m_max) act.erase(act.begin());
-    act.push_back(slot);
-    int m = (int)act.size();
-    memcpy(w->host + 48, act.data(), sizeof(int) * m);
-    CK(cudaMemcpyAsync(w->order, w->host + 48, sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    dim3 g(kRedBlocks, 1 + m);
-    k_multidot<<<g, 256, 0, s>>>(L, N, w->r, m, w->slot_e, L, w->order, slot, w->part);
-    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
-    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, w->ev0, w->ev1);
-    t_res_ms += ms;
-    if (w->profile) {
-      float mq = 0.f;
-      cudaEventElapsedTime(&mq, w->evq0, w->evq1);
-      w->t_quartic_ms += mq;
-      w->n_quartic++;
+    if (defect) {
+      // one outer step: FP64 residual and test, then J delta = -r by FP32
+      // finite-difference Jacobian products (DIIS-accelerated Jacobi)
+      if ((rc = S.eval(0, &res, &e))) return rc;
+      S.polish_evals++;
+      hist.push_back(res);
+      if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
+      if (have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
+      if (S.last_outer > 0.0 && res > 0.1 * S.last_outer) {
+        // the correction stopped paying: continue with plain FP64 iterations
+        defect = false;
+        D.reset();
+        e_old = e;
+        have_old = true;
+        if ((rc = S.step_plain(D, it)) != 0) return rc;
+        continue;
+      }
+      S.last_outer = res;
+      e_old = e;
+      have_old = true;
+      int inner = 0;
+      if ((rc = S.defect_correction(&inner, &it))) return rc;
+      continue;
     }
-    res = sqrt(w->host[0]);
-    e = w->host[m + 1];
-    if (prec == 0 && switched_at >= 0) polish++;
+    if ((rc = S.eval(prec, &res, &e))) return rc;
+    if (prec == 0 && switched_at > 0) S.polish_evals++;
     hist.push_back(res);
     if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
     if (prec == 0 && have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
-    // precision switch: reached switch_tol, or stagnation (< 10 % decrease over 3 iterations)
     if (prec == 1) {
       size_t k = hist.size();
       bool stagnant = k >= 4 && res < 1e-3 && hist[k - 1] > 0.9 * hist[k - 4];
@@ -554,67 +802,14 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
         prec = 0;
         switched_at = it;
         have_old = false;
-        ring.clear();  // restart DIIS with FP64 residuals
-        continue;      // re-evaluate the residual at the same t in FP64
+        D.reset();
+        if (o.polish == 1) defect = true;
+        continue;  // re-evaluate at the same t in FP64
       }
     }
     e_old = e;
     have_old = true;
-    // new row/column of the DIIS matrix, indexed by slot id
-    ring = act;
-    for (int i = 0; i < m; ++i) {
-      double d = w->host[1 + i];
-      B[act[i] * kDiisMax + slot] = d;
-      B[slot * kDiisMax + act[i]] = d;
-    }
-    bool extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
-    if (extrap) {
-      // solve [B -1; -1 0] [c; l] = [0; -1] on the host (m <= 16)
-      int nn = m + 1;
-      std::vector<double> A((size_t)nn * (nn + 1), 0.0);
-      double sc = 0.0;
-      for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(B[act[i] * kDiisMax + act[i]]));
-      if (sc <= 0.0) sc = 1.0;
-      for (int i = 0; i < m; ++i) {
-        for (int j = 0; j < m; ++j) A[i * (nn + 1) + j] = B[act[i] * kDiisMax + act[j]] / sc;
-        A[i * (nn + 1) + m] = -1.0;
-      }
-      for (int j = 0; j < m; ++j) A[m * (nn + 1) + j] = -1.0;
-      A[m * (nn + 1) + nn] = -1.0;
-      bool ok = true;
-      for (int c = 0; c < nn && ok; ++c) {
-        int piv = c;
-        for (int r2 = c + 1; r2 < nn; ++r2)
-          if (fabs(A[r2 * (nn + 1) + c]) > fabs(A[piv * (nn + 1) + c])) piv = r2;
-        if (fabs(A[piv * (nn + 1) + c]) < 1e-300) { ok = false; break; }
-        if (piv != c)
-          for (int k = 0; k <= nn; ++k) std::swap(A[c * (nn + 1) + k], A[piv * (nn + 1) + k]);
-        for (int r2 = c + 1; r2 < nn; ++r2) {
-          double f = A[r2 * (nn + 1) + c] / A[c * (nn + 1) + c];
-          for (int k = c; k <= nn; ++k) A[r2 * (nn + 1) + k] -= f * A[c * (nn + 1) + k];
-        }
-      }
-      std::vector<double> x(nn, 0.0);
-      if (ok) {
-        for (int r2 = nn - 1; r2 >= 0; --r2) {
-          double sum = A[r2 * (nn + 1) + nn];
-          for (int k = r2 + 1; k < nn; ++k) sum -= A[r2 * (nn + 1) + k] * x[k];
-          x[r2] = sum / A[r2 * (nn + 1) + r2];
-        }
-        for (int i = 0; i < m; ++i) w->host[8 + i] = x[i];
-      } else {
-        for (int i = 0; i < m; ++i) w->host[8 + i] = (i == m - 1) ? 1.0 : 0.0;
-      }
-    } else {
-      for (int i = 0; i < m; ++i) w->host[8 + i] = (i == m - 1) ? 1.0 : 0.0;
-    }
-    int one = 1;
-    memcpy(w->host + 32, &one, sizeof(int));
-    CK(cudaMemcpyAsync(w->coef, w->host + 8, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
-    ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, w->t);
-    w->n_launches += 1;
-    CK(cudaGetLastError());
+    if ((rc = S.step_plain(D, it)) != 0) return rc;
   }
   if (it > o.max_iter) it = o.max_iter;
   if (t_out) { if ((rc = copy_amps(t_out, w->t, L, s))) return rc; }
@@ -624,13 +819,13 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   if (e_total) *e_total = e + e_ref + e_const;
   if (info) {
     info->status = status;
-    info->iters = it;
-    info->polish_iters = o.precision ? polish : 0;
+    info->iters = S.evals;
+    info->polish_iters = o.precision ? S.polish_evals : 0;
     info->switched_at = o.precision ? switched_at : -1;
     info->res_norm = res;
     info->e_corr = e;
     info->e_total = e + e_ref + e_const;
-    info->t_residual_ms = t_res_ms;
+    info->t_residual_ms = S.t_res_ms;
     info->t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     info->residual_flops = residual_flops(N);
@@ -638,6 +833,10 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     info->t_quartic_ms = w->t_quartic_ms;
     info->n_quartic = w->n_quartic;
     info->n_launches = w->n_launches + 7;  // + staging kernels
+    info->evals_fp32 = S.evals32;
+    info->t_quartic32_ms = w->t_quartic32_ms;
+    info->n_quartic32 = w->n_quartic32;
+    info->evals_fp64 = S.evals - S.evals32;
   }
   return status;
 }
