@@ -123,6 +123,26 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);
 
+/* Solve n_sys independent PQ problems of (possibly different) sizes in one
+   call: the batched form of the paper's calculations, e.g. a bond-length scan
+   of H50-like chains (Results section).  Per system i: n_pairs[i],
+   occ_of_pair[i] / vir_of_pair[i] (host), h[i], eri[i] (host or device),
+   e_const[i] (nullable array), t_out[i] (nullable array of nullable
+   pointers); e_corr / e_total / info are host arrays of n_sys (nullable).
+   Every system starts from zero amplitudes with the same opts.  The systems
+   run concurrently on a pool of worker threads (PPQ_BATCH_THREADS, default
+   8), each with its own stream and cached workspace; every workspace replays
+   its residual pipeline as a captured CUDA graph, and the quartic GEMM tile
+   is autotuned once per pair count.  The batch starts after the work already
+   queued on `stream` and the call returns when every system is done.
+   Returns < 0 on invalid arguments, else the largest per-system status
+   (0 when all converged); per-system statuses are in info[i].status. */
+int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pair,
+                     const int* const* vir_of_pair, const double* const* h,
+                     const double* const* eri, const double* e_const, const ppq_opts* opts,
+                     double* const* t_out, double* e_corr, double* e_total, ppq_info* info,
+                     void* stream);
+
 /* pq_residual without any device allocation.  The paper has no counterpart:
    this entry point exists for callers that cannot call cudaMalloc.  Examples
    are code running inside another framework's memory pool or under a fixed

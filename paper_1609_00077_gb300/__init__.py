@@ -65,16 +65,18 @@ def lib():
         L.pq_residual_static.argtypes = [I, P, P, P, P, P, P, P, I, P]
         L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
                                ctypes.POINTER(Info), P]
+        L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
-                  L.pq_residual_static, L.pq_solve, L.ppq_release):
+                  L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.ppq_release):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
-            "pq_residual_static", "pq_solve", "ppq_release", "ppq_last_error"]
+            "pq_residual_static", "pq_solve", "pq_solve_batched", "ppq_release",
+            "ppq_last_error"]
 
 
 def _ptr(x):
@@ -179,6 +181,35 @@ def pq_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=Non
                         ctypes.byref(info), _stream(stream))
     _check(rc, "pq_solve")
     return rc, et.value, t_out, info.as_dict()
+
+
+def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):
+    """Solve many Hamiltonians in one call.  systems: list of (occ_of_pair,
+    vir_of_pair, h, eri, e_const) with h / eri torch CUDA tensors or numpy
+    arrays.  Returns (status, e_total array, info list[, amplitude list])."""
+    n = len(systems)
+    occs = [_pairs(o, v)[0] for o, v, *_ in systems]
+    virs = [_pairs(o, v)[1] for o, v, *_ in systems]
+    NP = np.array([len(o) for o in occs], dtype=np.int32)
+    occ_p = (ctypes.c_void_p * n)(*[o.ctypes.data for o in occs])
+    vir_p = (ctypes.c_void_p * n)(*[v.ctypes.data for v in virs])
+    h_p = (ctypes.c_void_p * n)(*[_ptr(s[2]) for s in systems])
+    e_p = (ctypes.c_void_p * n)(*[_ptr(s[3]) for s in systems])
+    ec = np.array([float(s[4]) for s in systems])
+    amps = [np.zeros(amp_count(int(k))) for k in NP] if with_amplitudes else None
+    t_p = (ctypes.c_void_p * n)(*[a.ctypes.data for a in amps]) if with_amplitudes else None
+    e_corr = np.zeros(n); e_total = np.zeros(n)
+    infos = (Info * n)()
+    o = default_opts(**opts)
+    rc = lib().pq_solve_batched(n, NP.ctypes.data, ctypes.cast(occ_p, ctypes.c_void_p),
+                                ctypes.cast(vir_p, ctypes.c_void_p), ctypes.cast(h_p, ctypes.c_void_p),
+                                ctypes.cast(e_p, ctypes.c_void_p), ec.ctypes.data, ctypes.byref(o),
+                                ctypes.cast(t_p, ctypes.c_void_p) if t_p is not None else None,
+                                e_corr.ctypes.data, e_total.ctypes.data,
+                                ctypes.cast(infos, ctypes.c_void_p), _stream(stream))
+    _check(rc, "pq_solve_batched")
+    out = (rc, e_total, [i.as_dict() for i in infos])
+    return out + (amps,) if with_amplitudes else out
 
 
 def release():

@@ -9,7 +9,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <type_traits>
 #include <utility>
 #include <map>
@@ -93,10 +95,16 @@ struct Workspace {
   double t_quartic32_ms = 0.0;  // FP32 launches only
   int n_quartic32 = 0;
   int n_launches = 0;
+  // captured residual pipeline per precision (index 0 FP64, 1 FP32)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int mt[2] = {1, 1};  // tuned GEMM micro-tile per precision for the current N
+  int graph_N[2] = {0, 0};
+  int graph_profile[2] = {0, 0};
 };
 
 std::mutex g_mu;
 std::map<int, Workspace*> g_ws;
+std::map<int, std::vector<Workspace*>> g_batch_ws;  // per-thread workspaces of pq_solve_batched
 
 size_t amp_len(int N) { return (size_t)3 * N + (size_t)PPQ_NA2 * N * N; }
 
@@ -113,6 +121,8 @@ void free_ws(Workspace* w) {
   if (w->ev1) cudaEventDestroy(w->ev1);
   if (w->evq0) cudaEventDestroy(w->evq0);
   if (w->evq1) cudaEventDestroy(w->evq1);
+  for (int i = 0; i < 2; ++i)
+    if (w->graph[i]) cudaGraphExecDestroy(w->graph[i]);
   *w = Workspace();
 }
 
@@ -286,8 +296,7 @@ int launch_t9_mt(Workspace* w, int N, cudaStream_t s) {
 }
 
 template <typename R>
-int launch_t9_gemm(Workspace* w, int N, cudaStream_t s) {
-  int mt = (N + 15) / 16;
+int launch_t9_mt_rt(Workspace* w, int N, int mt, cudaStream_t s) {
   switch (mt) {
     case 1: return launch_t9_mt<R, 1>(w, N, s);
     case 2: return launch_t9_mt<R, 2>(w, N, s);
@@ -299,6 +308,49 @@ int launch_t9_gemm(Workspace* w, int N, cudaStream_t s) {
     case 8: return launch_t9_mt<R, 8>(w, N, s);
     default: return fail(-5, "n_pairs > 128 is not supported by the quartic kernel");
   }
+}
+
+// Tile autotuner: the micro-tile MT of k_t9_gemm (thread grid ceil(N/MT)^2,
+// at most 256 threads) is chosen per (N, precision) by timing every candidate
+// once on the stream, the first time that size is seen on this device.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned_mt;  // key (device * 1024 + N, precision)
+
+template <typename R>
+int tuned_mt(Workspace* w, int N, cudaStream_t s, int* mt_out) {
+  int dev;
+  CK(cudaGetDevice(&dev));
+  int prec = std::is_same<R, float>::value ? 1 : 0;
+  auto key = std::make_pair(dev * 1024 + N, prec);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_mt.find(key);
+    if (it != g_tuned_mt.end()) { *mt_out = it->second; return 0; }
+  }
+  int lo = (N + 15) / 16;
+  if (lo > 8) return fail(-5, "n_pairs > 128 is not supported by the quartic kernel");
+  int best = lo;
+  float best_ms = 1e30f;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (int mt = lo; mt <= std::min(8, lo + 3); ++mt) {
+    int rc = launch_t9_mt_rt<R>(w, N, mt, s);  // warm-up
+    if (rc) return rc;
+    CK(cudaEventRecord(a, s));
+    if ((rc = launch_t9_mt_rt<R>(w, N, mt, s))) return rc;
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) { best_ms = ms; best = mt; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_mt[key] = best;
+  *mt_out = best;
+  return 0;
 }
 
 // one residual evaluation at w->t into w->r; energy pieces into esite/epair
@@ -325,11 +377,9 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl, (R*)w->clT);
   ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
   if (w->profile) CK(cudaEventRecord(w->evq0, s));
-  if ((rc = launch_t9_gemm<R>(w, N, s))) return rc;
+  if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
   if (w->profile) CK(cudaEventRecord(w->evq1, s));
   size_t epi_smem = 2 * sizeof(R) * N * PPQ_NS36;
-  if (epi_smem > 48 * 1024)
-    CK(cudaFuncSetAttribute(ppq::k_t9_epi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
   ppq::k_t9_epi<R><<<NN, 256, epi_smem, s>>>(N, (const R*)w->B9, cl, w->t9);
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
@@ -338,8 +388,39 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   return 0;
 }
 
+// One residual evaluation.  On a non-default stream the pipeline is captured
+// once per (workspace, N, precision) as a CUDA graph and replayed afterwards.
 int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
-  return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+  int rc;
+  int p = precision ? 1 : 0;
+  if (precision) { if ((rc = tuned_mt<float>(w, N, s, &w->mt[1]))) return rc; }
+  else { if ((rc = tuned_mt<double>(w, N, s, &w->mt[0]))) return rc; }
+  size_t epi_smem = 2 * (precision ? sizeof(float) : sizeof(double)) * N * PPQ_NS36;
+  if (epi_smem > 48 * 1024) {
+    if (precision)
+      CK(cudaFuncSetAttribute(ppq::k_t9_epi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
+    else
+      CK(cudaFuncSetAttribute(ppq::k_t9_epi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
+  }
+  if (s == 0) return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+  if (!w->graph[p] || w->graph_N[p] != N || w->graph_profile[p] != (int)w->profile) {
+    if (w->graph[p]) { cudaGraphExecDestroy(w->graph[p]); w->graph[p] = nullptr; }
+    cudaGraph_t g;
+    int nl = w->n_launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(-100, "graph capture failed: %s", cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&w->graph[p], g, 0));
+    cudaGraphDestroy(g);
+    w->graph_N[p] = N;
+    w->graph_profile[p] = (int)w->profile;
+    w->n_launches = nl;
+  }
+  CK(cudaGraphLaunch(w->graph[p], s));
+  w->n_launches += 10;
+  return 0;
 }
 
 // algorithmic FLOPs of one k_t9_gemm launch: for each unordered pair Y < Z and
@@ -361,17 +442,13 @@ double residual_flops(int N) {
   return 2.0 * fma;
 }
 
-// common entry preparation: workspace, pairing, staged inputs
-int prepare(int N, const int* occ, const int* vir, const double* h, const double* eri, int diis,
-            cudaStream_t s, Workspace** pw, Problem* P) {
+// common entry preparation on a given workspace: pairing, staged inputs
+int prepare_ws(Workspace* w, int N, const int* occ, const int* vir, const double* h,
+               const double* eri, int diis, cudaStream_t s, Problem* P) {
   std::vector<int> lab;
   int rc = check_pairing(N, occ, vir, lab);
   if (rc) return rc;
   if (!h || !eri) return fail(-2, "h and eri must be non-null");
-  int dev;
-  CK(cudaGetDevice(&dev));
-  Workspace*& w = g_ws[dev];
-  if (!w) w = new Workspace();
   if ((rc = grow(w, N, diis))) return rc;
   int n = 2 * N;
   CK(cudaMemcpyAsync(w->occ, occ, sizeof(int) * N, cudaMemcpyHostToDevice, s));
@@ -405,8 +482,21 @@ int prepare(int N, const int* occ, const int* vir, const double* h, const double
   CK(cudaStreamSynchronize(s));
   if (bad) return 3;
   if ((rc = stage(w, *P, s))) return rc;
-  *pw = w;
   return 0;
+}
+
+// the same on the per-device cached workspace
+int prepare(int N, const int* occ, const int* vir, const double* h, const double* eri, int diis,
+            cudaStream_t s, Workspace** pw, Problem* P) {
+  std::vector<int> lab;
+  int rc = check_pairing(N, occ, vir, lab);  // argument errors before any device call
+  if (rc) return rc;
+  int dev;
+  CK(cudaGetDevice(&dev));
+  Workspace*& w = g_ws[dev];
+  if (!w) w = new Workspace();
+  *pw = w;
+  return prepare_ws(w, N, occ, vir, h, eri, diis, s, P);
 }
 
 int copy_amps(double* dst, const double* src, size_t L, cudaStream_t s) {
@@ -713,31 +803,32 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
   return 0;
 }
 
-int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
-             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
-             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  g_err.clear();
-  auto wall0 = std::chrono::steady_clock::now();
-  cudaStream_t s = (cudaStream_t)stream;
-  ppq_opts o;
-  if (opts) o = *opts; else ppq_default_opts(&o);
+}  // extern "C"
+
+namespace {
+
+int validate_opts(const ppq_opts& o) {
   if (o.K != 2) return fail(-4, "pq_solve: K must be 2 (PQ)");
   if (o.K_H != 0 && o.K_H != 2) return fail(-4, "pq_solve: only the two-label integral truncation (K_H = 2) is built");
   if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
   if (o.polish != 0 && o.polish != 1) return fail(-4, "polish must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
-  if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
-  Workspace* w = nullptr;
-  Problem P;
+  return 0;
+}
+
+int diis_slots(const ppq_opts& o) {
   int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
-  int slots = (o.precision == 1 && o.polish == 1) ? kDiisMax : m_max;
-  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, slots, s, &w, &P);
-  if (rc) {
-    if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
-    return rc;
-  }
+  return (o.precision == 1 && o.polish == 1) ? kDiisMax : m_max;
+}
+
+// The solve of one system on a prepared workspace and stream.
+int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o,
+               const double* t_in, double* t_out, double* e_corr, double* e_total, ppq_info* info,
+               cudaStream_t s, std::chrono::steady_clock::time_point wall0) {
+  int rc = 0;
+  int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
+  int n_pairs = P.N;
   int N = n_pairs, n = 2 * N;
   size_t L = amp_len(N);
   w->profile = o.profile != 0;
@@ -839,6 +930,106 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     info->evals_fp64 = S.evals - S.evals32;
   }
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
+             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
+  Workspace* w = nullptr;
+  Problem P;
+  rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, diis_slots(o), s, &w, &P);
+  if (rc) {
+    if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
+    return rc;
+  }
+  return solve_core(w, P, e_const, o, t_in, t_out, e_corr, e_total, info, s, wall0);
+}
+
+int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pair,
+                     const int* const* vir_of_pair, const double* const* h,
+                     const double* const* eri, const double* e_const, const ppq_opts* opts,
+                     double* const* t_out, double* e_corr, double* e_total, ppq_info* info,
+                     void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  if (n_sys < 1 || !n_pairs || !occ_of_pair || !vir_of_pair || !h || !eri)
+    return fail(-2, "pq_solve_batched: n_sys >= 1 and non-null per-system arrays required");
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  if (o.guess == 1) return fail(-4, "pq_solve_batched starts from zero amplitudes (guess = 0)");
+  int dev;
+  CK(cudaGetDevice(&dev));
+  const char* env = getenv("PPQ_BATCH_THREADS");
+  int nthreads = env ? atoi(env) : 8;
+  nthreads = std::max(1, std::min(nthreads, n_sys));
+  auto& pool = g_batch_ws[dev];
+  while ((int)pool.size() < nthreads) pool.push_back(new Workspace());
+  // the batch starts after earlier work on the caller's stream and ends before return
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaEvent_t start_ev;
+  CK(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(start_ev, caller));
+  std::atomic<int> next(0);
+  std::vector<int> codes(n_sys, 0);
+  std::vector<std::string> msgs(nthreads);
+  std::vector<int> worst(nthreads, 0);
+  auto worker = [&](int tid) {
+    cudaSetDevice(dev);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      worst[tid] = -100;
+      msgs[tid] = "cudaStreamCreate failed";
+      return;
+    }
+    cudaStreamWaitEvent(s, start_ev, 0);
+    Workspace* w = pool[tid];
+    for (int i = next++; i < n_sys; i = next++) {
+      auto wall0 = std::chrono::steady_clock::now();
+      Problem P;
+      ppq_info tmp;
+      memset(&tmp, 0, sizeof tmp);
+      int r = prepare_ws(w, n_pairs[i], occ_of_pair[i], vir_of_pair[i], h[i], eri[i],
+                         diis_slots(o), s, &P);
+      if (r == 0) {
+        double ec = 0.0, et = 0.0;
+        r = solve_core(w, P, e_const ? e_const[i] : 0.0, o, nullptr, t_out ? t_out[i] : nullptr,
+                       &ec, &et, &tmp, s, wall0);
+        if (e_corr) e_corr[i] = ec;
+        if (e_total) e_total[i] = et;
+      } else {
+        tmp.status = r;
+      }
+      if (info) info[i] = tmp;
+      codes[i] = r;
+      if (r < 0 && worst[tid] == 0) { worst[tid] = r; msgs[tid] = g_err; }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t) th.emplace_back(worker, t);
+  for (auto& t : th) t.join();
+  cudaEventDestroy(start_ev);
+  for (int t = 0; t < nthreads; ++t)
+    if (worst[t] < 0) return fail(worst[t], "%s", msgs[t].c_str());
+  int status = 0;
+  for (int i = 0; i < n_sys; ++i) status = std::max(status, codes[i]);
+  return status;  // 0 when every system converged, else the largest status
 }
 
 }  // extern "C"
