@@ -150,7 +150,7 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->tb, sizeof(double) * L); AL(w->r64, sizeof(double) * L); AL(w->rb, sizeof(double) * L);
   AL(w->del, sizeof(double) * L); AL(w->rho, sizeof(double) * L);
   AL(w->amax, sizeof(unsigned long long));
-  AL(w->B9, sizeof(double) * NN * Nc * PPQ_NQ9); AL(w->t9, sizeof(double) * NN * PPQ_NA2);
+  AL(w->t9, sizeof(double) * NN * PPQ_NA2);
   {
     // quartic GEMM work items: chunks of at most 4 (c1, g) entries of one c2
     std::vector<int> wk;
@@ -288,10 +288,13 @@ template <typename R, int MT>
 int launch_t9_mt(Workspace* w, int N, cudaStream_t s) {
   int T = (N + MT - 1) / MT;           // thread grid T x T, micro-tile MT x MT
   int nth = ((T * T + 31) / 32) * 32;
-  size_t smem = 2 * 16 * (size_t)T * MT * sizeof(R);
+  size_t npd = (size_t)T * MT;
+  size_t smem = (2 * 16 * npd + npd * npd + (size_t)N * PPQ_NS36) * sizeof(R);
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(ppq::k_t9_gemm<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(w->n_work9, N);
-  ppq::k_t9_gemm<R, MT><<<grid, nth, smem, s>>>(N, T, (const R*)w->clT, (const R*)w->gT, w->work9,
-                                                 (R*)w->B9);
+  ppq::k_t9_gemm<R, MT><<<grid, nth, smem, s>>>(N, T, (const R*)w->clT, (const R*)w->gT,
+                                                 (const R*)w->cl, w->work9, w->t9);
   return 0;
 }
 
@@ -376,11 +379,10 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl, (R*)w->clT);
   ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
+  CK(cudaMemsetAsync(w->t9, 0, sizeof(double) * NN * PPQ_NA2, s));
   if (w->profile) CK(cudaEventRecord(w->evq0, s));
   if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
   if (w->profile) CK(cudaEventRecord(w->evq1, s));
-  size_t epi_smem = 2 * sizeof(R) * N * PPQ_NS36;
-  ppq::k_t9_epi<R><<<NN, 256, epi_smem, s>>>(N, (const R*)w->B9, cl, w->t9);
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
   CK(cudaGetLastError());
@@ -395,13 +397,6 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   int p = precision ? 1 : 0;
   if (precision) { if ((rc = tuned_mt<float>(w, N, s, &w->mt[1]))) return rc; }
   else { if ((rc = tuned_mt<double>(w, N, s, &w->mt[0]))) return rc; }
-  size_t epi_smem = 2 * (precision ? sizeof(float) : sizeof(double)) * N * PPQ_NS36;
-  if (epi_smem > 48 * 1024) {
-    if (precision)
-      CK(cudaFuncSetAttribute(ppq::k_t9_epi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
-    else
-      CK(cudaFuncSetAttribute(ppq::k_t9_epi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)epi_smem));
-  }
   if (s == 0) return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
   if (!w->graph[p] || w->graph_N[p] != N || w->graph_profile[p] != (int)w->profile) {
     if (w->graph[p]) { cudaGraphExecDestroy(w->graph[p]); w->graph[p] = nullptr; }
@@ -419,7 +414,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
     w->n_launches = nl;
   }
   CK(cudaGraphLaunch(w->graph[p], s));
-  w->n_launches += 10;
+  w->n_launches += 9;
   return 0;
 }
 
@@ -427,7 +422,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
 // each of the NQ9 (c1, c2, g) combinations, sum over X (N) for every W (N)
 double quartic_flops(int N) {
   double n = N;
-  return 2.0 * (n * (n - 1) / 2) * PPQ_NQ9 * n * n;
+  return 2.0 * (n * (n - 1) / 2) * (PPQ_NQ9 * n * n + PPQ_NC9 * n);  // GEMM + fused W-contraction
 }
 
 double residual_flops(int N) {
@@ -877,6 +872,12 @@ int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o
       S.last_outer = res;
       e_old = e;
       have_old = true;
+      if (res <= o.r_tol) {
+        // only the energy test is left: a Jacobi step changes E by O(|R|^2)
+        D.reset();
+        if ((rc = S.step_plain(D, 1)) != 0) return rc;
+        continue;
+      }
       int inner = 0;
       if ((rc = S.defect_correction(&inner, &it))) return rc;
       continue;
@@ -1108,7 +1109,7 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   w.pg = cv.take<double>(NN * PPQ_NS36); w.pt7 = cv.take<double>(NN * PPQ_NT7E);
   w.pc0 = cv.take<double>(NN * PPQ_NCOL0);
   w.clT = cv.take<double>(NN * PPQ_NS36); w.gT = cv.take<double>(NN * PPQ_NS36);
-  w.B9 = cv.take<double>(NN * N * PPQ_NQ9); w.t9 = cv.take<double>(NN * PPQ_NA2);
+  w.t9 = cv.take<double>(NN * PPQ_NA2);
   w.esite = cv.take<double>(N); w.epair = cv.take<double>(NN);
   w.part = cv.take<double>(kRedBlocks); w.scal = cv.take<double>(4);
   std::vector<int> wk;

@@ -507,12 +507,15 @@ namespace ppq {
 // Thread (tz, tw) of a 16x16 grid owns rows tz + 16 i and columns tw + 16 j.
 template <typename R, int MT>
 __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restrict__ clT,
-    const R* __restrict__ gT, const int* __restrict__ work, R* __restrict__ B) {
+    const R* __restrict__ gT, const R* __restrict__ cl, const int* __restrict__ work,
+    double* __restrict__ t9) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int KC = 16;
   const int NPD = T * MT;                       // padded row length (zeros beyond N)
   R* As = reinterpret_cast<R*>(smem_raw);      // [KC][NPD]
   R* Bs = As + KC * NPD;                        // [KC][NPD]
+  R* Cs = Bs + KC * NPD;                        // [NPD][NPD]  C tile for the epilogue
+  R* cy = Cs + NPD * NPD;                       // [N][36]     Cl[W,Y][c]
   int c2 = work[3 * blockIdx.x], q0 = work[3 * blockIdx.x + 1], q1 = work[3 * blockIdx.x + 2];
   int Y = blockIdx.y;
   int tz = threadIdx.x / T, tw = threadIdx.x % T;
@@ -521,6 +524,10 @@ __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restri
   const R* a_src = clT + (size_t)c2 * NN;      // [X][Z]
   int i0 = (Y + 1) / T;                        // first micro-row that can hold Z > Y
   int nth = blockDim.x;
+  for (int e = threadIdx.x; e < N * PPQ_NS36; e += nth) {
+    int W = e / PPQ_NS36, c = e % PPQ_NS36;
+    cy[e] = cl[((size_t)W * N + Y) * PPQ_NS36 + c];
+  }
   for (int qq = q0; qq < q1; ++qq) {
     int c1 = ppq_q9c[3 * qq], g = ppq_q9c[3 * qq + 1], q = ppq_q9c[3 * qq + 2];
     const R* ys = clT + (size_t)c1 * NN;       // [X][Y]
@@ -564,18 +571,26 @@ __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restri
         }
       }
     }
+    // fused epilogue: C tile to shared memory, then
+    // t9[Y,Z][o] += 1/2 sum_W sum_{ch of q} s C[Z][W] Cl[W,Y][c3] Cl[W,Z][c4]
     if (active) {
-      R* out = B + (((size_t)Y * PPQ_NQ9 + q) * N) * N;
 #pragma unroll
-      for (int i = 0; i < MT; ++i) {
-        int Z = tz + T * i;
-        if (Z <= Y || Z >= N) continue;
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < MT; ++j) {
-          int W = tw + T * j;
-          if (W < N) out[(size_t)Z * N + W] = acc[i][j];
-        }
-      }
+        for (int j = 0; j < MT; ++j) Cs[(tz + T * i) * NPD + tw + T * j] = acc[i][j];
+    }
+    __syncthreads();
+    int ch0 = ppq_c9qp[q], nch = ppq_c9qp[q + 1] - ch0;
+    int nz = N - (Y + 1);
+    for (int e = threadIdx.x; e < nch * nz; e += nth) {
+      int chn = e / nz, Z = Y + 1 + (e - chn * nz);
+      const int16_t* c = ppq_c9q + 4 * (ch0 + chn);
+      int c3 = c[0], c4 = c[1], o = c[2];
+      const R* crow = Cs + Z * NPD;
+      const R* z4 = clT + (size_t)c4 * NN + Z;   // Cl[W,Z][c4] = clT[c4][W][Z]
+      R v = R(0);
+      for (int W = 0; W < N; ++W) v += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
+      atomicAdd(&t9[((size_t)Y * N + Z) * PPQ_NA2 + o], 0.5 * double(c[3]) * double(v));
     }
   }
 }

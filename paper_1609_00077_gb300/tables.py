@@ -615,6 +615,9 @@ def emit_header(path):
             _c_array("ppq_q9cptr", "int16_t", g2ptr),
             _c_array("ppq_q9cptr_h", "int16_t", g2ptr).replace("static __device__ const", "static const")]
     ch9arr = np.array(ch9)
+    # channels grouped by q for the fused GEMM epilogue: (c3, c4, out, s)
+    c9q, c9qp = by_out(ch9arr, 0, len(q9))
+    out += [_c_array("ppq_c9q", "int16_t", c9q[:, 1:]), _c_array("ppq_c9qp", "int16_t", c9qp)]
     ch9, c9p = by_out(ch9arr, 3, 29)
     out.append(_c_array("ppq_c9p", "int16_t", c9p))
     out += [f"#define PPQ_NP9 {len(p9)}", f"#define PPQ_NQ9 {len(q9)}", f"#define PPQ_NC9 {len(ch9)}",
