@@ -143,6 +143,26 @@ int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pai
                      double* const* t_out, double* e_corr, double* e_total, ppq_info* info,
                      void* stream);
 
+/* Gradient of the Lagrangian L(t, lambda) = E_c(t) + sum_mu lambda_mu R_mu(t)
+   with respect to the amplitudes at arbitrary (t, lambda) (both in the
+   amplitude layout, two-pair copies consistent): grad = dE_c/dt + J^T lambda,
+   evaluated by the reverse-mode (adjoint) kernels with the transposed
+   contraction structure of the residual (Theory section: lambda lives on the
+   same truncated manifold as t, Table I).  grad is written in the same layout
+   (both copies of a two-pair entry hold the derivative with respect to the
+   one independent amplitude).  FP64.  e_corr (host, nullable) receives E_c(t). */
+int pq_lagrangian_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                           const double* h, const double* eri, const double* t,
+                           const double* lam, double* grad, double* e_corr, void* stream);
+
+/* Solve the Lambda (left) equations grad_t L(t, lambda) = 0 at converged
+   amplitudes t: Jacobi steps lambda += grad / D with DIIS, FP64, converged
+   when ||grad||_2 <= opts->r_tol (max_iter steps).  lam_out uses the amplitude
+   layout.  Returns 0, 1 (not converged) or 2 (diverged), or < 0 on errors. */
+int pq_lambda(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+              const double* eri, const double* t, const ppq_opts* opts, double* lam_out,
+              ppq_info* info, void* stream);
+
 /* pq_residual without any device allocation.  The paper has no counterpart:
    this entry point exists for callers that cannot call cudaMalloc.  Examples
    are code running inside another framework's memory pool or under a fixed

@@ -126,7 +126,7 @@ class DetCC:
         return len(self.manifold)
 
     def apply_T(self, t, v):
-        out = np.zeros_like(v)
+        out = np.zeros(v.shape, dtype=np.result_type(v, np.asarray(t)))
         for tk, ((sa, da, ga, _), (sb, db, gb, _)) in zip(t, self.ops):
             if tk == 0.0 or len(sa) == 0 or len(sb) == 0:
                 continue
@@ -134,7 +134,7 @@ class DetCC:
         return out
 
     def exp_T(self, t, v):
-        out = v.copy()
+        out = v.astype(np.result_type(v, np.asarray(t)))
         term = v
         for k in range(1, 4 * self.N + 2):
             term = self.apply_T(t, term) / k
@@ -143,21 +143,24 @@ class DetCC:
             out += term
         return out
 
-    def ref_vector(self):
-        v = np.zeros((self.S.n, self.S.n))
+    def ref_vector(self, dtype=float):
+        v = np.zeros((self.S.n, self.S.n), dtype=dtype)
         v[self.iref, self.iref] = 1.0
         return v
 
     def transformed(self, t, h1, v2):
-        """exp(-T) H exp(T) |Phi> as a determinant-space vector (bare H = h1, v2)."""
-        psi = self.exp_T(t, self.ref_vector())
+        """exp(-T) H exp(T) |Phi> as a determinant-space vector (bare H = h1, v2).
+        Complex amplitudes are allowed (complex-step derivatives)."""
+        t = np.asarray(t)
+        psi = self.exp_T(t, self.ref_vector(t.dtype if np.iscomplexobj(t) else float))
         phi = sigma(self.S, h1, v2, psi)
         return self.exp_T(-np.asarray(t), phi)
 
     def residual(self, t, h1, v2):
         """(R over the manifold, <Phi|exp(-T) H exp(T)|Phi>) for the bare H."""
         chi = self.transformed(t, h1, v2)
-        return chi[self.det_alpha, self.det_beta].copy(), float(chi[self.iref, self.iref])
+        e = chi[self.iref, self.iref]
+        return chi[self.det_alpha, self.det_beta].copy(), (e if np.iscomplexobj(chi) else float(e))
 
     def reference_energy(self, h1, v2):
         return self.residual(np.zeros(self.n_amp), h1, v2)[1]

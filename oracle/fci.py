@@ -65,7 +65,7 @@ def sigma(strings, h1, eri, C):
     n = h1.shape[0]
     E = strings.E()
     k = h1 - 0.5 * np.einsum('prrq->pq', eri)
-    D = np.empty((n, n) + C.shape)
+    D = np.empty((n, n) + C.shape, dtype=np.result_type(C, eri))
     for r in range(n):
         for s in range(n):
             D[r, s] = E[r][s] @ C + (E[r][s] @ C.T).T

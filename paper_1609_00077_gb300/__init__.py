@@ -66,17 +66,20 @@ def lib():
         L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
                                ctypes.POINTER(Info), P]
         L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
+        L.pq_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, P, P, P]
+        L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
-                  L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.ppq_release):
+                  L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.pq_lagrangian_gradient,
+                  L.pq_lambda, L.ppq_release):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
-            "pq_residual_static", "pq_solve", "pq_solve_batched", "ppq_release",
-            "ppq_last_error"]
+            "pq_residual_static", "pq_solve", "pq_solve_batched", "pq_lagrangian_gradient",
+            "pq_lambda", "ppq_release", "ppq_last_error"]
 
 
 def _ptr(x):
@@ -210,6 +213,33 @@ def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):
     _check(rc, "pq_solve_batched")
     out = (rc, e_total, [i.as_dict() for i in infos])
     return out + (amps,) if with_amplitudes else out
+
+
+def pq_lagrangian_gradient(occ_of_pair, vir_of_pair, h, eri, t, lam, grad=None, stream=None):
+    """grad_t L(t, lambda) = dE_c/dt + J^T lambda (FP64, adjoint kernels).
+    Returns (grad, e_corr)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    if grad is None:
+        grad = np.zeros(amp_count(len(occ))) if isinstance(t, np.ndarray) else t.new_zeros(amp_count(len(occ)))
+    e = ctypes.c_double()
+    rc = lib().pq_lagrangian_gradient(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
+                                      _ptr(t), _ptr(lam), _ptr(grad),
+                                      ctypes.cast(ctypes.pointer(e), ctypes.c_void_p), _stream(stream))
+    _check(rc, "pq_lagrangian_gradient")
+    return grad, e.value
+
+
+def pq_lambda(occ_of_pair, vir_of_pair, h, eri, t, lam_out=None, stream=None, **opts):
+    """Lambda amplitudes at converged t.  Returns (status, lambda, info)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    if lam_out is None:
+        lam_out = np.zeros(amp_count(len(occ)))
+    o = default_opts(**opts)
+    info = Info()
+    rc = lib().pq_lambda(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t),
+                         ctypes.byref(o), _ptr(lam_out), ctypes.byref(info), _stream(stream))
+    _check(rc, "pq_lambda")
+    return rc, lam_out, info.as_dict()
 
 
 def release():

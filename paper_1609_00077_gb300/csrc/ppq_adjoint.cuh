@@ -1,0 +1,494 @@
+// ppq_adjoint.cuh -- reverse-mode (adjoint) kernels of the PQ residual pipeline.
+//
+// The Lagrangian of the projected equations is L(t, lambda) = E_c(t) +
+// sum_mu lambda_mu R_mu(t) (Theory section: lambda lives on the same truncated
+// manifold as t, Table I).  These kernels evaluate grad_t L = dE_c/dt +
+// J^T lambda by running the residual pipeline backwards with the transposed
+// contraction structure of every topology:
+//   assembly -> (T4, T5, T9 | T2 + T7 through exp(-T_YZ)) -> (T1, T3, T6, T8)
+//   -> closures exp(-I) H exp(I)  (dL/dt_k = tr(Hbar^T [Ht, O_k]))
+//   -> links exp(T_XY)|ref>        (reverse sweep over the 29 factors).
+// Adjoints of shared intermediates are accumulated with atomics (FP64).
+// The same channel tables as the forward kernels are used.
+#pragma once
+#include "ppq_kernels.cuh"
+
+namespace ppq {
+namespace adj {
+
+__device__ __forceinline__ void aadd(double* p, double v) { atomicAdd(p, v); }
+
+// seeds of the assembly: abar = lambda (consistent copies), split to the
+// direct terms (averaged orientations), the quartic term and the transformed pieces
+__global__ void k_assemble(int N, const double* __restrict__ lam2, double* __restrict__ dirb,
+                           double* __restrict__ abufb, double* __restrict__ t9b) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * N * PPQ_NA2) return;
+  int k = i % PPQ_NA2;
+  int YZ = i / PPQ_NA2;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) { dirb[i] = 0.0; abufb[i] = 0.0; t9b[i] = 0.0; return; }
+  if (Y > Z) { t9b[i] = 0.0; return; }
+  int k2 = ppq_a2_swap[k];
+  double sg = double(ppq_a2_swsg[k]);
+  size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + k2;
+  // r2[i] = a, r2[j] = sg a with weights 1/2 each: abar = (lam[i] + sg lam[j]) / 2
+  double ab = 0.5 * (lam2[i] + sg * lam2[j]);
+  dirb[i] = 0.5 * ab;
+  dirb[j] = 0.5 * sg * ab;
+  t9b[i] = ab;
+  abufb[i] = ab;
+  abufb[j] = sg * ab;
+}
+
+// r1 adjoint: T1, T6, T3, T8
+__global__ void k_r1(int N, const double* __restrict__ lam1, const double* __restrict__ hs,
+                     const double* __restrict__ cl, const double* __restrict__ pg,
+                     double* __restrict__ hsb, double* __restrict__ pc0b, double* __restrict__ clb,
+                     double* __restrict__ pgb) {
+  int Y = blockIdx.x;
+  double l[3] = {lam1[Y * 3], lam1[Y * 3 + 1], lam1[Y * 3 + 2]};
+  if (threadIdx.x < 3) aadd(&hsb[(size_t)Y * 256 + ppq_A1[threadIdx.x] * 16], l[threadIdx.x]);
+  for (int X = threadIdx.x; X < N; X += blockDim.x) {
+    if (X == Y) continue;
+    for (int k = 0; k < 3; ++k) aadd(&pc0b[((size_t)Y * N + X) * PPQ_NCOL0 + 29 + k], l[k]);
+    const double* c = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    double* cb = clb + ((size_t)X * N + Y) * PPQ_NS36;
+    const double* h0 = hs + (size_t)X * 256;
+    for (int k = 0; k < 3; ++k)
+      for (int e = ppq_t3p[k]; e < ppq_t3p[k + 1]; ++e) {
+        int ci = ppq_t3[3 * e], a = ppq_t3[3 * e + 1];
+        aadd(&hsb[(size_t)X * 256 + a], l[k] * c[ci]);
+        aadd(&cb[ci], l[k] * h0[a]);
+      }
+  }
+  for (int XW = threadIdx.x; XW < N * N; XW += blockDim.x) {
+    int X = XW / N, W = XW % N;
+    if (X == W || X == Y || W == Y) continue;
+    const double* cx = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    const double* cw = cl + ((size_t)W * N + Y) * PPQ_NS36;
+    const double* g = pg + (size_t)XW * PPQ_NS36;
+    double* cxb = clb + ((size_t)X * N + Y) * PPQ_NS36;
+    double* cwb = clb + ((size_t)W * N + Y) * PPQ_NS36;
+    double* gb = pgb + (size_t)XW * PPQ_NS36;
+    for (int k = 0; k < 3; ++k)
+      for (int e = ppq_t8p[k]; e < ppq_t8p[k + 1]; ++e) {
+        const int16_t* q = ppq_t8 + 5 * e;
+        double f = 0.5 * q[4] * l[k];
+        aadd(&cxb[q[0]], f * cw[q[1]] * g[q[2]]);
+        aadd(&cwb[q[1]], f * cx[q[0]] * g[q[2]]);
+        aadd(&gb[q[2]], f * cx[q[0]] * cw[q[1]]);
+      }
+  }
+}
+
+// r2 adjoint for ordered (Y,Z): T5, T4 (direct) and T2 + T7 through exp(-T_YZ)
+__global__ void __launch_bounds__(128) k_r2(int N, const double* __restrict__ dirb,
+    const double* __restrict__ abufb, const double* __restrict__ t2, const double* __restrict__ hs,
+    const double* __restrict__ cl, const double* __restrict__ pt7, double* __restrict__ hsb,
+    double* __restrict__ clb, double* __restrict__ pt7b, double* __restrict__ pc0b,
+    double* __restrict__ gt2) {
+  __shared__ double Us[PPQ_NA2 + 1][PPQ_NS36];   // U_0 .. U_29
+  __shared__ double Ub[PPQ_NS36];
+  int YZ = blockIdx.x;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) return;
+  const double* clYZ = cl + (size_t)YZ * PPQ_NS36;
+  double* clbYZ = clb + (size_t)YZ * PPQ_NS36;
+  const double* db = dirb + (size_t)YZ * PPQ_NA2;
+  // T5
+  for (int o = threadIdx.x; o < PPQ_NA2; o += blockDim.x) aadd(&pc0b[(size_t)YZ * PPQ_NCOL0 + o], db[o]);
+  // T4
+  for (int X = threadIdx.x; X < N; X += blockDim.x) {
+    if (X == Y || X == Z) continue;
+    const double* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    const double* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
+    const double* h0 = hs + (size_t)X * 256;
+    for (int e = 0; e < PPQ_NT4; ++e) {
+      const int16_t* q = ppq_t4 + 5 * e;
+      double d = db[q[3]] * q[4];
+      if (d == 0.0) continue;
+      aadd(&clb[((size_t)X * N + Y) * PPQ_NS36 + q[0]], d * cz[q[1]] * h0[q[2]]);
+      aadd(&clb[((size_t)X * N + Z) * PPQ_NS36 + q[1]], d * cy[q[0]] * h0[q[2]]);
+      aadd(&hsb[(size_t)X * 256 + q[2]], d * cy[q[0]] * cz[q[1]]);
+    }
+  }
+  // forward U (T2 + T7) and the transform intermediates
+  if (threadIdx.x < PPQ_NS36) {
+    int nu = threadIdx.x;
+    double acc = 0.0;
+    const double* hY = hs + (size_t)Y * 256;
+    for (int e = ppq_t2p[nu]; e < ppq_t2p[nu + 1]; ++e) {
+      const int16_t* q = ppq_t2 + 4 * e;
+      acc += clYZ[q[0]] * hY[q[1] * 16 + q[2]];
+    }
+    for (int W = 0; W < N; ++W) {
+      if (W == Y || W == Z) continue;
+      const double* cw = cl + ((size_t)W * N + Z) * PPQ_NS36;
+      const double* p7 = pt7 + ((size_t)Y * N + W) * PPQ_NT7E;
+      for (int e = ppq_t7p[nu]; e < ppq_t7p[nu + 1]; ++e) {
+        const int16_t* q = ppq_t7 + 5 * e;
+        acc += q[4] * clYZ[q[0]] * cw[q[1]] * p7[q[2]];
+      }
+    }
+    Us[0][nu] = acc;
+  }
+  __syncthreads();
+  const double* t = t2 + (size_t)YZ * PPQ_NA2;
+  for (int k = 0; k < PPQ_NA2; ++k) {
+    if (threadIdx.x < PPQ_NS36) Us[k + 1][threadIdx.x] = Us[k][threadIdx.x];
+    __syncthreads();
+    int e = ppq_sop_ptr[k] + threadIdx.x;
+    if (e < ppq_sop_ptr[k + 1]) {
+      int32_t w = ppq_sop[e];
+      Us[k + 1][unpack_t(w)] -= t[k] * unpack_sign<double>(w) * Us[k][unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  // reverse sweep: Ubar_29 = abufb on the A2 entries
+  if (threadIdx.x < PPQ_NS36) {
+    int nu = threadIdx.x;
+    Ub[nu] = (nu >= 1 && nu <= PPQ_NA2) ? abufb[(size_t)YZ * PPQ_NA2 + nu - 1] : 0.0;
+  }
+  __syncthreads();
+  for (int k = PPQ_NA2 - 1; k >= 0; --k) {
+    // forward step: U_{k+1}[d] = U_k[d] - t_k s U_k[s]
+    // dL/dt_k = -sum_maps Ubar[d] s U_k[s];  Ubar_k[s] = Ubar[s] - t_k s Ubar[d]
+    double part = 0.0;
+    int e = ppq_sop_ptr[k] + threadIdx.x;
+    double upd = 0.0;
+    int src = -1;
+    if (e < ppq_sop_ptr[k + 1]) {
+      int32_t w = ppq_sop[e];
+      double sg = unpack_sign<double>(w);
+      part = -Ub[unpack_t(w)] * sg * Us[k][unpack_s(w)];
+      upd = -t[k] * sg * Ub[unpack_t(w)];
+      src = unpack_s(w);
+    }
+    // warp 0 holds all entries of one factor (at most 32)
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncthreads();
+    if (src >= 0) Ub[src] += upd;
+    if (threadIdx.x == 0) aadd(&gt2[(size_t)YZ * PPQ_NA2 + k], part);
+    __syncthreads();
+  }
+  // T2 and T7 adjoints with Ubar_0
+  if (threadIdx.x < PPQ_NS36) {
+    int nu = threadIdx.x;
+    double u = Ub[nu];
+    if (u != 0.0) {
+      const double* hY = hs + (size_t)Y * 256;
+      for (int e = ppq_t2p[nu]; e < ppq_t2p[nu + 1]; ++e) {
+        const int16_t* q = ppq_t2 + 4 * e;
+        aadd(&clbYZ[q[0]], u * hY[q[1] * 16 + q[2]]);
+        aadd(&hsb[(size_t)Y * 256 + q[1] * 16 + q[2]], u * clYZ[q[0]]);
+      }
+      for (int W = 0; W < N; ++W) {
+        if (W == Y || W == Z) continue;
+        const double* cw = cl + ((size_t)W * N + Z) * PPQ_NS36;
+        const double* p7 = pt7 + ((size_t)Y * N + W) * PPQ_NT7E;
+        double* cwb = clb + ((size_t)W * N + Z) * PPQ_NS36;
+        double* p7b = pt7b + ((size_t)Y * N + W) * PPQ_NT7E;
+        for (int e = ppq_t7p[nu]; e < ppq_t7p[nu + 1]; ++e) {
+          const int16_t* q = ppq_t7 + 5 * e;
+          double f = q[4] * u;
+          aadd(&clbYZ[q[0]], f * cw[q[1]] * p7[q[2]]);
+          aadd(&cwb[q[1]], f * clYZ[q[0]] * p7[q[2]]);
+          aadd(&p7b[q[2]], f * clYZ[q[0]] * cw[q[1]]);
+        }
+      }
+    }
+  }
+}
+
+// quartic term, forward intermediate B[Y][q][Z][W] for Y < Z
+__global__ void k_b9(int N, const double* __restrict__ cl, const double* __restrict__ pg,
+                     double* __restrict__ B) {
+  int YZ = blockIdx.x;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y >= Z) return;
+  for (int e = threadIdx.x; e < PPQ_NQ9 * N; e += blockDim.x) {
+    int q = e / N, W = e % N;
+    int p = ppq_q9[2 * q], g = ppq_q9[2 * q + 1];
+    int c1 = ppq_p9[2 * p], c2 = ppq_p9[2 * p + 1];
+    double s = 0.0;
+    for (int X = 0; X < N; ++X)
+      s += cl[((size_t)X * N + Y) * PPQ_NS36 + c1] * cl[((size_t)X * N + Z) * PPQ_NS36 + c2] *
+           pg[((size_t)X * N + W) * PPQ_NS36 + g];
+    B[(((size_t)Y * PPQ_NQ9 + q) * N + Z) * N + W] = s;
+  }
+}
+
+// quartic term: Bbar and the W-side link adjoints
+__global__ void k_t9_epi(int N, const double* __restrict__ t9b, const double* __restrict__ B,
+                         const double* __restrict__ cl, double* __restrict__ Bb,
+                         double* __restrict__ clb) {
+  int YZ = blockIdx.x;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y >= Z) return;
+  const double* tb = t9b + (size_t)YZ * PPQ_NA2;
+  for (int e = threadIdx.x; e < PPQ_NQ9 * N; e += blockDim.x) {
+    int q = e / N, W = e % N;
+    size_t bi = (((size_t)Y * PPQ_NQ9 + q) * N + Z) * N + W;
+    double b = B[bi], bb = 0.0;
+    const double* cy = cl + ((size_t)W * N + Y) * PPQ_NS36;
+    const double* cz = cl + ((size_t)W * N + Z) * PPQ_NS36;
+    for (int c = ppq_c9qp[q]; c < ppq_c9qp[q + 1]; ++c) {
+      const int16_t* ch = ppq_c9q + 4 * c;
+      double f = 0.5 * ch[3] * tb[ch[2]];
+      if (f == 0.0) continue;
+      bb += f * cy[ch[0]] * cz[ch[1]];
+      aadd(&clb[((size_t)W * N + Y) * PPQ_NS36 + ch[0]], f * b * cz[ch[1]]);
+      aadd(&clb[((size_t)W * N + Z) * PPQ_NS36 + ch[1]], f * b * cy[ch[0]]);
+    }
+    Bb[bi] = bb;
+  }
+}
+
+// quartic term: Gbar[X,W][g] = sum_{Y<Z} sum_{q of g} Bbar Cl[X,Y][c1] Cl[X,Z][c2]
+__global__ void k_t9_gbar(int N, const double* __restrict__ Bb, const double* __restrict__ cl,
+                          double* __restrict__ pgb) {
+  int XW = blockIdx.x * blockDim.x + threadIdx.x;
+  if (XW >= N * N) return;
+  int X = XW / N, W = XW % N;
+  if (X == W) return;
+  double acc[PPQ_NS36];
+  for (int g = 0; g < PPQ_NS36; ++g) acc[g] = 0.0;
+  for (int Y = 0; Y < N; ++Y)
+    for (int Z = Y + 1; Z < N; ++Z) {
+      if (X == Y || X == Z) continue;
+      const double* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
+      const double* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
+      for (int q = 0; q < PPQ_NQ9; ++q) {
+        int p = ppq_q9[2 * q], g = ppq_q9[2 * q + 1];
+        double bb = Bb[(((size_t)Y * PPQ_NQ9 + q) * N + Z) * N + W];
+        acc[g] += bb * cy[ppq_p9[2 * p]] * cz[ppq_p9[2 * p + 1]];
+      }
+    }
+  for (int g = 0; g < PPQ_NS36; ++g) aadd(&pgb[(size_t)XW * PPQ_NS36 + g], acc[g]);
+}
+
+// quartic term: X-side link adjoints, Cl[X,Y][c1] (slot 1) and Cl[X,Z][c2] (slot 2)
+__global__ void k_t9_clbar(int N, const double* __restrict__ Bb, const double* __restrict__ cl,
+                           const double* __restrict__ pg, double* __restrict__ clb) {
+  int XA = blockIdx.x * blockDim.x + threadIdx.x;
+  if (XA >= N * N) return;
+  int X = XA / N, A = XA % N;
+  if (X == A) return;
+  double acc[PPQ_NS36];
+  for (int c = 0; c < PPQ_NS36; ++c) acc[c] = 0.0;
+  // slot 1: A = Y, sum over Z > Y
+  for (int Z = A + 1; Z < N; ++Z) {
+    if (Z == X) continue;
+    const double* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
+    for (int q = 0; q < PPQ_NQ9; ++q) {
+      int p = ppq_q9[2 * q], g = ppq_q9[2 * q + 1];
+      int c1 = ppq_p9[2 * p], c2 = ppq_p9[2 * p + 1];
+      double czv = cz[c2];
+      if (czv == 0.0) continue;
+      const double* bb = Bb + (((size_t)A * PPQ_NQ9 + q) * N + Z) * N;
+      double s = 0.0;
+      for (int W = 0; W < N; ++W) s += bb[W] * pg[((size_t)X * N + W) * PPQ_NS36 + g];
+      acc[c1] += s * czv;
+    }
+  }
+  // slot 2: A = Z, sum over Y < Z
+  for (int Y = 0; Y < A; ++Y) {
+    if (Y == X) continue;
+    const double* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
+    for (int q = 0; q < PPQ_NQ9; ++q) {
+      int p = ppq_q9[2 * q], g = ppq_q9[2 * q + 1];
+      int c1 = ppq_p9[2 * p], c2 = ppq_p9[2 * p + 1];
+      double cyv = cy[c1];
+      if (cyv == 0.0) continue;
+      const double* bb = Bb + (((size_t)Y * PPQ_NQ9 + q) * N + A) * N;
+      double s = 0.0;
+      for (int W = 0; W < N; ++W) s += bb[W] * pg[((size_t)X * N + W) * PPQ_NS36 + g];
+      acc[c2] += s * cyv;
+    }
+  }
+  for (int c = 0; c < PPQ_NS36; ++c) aadd(&clb[(size_t)XA * PPQ_NS36 + c], acc[c]);
+}
+
+// pair closure adjoint: dL/dt_o = tr(Mbar^T [Ht, O_o]) for the 35 operators of
+// I = T_X + T_W + T_XW (Ht recomputed); Mbar holds the adjoints of the entries
+// the topologies read plus 1/2 for the energy element
+__global__ void __launch_bounds__(256) k_pair_closure(int N, const double* __restrict__ g2,
+    const double* __restrict__ t1, const double* __restrict__ t2, const double* __restrict__ pgb,
+    const double* __restrict__ pt7b, const double* __restrict__ pc0b, double* __restrict__ gt) {
+  extern __shared__ unsigned char smem_raw[];
+  double* M = reinterpret_cast<double*>(smem_raw);
+  double* Mb = M + PPQ_BLK;
+  __shared__ double tops[35];
+  __shared__ double tb[35];
+  int XW = blockIdx.x;
+  int X = XW / N, W = XW % N;
+  if (X == W) return;
+  if (threadIdx.x < 35) {
+    int o = threadIdx.x;
+    tops[o] = o < 3 ? t1[X * 3 + o] : (o < 6 ? t1[W * 3 + o - 3] : t2[(size_t)XW * PPQ_NA2 + o - 6]);
+    tb[o] = 0.0;
+  }
+  for (int i = threadIdx.x; i < PPQ_BLK; i += blockDim.x) { M[i] = 0.0; Mb[i] = 0.0; }
+  __syncthreads();
+  const double* g = g2 + (size_t)XW * PPQ_NG2;
+  for (int el = threadIdx.x; el < PPQ_H2_NEL; el += blockDim.x) {
+    double s = 0.0;
+    for (int p = ppq_h2_ptr[el]; p < ppq_h2_ptr[el + 1]; ++p) s += double(ppq_h2_c[p]) * g[ppq_h2_j[p]];
+    M[ppq_h2_el[el]] = s;
+  }
+  __syncthreads();
+  for (int o = 0; o < 35; ++o) {
+    double to = tops[o];
+    if (to != 0.0)
+      for (int e = ppq_p_rptr[o] + threadIdx.x; e < ppq_p_rptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_right[e];
+        M[unpack_t(w)] += to * unpack_sign<double>(w) * M[unpack_s(w)];
+      }
+    __syncthreads();
+  }
+  for (int o = 0; o < 35; ++o) {
+    double to = tops[o];
+    if (to != 0.0)
+      for (int e = ppq_p_lptr[o] + threadIdx.x; e < ppq_p_lptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_left[e];
+        M[unpack_t(w)] -= to * unpack_sign<double>(w) * M[unpack_s(w)];
+      }
+    __syncthreads();
+  }
+  // Mbar: adjoints of the entries read downstream (entries are distinct within each list;
+  // lists may share entries, so accumulate)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < PPQ_NS36; ++i) Mb[ppq_g_el[i]] += pgb[(size_t)XW * PPQ_NS36 + i];
+    for (int i = 0; i < PPQ_NT7E; ++i) Mb[ppq_t7_el[i]] += pt7b[(size_t)XW * PPQ_NT7E + i];
+    for (int i = 0; i < PPQ_NCOL0; ++i) Mb[ppq_col0_el[i]] += pc0b[(size_t)XW * PPQ_NCOL0 + i];
+    Mb[PPQ_EL00] += 0.5;  // E_c = ... + 1/2 sum_{X != W} epair
+  }
+  __syncthreads();
+  // right list (M O)[r, src] = s M[r, dst]; left list (O M)[dst, c] = s M[src, c]
+  for (int o = 0; o < 35; ++o) {
+    double part = 0.0;
+    for (int e = ppq_p_rptr[o] + threadIdx.x; e < ppq_p_rptr[o + 1]; e += blockDim.x) {
+      int32_t w = ppq_p_right[e];
+      part += unpack_sign<double>(w) * Mb[unpack_t(w)] * M[unpack_s(w)];
+    }
+    for (int e = ppq_p_lptr[o] + threadIdx.x; e < ppq_p_lptr[o + 1]; e += blockDim.x) {
+      int32_t w = ppq_p_left[e];
+      part -= unpack_sign<double>(w) * Mb[unpack_t(w)] * M[unpack_s(w)];
+    }
+    for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(&tb[o], part);
+  }
+  __syncthreads();
+  if (threadIdx.x < 35) {
+    int o = threadIdx.x;
+    double* dst = o < 3 ? &gt[X * 3 + o] : (o < 6 ? &gt[W * 3 + o - 3] : &gt[3 * N + (size_t)XW * PPQ_NA2 + o - 6]);
+    aadd(dst, tb[o]);
+  }
+}
+
+// site closure adjoint (16 x 16, 3 operators); hsb includes the energy seed
+__global__ void k_site_closure(int N, const double* __restrict__ g1, const double* __restrict__ t1,
+                               const double* __restrict__ hsb, double* __restrict__ gt) {
+  __shared__ double M[256];
+  __shared__ double Mb[256];
+  __shared__ double tb[3];
+  int X = blockIdx.x;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) { M[i] = 0.0; Mb[i] = hsb[(size_t)X * 256 + i]; }
+  if (threadIdx.x < 3) tb[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) Mb[0] += 1.0;  // E_c = sum_X esite + ...
+  const double* g = g1 + (size_t)X * PPQ_NG1;
+  for (int el = threadIdx.x; el < PPQ_H1_NEL; el += blockDim.x) {
+    double s = 0.0;
+    for (int p = ppq_h1_ptr[el]; p < ppq_h1_ptr[el + 1]; ++p) s += double(ppq_h1_c[p]) * g[ppq_h1_j[p]];
+    M[ppq_h1_el[el]] = s;
+  }
+  __syncthreads();
+  for (int k = 0; k < 3; ++k) {
+    double tk = t1[X * 3 + k];
+    for (int e = ppq_s_rptr[k] + threadIdx.x; e < ppq_s_rptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_right[e];
+      M[unpack_t(w)] += tk * unpack_sign<double>(w) * M[unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < 3; ++k) {
+    double tk = t1[X * 3 + k];
+    for (int e = ppq_s_lptr[k] + threadIdx.x; e < ppq_s_lptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_left[e];
+      M[unpack_t(w)] -= tk * unpack_sign<double>(w) * M[unpack_s(w)];
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < 3; ++k) {
+    double part = 0.0;
+    for (int e = ppq_s_rptr[k] + threadIdx.x; e < ppq_s_rptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_right[e];
+      part += unpack_sign<double>(w) * Mb[unpack_t(w)] * M[unpack_s(w)];
+    }
+    for (int e = ppq_s_lptr[k] + threadIdx.x; e < ppq_s_lptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_left[e];
+      part -= unpack_sign<double>(w) * Mb[unpack_t(w)] * M[unpack_s(w)];
+    }
+    for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(&tb[k], part);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) aadd(&gt[X * 3 + threadIdx.x], tb[threadIdx.x]);
+}
+
+// links adjoint: reverse sweep over exp(T_XY) = prod_k (1 + t_k O_k)
+__global__ void k_links(int N, const double* __restrict__ t2, const double* __restrict__ clb,
+                        double* __restrict__ gt2) {
+  int XY = blockIdx.x * blockDim.x + threadIdx.x;
+  if (XY >= N * N) return;
+  int X = XY / N, Y = XY % N;
+  if (X == Y) return;
+  const double* t = t2 + (size_t)XY * PPQ_NA2;
+  double v[PPQ_NA2 + 1][PPQ_NS36];
+  for (int c = 0; c < PPQ_NS36; ++c) v[0][c] = 0.0;
+  v[0][0] = 1.0;
+  for (int k = 0; k < PPQ_NA2; ++k) {
+    for (int c = 0; c < PPQ_NS36; ++c) v[k + 1][c] = v[k][c];
+    for (int e = ppq_sop_ptr[k]; e < ppq_sop_ptr[k + 1]; ++e) {
+      int32_t w = ppq_sop[e];
+      v[k + 1][unpack_t(w)] += t[k] * unpack_sign<double>(w) * v[k][unpack_s(w)];
+    }
+  }
+  double vb[PPQ_NS36];
+  for (int c = 0; c < PPQ_NS36; ++c) vb[c] = clb[(size_t)XY * PPQ_NS36 + c];
+  for (int k = PPQ_NA2 - 1; k >= 0; --k) {
+    double part = 0.0;
+    for (int e = ppq_sop_ptr[k]; e < ppq_sop_ptr[k + 1]; ++e) {
+      int32_t w = ppq_sop[e];
+      double sg = unpack_sign<double>(w);
+      part += vb[unpack_t(w)] * sg * v[k][unpack_s(w)];
+    }
+    for (int e = ppq_sop_ptr[k]; e < ppq_sop_ptr[k + 1]; ++e) {
+      int32_t w = ppq_sop[e];
+      vb[unpack_s(w)] += t[k] * unpack_sign<double>(w) * vb[unpack_t(w)];
+    }
+    aadd(&gt2[(size_t)XY * PPQ_NA2 + k], part);
+  }
+}
+
+// gradient w.r.t. unique amplitudes, written to both stored copies:
+// gu[P,Q,k] = g[P,Q,k] + sg g[Q,P,k']  (t1 entries unchanged)
+__global__ void k_unique(int N, const double* __restrict__ gt2, double* __restrict__ gu2) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * N * PPQ_NA2) return;
+  int k = i % PPQ_NA2;
+  int YZ = i / PPQ_NA2;
+  int Y = YZ / N, Z = YZ % N;
+  if (Y == Z) { gu2[i] = 0.0; return; }
+  if (Y > Z) return;
+  size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + ppq_a2_swap[k];
+  double sg = double(ppq_a2_swsg[k]);
+  double v = gt2[i] + sg * gt2[j];
+  gu2[i] = v;
+  gu2[j] = sg * v;
+}
+
+}  // namespace adj
+}  // namespace ppq

@@ -21,6 +21,7 @@
 
 #include "../../include/ppq.h"
 #include "ppq_kernels.cuh"
+#include "ppq_adjoint.cuh"
 
 namespace {
 
@@ -95,6 +96,11 @@ struct Workspace {
   double t_quartic32_ms = 0.0;  // FP32 launches only
   int n_quartic32 = 0;
   int n_launches = 0;
+  // adjoint (Lambda / gradient) buffers, allocated on first use
+  int adjN = 0;
+  double *clb = nullptr, *hsb = nullptr, *pgb = nullptr, *pt7b = nullptr, *pc0b = nullptr;
+  double *dirb = nullptr, *abufb = nullptr, *t9b = nullptr, *gt = nullptr, *gu = nullptr;
+  double *B9a = nullptr, *B9b = nullptr, *lam = nullptr;
   // captured residual pipeline per precision (index 0 FP64, 1 FP32)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int mt[2] = {1, 1};  // tuned GEMM micro-tile per precision for the current N
@@ -123,6 +129,10 @@ void free_ws(Workspace* w) {
   if (w->evq1) cudaEventDestroy(w->evq1);
   for (int i = 0; i < 2; ++i)
     if (w->graph[i]) cudaGraphExecDestroy(w->graph[i]);
+  void* pa[] = {w->clb, w->hsb, w->pgb, w->pt7b, w->pc0b, w->dirb, w->abufb, w->t9b, w->gt, w->gu,
+                w->B9a, w->B9b, w->lam};
+  for (void* p : pa)
+    if (p) cudaFree(p);
   *w = Workspace();
 }
 
@@ -501,6 +511,75 @@ int copy_amps(double* dst, const double* src, size_t L, cudaStream_t s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- adjoint driver
+int grow_adjoint(Workspace* w, int N) {
+  if (w->adjN >= N) return 0;
+  void** ps[] = {(void**)&w->clb, (void**)&w->hsb, (void**)&w->pgb, (void**)&w->pt7b, (void**)&w->pc0b,
+                 (void**)&w->dirb, (void**)&w->abufb, (void**)&w->t9b, (void**)&w->gt, (void**)&w->gu,
+                 (void**)&w->B9a, (void**)&w->B9b, (void**)&w->lam};
+  for (void** p : ps)
+    if (*p) { cudaFree(*p); *p = nullptr; }
+  size_t NN = (size_t)N * N, L = amp_len(N);
+  CK(cudaMalloc((void**)&w->clb, sizeof(double) * NN * PPQ_NS36));
+  CK(cudaMalloc((void**)&w->hsb, sizeof(double) * N * 256));
+  CK(cudaMalloc((void**)&w->pgb, sizeof(double) * NN * PPQ_NS36));
+  CK(cudaMalloc((void**)&w->pt7b, sizeof(double) * NN * PPQ_NT7E));
+  CK(cudaMalloc((void**)&w->pc0b, sizeof(double) * NN * PPQ_NCOL0));
+  CK(cudaMalloc((void**)&w->dirb, sizeof(double) * NN * PPQ_NA2));
+  CK(cudaMalloc((void**)&w->abufb, sizeof(double) * NN * PPQ_NA2));
+  CK(cudaMalloc((void**)&w->t9b, sizeof(double) * NN * PPQ_NA2));
+  CK(cudaMalloc((void**)&w->gt, sizeof(double) * L));
+  CK(cudaMalloc((void**)&w->gu, sizeof(double) * L));
+  CK(cudaMalloc((void**)&w->B9a, sizeof(double) * NN * N * PPQ_NQ9));
+  CK(cudaMalloc((void**)&w->B9b, sizeof(double) * NN * N * PPQ_NQ9));
+  CK(cudaMalloc((void**)&w->lam, sizeof(double) * L));
+  w->adjN = N;
+  return 0;
+}
+
+// grad_t L(t, lambda) for t = w->t, lambda = lam (stored layout, consistent
+// copies) into w->gu (gradient w.r.t. unique amplitudes, in both copies);
+// also leaves R(t) in w->r and the energy pieces (FP64 forward pass)
+int lagrangian_gradient(Workspace* w, int N, const double* lam, cudaStream_t s) {
+  int rc = grow_adjoint(w, N);
+  if (rc) return rc;
+  size_t NN = (size_t)N * N, L = amp_len(N);
+  if ((rc = run_residual(w, N, 0, s))) return rc;
+  const double* t1 = w->t;
+  const double* t2 = w->t + 3 * N;
+  CK(cudaMemsetAsync(w->clb, 0, sizeof(double) * NN * PPQ_NS36, s));
+  CK(cudaMemsetAsync(w->hsb, 0, sizeof(double) * N * 256, s));
+  CK(cudaMemsetAsync(w->pgb, 0, sizeof(double) * NN * PPQ_NS36, s));
+  CK(cudaMemsetAsync(w->pt7b, 0, sizeof(double) * NN * PPQ_NT7E, s));
+  CK(cudaMemsetAsync(w->pc0b, 0, sizeof(double) * NN * PPQ_NCOL0, s));
+  CK(cudaMemsetAsync(w->gt, 0, sizeof(double) * L, s));
+  size_t L2 = NN * PPQ_NA2;
+  unsigned b2 = (unsigned)((L2 + 255) / 256);
+  const double* cl = (const double*)w->cl;
+  const double* hs = (const double*)w->hs;
+  const double* pg = (const double*)w->pg;
+  const double* pt7 = (const double*)w->pt7;
+  ppq::adj::k_assemble<<<b2, 256, 0, s>>>(N, lam + 3 * N, w->dirb, w->abufb, w->t9b);
+  ppq::adj::k_r1<<<N, 256, 0, s>>>(N, lam, hs, cl, pg, w->hsb, w->pc0b, w->clb, w->pgb);
+  ppq::adj::k_r2<<<(unsigned)NN, 128, 0, s>>>(N, w->dirb, w->abufb, t2, hs, cl, pt7, w->hsb, w->clb,
+                                              w->pt7b, w->pc0b, w->gt + 3 * N);
+  ppq::adj::k_b9<<<(unsigned)NN, 256, 0, s>>>(N, cl, pg, w->B9a);
+  ppq::adj::k_t9_epi<<<(unsigned)NN, 256, 0, s>>>(N, w->t9b, w->B9a, cl, w->B9b, w->clb);
+  unsigned bn = (unsigned)((NN + 63) / 64);
+  ppq::adj::k_t9_gbar<<<bn, 64, 0, s>>>(N, w->B9b, cl, w->pgb);
+  ppq::adj::k_t9_clbar<<<bn, 64, 0, s>>>(N, w->B9b, cl, pg, w->clb);
+  size_t smem = 2 * sizeof(double) * PPQ_BLK;
+  CK(cudaFuncSetAttribute(ppq::adj::k_pair_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ppq::adj::k_pair_closure<<<(unsigned)NN, 256, smem, s>>>(N, w->g2d, t1, t2, w->pgb, w->pt7b, w->pc0b, w->gt);
+  ppq::adj::k_site_closure<<<N, 64, 0, s>>>(N, w->g1d, t1, w->hsb, w->gt);
+  ppq::adj::k_links<<<bn, 64, 0, s>>>(N, t2, w->clb, w->gt + 3 * N);
+  CK(cudaMemcpyAsync(w->gu, w->gt, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  ppq::adj::k_unique<<<b2, 256, 0, s>>>(N, w->gt + 3 * N, w->gu + 3 * N);
+  CK(cudaGetLastError());
+  w->n_launches += 13;
+  return 0;
+}
+
 // ---------------------------------------------------------------- solver pieces
 __global__ void k_absmax(size_t L, const double* __restrict__ x, unsigned long long* __restrict__ out) {
   double m = 0.0;
@@ -678,6 +757,32 @@ struct Solver {
   }
 
   int step_plain(Diis& d, int it) { return diis_step(d, w->t, w->r, it); }
+
+  // Lambda equations at the converged t in w->t: grad_t L(t, lambda) = 0 by
+  // Jacobi steps lambda += grad / D with DIIS (FP64)
+  int solve_lambda(double tol, int max_iter, double* res_out, int* iters_out) {
+    int rc;
+    CK(cudaMemsetAsync(w->lam, 0, sizeof(double) * L, s));
+    Diis d(o.diis_dim > 0 ? o.diis_dim : 1);
+    double res = 0.0;
+    int it = 1;
+    for (; it <= max_iter; ++it) {
+      if ((rc = lagrangian_gradient(w, N, w->lam, s))) return rc;
+      dim3 g(kRedBlocks, 1);
+      k_multidot<<<g, 256, 0, s>>>(L, N, w->gu, 0, w->slot_e, L, w->order, 0, w->part);
+      k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+      CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      res = sqrt(w->host[0]);
+      if (trace_on()) fprintf(stderr, "ppq lambda %3d |grad_t L| %.3e\n", it, res);
+      if (!isfinite(res) || res > 1e6) { *res_out = res; *iters_out = it; return 2; }
+      if (res <= tol) break;
+      if ((rc = diis_step(d, w->lam, w->gu, it))) return rc;
+    }
+    *res_out = res;
+    *iters_out = it > max_iter ? max_iter : it;
+    return it > max_iter ? 1 : 0;
+  }
 
   // FP64 defect correction: w->r holds R_64(t) on entry.  Solves
   // r + J delta = 0 to a relative accuracy of ~3e-4 with forward-difference
@@ -1032,6 +1137,73 @@ int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pai
   for (int i = 0; i < n_sys; ++i) status = std::max(status, codes[i]);
   return status;  // 0 when every system converged, else the largest status
 }
+
+int pq_lagrangian_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                           const double* h, const double* eri, const double* t, const double* lam,
+                           double* grad, double* e_corr, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!t || !lam || !grad) return fail(-2, "t, lam and grad must be non-null");
+  Workspace* w = nullptr;
+  Problem P;
+  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 0, s, &w, &P);
+  if (rc) return rc;
+  int N = n_pairs;
+  size_t L = amp_len(N);
+  if ((rc = grow_adjoint(w, N))) return rc;
+  if ((rc = copy_amps(w->t, t, L, s))) return rc;
+  if ((rc = copy_amps(w->lam, lam, L, s))) return rc;
+  if ((rc = lagrangian_gradient(w, N, w->lam, s))) return rc;
+  k_rowsum<<<1, 256, 0, s>>>(1, 0, w->part, N, w->esite, w->epair, w->scal);
+  if ((rc = copy_amps(grad, w->gu, L, s))) return rc;
+  CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e_corr) *e_corr = w->host[0];
+  return 0;
+}
+
+int pq_lambda(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+              const double* eri, const double* t, const ppq_opts* opts, double* lam_out,
+              ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!t || !lam_out) return fail(-2, "t and lam_out must be non-null");
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  Workspace* w = nullptr;
+  Problem P;
+  rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, diis_slots(o), s, &w, &P);
+  if (rc) return rc;
+  int N = n_pairs;
+  size_t L = amp_len(N);
+  if ((rc = grow_adjoint(w, N))) return rc;
+  if ((rc = copy_amps(w->t, t, L, s))) return rc;
+  size_t L2 = (size_t)N * N * PPQ_NA2;
+  ppq::k_symmetrize<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->t + 3 * N);
+  o.precision = 0;
+  Solver S(w, N, L, o, s);
+  double res = 0.0;
+  int iters = 0;
+  int status = S.solve_lambda(o.r_tol, o.max_iter, &res, &iters);
+  if (status < 0) return status;
+  if ((rc = copy_amps(lam_out, w->lam, L, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->status = status;
+    info->iters = iters;
+    info->res_norm = res;
+    info->t_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+  }
+  return status;
+}
+
 
 }  // extern "C"
 
