@@ -163,6 +163,21 @@ int pq_lambda(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const
               const double* eri, const double* t, const ppq_opts* opts, double* lam_out,
               ppq_info* info, void* stream);
 
+/* Energy gradients of the PQ model through the Lambda (left) equations:
+   solve the amplitudes (opts as pq_solve, from zero), solve Lambda (FP64),
+   then form dE_total/dh (n_orb^2), dE_total/d(pq|rs) (n_orb^4) and the
+   orbital-rotation gradient dE/dkappa (n_orb^2, antisymmetric) for
+   C -> C exp(kappa) with the pairing kept by index.  The integral gradients
+   are symmetrised: dE = sum G delta for symmetric perturbations delta (all
+   copies of an integral perturbed together).  E_total includes E_ref and
+   e_const, so the gradients include their explicit dependence.  Every
+   output is nullable and may be host or device memory.  Returns the larger
+   of the amplitude and Lambda statuses, or < 0 on errors. */
+int pq_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                const double* eri, double e_const, const ppq_opts* opts, double* t_out,
+                double* lam_out, double* dE_dh, double* dE_deri, double* dE_dkappa,
+                double* e_total, ppq_info* info, void* stream);
+
 /* pq_residual without any device allocation.  The paper has no counterpart:
    this entry point exists for callers that cannot call cudaMalloc.  Examples
    are code running inside another framework's memory pool or under a fixed

@@ -68,10 +68,12 @@ def lib():
         L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
         L.pq_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, P, P, P]
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
+        L.pq_gradient.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P, P, P,
+                                  ctypes.POINTER(Info), P]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
                   L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.pq_lagrangian_gradient,
-                  L.pq_lambda, L.ppq_release):
+                  L.pq_lambda, L.pq_gradient, L.ppq_release):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -79,7 +81,7 @@ def lib():
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
             "pq_residual_static", "pq_solve", "pq_solve_batched", "pq_lagrangian_gradient",
-            "pq_lambda", "ppq_release", "ppq_last_error"]
+            "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error"]
 
 
 def _ptr(x):
@@ -240,6 +242,59 @@ def pq_lambda(occ_of_pair, vir_of_pair, h, eri, t, lam_out=None, stream=None, **
                          ctypes.byref(o), _ptr(lam_out), ctypes.byref(info), _stream(stream))
     _check(rc, "pq_lambda")
     return rc, lam_out, info.as_dict()
+
+
+def pq_gradient(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, want_eri=True,
+                **opts):
+    """Solve PQ, then Lambda, then return (status, e_total, dE/dh, dE/d(pq|rs) or None,
+    dE/dkappa, info).  Outputs are torch CUDA tensors when h is one, else numpy."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    n = 2 * len(occ)
+    if isinstance(h, np.ndarray):
+        dh = np.zeros((n, n)); dk = np.zeros((n, n))
+        dv = np.zeros((n, n, n, n)) if want_eri else None
+    else:
+        dh = h.new_zeros((n, n)); dk = h.new_zeros((n, n))
+        dv = h.new_zeros((n, n, n, n)) if want_eri else None
+    et = ctypes.c_double()
+    info = Info()
+    o = default_opts(**opts)
+    rc = lib().pq_gradient(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
+                           float(e_const), ctypes.byref(o), None, None, _ptr(dh),
+                           _ptr(dv) if dv is not None else None, _ptr(dk),
+                           ctypes.cast(ctypes.pointer(et), ctypes.c_void_p), ctypes.byref(info),
+                           _stream(stream))
+    _check(rc, "pq_gradient")
+    return rc, et.value, dh, dv, dk, info.as_dict()
+
+
+def _autograd_function():
+    import torch
+
+    class PQEnergy(torch.autograd.Function):
+        """E_PQ(h, (pq|rs)) with the adjoint gradient in backward (FP64 CUDA tensors)."""
+
+        @staticmethod
+        def forward(ctx, h, eri, occ_of_pair, vir_of_pair, e_const, opts):
+            rc, e, dh, dv, dk, info = pq_gradient(occ_of_pair, vir_of_pair, h.contiguous(),
+                                                  eri.contiguous(), e_const, **(opts or {}))
+            if rc != 0:
+                raise PPQError(f"pq_gradient status {rc}")
+            ctx.save_for_backward(dh, dv)
+            return h.new_tensor(e)
+
+        @staticmethod
+        def backward(ctx, g):
+            dh, dv = ctx.saved_tensors
+            return g * dh, g * dv, None, None, None, None
+
+    return PQEnergy
+
+
+def pq_energy(h, eri, occ_of_pair, vir_of_pair, e_const=0.0, **opts):
+    """Differentiable PQ total energy (torch.autograd): gradients w.r.t. h and
+    (pq|rs) come from the Lambda equations (pq_gradient)."""
+    return _autograd_function().apply(h, eri, occ_of_pair, vir_of_pair, e_const, opts)
 
 
 def release():

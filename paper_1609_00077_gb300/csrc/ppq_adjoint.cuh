@@ -315,7 +315,8 @@ __global__ void k_t9_clbar(int N, const double* __restrict__ Bb, const double* _
 // the topologies read plus 1/2 for the energy element
 __global__ void __launch_bounds__(256) k_pair_closure(int N, const double* __restrict__ g2,
     const double* __restrict__ t1, const double* __restrict__ t2, const double* __restrict__ pgb,
-    const double* __restrict__ pt7b, const double* __restrict__ pc0b, double* __restrict__ gt) {
+    const double* __restrict__ pt7b, const double* __restrict__ pc0b, double* __restrict__ gt,
+    double* __restrict__ gb2) {
   extern __shared__ unsigned char smem_raw[];
   double* M = reinterpret_cast<double*>(smem_raw);
   double* Mb = M + PPQ_BLK;
@@ -385,11 +386,44 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const double* __res
     double* dst = o < 3 ? &gt[X * 3 + o] : (o < 6 ? &gt[W * 3 + o - 3] : &gt[3 * N + (size_t)XW * PPQ_NA2 + o - 6]);
     aadd(dst, tb[o]);
   }
+  if (!gb2) return;
+  // dL/dH' = A^T Mbar B^T with A = exp(-I), B = exp(I): the same operator lists
+  // with target and source exchanged (transposed operators)
+  for (int o = 0; o < 35; ++o) {
+    double to = tops[o];
+    if (to != 0.0)
+      for (int e = ppq_p_rptr[o] + threadIdx.x; e < ppq_p_rptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_right[e];
+        Mb[unpack_s(w)] += to * unpack_sign<double>(w) * Mb[unpack_t(w)];
+      }
+    __syncthreads();
+  }
+  for (int o = 0; o < 35; ++o) {
+    double to = tops[o];
+    if (to != 0.0)
+      for (int e = ppq_p_lptr[o] + threadIdx.x; e < ppq_p_lptr[o + 1]; e += blockDim.x) {
+        int32_t w = ppq_p_left[e];
+        Mb[unpack_s(w)] -= to * unpack_sign<double>(w) * Mb[unpack_t(w)];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Mb[PPQ_EL00] -= 0.5;  // epair = Ht(0,0) - H'(0,0)
+  __syncthreads();
+  // CSR transpose: dL/dg2[j] = sum over elements of coef * dL/dH'[el]
+  double* gb = gb2 + (size_t)XW * PPQ_NG2;
+  for (int j = threadIdx.x; j < PPQ_NG2; j += blockDim.x) gb[j] = 0.0;
+  __syncthreads();
+  for (int el = threadIdx.x; el < PPQ_H2_NEL; el += blockDim.x) {
+    double m = Mb[ppq_h2_el[el]];
+    if (m == 0.0) continue;
+    for (int p = ppq_h2_ptr[el]; p < ppq_h2_ptr[el + 1]; ++p) atomicAdd(&gb[ppq_h2_j[p]], double(ppq_h2_c[p]) * m);
+  }
 }
 
 // site closure adjoint (16 x 16, 3 operators); hsb includes the energy seed
 __global__ void k_site_closure(int N, const double* __restrict__ g1, const double* __restrict__ t1,
-                               const double* __restrict__ hsb, double* __restrict__ gt) {
+                               const double* __restrict__ hsb, double* __restrict__ gt,
+                               double* __restrict__ gb1) {
   __shared__ double M[256];
   __shared__ double Mb[256];
   __shared__ double tb[3];
@@ -436,6 +470,144 @@ __global__ void k_site_closure(int N, const double* __restrict__ g1, const doubl
   }
   __syncthreads();
   if (threadIdx.x < 3) aadd(&gt[X * 3 + threadIdx.x], tb[threadIdx.x]);
+  if (!gb1) return;
+  for (int k = 0; k < 3; ++k) {
+    double tk = t1[X * 3 + k];
+    for (int e = ppq_s_rptr[k] + threadIdx.x; e < ppq_s_rptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_right[e];
+      Mb[unpack_s(w)] += tk * unpack_sign<double>(w) * Mb[unpack_t(w)];
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < 3; ++k) {
+    double tk = t1[X * 3 + k];
+    for (int e = ppq_s_lptr[k] + threadIdx.x; e < ppq_s_lptr[k + 1]; e += blockDim.x) {
+      int32_t w = ppq_s_left[e];
+      Mb[unpack_s(w)] -= tk * unpack_sign<double>(w) * Mb[unpack_t(w)];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Mb[0] -= 1.0;  // esite = Ht(0,0) - H'(0,0)
+    double* gb = gb1 + (size_t)X * PPQ_NG1;
+    for (int j = 0; j < PPQ_NG1; ++j) gb[j] = 0.0;
+    for (int el = 0; el < PPQ_H1_NEL; ++el) {
+      double m = Mb[ppq_h1_el[el]];
+      for (int p = ppq_h1_ptr[el]; p < ppq_h1_ptr[el + 1]; ++p) gb[ppq_h1_j[p]] += double(ppq_h1_c[p]) * m;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- integral gradients
+// scatter dL/dg (per-site and per-pair gathered integrals) to dL/dh' (n^2) and
+// dL/dv (n^4): the transpose of k_gather
+__global__ void k_scatter_gather(int n, int N, const double* __restrict__ gb1,
+                                 const double* __restrict__ gb2, const int* __restrict__ occ,
+                                 const int* __restrict__ vir, double* __restrict__ dh,
+                                 double* __restrict__ dv) {
+  size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  size_t tot2 = (size_t)N * N * PPQ_NG2;
+  if (tid < tot2) {
+    int j = tid % PPQ_NG2;
+    int XW = tid / PPQ_NG2;
+    int X = XW / N, W = XW % N;
+    if (X == W) return;
+    const int8_t* k = ppq_g2key + 5 * j;
+    int o[4] = {occ[X], vir[X], occ[W], vir[W]};
+    double v = gb2[tid];
+    if (v == 0.0) return;
+    if (k[0] == 0) aadd(&dh[o[k[1]] * n1 + o[k[2]]], v);
+    else aadd(&dv[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]], v);
+    return;
+  }
+  tid -= tot2;
+  if (tid < (size_t)N * PPQ_NG1) {
+    int j = tid % PPQ_NG1, X = tid / PPQ_NG1;
+    const int8_t* k = ppq_g1key + 5 * j;
+    int o[2] = {occ[X], vir[X]};
+    double v = gb1[tid];
+    if (v == 0.0) return;
+    if (k[0] == 0) aadd(&dh[o[k[1]] * n1 + o[k[2]]], v);
+    else aadd(&dv[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]], v);
+  }
+}
+
+// chain rule through h'_pq = h_pq + sum_{k not in {L(p),L(q)}} [2 (pq|ii) - (pi|iq)]
+// (for L(p) != L(q)) and through E_ref = sum_i (h_ii + f_ii):
+// dv[p,q,i,i] += 2 dh'[p,q], dv[p,i,i,q] -= dh'[p,q]; E_ref terms on occupied i, j
+__global__ void k_grad_chain(int n, int N, const double* __restrict__ dhp, const int* __restrict__ occ,
+                             const int* __restrict__ lab, double* __restrict__ dh, double* __restrict__ dv) {
+  int pq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= n * n) return;
+  int p = pq / n, q = pq % n;
+  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  double d = dhp[pq];
+  dh[pq] = d;
+  int lp = lab[p], lq = lab[q];
+  if (lp != lq && d != 0.0) {
+    for (int k = 0; k < N; ++k) {
+      if (k == lp || k == lq) continue;
+      size_t i = occ[k];
+      aadd(&dv[p * n3 + q * n2 + i * n1 + i], 2.0 * d);
+      aadd(&dv[p * n3 + i * n2 + i * n1 + q], -d);
+    }
+  }
+  // E_ref: sum_i 2 h_ii + sum_ij [2 (ii|jj) - (ij|ji)] over occupied i, j
+  if (p < N && q < N) {
+    size_t i = occ[p], j = occ[q];
+    aadd(&dv[i * n3 + i * n2 + j * n1 + j], 2.0);
+    aadd(&dv[i * n3 + j * n2 + j * n1 + i], -1.0);
+    if (p == q) aadd(&dh[i * n1 + i], 2.0);
+  }
+}
+
+// symmetrise: h gradient over (p,q)~(q,p); eri gradient over the 8 index
+// permutations of (pq|rs).  dE = sum G delta for symmetric perturbations.
+__global__ void k_sym_h(int n, const double* __restrict__ g, double* __restrict__ out) {
+  int pq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= n * n) return;
+  int p = pq / n, q = pq % n;
+  out[pq] = 0.5 * (g[pq] + g[q * n + p]);
+}
+
+__global__ void k_sym_v(int n, const double* __restrict__ g, double* __restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  if (i >= n3 * n) return;
+  size_t p = i / n3, q = (i / n2) % n1, r = (i / n1) % n1, s = i % n1;
+  auto at = [&](size_t a, size_t b, size_t c, size_t d) { return g[a * n3 + b * n2 + c * n1 + d]; };
+  out[i] = 0.125 * (at(p, q, r, s) + at(q, p, r, s) + at(p, q, s, r) + at(q, p, s, r) +
+                    at(r, s, p, q) + at(s, r, p, q) + at(r, s, q, p) + at(s, r, q, p));
+}
+
+// orbital-rotation gradient for C -> C exp(kappa), kappa antisymmetric:
+// dE/dkappa_pq = (A_qp - A_pq) + (B_pq - B_qp),
+// A = Gh^T h - h Gh^T,  B_xr = 4 sum_stu (xs|tu) Gv(rs|tu)   (Gh, Gv symmetrised)
+__global__ void k_orbital_grad(int n, const double* __restrict__ h, const double* __restrict__ eri,
+                               const double* __restrict__ gh, const double* __restrict__ gv,
+                               double* __restrict__ AB) {
+  int xr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xr >= n * n) return;
+  int x = xr / n, r = xr % n;
+  size_t n1 = n, n3 = n1 * n * n;
+  double a = 0.0;
+  for (int t = 0; t < n; ++t) a += gh[t * n1 + x] * h[t * n1 + r] - h[x * n1 + t] * gh[r * n1 + t];
+  double b = 0.0;
+  const double* vx = eri + (size_t)x * n3;
+  const double* gr = gv + (size_t)r * n3;
+  for (size_t k = 0; k < n3; ++k) b += vx[k] * gr[k];
+  AB[xr] = a;                 // A_xr
+  AB[(size_t)n * n + xr] = 4.0 * b;  // B_xr
+}
+
+__global__ void k_orbital_final(int n, const double* __restrict__ AB, double* __restrict__ dk) {
+  int pq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= n * n) return;
+  int p = pq / n, q = pq % n;
+  const double* A = AB;
+  const double* B = AB + (size_t)n * n;
+  dk[pq] = (A[q * n + p] - A[p * n + q]) + (B[p * n + q] - B[q * n + p]);
 }
 
 // links adjoint: reverse sweep over exp(T_XY) = prod_k (1 + t_k O_k)

@@ -101,6 +101,9 @@ struct Workspace {
   double *clb = nullptr, *hsb = nullptr, *pgb = nullptr, *pt7b = nullptr, *pc0b = nullptr;
   double *dirb = nullptr, *abufb = nullptr, *t9b = nullptr, *gt = nullptr, *gu = nullptr;
   double *B9a = nullptr, *B9b = nullptr, *lam = nullptr;
+  double *gb1 = nullptr, *gb2 = nullptr;                 // dL/d(gathered integrals)
+  double *gh_raw = nullptr, *gh = nullptr, *gv_raw = nullptr, *gv = nullptr, *dk = nullptr, *ab = nullptr;
+  size_t grad_n = 0;
   // captured residual pipeline per precision (index 0 FP64, 1 FP32)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int mt[2] = {1, 1};  // tuned GEMM micro-tile per precision for the current N
@@ -130,7 +133,8 @@ void free_ws(Workspace* w) {
   for (int i = 0; i < 2; ++i)
     if (w->graph[i]) cudaGraphExecDestroy(w->graph[i]);
   void* pa[] = {w->clb, w->hsb, w->pgb, w->pt7b, w->pc0b, w->dirb, w->abufb, w->t9b, w->gt, w->gu,
-                w->B9a, w->B9b, w->lam};
+                w->B9a, w->B9b, w->lam, w->gb1, w->gb2, w->gh_raw, w->gh, w->gv_raw, w->gv, w->dk,
+                w->ab};
   for (void* p : pa)
     if (p) cudaFree(p);
   *w = Workspace();
@@ -540,7 +544,8 @@ int grow_adjoint(Workspace* w, int N) {
 // grad_t L(t, lambda) for t = w->t, lambda = lam (stored layout, consistent
 // copies) into w->gu (gradient w.r.t. unique amplitudes, in both copies);
 // also leaves R(t) in w->r and the energy pieces (FP64 forward pass)
-int lagrangian_gradient(Workspace* w, int N, const double* lam, cudaStream_t s) {
+int lagrangian_gradient(Workspace* w, int N, const double* lam, cudaStream_t s,
+                        bool integral_adjoints = false) {
   int rc = grow_adjoint(w, N);
   if (rc) return rc;
   size_t NN = (size_t)N * N, L = amp_len(N);
@@ -570,13 +575,54 @@ int lagrangian_gradient(Workspace* w, int N, const double* lam, cudaStream_t s) 
   ppq::adj::k_t9_clbar<<<bn, 64, 0, s>>>(N, w->B9b, cl, pg, w->clb);
   size_t smem = 2 * sizeof(double) * PPQ_BLK;
   CK(cudaFuncSetAttribute(ppq::adj::k_pair_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ppq::adj::k_pair_closure<<<(unsigned)NN, 256, smem, s>>>(N, w->g2d, t1, t2, w->pgb, w->pt7b, w->pc0b, w->gt);
-  ppq::adj::k_site_closure<<<N, 64, 0, s>>>(N, w->g1d, t1, w->hsb, w->gt);
+  ppq::adj::k_pair_closure<<<(unsigned)NN, 256, smem, s>>>(N, w->g2d, t1, t2, w->pgb, w->pt7b, w->pc0b, w->gt,
+                                                            integral_adjoints ? w->gb2 : nullptr);
+  ppq::adj::k_site_closure<<<N, 64, 0, s>>>(N, w->g1d, t1, w->hsb, w->gt, integral_adjoints ? w->gb1 : nullptr);
   ppq::adj::k_links<<<bn, 64, 0, s>>>(N, t2, w->clb, w->gt + 3 * N);
   CK(cudaMemcpyAsync(w->gu, w->gt, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   ppq::adj::k_unique<<<b2, 256, 0, s>>>(N, w->gt + 3 * N, w->gu + 3 * N);
   CK(cudaGetLastError());
   w->n_launches += 13;
+  return 0;
+}
+
+// dE_total/dh, dE_total/d(pq|rs) and dE/dkappa at converged t (w->t) and
+// lambda (w->lam): dL/d(gathered integrals) from the closure adjoints, the
+// transposed gather, the chain rule through h' and E_ref, 8-fold symmetrisation
+int integral_gradients(Workspace* w, const Problem& P, cudaStream_t s) {
+  int N = P.N, n = P.n;
+  size_t n2 = (size_t)n * n, n4 = n2 * n2, NN = (size_t)N * N;
+  if (w->grad_n < (size_t)n) {
+    void** ps[] = {(void**)&w->gb1, (void**)&w->gb2, (void**)&w->gh_raw, (void**)&w->gh,
+                   (void**)&w->gv_raw, (void**)&w->gv, (void**)&w->dk, (void**)&w->ab};
+    for (void** p : ps)
+      if (*p) { cudaFree(*p); *p = nullptr; }
+    CK(cudaMalloc((void**)&w->gb1, sizeof(double) * N * PPQ_NG1));
+    CK(cudaMalloc((void**)&w->gb2, sizeof(double) * NN * PPQ_NG2));
+    CK(cudaMalloc((void**)&w->gh_raw, sizeof(double) * n2));
+    CK(cudaMalloc((void**)&w->gh, sizeof(double) * n2));
+    CK(cudaMalloc((void**)&w->gv_raw, sizeof(double) * n4));
+    CK(cudaMalloc((void**)&w->gv, sizeof(double) * n4));
+    CK(cudaMalloc((void**)&w->dk, sizeof(double) * n2));
+    CK(cudaMalloc((void**)&w->ab, sizeof(double) * 2 * n2));
+    w->grad_n = n;
+  }
+  int rc = lagrangian_gradient(w, N, w->lam, s, true);
+  if (rc) return rc;
+  // dh' into gh (scratch), dv into gv_raw
+  CK(cudaMemsetAsync(w->gh, 0, sizeof(double) * n2, s));
+  CK(cudaMemsetAsync(w->gv_raw, 0, sizeof(double) * n4, s));
+  size_t tot = NN * PPQ_NG2 + (size_t)N * PPQ_NG1;
+  ppq::adj::k_scatter_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, w->gb1, w->gb2, w->occ,
+                                                                            w->vir, w->gh, w->gv_raw);
+  ppq::adj::k_grad_chain<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, N, w->gh, w->occ, w->lab,
+                                                                      w->gh_raw, w->gv_raw);
+  ppq::adj::k_sym_h<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, w->gh_raw, w->gh);
+  ppq::adj::k_sym_v<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n, w->gv_raw, w->gv);
+  ppq::adj::k_orbital_grad<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, P.h, P.eri, w->gh, w->gv, w->ab);
+  ppq::adj::k_orbital_final<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, w->ab, w->dk);
+  CK(cudaGetLastError());
+  w->n_launches += 6;
   return 0;
 }
 
@@ -1202,6 +1248,54 @@ int pq_lambda(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   }
   return status;
+}
+
+int pq_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                const double* eri, double e_const, const ppq_opts* opts, double* t_out,
+                double* lam_out, double* dE_dh, double* dE_deri, double* dE_dkappa,
+                double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  if (o.guess == 1) return fail(-4, "pq_gradient starts from zero amplitudes (guess = 0)");
+  Workspace* w = nullptr;
+  Problem P;
+  rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, diis_slots(o), s, &w, &P);
+  if (rc) return rc;
+  int N = n_pairs, n = 2 * N;
+  size_t L = amp_len(N), n2 = (size_t)n * n;
+  double ec = 0.0, et = 0.0;
+  ppq_info si;
+  int status = solve_core(w, P, e_const, o, nullptr, nullptr, &ec, &et, &si, s, wall0);
+  if (status < 0) return status;
+  if ((rc = grow_adjoint(w, N))) return rc;
+  ppq_opts ol = o;
+  ol.precision = 0;
+  Solver S(w, N, L, ol, s);
+  double lres = 0.0;
+  int liters = 0;
+  int lstat = S.solve_lambda(o.r_tol, o.max_iter, &lres, &liters);
+  if (lstat < 0) return lstat;
+  if ((rc = integral_gradients(w, P, s))) return rc;
+  if (t_out) { if ((rc = copy_amps(t_out, w->t, L, s))) return rc; }
+  if (lam_out) { if ((rc = copy_amps(lam_out, w->lam, L, s))) return rc; }
+  if (dE_dh) CK(cudaMemcpyAsync(dE_dh, w->gh, sizeof(double) * n2, cudaMemcpyDefault, s));
+  if (dE_deri) CK(cudaMemcpyAsync(dE_deri, w->gv, sizeof(double) * n2 * n2, cudaMemcpyDefault, s));
+  if (dE_dkappa) CK(cudaMemcpyAsync(dE_dkappa, w->dk, sizeof(double) * n2, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  if (e_total) *e_total = et;
+  if (info) {
+    *info = si;
+    info->status = std::max(status, lstat);
+    info->t_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+  }
+  return std::max(status, lstat);
 }
 
 

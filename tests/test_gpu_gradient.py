@@ -1,0 +1,105 @@
+"""Energy gradients through the Lambda equations (pq_gradient) against
+facts the paper and mathematics fix:
+
+* 4 electrons in 4 orbitals: PQ is FCI (Abstract), so by Hellmann-Feynman
+  dE/dh is the FCI one-particle density matrix and dE/dkappa vanishes (FCI is
+  invariant to orbital rotations);
+* central finite differences (step 1e-4) of converged oracle energies along
+  random symmetric directions in h and (pq|rs), and along a random orbital
+  rotation, for 6 and 8 orbitals; tolerance 1e-6;
+* the same against GPU energies for 16 orbitals;
+* the torch.autograd function returns the same gradients.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1609_00077_gb300 as ppq
+from workloads import build_ppp, build_hchain
+from oracle.gradient import fci_one_rdm, energy
+
+TIGHT = dict(r_tol=1e-12, e_tol=1e-14, max_iter=600)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def sym_dirs(n, rng):
+    dh = rng.normal(size=(n, n)); dh = dh + dh.T
+    dv = rng.normal(size=(n, n, n, n))
+    dv = (dv + dv.transpose(1, 0, 2, 3)); dv = dv + dv.transpose(0, 1, 3, 2)
+    dv = dv + dv.transpose(2, 3, 0, 1)
+    return dh, dv
+
+
+def rotate(h, eri, U):
+    return U.T @ h @ U, np.einsum('pqrs,pi,qj,rk,sl->ijkl', eri, U, U, U, U, optimize=True)
+
+
+@pytest.mark.parametrize("which", ["butadiene", "H4"])
+def test_fci_hellmann_feynman_at_4e4o(which):
+    H = build_ppp('polyene', 4) if which == "butadiene" else build_hchain(4, 1.6)
+    rc, e, dh, dv, dk, info = ppq.pq_gradient(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri),
+                                              H.e_const, **TIGHT)
+    assert rc == 0
+    g = fci_one_rdm(H.h, H.eri, 2)
+    assert np.abs(dh.cpu().numpy() - g).max() < 1e-8
+    assert np.abs(dk.cpu().numpy()).max() < 1e-8
+
+
+@pytest.mark.parametrize("which", ["C6H8", "H8"])
+def test_integral_and_orbital_gradients_vs_oracle_fd(which):
+    H = build_ppp('polyene', 6) if which == "C6H8" else build_hchain(8, 1.4)
+    n = H.n_orb
+    rc, e, dh, dv, dk, info = ppq.pq_gradient(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri),
+                                              H.e_const, **TIGHT)
+    assert rc == 0
+    dh, dv, dk = dh.cpu().numpy(), dv.cpu().numpy(), dk.cpu().numpy()
+    rng = np.random.default_rng(7)
+    eps = 1e-4
+    ddh, ddv = sym_dirs(n, rng)
+    ddh *= 0.1; ddv *= 0.01
+    E = lambda hh, vv: energy(hh, vv, H.occ_of_pair, H.vir_of_pair, 2, H.e_const)
+    fd = (E(H.h + eps * ddh, H.eri + eps * ddv) - E(H.h - eps * ddh, H.eri - eps * ddv)) / (2 * eps)
+    an = np.sum(dh * ddh) + np.sum(dv * ddv)
+    assert abs(fd - an) < 1e-6, (fd, an)
+    # orbital rotation C -> C exp(eps kappa)
+    K = rng.normal(size=(n, n)); K = K - K.T
+    Ep = E(*rotate(H.h, H.eri, expm(eps * K)))
+    Em = E(*rotate(H.h, H.eri, expm(-eps * K)))
+    fdk = (Ep - Em) / (2 * eps)
+    ank = sum(dk[p, q] * K[p, q] for p in range(n) for q in range(p + 1, n))
+    assert abs(fdk - ank) < 1e-6, (fdk, ank)
+
+
+def test_gradient_vs_gpu_fd_h16_and_autograd():
+    H = build_hchain(16, 1.3)
+    h, eri = dev(H.h), dev(H.eri)
+    rc, e, dh, dv, dk, info = ppq.pq_gradient(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, **TIGHT)
+    assert rc == 0
+    rng = np.random.default_rng(11)
+    ddh, ddv = sym_dirs(H.n_orb, rng)
+    ddh *= 0.1; ddv *= 0.01
+    eps = 1e-4
+
+    def E(hh, vv):
+        r, ee, _, _ = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(hh), dev(vv), H.e_const, **TIGHT)
+        assert r == 0
+        return ee
+    fd = (E(H.h + eps * ddh, H.eri + eps * ddv) - E(H.h - eps * ddh, H.eri - eps * ddv)) / (2 * eps)
+    an = float((dh.cpu() * torch.from_numpy(ddh)).sum() + (dv.cpu() * torch.from_numpy(ddv)).sum())
+    assert abs(fd - an) < 1e-6, (fd, an)
+    # torch.autograd
+    h2 = h.clone().requires_grad_(True); v2 = eri.clone().requires_grad_(True)
+    E2 = ppq.pq_energy(h2, v2, H.occ_of_pair, H.vir_of_pair, H.e_const, **TIGHT)
+    E2.backward()
+    assert abs(float(E2.detach()) - e) < 1e-10
+    assert float((h2.grad - dh).abs().max()) < 1e-10
+    assert float((v2.grad - dv).abs().max()) < 1e-10
