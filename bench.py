@@ -49,7 +49,37 @@ def parse():
     ap.add_argument("--mode", default="solve", choices=["solve", "residual"],
                     help="'residual': only --steps residual evaluations (for ncu captures)")
     ap.add_argument("--precision", type=int, default=1, help="residual mode: 0 FP64, 1 FP32")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time a batched solve of this many H chains (H10-H50, 0.7-3.0 A)")
+    ap.add_argument("--gradient", action="store_true",
+                    help="also time the H50 (1.8 A) energy gradient through the Lambda equations")
     return ap.parse_args()
+
+
+def max_over_ranks(value, dist=None):
+    """Largest value over the ranks of the default process group (the timing
+    rule: the job is as slow as its slowest rank)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_systems(count, seed=1609):
+    """H chains with an even number of atoms uniform over 10..50 and a spacing
+    uniform over 0.7-3.0 A (numpy.random.default_rng(seed)), canonical RHF
+    orbitals with Fig. 1 pairing, built with torch on the device."""
+    from workloads.hchain_torch import build_hchain_torch
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(np.arange(10, 51, 2)))
+        d = float(rng.uniform(0.7, 3.0))
+        out.append(build_hchain_torch(n, d, device="cuda"))
+    return out
 
 
 def peaks():
@@ -246,11 +276,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist: dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist)
     info = infos[-1]
     # FP64-only solve beside it
     fp64 = None
@@ -325,6 +351,39 @@ def main():
                 "d2h_bytes_per_step": int(L * 8 + 16)},
         "clocks": clk.summary(),
     }
+    if args.batch > 0:
+        t0 = time.perf_counter()
+        Hs = batch_systems(args.batch)
+        t_build = time.perf_counter() - t0
+        syst = [(H.occ_of_pair, H.vir_of_pair, H.h, H.eri, H.e_const) for H in Hs]
+        ppq.pq_solve_batched(syst[:min(8, len(syst))], precision=1, max_iter=300)  # warm-up, tuning
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rcb, eb, ib = ppq.pq_solve_batched(syst, precision=1, max_iter=300, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        ok = sum(1 for i in ib if i["status"] == 0)
+        out["batched"] = {"systems": len(syst), "converged": ok,
+                          "not_converged_or_diverged": len(syst) - ok, "seconds": sec,
+                          "solves_per_s": len(syst) / sec, "input_build_s": t_build,
+                          "pairs_range": [int(min(H.n_pairs for H in Hs)), int(max(H.n_pairs for H in Hs))],
+                          "evals_total": int(sum(i["iters"] for i in ib))}
+    if args.gradient:
+        from workloads.hchain_torch import build_hchain_torch
+        H50 = build_hchain_torch(50, 1.8, device="cuda")
+        ppq.pq_gradient(H50.occ_of_pair, H50.vir_of_pair, H50.h, H50.eri, H50.e_const,
+                        r_tol=1e-11, e_tol=1e-13, max_iter=400, want_eri=False)  # warm-up
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        rcg, eg, dhg, dvg, dkg, ig = ppq.pq_gradient(H50.occ_of_pair, H50.vir_of_pair, H50.h, H50.eri,
+                                                     H50.e_const, r_tol=1e-11, e_tol=1e-13,
+                                                     max_iter=400, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        out["gradient_h50"] = {"status": rcg, "seconds": time.perf_counter() - w0,
+                               "e_total": eg, "max_abs_dE_dkappa": float(dkg.abs().max()),
+                               "note": "solve + Lambda + dE/dh, dE/d(pq|rs), dE/dkappa, FP64 adjoint"}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args.sites, args.cpu_seconds, info["iters"])
         out["cpu_baseline"]["cores"] = 1
