@@ -20,9 +20,19 @@ def _boys0(t):
     return out
 
 
-def hchain_ao_integrals(n_atoms, spacing_angstrom):
+def chain_positions(n_atoms, spacing_angstrom, bond_bohr=None):
+    """z coordinates (bohr).  Equidistant chain, or with bond_bohr the
+    asymmetric chain of n/2 H2 units (bond bond_bohr, unit-to-unit gap
+    spacing_angstrom) of the paper's asymmetric H50 dissociation."""
     d = spacing_angstrom * BOHR_PER_ANGSTROM
-    z = np.arange(n_atoms) * d
+    if bond_bohr is None:
+        return np.arange(n_atoms) * d
+    k = np.arange(n_atoms) // 2
+    return k * (bond_bohr + d) + (np.arange(n_atoms) % 2) * bond_bohr
+
+
+def hchain_ao_integrals(n_atoms, spacing_angstrom, bond_bohr=None):
+    z = chain_positions(n_atoms, spacing_angstrom, bond_bohr)
     a = STO3G_EXPONENTS
     c = STO3G_COEFFS * (2.0 * a / np.pi) ** 0.75
     # renormalise the contraction exactly
@@ -58,3 +68,20 @@ def hchain_ao_integrals(n_atoms, spacing_angstrom):
     r = np.abs(z[:, None] - z[None, :])
     e_nuc = sum(1.0 / r[i, j] for i in range(n) for j in range(i + 1, n))
     return S, T + V, eri, e_nuc
+
+
+def hchain_dipole_z(n_atoms, spacing_angstrom, bond_bohr=None):
+    """AO matrix of the z coordinate, <mu| z |nu> (s functions: the product
+    centre times the primitive overlap)."""
+    z = chain_positions(n_atoms, spacing_angstrom, bond_bohr)
+    a = STO3G_EXPONENTS
+    c = STO3G_COEFFS * (2.0 * a / np.pi) ** 0.75
+    pab = a[:, None] + a[None, :]
+    c = c / np.sqrt((c[:, None] * c[None, :] * (np.pi / pab) ** 1.5).sum())
+    A = z[:, None, None, None]; B = z[None, :, None, None]
+    al = a[None, None, :, None]; be = a[None, None, None, :]
+    p = al + be
+    P = (al * A + be * B) / p
+    kab = np.exp(-al * be / p * (A - B) ** 2)
+    cc = c[None, None, :, None] * c[None, None, None, :]
+    return (cc * (np.pi / p) ** 1.5 * kab * P).sum(axis=(2, 3))

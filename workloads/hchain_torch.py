@@ -5,7 +5,7 @@ import math
 
 import numpy as np
 
-from .hchain import BOHR_PER_ANGSTROM, STO3G_EXPONENTS, STO3G_COEFFS
+from .hchain import BOHR_PER_ANGSTROM, STO3G_EXPONENTS, STO3G_COEFFS, chain_positions
 from .scf import Hamiltonian, pair_orbitals
 
 
@@ -15,11 +15,10 @@ def _boys0(t, torch):
     return torch.where(t > 1e-12, big, 1.0 - t / 3.0)
 
 
-def hchain_integrals_torch(n_atoms, spacing_angstrom, device="cuda"):
+def hchain_integrals_torch(n_atoms, spacing_angstrom, device="cuda", bond_bohr=None):
     import torch
     dt = torch.float64
-    d = spacing_angstrom * BOHR_PER_ANGSTROM
-    z = torch.arange(n_atoms, dtype=dt, device=device) * d
+    z = torch.tensor(chain_positions(n_atoms, spacing_angstrom, bond_bohr), dtype=dt, device=device)
     a = torch.tensor(STO3G_EXPONENTS, dtype=dt, device=device)
     c = torch.tensor(STO3G_COEFFS, dtype=dt, device=device) * (2.0 * a / math.pi) ** 0.75
     pab = a[:, None] + a[None, :]
@@ -53,11 +52,12 @@ def hchain_integrals_torch(n_atoms, spacing_angstrom, device="cuda"):
     return S, T + V, eri, e_nuc
 
 
-def build_hchain_torch(n_atoms, spacing_angstrom, device="cuda", max_iter=500, tol=1e-11, with_host=False):
+def build_hchain_torch(n_atoms, spacing_angstrom, device="cuda", max_iter=500, tol=1e-11, with_host=False,
+                       orbitals="canonical", bond_bohr=None):
     """RHF + MO integrals on `device`.  Returns a Hamiltonian whose h / eri are
     torch tensors on the device (numpy copies when with_host)."""
     import torch
-    S, h, eri, e_nuc = hchain_integrals_torch(n_atoms, spacing_angstrom, device)
+    S, h, eri, e_nuc = hchain_integrals_torch(n_atoms, spacing_angstrom, device, bond_bohr)
     n = n_atoms
     nocc = n // 2
     s, U = torch.linalg.eigh(S)
@@ -103,14 +103,22 @@ def build_hchain_torch(n_atoms, spacing_angstrom, device="cuda", max_iter=500, t
     sgn = torch.sign(C[idx, torch.arange(n, device=device)])
     C = C * sgn[None, :]
     e_el = float(0.5 * (Pm * (h + F)).sum())
+    occ, vir = pair_orbitals(nocc)
+    name = f"H{n_atoms} d={spacing_angstrom:.3f}A" + (f" (H2 units, R={bond_bohr} bohr)" if bond_bohr else "")
+    if orbitals == "local":
+        from .localize import localized_pairs_general
+        from .hchain import hchain_dipole_z
+        Cn, occ, vir = localized_pairs_general(C.cpu().numpy(),
+                                               [hchain_dipole_z(n_atoms, spacing_angstrom, bond_bohr)], nocc)
+        C = torch.from_numpy(Cn).to(device)
+        e = torch.diagonal(C.T @ F @ C)
+        name += " (Boys-localised pairs)"
     h_mo = C.T @ h @ C
     eri_mo = torch.einsum('pqrs,pi->iqrs', eri, C)
     eri_mo = torch.einsum('iqrs,qj->ijrs', eri_mo, C)
     eri_mo = torch.einsum('ijrs,rk->ijks', eri_mo, C)
     eri_mo = torch.einsum('ijks,sl->ijkl', eri_mo, C).contiguous()
-    occ, vir = pair_orbitals(nocc)
-    Hm = Hamiltonian(f"H{n_atoms} d={spacing_angstrom:.3f}A", h_mo, eri_mo, e_nuc, occ, vir,
-                     e.cpu().numpy(), e_el + e_nuc)
+    Hm = Hamiltonian(name, h_mo, eri_mo, e_nuc, occ, vir, e.cpu().numpy(), e_el + e_nuc)
     if with_host:
         Hm.h_host = h_mo.cpu().numpy(); Hm.eri_host = eri_mo.cpu().numpy()
     return Hm

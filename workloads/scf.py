@@ -97,7 +97,11 @@ def mo_integrals(C, h_ao, eri_ao=None, gamma_zdo=None):
         D = (C[:, :, None] * C[:, None, :]).reshape(C.shape[0], n * n)
         eri = (D.T @ gamma_zdo @ D).reshape(n, n, n, n)
     else:
-        eri = np.einsum('pqrs,pi,qj,rk,sl->ijkl', eri_ao, C, C, C, C, optimize=True)
+        n = C.shape[1]
+        t = np.tensordot(eri_ao, C, axes=([0], [0]))          # qrs i
+        t = np.tensordot(t, C, axes=([0], [0]))               # rs i j
+        t = np.tensordot(t, C, axes=([0], [0]))               # s i j k
+        eri = np.tensordot(t, C, axes=([0], [0]))             # i j k l
     return h_mo, eri
 
 
@@ -152,16 +156,30 @@ def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True, orbitals="can
     return H
 
 
-def build_hchain(n_atoms, spacing_angstrom):
-    S, h, eri, e_nuc = hchain_ao_integrals(n_atoms, spacing_angstrom)
+def build_hchain(n_atoms, spacing_angstrom, orbitals="canonical", bond_bohr=None):
+    """orbitals: 'canonical' (Fig. 1 energy pairing) or 'local' (Boys-localised
+    occupied and virtual orbitals paired by nearest centroid, the stand-in
+    for the paper's perfect-pairing orbitals of H50)."""
+    S, h, eri, e_nuc = hchain_ao_integrals(n_atoms, spacing_angstrom, bond_bohr)
     nocc = n_atoms // 2
 
     def jk(P):
-        J = np.einsum('mnls,ls->mn', eri, P)
-        K = np.einsum('mlns,ls->mn', eri, P)
+        n = P.shape[0]
+        J = (eri.reshape(n * n, n * n) @ P.ravel()).reshape(n, n)
+        K = (eri.transpose(0, 2, 1, 3).reshape(n * n, n * n) @ P.ravel()).reshape(n, n)
         return J, K
     e, C, e_elec = rhf(S, h, nocc, jk)
     occ, vir = pair_orbitals(nocc)
+    name = f"H{n_atoms} d={spacing_angstrom:.3f}A" + (f" (H2 units, R={bond_bohr} bohr)" if bond_bohr else "")
+    if orbitals == "local":
+        from .localize import localized_pairs_general
+        from .hchain import hchain_dipole_z
+        C, occ, vir = localized_pairs_general(C, [hchain_dipole_z(n_atoms, spacing_angstrom, bond_bohr)], nocc)
+        P = 2.0 * C[:, occ] @ C[:, occ].T
+        J, K = jk(P)
+        e = np.diag(C.T @ (h + J - 0.5 * K) @ C)
+        name += " (Boys-localised pairs)"
+    elif orbitals != "canonical":
+        raise ValueError(orbitals)
     h_mo, eri_mo = mo_integrals(C, h, eri_ao=eri)
-    return Hamiltonian(f"H{n_atoms} d={spacing_angstrom:.3f}A", h_mo, eri_mo,
-                       e_nuc, occ, vir, e, e_elec + e_nuc)
+    return Hamiltonian(name, h_mo, eri_mo, e_nuc, occ, vir, e, e_elec + e_nuc)
