@@ -103,3 +103,46 @@ def test_gradient_vs_gpu_fd_h16_and_autograd():
     assert abs(float(E2.detach()) - e) < 1e-10
     assert float((h2.grad - dh).abs().max()) < 1e-10
     assert float((v2.grad - dv).abs().max()) < 1e-10
+
+
+def test_h50_asymmetric_gradient_vs_central_differences():
+    """The gradient configuration: H50 as 25 H2 units (R = 1.4 bohr, unit gap
+    1.8 A, Boys-localised pairs).  Central differences (step 1e-4) of GPU
+    energies along a random symmetric (h, (pq|rs)) direction and a random
+    orbital rotation agree with pq_gradient to 1e-6."""
+    from workloads.hchain_torch import build_hchain_torch
+    H = build_hchain_torch(50, 1.8, device="cuda", orbitals="local", bond_bohr=1.4)
+    n = H.n_orb
+    rc, e, dh, dv, dk, info = ppq.pq_gradient(H.occ_of_pair, H.vir_of_pair, H.h, H.eri, H.e_const,
+                                              **TIGHT)
+    assert rc == 0
+    g = torch.Generator(device="cuda").manual_seed(1234)
+    ddh = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    ddh = 0.1 * (ddh + ddh.T)
+    ddv = torch.randn((n, n, n, n), generator=g, device="cuda", dtype=torch.float64)
+    ddv = ddv + ddv.permute(1, 0, 2, 3); ddv = ddv + ddv.permute(0, 1, 3, 2)
+    ddv = 0.01 * (ddv + ddv.permute(2, 3, 0, 1))
+    eps = 1e-4
+
+    def E(hh, vv):
+        r, ee, _, _ = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, hh.contiguous(), vv.contiguous(),
+                                   H.e_const, **TIGHT)
+        assert r == 0
+        return ee
+    fd = (E(H.h + eps * ddh, H.eri + eps * ddv) - E(H.h - eps * ddh, H.eri - eps * ddv)) / (2 * eps)
+    an = float((dh * ddh).sum() + (dv * ddv).sum())
+    assert abs(fd - an) < 1e-6, (fd, an)
+    K = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    K = 0.1 * (K - K.T)
+
+    def rotated(sign):
+        U = torch.linalg.matrix_exp(sign * eps * K)
+        hh = U.T @ H.h @ U
+        vv = torch.einsum('pqrs,pi->iqrs', H.eri, U)
+        vv = torch.einsum('iqrs,qj->ijrs', vv, U)
+        vv = torch.einsum('ijrs,rk->ijks', vv, U)
+        return hh, torch.einsum('ijks,sl->ijkl', vv, U)
+    fdk = (E(*rotated(1.0)) - E(*rotated(-1.0))) / (2 * eps)
+    iu = torch.triu_indices(n, n, 1, device="cuda")
+    ank = float((dk[iu[0], iu[1]] * K[iu[0], iu[1]]).sum())
+    assert abs(fdk - ank) < 1e-6, (fdk, ank)

@@ -118,7 +118,9 @@ def test_solve_matches_oracle_energy(name):
 @pytest.mark.parametrize("name", ["C8H10", "H10", "C16H18"])
 def test_mixed_precision_matches_fp64(name):
     H = SYSTEMS[name]()
-    kw = dict(r_tol=1e-10, e_tol=1e-12, max_iter=400)
+    # the stretched H10 (1.9 A) converges slowly: its FP32 phase stagnates early
+    # and the polish may fall back to plain FP64 DIIS
+    kw = dict(r_tol=1e-10, e_tol=1e-12, max_iter=800)
     rc0, e0, _, i0 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const,
                                   precision=0, **kw)
     rc1, e1, _, i1 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const,
