@@ -34,8 +34,8 @@ __global__ void k_assemble(int N, const double* __restrict__ lam2, double* __res
   size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + k2;
   // r2[i] = a, r2[j] = sg a with weights 1/2 each: abar = (lam[i] + sg lam[j]) / 2
   double ab = 0.5 * (lam2[i] + sg * lam2[j]);
-  dirb[i] = 0.5 * ab;
-  dirb[j] = 0.5 * sg * ab;
+  dirb[i] = ab;
+  dirb[j] = 0.0;
   t9b[i] = ab;
   abufb[i] = ab;
   abufb[j] = sg * ab;

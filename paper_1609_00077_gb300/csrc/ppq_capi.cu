@@ -75,6 +75,7 @@ struct Workspace {
   // residual scratch (sized for double, reused as float)
   void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
   void *clT = nullptr, *gT = nullptr, *B9 = nullptr;  // quartic GEMM operands / output
+  void *pt7T = nullptr, *m7 = nullptr;                 // T7 GEMM operand / output
   double* t9 = nullptr;
   double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;
   unsigned long long* amax = nullptr;
@@ -122,7 +123,7 @@ void free_ws(Workspace* w) {
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
                 w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
                 w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
-                w->amax};
+                w->amax, w->pt7T, w->m7};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -165,6 +166,7 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->del, sizeof(double) * L); AL(w->rho, sizeof(double) * L);
   AL(w->amax, sizeof(unsigned long long));
   AL(w->t9, sizeof(double) * NN * PPQ_NA2);
+  AL(w->pt7T, sizeof(double) * NN * PPQ_NT7E); AL(w->m7, sizeof(double) * NN * PPQ_NK7);
   {
     // quartic GEMM work items: chunks of at most 4 (c1, g) entries of one c2
     std::vector<int> wk;
@@ -327,6 +329,30 @@ int launch_t9_mt_rt(Workspace* w, int N, int mt, cudaStream_t s) {
   }
 }
 
+template <typename R, int MT>
+int launch_t7_mt(Workspace* w, int N, cudaStream_t s) {
+  int T = (N + MT - 1) / MT;
+  int nth = ((T * T + 31) / 32) * 32;
+  size_t smem = 2 * 16 * (size_t)T * MT * sizeof(R);
+  ppq::k_t7_gemm<R, MT><<<PPQ_NK7, nth, smem, s>>>(N, T, (const R*)w->pt7T, (const R*)w->clT, (R*)w->m7);
+  return 0;
+}
+
+template <typename R>
+int launch_t7_gemm(Workspace* w, int N, int mt, cudaStream_t s) {
+  switch (mt) {
+    case 1: return launch_t7_mt<R, 1>(w, N, s);
+    case 2: return launch_t7_mt<R, 2>(w, N, s);
+    case 3: return launch_t7_mt<R, 3>(w, N, s);
+    case 4: return launch_t7_mt<R, 4>(w, N, s);
+    case 5: return launch_t7_mt<R, 5>(w, N, s);
+    case 6: return launch_t7_mt<R, 6>(w, N, s);
+    case 7: return launch_t7_mt<R, 7>(w, N, s);
+    case 8: return launch_t7_mt<R, 8>(w, N, s);
+    default: return fail(-5, "n_pairs > 128 is not supported");
+  }
+}
+
 // Tile autotuner: the micro-tile MT of k_t9_gemm (thread grid ceil(N/MT)^2,
 // at most 256 threads) is chosen per (N, precision) by timing every candidate
 // once on the stream, the first time that size is seen on this device.
@@ -386,12 +412,18 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   int NN = N * N;
   ppq::k_links<R><<<(NN + 63) / 64, 64, 0, s>>>(N, t2, cl);
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
-  ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair);
+  ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair,
+                                                               (R*)w->pt7T);
   ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
-  ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, pt7, pg, cl, t2, w->dir, w->abuf);
-  // quartic term: transposed operands, GEMM, W-contraction
   size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl, (R*)w->clT);
+  {
+    // T7 as GEMMs over W
+    int mt = std::max(1, (N + 15) / 16);
+    if ((rc = launch_t7_gemm<R>(w, N, mt, s))) return rc;
+  }
+  ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, (const R*)w->m7, pg, cl, t2, w->dir, w->abuf);
+  // quartic term: transposed operands, GEMM, W-contraction
   ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
   CK(cudaMemsetAsync(w->t9, 0, sizeof(double) * NN * PPQ_NA2, s));
   if (w->profile) CK(cudaEventRecord(w->evq0, s));
@@ -428,7 +460,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
     w->n_launches = nl;
   }
   CK(cudaGraphLaunch(w->graph[p], s));
-  w->n_launches += 9;
+  w->n_launches += 10;
   return 0;
 }
 
@@ -446,7 +478,8 @@ double residual_flops(int N) {
   fma += n * (PPQ_H1_NEL + 2 * 3 * 16 * 3);                                 // site closures (approx)
   fma += pairs * (17792.0 + PPQ_PR_N + PPQ_PL_N);                           // pair closures
   fma += n * ((n - 1) * PPQ_NT3 + (n - 1) * (n - 2) * PPQ_NT8);             // r1
-  fma += pairs * ((n - 2) * PPQ_NT4 + PPQ_NT2 + (n - 2) * PPQ_NT7 + PPQ_NSOP);  // r2
+  fma += pairs / 2 * (n - 2) * PPQ_NT4 + pairs * (PPQ_NT2 + PPQ_NT7 + PPQ_NSOP);  // r2
+  fma += (double)PPQ_NK7 * n * n * n;                                        // T7 GEMMs
   fma += (pairs / 2) * (n * n * PPQ_NQ9 + n * PPQ_NC9);                      // quartic
   return 2.0 * fma;
 }
@@ -1376,6 +1409,7 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   w.pc0 = cv.take<double>(NN * PPQ_NCOL0);
   w.clT = cv.take<double>(NN * PPQ_NS36); w.gT = cv.take<double>(NN * PPQ_NS36);
   w.t9 = cv.take<double>(NN * PPQ_NA2);
+  w.pt7T = cv.take<double>(NN * PPQ_NT7E); w.m7 = cv.take<double>(NN * PPQ_NK7);
   w.esite = cv.take<double>(N); w.epair = cv.take<double>(NN);
   w.part = cv.take<double>(kRedBlocks); w.scal = cv.take<double>(4);
   std::vector<int> wk;

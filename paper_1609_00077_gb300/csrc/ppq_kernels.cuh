@@ -152,7 +152,7 @@ __global__ void k_site_closure(int N, const R* __restrict__ g1, const double* __
 template <typename R>
 __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict__ g2,
     const double* __restrict__ t1, const double* __restrict__ t2, R* __restrict__ pg,
-    R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair) {
+    R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair, R* __restrict__ pt7T) {
   extern __shared__ unsigned char smem_raw[];
   R* M = reinterpret_cast<R*>(smem_raw);
   __shared__ R h00;
@@ -161,7 +161,10 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict
   int X = XW / N, W = XW % N;
   if (X == W) {
     for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = R(0);
-    for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) pt7[(size_t)XW * PPQ_NT7E + i] = R(0);
+    for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) {
+      pt7[(size_t)XW * PPQ_NT7E + i] = R(0);
+      pt7T[(size_t)i * N * N + XW] = R(0);  // diagonal: [W][X] = [X][W]
+    }
     for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = R(0);
     if (threadIdx.x == 0) epair[XW] = 0.0;
     return;
@@ -201,7 +204,11 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict
     __syncthreads();
   }
   for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = M[ppq_g_el[i]];
-  for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) pt7[(size_t)XW * PPQ_NT7E + i] = M[ppq_t7_el[i]];
+  for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) {
+    R v = M[ppq_t7_el[i]];
+    pt7[(size_t)XW * PPQ_NT7E + i] = v;
+    pt7T[(size_t)i * N * N + (size_t)W * N + X] = v;  // stored [e][W][X]
+  }
   for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = M[ppq_col0_el[i]];
   if (threadIdx.x == 0) epair[XW] = double(M[PPQ_EL00]) - double(h00);
 }
@@ -260,7 +267,7 @@ __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
 // exp(-T_YZ) transform (abuf, mirrored later); T9 is k_t9_gemm + k_t9_epi
 template <typename R>
 __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
-    const R* __restrict__ pt7, const R* __restrict__ pg, const R* __restrict__ cl,
+    const R* __restrict__ m7, const R* __restrict__ pg, const R* __restrict__ cl,
     const double* __restrict__ t2, double* __restrict__ dir, double* __restrict__ abuf) {
   __shared__ R U[PPQ_NS36];
   __shared__ R outs[PPQ_NA2];
@@ -277,8 +284,8 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
   constexpr int S4 = 8, S7 = 7;
   __shared__ R part4[PPQ_NA2][S4];
   __shared__ R part7[PPQ_NS36][S7];
-  // T4: thread (o, s) sums X = s, s + S4, ...
-  if (threadIdx.x < PPQ_NA2 * S4) {
+  // T4 (direct term, needed for Y < Z only): thread (o, s) sums X = s, s + S4, ...
+  if (Y < Z && threadIdx.x < PPQ_NA2 * S4) {
     int o = threadIdx.x / S4, sl = threadIdx.x % S4;
     R acc = R(0);
     for (int X = sl; X < N; X += S4) {
@@ -293,26 +300,26 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
     }
     part4[o][sl] = acc;
   }
-  // T7: thread (nu, s) sums W = s, s + S7, ...
+  // T7 from the GEMM products M7[Y,Z][k] = sum_W pt7[Y,W][e] Cl[W,Z][c2]
+  // (W = Y and W = Z contribute zero: Cl[Z,Z] = 0, pt7[Y,Y] = 0)
+  const R* m7y = m7 + (size_t)YZ * PPQ_NK7;
   if (threadIdx.x < PPQ_NS36 * S7) {
     int nu = threadIdx.x / S7, sl = threadIdx.x % S7;
     R acc = R(0);
-    for (int W = sl; W < N; W += S7) {
-      if (W == Y || W == Z) continue;
-      const R* cw = cl + ((size_t)W * N + Z) * PPQ_NS36;
-      const R* p7 = pt7 + ((size_t)Y * N + W) * PPQ_NT7E;
-      for (int e = ppq_t7p[nu]; e < ppq_t7p[nu + 1]; ++e) {
-        const int16_t* q = ppq_t7 + 5 * e;
-        acc += R(q[4]) * clYZ[q[0]] * cw[q[1]] * p7[q[2]];
-      }
+    for (int e = ppq_t7p[nu] + sl; e < ppq_t7p[nu + 1]; e += S7) {
+      const int16_t* q = ppq_t7g + 4 * e;
+      acc += R(q[3]) * clYZ[q[0]] * m7y[q[1]];
     }
     part7[nu][sl] = acc;
   }
   __syncthreads();
   if (threadIdx.x < PPQ_NA2) {
     int o = threadIdx.x;
-    R acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
-    for (int sl = 0; sl < S4; ++sl) acc += part4[o][sl];
+    R acc = R(0);
+    if (Y < Z) {
+      acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
+      for (int sl = 0; sl < S4; ++sl) acc += part4[o][sl];
+    }
     outs[o] = acc;
   }
   if (threadIdx.x >= 64 && threadIdx.x < 64 + PPQ_NS36) {
@@ -359,9 +366,9 @@ __global__ void k_assemble(int N, const double* __restrict__ dir, const double* 
   int k2 = ppq_a2_swap[k];
   double sg = double(ppq_a2_swsg[k]);
   size_t j = ((size_t)Z * N + Y) * PPQ_NA2 + k2;
-  // direct terms evaluated in both orientations are averaged; the quartic
-  // term (Y < Z only) and the two transformed pieces add
-  double a = 0.5 * (dir[i] + sg * dir[j]) + t9[i] + abuf[i] + sg * abuf[j];
+  // direct terms (T4, T5) and the quartic term are evaluated for Y < Z; the
+  // two transformed pieces (in-S site Y or Z) add
+  double a = dir[i] + t9[i] + abuf[i] + sg * abuf[j];
   r2[i] = a;
   r2[j] = sg * a;
 }
@@ -588,8 +595,16 @@ __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restri
       int c3 = c[0], c4 = c[1], o = c[2];
       const R* crow = Cs + Z * NPD;
       const R* z4 = clT + (size_t)c4 * NN + Z;   // Cl[W,Z][c4] = clT[c4][W][Z]
-      R v = R(0);
-      for (int W = 0; W < N; ++W) v += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
+      R v0 = R(0), v1 = R(0), v2 = R(0), v3 = R(0);
+      int W = 0;
+      for (; W + 3 < N; W += 4) {
+        v0 += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
+        v1 += crow[W + 1] * cy[(W + 1) * PPQ_NS36 + c3] * z4[(size_t)(W + 1) * N];
+        v2 += crow[W + 2] * cy[(W + 2) * PPQ_NS36 + c3] * z4[(size_t)(W + 2) * N];
+        v3 += crow[W + 3] * cy[(W + 3) * PPQ_NS36 + c3] * z4[(size_t)(W + 3) * N];
+      }
+      for (; W < N; ++W) v0 += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
+      R v = (v0 + v1) + (v2 + v3);
       atomicAdd(&t9[((size_t)Y * N + Z) * PPQ_NA2 + o], 0.5 * double(c[3]) * double(v));
     }
   }
@@ -649,6 +664,75 @@ __global__ void k_transpose_g(int N, const R* __restrict__ pg, R* __restrict__ g
   int g = i / NN;
   size_t XW = i % NN;
   gT[i] = pg[XW * PPQ_NS36 + g];
+}
+
+}  // namespace ppq
+
+
+namespace ppq {
+
+// T7 GEMMs: M7[Y,Z][k] = sum_W pt7[Y,W][e] * Cl[W,Z][c2] for the distinct
+// (c2, e) = k of the T7 channels, one CTA per k; operands pt7T[e][W][Y] and
+// clT[c2][W][Z]; thread grid T x T, micro-tile MT x MT
+template <typename R, int MT>
+__global__ void __launch_bounds__(256) k_t7_gemm(int N, int T, const R* __restrict__ pt7T,
+                                                 const R* __restrict__ clT, R* __restrict__ m7) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int KC = 16;
+  const int NPD = T * MT;
+  R* As = reinterpret_cast<R*>(smem_raw);      // [KC][NPD]  A^T chunk: As[w][y] = A[y][w]
+  R* Bs = As + KC * NPD;                        // [KC][NPD]  B chunk:   Bs[w][z]
+  int k = blockIdx.x;
+  int c2 = ppq_k7[2 * k], e = ppq_k7[2 * k + 1];
+  size_t NN = (size_t)N * N;
+  const R* A = pt7T + (size_t)e * NN;          // [W][Y]
+  const R* Bm = clT + (size_t)c2 * NN;         // [W][Z]
+  int tz = threadIdx.x / T, tw = threadIdx.x % T;
+  bool active = tz < T;
+  R acc[MT][MT];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < MT; ++j) acc[i][j] = R(0);
+  for (int k0 = 0; k0 < N; k0 += KC) {
+    int kc = min(KC, N - k0);
+    __syncthreads();
+    for (int x = threadIdx.x; x < kc * NPD; x += blockDim.x) {
+      int kk = x / NPD, yz = x - kk * NPD, W = k0 + kk;
+      As[x] = yz < N ? A[(size_t)W * N + yz] : R(0);
+      Bs[x] = yz < N ? Bm[(size_t)W * N + yz] : R(0);
+    }
+    __syncthreads();
+    if (active) {
+      const R* ap = As + tz;
+      const R* bp = Bs + tw;
+      for (int kk = 0; kk < kc; ++kk) {
+        R a[MT], b[MT];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) a[i] = ap[T * i];
+#pragma unroll
+        for (int j = 0; j < MT; ++j) b[j] = bp[T * j];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+          for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        ap += NPD;
+        bp += NPD;
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      int Y = tz + T * i;
+      if (Y >= N) continue;
+#pragma unroll
+      for (int j = 0; j < MT; ++j) {
+        int Z = tw + T * j;
+        if (Z < N) m7[((size_t)Y * N + Z) * PPQ_NK7 + k] = acc[i][j];
+      }
+    }
+  }
 }
 
 }  // namespace ppq

@@ -596,6 +596,13 @@ def emit_header(path):
             f"#define PPQ_NT8 {len(t8)}", _c_array("ppq_t8", "int16_t", t8), _c_array("ppq_t8p", "int16_t", t8p)]
     t7c, t7p = by_out(np.array([(c1, c2, t7e[(int(r), int(c))], nu, s) for c1, c2, r, c, nu, s in t7]), 3, 36)
     out += [f"#define PPQ_NT7 {len(t7c)}", _c_array("ppq_t7", "int16_t", t7c), _c_array("ppq_t7p", "int16_t", t7p)]
+    # GEMM form of T7: M7[k][Y][Z] = sum_W pt7[Y,W][e] Cl[W,Z][c2] for each
+    # distinct (c2, e); channels in the order of ppq_t7 as (c1, k, nu, s)
+    k7 = sorted(set((int(r[1]), int(r[2])) for r in t7c))
+    k7i = {x: i for i, x in enumerate(k7)}
+    t7g = np.array([(int(r[0]), k7i[(int(r[1]), int(r[2]))], int(r[3]), int(r[4])) for r in t7c])
+    out += [f"#define PPQ_NK7 {len(k7)}", _c_array("ppq_k7", "int16_t", np.array(k7)),
+            _c_array("ppq_t7g", "int16_t", t7g)]
     swap = [T.a2_index[(b, a)] for a, b in T.A2]
     swsg = [(-1) ** (_p(a) * _p(b)) for a, b in T.A2]
     out += [_c_array("ppq_a2_swap", "int8_t", swap), _c_array("ppq_a2_swsg", "int8_t", swsg)]
