@@ -139,14 +139,9 @@ def workload(sites):
     return H
 
 
-def device_eri(H, torch):
-    C = torch.from_numpy(H.C).cuda()
-    g = torch.from_numpy(H.gamma_site).cuda()
-    n = C.shape[1]
-    D = (C[:, :, None] * C[:, None, :]).reshape(C.shape[0], n * n)
-    eri = (D.T @ g @ D).reshape(n, n, n, n).contiguous()
-    del D
-    return eri
+def ppp_eri_device(H, torch):
+    from workloads import ppp_eri_device as build
+    return build(H, torch)
 
 
 def cpu_baseline(sites, seconds, iters, seed=0):
@@ -219,7 +214,7 @@ def residual_mode(args):
     import torch
     import paper_1609_00077_gb300 as ppq
     H = workload(args.sites)
-    eri = device_eri(H, torch)
+    eri = ppp_eri_device(H, torch)
     h = torch.from_numpy(H.h).cuda()
     t = torch.zeros(ppq.amp_count(H.n_pairs), dtype=torch.float64, device="cuda")
     ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, t_out=t,
@@ -250,7 +245,7 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     H = workload(args.sites)
-    eri = device_eri(H, torch)
+    eri = ppp_eri_device(H, torch)
     h = torch.from_numpy(H.h).cuda()
     N = H.n_pairs
     L = ppq.amp_count(N)

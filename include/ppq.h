@@ -40,6 +40,7 @@
  */
 #ifndef PPQ_H
 #define PPQ_H
+#include <stdint.h>
 #include <stddef.h>
 #ifdef __cplusplus
 extern "C" {
@@ -203,6 +204,21 @@ int ppq_release(void);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* ppq_last_error(void);
+
+/* Work list of the tensor-core form of the quartic topology (Sec. II, the
+   four-link term of the linked residual) for n_pairs <= 80; host only, no
+   device call.  The paper has no counterpart: it is how this library tiles the
+   term on the GPU.  A chunk is one link pair (c1, c2) with up to four
+   Hamiltonian components g: 12 int16 fields
+     c1, c2, n_g, n_cols (= n_g * 16 ceil(n_pairs / 16)), g[4], q[4]
+   (q = index of the (c1, c2, g) combination, unused slots 0).  A CTA record
+   is 3 ints: row tile (128 unordered pairs Y < Z, in order of Y then Z),
+   first chunk, end chunk.  chunks (room for max_chunks records) and ctas
+   (room for max_ctas records) may be NULL to query the counts; n_chunks and
+   n_ctas receive them.  Returns 0, -2 (too little room) or -5 (n_pairs out of
+   range). */
+int ppq_tc_plan(int n_pairs, int16_t* chunks, int max_chunks, int* ctas, int max_ctas, int* n_chunks,
+                int* n_ctas);
 
 #ifdef __cplusplus
 }

@@ -70,10 +70,11 @@ def lib():
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
         L.pq_gradient.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P, P, P,
                                   ctypes.POINTER(Info), P]
+        L.ppq_tc_plan.argtypes = [I, P, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
                   L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.pq_lagrangian_gradient,
-                  L.pq_lambda, L.pq_gradient, L.ppq_release):
+                  L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -81,7 +82,7 @@ def lib():
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
             "pq_residual_static", "pq_solve", "pq_solve_batched", "pq_lagrangian_gradient",
-            "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error"]
+            "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error", "ppq_tc_plan"]
 
 
 def _ptr(x):
@@ -123,6 +124,19 @@ def amp_layout():
     d = np.zeros(96, dtype=np.int32)
     _check(lib().ppq_amp_layout(2, d.ctypes.data), "ppq_amp_layout")
     return d.reshape(32, 3)
+
+
+def tc_plan(n_pairs):
+    """Work list of the tensor-core quartic kernel (host only): chunks as an
+    (n, 12) int16 array (c1, c2, n_g, n_cols, g[4], q[4]) and CTAs as an (m, 3)
+    int32 array (row tile, first chunk, end chunk)."""
+    nc, nt = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ppq_tc_plan(n_pairs, None, 0, None, 0, ctypes.byref(nc), ctypes.byref(nt)), "ppq_tc_plan")
+    ch = np.zeros((nc.value, 12), dtype=np.int16)
+    ct = np.zeros((nt.value, 3), dtype=np.int32)
+    _check(lib().ppq_tc_plan(n_pairs, ch.ctypes.data, nc.value, ct.ctypes.data, nt.value,
+                             ctypes.byref(nc), ctypes.byref(nt)), "ppq_tc_plan")
+    return ch, ct
 
 
 def default_opts(**kw):

@@ -22,6 +22,7 @@
 #include "../../include/ppq.h"
 #include "ppq_kernels.cuh"
 #include "ppq_adjoint.cuh"
+#include "ppq_tc.cuh"
 
 namespace {
 
@@ -76,6 +77,17 @@ struct Workspace {
   void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
   void *clT = nullptr, *gT = nullptr, *B9 = nullptr;  // quartic GEMM operands / output
   void *pt7T = nullptr, *m7 = nullptr;                 // T7 GEMM operand / output
+  // tensor-core quartic kernel (FP32 residual): split B operands, work list
+  bool tc_allowed = false;  // set for workspaces that own their buffers
+  int tc_N = 0, tc_Npad = 0, tc_Kc = 0, tc_nctas = 0;
+  size_t tc_smem = 0;
+  float* bpre = nullptr;
+  int16_t* tc_chunk = nullptr;
+  int* tc_cta = nullptr;
+  int* tc_err = nullptr;
+  int tc_nslot = 0;
+  float* tc_part = nullptr;   // per-CTA row sums, [slot][p][29]
+  double* t9part = nullptr;   // per-work-item row sums of the SIMT kernel, [item][p][29]
   double* t9 = nullptr;
   double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;
   unsigned long long* amax = nullptr;
@@ -118,12 +130,19 @@ std::map<int, std::vector<Workspace*>> g_batch_ws;  // per-thread workspaces of 
 
 size_t amp_len(int N) { return (size_t)3 * N + (size_t)PPQ_NA2 * N * N; }
 
+// slice stride of the transposed link coefficients clT[c][X][Y]
+inline int cl_ld(int N) { return (N * N + 3) & ~3; }
+
+constexpr int kTcMaxN = 80;      // largest N of the tensor-core quartic kernel
+constexpr int kTcMaxCtas = 1024;
+constexpr int kTcPartRows = 152 * 128;  // slots x unordered pairs of the partial buffer
+
 void free_ws(Workspace* w) {
   void* ps[] = {w->h, w->eri, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
                 w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
                 w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
-                w->amax, w->pt7T, w->m7};
+                w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -161,12 +180,24 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->cl, sizeof(double) * NN * PPQ_NS36); AL(w->hs, sizeof(double) * Nc * 256);
   AL(w->pg, sizeof(double) * NN * PPQ_NS36); AL(w->pt7, sizeof(double) * NN * PPQ_NT7E);
   AL(w->pc0, sizeof(double) * NN * PPQ_NCOL0);
-  AL(w->clT, sizeof(double) * NN * PPQ_NS36); AL(w->gT, sizeof(double) * NN * PPQ_NS36);
+  AL(w->clT, sizeof(double) * cl_ld(Nc) * PPQ_NS36); AL(w->gT, sizeof(double) * NN * PPQ_NS36);
   AL(w->tb, sizeof(double) * L); AL(w->r64, sizeof(double) * L); AL(w->rb, sizeof(double) * L);
   AL(w->del, sizeof(double) * L); AL(w->rho, sizeof(double) * L);
   AL(w->amax, sizeof(unsigned long long));
   AL(w->t9, sizeof(double) * NN * PPQ_NA2);
   AL(w->pt7T, sizeof(double) * NN * PPQ_NT7E); AL(w->m7, sizeof(double) * NN * PPQ_NK7);
+  {
+    int Nt = std::min(Nc, kTcMaxN);
+    size_t npad = (size_t)(Nt + 15) / 16 * 16, kc = (size_t)(Nt + 7) / 8;
+    AL(w->bpre, sizeof(float) * PPQ_NS36 * 2 * kc * npad * 8);
+    AL(w->tc_chunk, sizeof(int16_t) * ppq::tc::kChunkFields * PPQ_NQ9);
+    AL(w->tc_cta, sizeof(int) * 3 * kTcMaxCtas);
+    AL(w->tc_err, sizeof(int));
+    AL(w->tc_part, sizeof(float) * kTcPartRows * PPQ_NA2);
+    CK(cudaMemset(w->tc_err, 0, sizeof(int)));
+    w->tc_allowed = true;
+    w->tc_N = 0;
+  }
   {
     // quartic GEMM work items: chunks of at most 4 (c1, g) entries of one c2
     std::vector<int> wk;
@@ -177,6 +208,7 @@ int grow(Workspace* w, int N, int diis) {
     w->n_work9 = (int)wk.size() / 3;
     AL(w->work9, sizeof(int) * wk.size());
     CK(cudaMemcpy(w->work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice));
+    AL(w->t9part, sizeof(double) * w->n_work9 * (NN - Nc) / 2 * PPQ_NA2);
   }
   AL(w->esite, sizeof(double) * Nc); AL(w->epair, sizeof(double) * NN);
   AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
@@ -305,12 +337,13 @@ int launch_t9_mt(Workspace* w, int N, cudaStream_t s) {
   int T = (N + MT - 1) / MT;           // thread grid T x T, micro-tile MT x MT
   int nth = ((T * T + 31) / 32) * 32;
   size_t npd = (size_t)T * MT;
-  size_t smem = (2 * 16 * npd + npd * npd + (size_t)N * PPQ_NS36) * sizeof(R);
+  // GEMM tiles, then the [N][29] double row sums (16-byte aligned)
+  size_t smem = ((2 * 16 * npd + npd * npd) * sizeof(R) + 15) / 16 * 16 + (size_t)N * PPQ_NA2 * sizeof(double);
   if (smem > 48 * 1024)
     CK(cudaFuncSetAttribute(ppq::k_t9_gemm<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(w->n_work9, N);
-  ppq::k_t9_gemm<R, MT><<<grid, nth, smem, s>>>(N, T, (const R*)w->clT, (const R*)w->gT,
-                                                 (const R*)w->cl, w->work9, w->t9);
+  ppq::k_t9_gemm<R, MT><<<grid, nth, smem, s>>>(N, T, cl_ld(N), (const R*)w->clT, (const R*)w->gT,
+                                                 w->work9, w->t9part);
   return 0;
 }
 
@@ -334,7 +367,8 @@ int launch_t7_mt(Workspace* w, int N, cudaStream_t s) {
   int T = (N + MT - 1) / MT;
   int nth = ((T * T + 31) / 32) * 32;
   size_t smem = 2 * 16 * (size_t)T * MT * sizeof(R);
-  ppq::k_t7_gemm<R, MT><<<PPQ_NK7, nth, smem, s>>>(N, T, (const R*)w->pt7T, (const R*)w->clT, (R*)w->m7);
+  ppq::k_t7_gemm<R, MT><<<PPQ_NK7, nth, smem, s>>>(N, T, cl_ld(N), (const R*)w->pt7T, (const R*)w->clT,
+                                                   (R*)w->m7);
   return 0;
 }
 
@@ -350,6 +384,121 @@ int launch_t7_gemm(Workspace* w, int N, int mt, cudaStream_t s) {
     case 7: return launch_t7_mt<R, 7>(w, N, s);
     case 8: return launch_t7_mt<R, 8>(w, N, s);
     default: return fail(-5, "n_pairs > 128 is not supported");
+  }
+}
+
+// Work list of the tensor-core quartic kernel for N pairs.  A chunk is one
+// link pair (c1, c2) with up to four of its g, as many as fit 256 TMEM
+// columns at Npad = 16 ceil(N / 16) columns each; the rows (unordered pairs)
+// come in tiles of 128, and each CTA takes one tile and a run of chunks of
+// about equal cost, about one CTA per SM in all.  Host only.
+struct TcPlan {
+  int Npad = 0, Kc = 0, nchunks = 0;
+  std::vector<int16_t> chunk;  // kChunkFields per chunk
+  std::vector<int> cta;        // tile, first chunk, end chunk
+};
+
+int plan_tc(int N, TcPlan* pl) {
+  if (N < 1 || N > kTcMaxN) return fail(-5, "no tensor-core quartic kernel for n_pairs = %d", N);
+  const int Npad = (N + 15) / 16 * 16, Kc = (N + 7) / 8;
+  const int max_g = std::max(1, std::min(4, ppq::tc::kMaxCols / Npad));
+  pl->chunk.clear();
+  pl->cta.clear();
+  std::vector<double> cost;
+  for (int q0 = 0; q0 < PPQ_NQ9;) {
+    int p = ppq_q9_h[2 * q0], q1 = q0;
+    while (q1 < PPQ_NQ9 && ppq_q9_h[2 * q1] == p) ++q1;
+    int n = q1 - q0, parts = (n + max_g - 1) / max_g;
+    for (int k = 0, a = q0; k < parts; ++k) {
+      int ng = n / parts + (k < n % parts ? 1 : 0);
+      int16_t rec[ppq::tc::kChunkFields] = {0};
+      rec[0] = ppq_p9_h[2 * p]; rec[1] = ppq_p9_h[2 * p + 1];
+      rec[2] = (int16_t)ng; rec[3] = (int16_t)(ng * Npad);
+      int nch = 0;
+      for (int j = 0; j < ng; ++j) {
+        rec[4 + j] = ppq_q9_h[2 * (a + j) + 1];
+        rec[8 + j] = (int16_t)(a + j);
+        nch += ppq_c9qp_h[a + j + 1] - ppq_c9qp_h[a + j];
+      }
+      pl->chunk.insert(pl->chunk.end(), rec, rec + ppq::tc::kChunkFields);
+      // MMA clocks (3 TF32 MMAs of 128 x n_cols x 8 per stage) + epilogue loads
+      cost.push_back(3.0 * Kc * 128.0 * ng * Npad * 8 / 1620.0 + 8.0 * nch * N);
+      a += ng;
+    }
+    q0 = q1;
+  }
+  const int nchunks = (int)cost.size();
+  const int P = N * (N - 1) / 2, ntiles = (P + ppq::tc::kRows - 1) / ppq::tc::kRows;
+  const int nsplit = std::max(1, std::min(nchunks, 152 / std::max(1, ntiles)));
+  if (ntiles * nsplit > kTcMaxCtas) return fail(-5, "tensor-core work list too long");
+  std::vector<double> pre(nchunks + 1, 0.0);
+  for (int i = 0; i < nchunks; ++i) pre[i + 1] = pre[i] + cost[i];
+  std::vector<int> bounds(nsplit + 1, 0);
+  bounds[nsplit] = nchunks;
+  for (int k = 1; k < nsplit; ++k) {
+    double target = pre[nchunks] * k / nsplit;
+    int i = (int)(std::lower_bound(pre.begin(), pre.end(), target) - pre.begin());
+    bounds[k] = std::max(bounds[k - 1], std::min(i, nchunks));
+  }
+  for (int t = 0; t < ntiles; ++t)
+    for (int k = 0; k < nsplit; ++k)
+      if (bounds[k + 1] > bounds[k]) {
+        pl->cta.push_back(t); pl->cta.push_back(bounds[k]); pl->cta.push_back(bounds[k + 1]);
+      }
+  pl->Npad = Npad;
+  pl->Kc = Kc;
+  pl->nchunks = nchunks;
+  return 0;
+}
+
+int prepare_tc(Workspace* w, int N, cudaStream_t s) {
+  TcPlan pl;
+  int rc = plan_tc(N, &pl);
+  if (rc) return rc;
+  if (!pl.cta.empty())
+    CK(cudaMemcpyAsync(w->tc_cta, pl.cta.data(), sizeof(int) * pl.cta.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->tc_chunk, pl.chunk.data(), sizeof(int16_t) * pl.chunk.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  w->tc_Npad = pl.Npad;
+  w->tc_Kc = pl.Kc;
+  w->tc_nctas = (int)pl.cta.size() / 3;
+  const int P = N * (N - 1) / 2, ntiles = (P + ppq::tc::kRows - 1) / ppq::tc::kRows;
+  w->tc_nslot = ntiles > 0 ? w->tc_nctas / ntiles : 0;
+  if (w->tc_nslot * ntiles != w->tc_nctas || (size_t)w->tc_nslot * P > (size_t)kTcPartRows)
+    return fail(-5, "tensor-core work list does not fit its partial buffer");
+  // at least 120 KB, so that one CTA (holding all 512 TMEM columns) runs per SM
+  w->tc_smem = std::max(ppq::tc::Smem::total(cl_ld(N)), (size_t)120 * 1024);
+  w->tc_N = N;
+  return 0;
+}
+
+template <int NW>
+int launch_t9_tc_nw(Workspace* w, int N, cudaStream_t s) {
+  static std::once_flag attr[64];  // per device
+  int dev;
+  CK(cudaGetDevice(&dev));
+  cudaError_t e = cudaSuccess;
+  std::call_once(attr[dev & 63], [&] {
+    e = cudaFuncSetAttribute(ppq::tc::k_t9_tc<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ppq::tc::Smem::total(cl_ld(kTcMaxN)));
+  });
+  if (e != cudaSuccess) return fail(-100, "k_t9_tc attribute: %s", cudaGetErrorString(e));
+  const int P = N * (N - 1) / 2;
+  ppq::tc::k_t9_tc<NW><<<w->tc_nctas, ppq::tc::kThreads, w->tc_smem, s>>>(
+      N, P, w->tc_Kc, cl_ld(N), (const float*)w->clT, w->bpre, w->tc_cta, w->tc_chunk, w->tc_nslot, w->tc_part,
+      w->tc_err);
+  return 0;
+}
+
+int launch_t9_tc(Workspace* w, int N, cudaStream_t s) {
+  if (w->tc_nctas == 0) return 0;  // no unordered pairs
+  switch (w->tc_Npad) {
+    case 16: return launch_t9_tc_nw<16>(w, N, s);
+    case 32: return launch_t9_tc_nw<32>(w, N, s);
+    case 48: return launch_t9_tc_nw<48>(w, N, s);
+    case 64: return launch_t9_tc_nw<64>(w, N, s);
+    case 80: return launch_t9_tc_nw<80>(w, N, s);
+    default: return fail(-5, "no tensor-core quartic kernel for n_pairs = %d", N);
   }
 }
 
@@ -416,23 +565,37 @@ int residual(Workspace* w, int N, cudaStream_t s) {
                                                                (R*)w->pt7T);
   ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
   size_t T36 = (size_t)NN * PPQ_NS36;
-  ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl, (R*)w->clT);
+  ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl_ld(N), cl, (R*)w->clT);
   {
     // T7 as GEMMs over W
     int mt = std::max(1, (N + 15) / 16);
     if ((rc = launch_t7_gemm<R>(w, N, mt, s))) return rc;
   }
   ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, (const R*)w->m7, pg, cl, t2, w->dir, w->abuf);
-  // quartic term: transposed operands, GEMM, W-contraction
-  ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
-  CK(cudaMemsetAsync(w->t9, 0, sizeof(double) * NN * PPQ_NA2, s));
-  if (w->profile) CK(cudaEventRecord(w->evq0, s));
-  if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
-  if (w->profile) CK(cudaEventRecord(w->evq1, s));
+  // quartic term
+  if (std::is_same<R, float>::value && w->tc_N == N) {
+    // tensor cores: split B operands, then the fused MMA + W-contraction kernel
+    size_t nb = (size_t)PPQ_NS36 * w->tc_Kc * w->tc_Npad * 8;
+    ppq::tc::k_t9_bprep<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(N, w->tc_Npad, w->tc_Kc, (const float*)pg,
+                                                                       w->bpre);
+    if (w->profile) CK(cudaEventRecord(w->evq0, s));
+    if ((rc = launch_t9_tc(w, N, s))) return rc;
+    if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    ppq::k_t9_reduce<float><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc_nslot, w->tc_part,
+                                                                                   w->t9);
+  } else {
+    // SIMT: transposed operands, GEMM, W-contraction
+    ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
+    if (w->profile) CK(cudaEventRecord(w->evq0, s));
+    if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
+    if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->n_work9, w->t9part,
+                                                                                    w->t9);
+  }
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
   CK(cudaGetLastError());
-  w->n_launches += 10;
+  w->n_launches += 11;
   return 0;
 }
 
@@ -441,8 +604,13 @@ int residual(Workspace* w, int N, cudaStream_t s) {
 int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   int rc;
   int p = precision ? 1 : 0;
-  if (precision) { if ((rc = tuned_mt<float>(w, N, s, &w->mt[1]))) return rc; }
-  else { if ((rc = tuned_mt<double>(w, N, s, &w->mt[0]))) return rc; }
+  if (precision && w->tc_allowed && N <= kTcMaxN) {
+    if (w->tc_N != N && (rc = prepare_tc(w, N, s))) return rc;
+  } else if (precision) {
+    if ((rc = tuned_mt<float>(w, N, s, &w->mt[1]))) return rc;
+  } else {
+    if ((rc = tuned_mt<double>(w, N, s, &w->mt[0]))) return rc;
+  }
   if (s == 0) return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
   if (!w->graph[p] || w->graph_N[p] != N || w->graph_profile[p] != (int)w->profile) {
     if (w->graph[p]) { cudaGraphExecDestroy(w->graph[p]); w->graph[p] = nullptr; }
@@ -460,7 +628,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
     w->n_launches = nl;
   }
   CK(cudaGraphLaunch(w->graph[p], s));
-  w->n_launches += 10;
+  w->n_launches += 11;
   return 0;
 }
 
@@ -958,6 +1126,25 @@ int ppq_release(void) {
 
 const char* ppq_last_error(void) { return g_err.c_str(); }
 
+int ppq_tc_plan(int n_pairs, int16_t* chunks, int max_chunks, int* ctas, int max_ctas, int* n_chunks,
+                int* n_ctas) {
+  TcPlan pl;
+  int rc = plan_tc(n_pairs, &pl);
+  if (rc) return rc;
+  int nc = pl.nchunks, nt = (int)pl.cta.size() / 3;
+  if (n_chunks) *n_chunks = nc;
+  if (n_ctas) *n_ctas = nt;
+  if (chunks) {
+    if (max_chunks < nc) return fail(-2, "ppq_tc_plan: %d chunks do not fit %d", nc, max_chunks);
+    std::copy(pl.chunk.begin(), pl.chunk.end(), chunks);
+  }
+  if (ctas) {
+    if (max_ctas < nt) return fail(-2, "ppq_tc_plan: %d CTAs do not fit %d", nt, max_ctas);
+    std::copy(pl.cta.begin(), pl.cta.end(), ctas);
+  }
+  return 0;
+}
+
 int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
                 const double* eri, const double* t, double* r, double* e_corr, int precision,
                 void* stream) {
@@ -1407,7 +1594,7 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   w.cl = cv.take<double>(NN * PPQ_NS36); w.hs = cv.take<double>((size_t)N * 256);
   w.pg = cv.take<double>(NN * PPQ_NS36); w.pt7 = cv.take<double>(NN * PPQ_NT7E);
   w.pc0 = cv.take<double>(NN * PPQ_NCOL0);
-  w.clT = cv.take<double>(NN * PPQ_NS36); w.gT = cv.take<double>(NN * PPQ_NS36);
+  w.clT = cv.take<double>((size_t)cl_ld(N) * PPQ_NS36); w.gT = cv.take<double>(NN * PPQ_NS36);
   w.t9 = cv.take<double>(NN * PPQ_NA2);
   w.pt7T = cv.take<double>(NN * PPQ_NT7E); w.m7 = cv.take<double>(NN * PPQ_NK7);
   w.esite = cv.take<double>(N); w.epair = cv.take<double>(NN);
@@ -1419,6 +1606,7 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
     }
   w.n_work9 = (int)wk.size() / 3;
   w.work9 = cv.take<int>(wk.size());
+  w.t9part = cv.take<double>((size_t)w.n_work9 * (NN - N) / 2 * PPQ_NA2);
   if (cv.off > kStaticScratchBytes)
     return fail(-6, "pq_residual_static: %zu bytes of scratch needed, %zu available", cv.off,
                 kStaticScratchBytes);

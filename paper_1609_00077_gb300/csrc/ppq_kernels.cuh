@@ -513,37 +513,34 @@ namespace ppq {
 // a GEMM with M = Z, N = W, K = X: rows Z <= Y are skipped (Y < Z symmetry).
 // Thread (tz, tw) of a 16x16 grid owns rows tz + 16 i and columns tw + 16 j.
 template <typename R, int MT>
-__global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restrict__ clT,
-    const R* __restrict__ gT, const R* __restrict__ cl, const int* __restrict__ work,
-    double* __restrict__ t9) {
+__global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, int ldc, const R* __restrict__ clT,
+    const R* __restrict__ gT, const int* __restrict__ work, double* __restrict__ part) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int KC = 16;
   const int NPD = T * MT;                       // padded row length (zeros beyond N)
   R* As = reinterpret_cast<R*>(smem_raw);      // [KC][NPD]
   R* Bs = As + KC * NPD;                        // [KC][NPD]
   R* Cs = Bs + KC * NPD;                        // [NPD][NPD]  C tile for the epilogue
-  R* cy = Cs + NPD * NPD;                       // [N][36]     Cl[W,Y][c]
+  // [N][29] per-row sums of this work item, 16-byte aligned after the tiles
+  double* acc = reinterpret_cast<double*>(smem_raw + ((2 * KC * NPD + NPD * NPD) * sizeof(R) + 15) / 16 * 16);
   int c2 = work[3 * blockIdx.x], q0 = work[3 * blockIdx.x + 1], q1 = work[3 * blockIdx.x + 2];
   int Y = blockIdx.y;
   int tz = threadIdx.x / T, tw = threadIdx.x % T;
   bool active = tz < T;
   size_t NN = (size_t)N * N;
-  const R* a_src = clT + (size_t)c2 * NN;      // [X][Z]
+  const R* a_src = clT + (size_t)c2 * ldc;     // [X][Z]
   int i0 = (Y + 1) / T;                        // first micro-row that can hold Z > Y
   int nth = blockDim.x;
-  for (int e = threadIdx.x; e < N * PPQ_NS36; e += nth) {
-    int W = e / PPQ_NS36, c = e % PPQ_NS36;
-    cy[e] = cl[((size_t)W * N + Y) * PPQ_NS36 + c];
-  }
+  for (int e = threadIdx.x; e < N * PPQ_NA2; e += nth) acc[e] = 0.0;
   for (int qq = q0; qq < q1; ++qq) {
     int c1 = ppq_q9c[3 * qq], g = ppq_q9c[3 * qq + 1], q = ppq_q9c[3 * qq + 2];
-    const R* ys = clT + (size_t)c1 * NN;       // [X][Y]
+    const R* ys = clT + (size_t)c1 * ldc;      // [X][Y]
     const R* gs = gT + (size_t)g * NN;         // [X][W]
-    R acc[MT][MT];
+    R accm[MT][MT];
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int j = 0; j < MT; ++j) acc[i][j] = R(0);
+      for (int j = 0; j < MT; ++j) accm[i][j] = R(0);
     for (int k0 = 0; k0 < N; k0 += KC) {
       int kc = min(KC, N - k0);
       __syncthreads();
@@ -571,7 +568,7 @@ __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restri
           for (int i = 0; i < MT; ++i) {
             if (i < i0) continue;
 #pragma unroll
-            for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < MT; ++j) accm[i][j] = fma(a[i], b[j], accm[i][j]);
           }
           ap += NPD;
           bp += NPD;
@@ -579,35 +576,69 @@ __global__ void __launch_bounds__(256) k_t9_gemm(int N, int T, const R* __restri
       }
     }
     // fused epilogue: C tile to shared memory, then
-    // t9[Y,Z][o] += 1/2 sum_W sum_{ch of q} s C[Z][W] Cl[W,Y][c3] Cl[W,Z][c4]
+    // acc[Z][o] += 1/2 sum_W sum_{ch of q -> o} s C[Z][W] Cl[W,Y][c3] Cl[W,Z][c4];
+    // one thread per (output group, Z), so every sum has a fixed order
     if (active) {
 #pragma unroll
       for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < MT; ++j) Cs[(tz + T * i) * NPD + tw + T * j] = acc[i][j];
+        for (int j = 0; j < MT; ++j) Cs[(tz + T * i) * NPD + tw + T * j] = accm[i][j];
     }
     __syncthreads();
-    int ch0 = ppq_c9qp[q], nch = ppq_c9qp[q + 1] - ch0;
+    int g0 = ppq_c9gp[q], ngr = ppq_c9gp[q + 1] - g0;
     int nz = N - (Y + 1);
-    for (int e = threadIdx.x; e < nch * nz; e += nth) {
-      int chn = e / nz, Z = Y + 1 + (e - chn * nz);
-      const int16_t* c = ppq_c9q + 4 * (ch0 + chn);
-      int c3 = c[0], c4 = c[1], o = c[2];
+    for (int e = threadIdx.x; e < ngr * nz; e += nth) {
+      int gi = e / nz, Z = Y + 1 + (e - gi * nz);
       const R* crow = Cs + Z * NPD;
-      const R* z4 = clT + (size_t)c4 * NN + Z;   // Cl[W,Z][c4] = clT[c4][W][Z]
-      R v0 = R(0), v1 = R(0), v2 = R(0), v3 = R(0);
-      int W = 0;
-      for (; W + 3 < N; W += 4) {
-        v0 += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
-        v1 += crow[W + 1] * cy[(W + 1) * PPQ_NS36 + c3] * z4[(size_t)(W + 1) * N];
-        v2 += crow[W + 2] * cy[(W + 2) * PPQ_NS36 + c3] * z4[(size_t)(W + 2) * N];
-        v3 += crow[W + 3] * cy[(W + 3) * PPQ_NS36 + c3] * z4[(size_t)(W + 3) * N];
+      double sum = 0.0;
+      int o = 0;
+      for (int ch = ppq_c9g[g0 + gi]; ch < ppq_c9g[g0 + gi + 1]; ++ch) {
+        const int16_t* c = ppq_c9q + 4 * ch;
+        o = c[2];
+        const R* y3 = clT + (size_t)c[0] * ldc + Y;   // Cl[W,Y][c3] = clT[c3][W][Y]
+        const R* z4 = clT + (size_t)c[1] * ldc + Z;   // Cl[W,Z][c4] = clT[c4][W][Z]
+        R v0 = R(0), v1 = R(0), v2 = R(0), v3 = R(0);
+        int W = 0;
+        for (; W + 3 < N; W += 4) {
+          v0 += crow[W] * __ldg(y3 + (size_t)W * N) * __ldg(z4 + (size_t)W * N);
+          v1 += crow[W + 1] * __ldg(y3 + (size_t)(W + 1) * N) * __ldg(z4 + (size_t)(W + 1) * N);
+          v2 += crow[W + 2] * __ldg(y3 + (size_t)(W + 2) * N) * __ldg(z4 + (size_t)(W + 2) * N);
+          v3 += crow[W + 3] * __ldg(y3 + (size_t)(W + 3) * N) * __ldg(z4 + (size_t)(W + 3) * N);
+        }
+        for (; W < N; ++W) v0 += crow[W] * __ldg(y3 + (size_t)W * N) * __ldg(z4 + (size_t)W * N);
+        sum += 0.5 * double(c[3]) * double((v0 + v1) + (v2 + v3));
       }
-      for (; W < N; ++W) v0 += crow[W] * cy[W * PPQ_NS36 + c3] * z4[(size_t)W * N];
-      R v = (v0 + v1) + (v2 + v3);
-      atomicAdd(&t9[((size_t)Y * N + Z) * PPQ_NA2 + o], 0.5 * double(c[3]) * double(v));
+      acc[Z * PPQ_NA2 + o] += sum;
     }
   }
+  // this work item's rows Z > Y, all outputs (zeros included), to its slot:
+  // part[item][p][o] with p = Y (2N - Y - 1) / 2 + Z - Y - 1
+  __syncthreads();
+  size_t P = (size_t)N * (N - 1) / 2;
+  size_t pY = (size_t)Y * (2 * N - Y - 1) / 2;
+  double* dst = part + ((size_t)blockIdx.x * P + pY) * PPQ_NA2;
+  int nz = N - (Y + 1);
+  for (int e = threadIdx.x; e < nz * PPQ_NA2; e += nth) dst[e] = acc[(Y + 1) * PPQ_NA2 + e];
+}
+
+// t9[Y,Z][o] = sum over slots k of part[k][p(Y, Z)][o] in slot order (Y < Z),
+// zero for Y >= Z
+template <typename P_>
+__global__ void k_t9_reduce(int N, int nslot, const P_* __restrict__ part, double* __restrict__ t9) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t NN = (size_t)N * N;
+  if (i >= NN * PPQ_NA2) return;
+  int o = (int)(i % PPQ_NA2);
+  size_t YZ = i / PPQ_NA2;
+  int Y = (int)(YZ / N), Z = (int)(YZ % N);
+  double v = 0.0;
+  if (Y < Z) {
+    size_t P = NN > 0 ? (size_t)N * (N - 1) / 2 : 0;
+    size_t p = (size_t)Y * (2 * N - Y - 1) / 2 + (Z - Y - 1);
+    const P_* src = part + p * PPQ_NA2 + o;
+    for (int k = 0; k < nslot; ++k) v += double(src[(size_t)k * P * PPQ_NA2]);
+  }
+  t9[i] = v;
 }
 
 // Stage 2: t9[Y,Z][o] = 1/2 sum_W sum_{ch -> o} s B[Y][q][Z][W] Cl[W,Y][c3] Cl[W,Z][c4], Y < Z
@@ -644,15 +675,16 @@ __global__ void __launch_bounds__(256) k_t9_epi(int N, const R* __restrict__ B, 
   }
 }
 
-// transposed link coefficients clT[c][X][Y] = Cl[X,Y][c]
+// transposed link coefficients clT[c][X][Y] = Cl[X,Y][c]; slices ldc apart
+// (N^2 rounded up to a multiple of 4, so that every slice is 16-byte aligned)
 template <typename R>
-__global__ void k_transpose_cl(int N, const R* __restrict__ cl, R* __restrict__ clT) {
+__global__ void k_transpose_cl(int N, int ldc, const R* __restrict__ cl, R* __restrict__ clT) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t NN = (size_t)N * N;
   if (i >= NN * PPQ_NS36) return;
   int c = i / NN;
   size_t XY = i % NN;
-  clT[i] = cl[XY * PPQ_NS36 + c];
+  clT[(size_t)c * ldc + XY] = cl[XY * PPQ_NS36 + c];
 }
 
 // transposed closure row gT[g][X][W] = G[X,W][g]
@@ -675,7 +707,7 @@ namespace ppq {
 // (c2, e) = k of the T7 channels, one CTA per k; operands pt7T[e][W][Y] and
 // clT[c2][W][Z]; thread grid T x T, micro-tile MT x MT
 template <typename R, int MT>
-__global__ void __launch_bounds__(256) k_t7_gemm(int N, int T, const R* __restrict__ pt7T,
+__global__ void __launch_bounds__(256) k_t7_gemm(int N, int T, int ldc, const R* __restrict__ pt7T,
                                                  const R* __restrict__ clT, R* __restrict__ m7) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int KC = 16;
@@ -686,7 +718,7 @@ __global__ void __launch_bounds__(256) k_t7_gemm(int N, int T, const R* __restri
   int c2 = ppq_k7[2 * k], e = ppq_k7[2 * k + 1];
   size_t NN = (size_t)N * N;
   const R* A = pt7T + (size_t)e * NN;          // [W][Y]
-  const R* Bm = clT + (size_t)c2 * NN;         // [W][Z]
+  const R* Bm = clT + (size_t)c2 * ldc;        // [W][Z]
   int tz = threadIdx.x / T, tw = threadIdx.x % T;
   bool active = tz < T;
   R acc[MT][MT];

@@ -623,13 +623,25 @@ def emit_header(path):
             _c_array("ppq_q9cptr_h", "int16_t", g2ptr).replace("static __device__ const", "static const")]
     ch9arr = np.array(ch9)
     # channels grouped by q for the fused GEMM epilogue: (c3, c4, out, s)
-    c9q, c9qp = by_out(ch9arr, 0, len(q9))
-    out += [_c_array("ppq_c9q", "int16_t", c9q[:, 1:]), _c_array("ppq_c9qp", "int16_t", c9qp)]
+    # (ordered by q, then by output o; a run of equal (q, o) is one output group,
+    # which lets one thread own each (group, row) and sum in a fixed order)
+    c9q = ch9arr[np.lexsort((ch9arr[:, 3], ch9arr[:, 0]))]
+    c9qp = [int(np.sum(c9q[:, 0] < q)) for q in range(len(q9) + 1)]
+    gstart = [i for i in range(len(c9q)) if i == 0 or tuple(c9q[i, [0, 3]]) != tuple(c9q[i - 1, [0, 3]])]
+    c9g = gstart + [len(c9q)]
+    gq = c9q[gstart, 0]
+    c9gp = [int(np.sum(gq < q)) for q in range(len(q9) + 1)]
+    out += [_c_array("ppq_c9q", "int16_t", c9q[:, 1:]), _c_array("ppq_c9qp", "int16_t", c9qp),
+            _c_array("ppq_c9g", "int16_t", np.array(c9g)), _c_array("ppq_c9gp", "int16_t", np.array(c9gp))]
     ch9, c9p = by_out(ch9arr, 3, 29)
     out.append(_c_array("ppq_c9p", "int16_t", c9p))
     out += [f"#define PPQ_NP9 {len(p9)}", f"#define PPQ_NQ9 {len(q9)}", f"#define PPQ_NC9 {len(ch9)}",
             _c_array("ppq_p9", "int8_t", np.array(p9)), _c_array("ppq_q9", "int16_t", np.array(q9)),
             _c_array("ppq_c9", "int16_t", np.array(ch9))]
+    # host copies for planning the tensor-core work list
+    host = lambda a: a.replace("static __device__ const", "static const")
+    out += [host(_c_array("ppq_p9_h", "int8_t", np.array(p9))), host(_c_array("ppq_q9_h", "int16_t", np.array(q9))),
+            host(_c_array("ppq_c9qp_h", "int16_t", c9qp))]
     # integral gather keys
     k1 = site_integral_keys(); k2 = pair_integral_keys()
     enc1 = [(0, k[1], k[2], 0, 0) if k[0] == "h" else (1,) + k[1:] for k in k1]

@@ -1,0 +1,87 @@
+"""The FP32 residual with the quartic topology on the tensor cores (tcgen05,
+3xTF32 split) beyond one 128-row tile.
+
+* N = 20 (190 unordered pairs: a full tile and a ragged one of 62 rows):
+  every pair-amplitude element of two sampled pairs of the second tile
+  against the oracle's local assembly restricted to the label subsets that
+  contain the pair (exact for those elements), FP32 within 2e-5 * max|R|,
+  FP64 within 1e-11;
+* N = 40 and 70 (7 and 19 tiles, 48 and 80 TMEM columns per g): the whole
+  FP32 residual against the FP64 one (SIMT path, oracle-pinned at small N)
+  within the same FP32 bound -- a property that holds at any size.
+"""
+from itertools import combinations
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1609_00077_gb300 as ppq
+from workloads import build_ppp, ppp_eri_device, random_pair_amplitude_seed
+from oracle.loccc import LocalAssembly
+from oracle.detcc import enumerate_manifold
+from tests.layout import LayoutMap
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def residuals(H, tl, eri=None):
+    eri = dev(H.eri) if eri is None else eri
+    out = {}
+    for prec in (0, 1):
+        r, e = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), eri, dev(tl), precision=prec)
+        out[prec] = (r.cpu().numpy(), e)
+    return out
+
+
+def test_two_tiles_sampled_pairs_match_oracle():
+    H = build_ppp('polyene', 40, orbitals='local')
+    N = H.n_pairs
+    assert N == 20
+    sampled = [(8, 13), (18, 19)]   # unordered-pair rows 128 and 189: first and last of tile 2
+    subs = set()
+    for Y, Z in sampled:
+        others = [k for k in range(N) if k not in (Y, Z)]
+        for extra in [()] + [(a,) for a in others] + list(combinations(others, 2)):
+            subs.add(tuple(sorted((Y, Z) + extra)))   # each label set once
+    L = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, subsets=sorted(subs))
+    man = L.manifold
+    lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+    rng = np.random.default_rng(random_pair_amplitude_seed(N))
+    t = rng.uniform(-0.1, 0.1, len(man))
+    R_ref, _ = L.residual(t)
+    idx = [k for k, d in enumerate(man) if L._labels(d) in [{Y, Z} for Y, Z in sampled]]
+    assert len(idx) == 29 * len(sampled)
+    res = residuals(H, lm.to_layout(t))
+    R64 = lm.from_layout(res[0][0])
+    R32 = lm.from_layout(res[1][0])
+    assert np.abs(R64[idx] - R_ref[idx]).max() < 1e-11
+    scale = max(np.abs(R_ref[idx]).max(), np.abs(R64).max())
+    assert np.abs(R32[idx] - R_ref[idx]).max() < 2e-5 * scale
+    assert np.abs(R32 - R64).max() < 2e-5 * scale
+
+
+@pytest.mark.parametrize("size", [80, 140])
+def test_fp32_tensor_core_residual_matches_fp64(size):
+    H = build_ppp('polyene', size, orbitals='local', with_eri=False)
+    eri = ppp_eri_device(H, torch)
+    N = H.n_pairs
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+    rng = np.random.default_rng(random_pair_amplitude_seed(N))
+    t = rng.uniform(-0.1, 0.1, len(man))
+    res = residuals(H, lm.to_layout(t), eri)
+    del eri
+    r64, e64 = res[0]
+    r32, e32 = res[1]
+    assert np.all(np.isfinite(r32))
+    scale = np.abs(r64).max()
+    assert np.abs(r32 - r64).max() < 2e-5 * scale
+    assert abs(e32 - e64) < 2e-5 * max(1.0, abs(e64))

@@ -8,7 +8,7 @@ it without sharing any of the method's code.
 """
 from .ppp import polyene_geometry, acene_geometry, ppp_site_hamiltonian
 from .hchain import hchain_ao_integrals
-from .scf import rhf, mo_integrals, pair_orbitals, Hamiltonian, build_ppp, build_hchain
+from .scf import rhf, mo_integrals, pair_orbitals, Hamiltonian, build_ppp, build_hchain, ppp_eri_device
 from .rng import random_pair_amplitude_seed
 
 __all__ = [

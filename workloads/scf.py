@@ -183,3 +183,17 @@ def build_hchain(n_atoms, spacing_angstrom, orbitals="canonical", bond_bohr=None
         raise ValueError(orbitals)
     h_mo, eri_mo = mo_integrals(C, h, eri_ao=eri)
     return Hamiltonian(name, h_mo, eri_mo, e_nuc, occ, vir, e, e_elec + e_nuc)
+
+
+def ppp_eri_device(H, torch):
+    """MO two-electron integrals of a PPP workload (built with with_eri=False)
+    on the current CUDA device: (pq|rs) = sum_{AB} D[A,pq] gamma[A,B] D[B,rs]
+    with D[A,pq] = C[A,p] C[A,q] (zero differential overlap), as a contiguous
+    float64 tensor of shape (n, n, n, n).  Keeps the n^4 array off the host."""
+    C = torch.from_numpy(H.C).cuda()
+    g = torch.from_numpy(H.gamma_site).cuda()
+    n = C.shape[1]
+    D = (C[:, :, None] * C[:, None, :]).reshape(C.shape[0], n * n)
+    eri = (D.T @ g @ D).reshape(n, n, n, n).contiguous()
+    del D
+    return eri
