@@ -387,6 +387,24 @@ int launch_t7_gemm(Workspace* w, int N, int mt, cudaStream_t s) {
   }
 }
 
+// persistent pair closure: about two CTAs per SM, each looping over pairs
+template <typename R>
+int launch_pair_closure(int N, const R* g2, const double* t1, const double* t2, R* pg, R* pt7, R* pc0,
+                        double* epair, R* pt7T, cudaStream_t s) {
+  static std::once_flag attr[64];  // per device
+  int dev;
+  CK(cudaGetDevice(&dev));
+  cudaError_t e = cudaSuccess;
+  const size_t smem = ppq::ClosureSmem::total<R>();
+  std::call_once(attr[dev & 63], [&] {
+    e = cudaFuncSetAttribute(ppq::k_pair_closure_p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return fail(-100, "k_pair_closure_p attribute: %s", cudaGetErrorString(e));
+  const int grid = std::min(N * N, kRedBlocks);
+  ppq::k_pair_closure_p<R><<<grid, 256, smem, s>>>(N, g2, t1, t2, pg, pt7, pc0, epair, pt7T);
+  return 0;
+}
+
 // Work list of the tensor-core quartic kernel for N pairs.  A chunk is one
 // link pair (c1, c2) with up to four of its g, as many as fit 256 TMEM
 // columns at Npad = 16 ceil(N / 16) columns each; the rows (unordered pairs)
@@ -561,8 +579,7 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   int NN = N * N;
   ppq::k_links<R><<<(NN + 63) / 64, 64, 0, s>>>(N, t2, cl);
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
-  ppq::k_pair_closure<R><<<NN, 256, sizeof(R) * PPQ_BLK, s>>>(N, g2, t1, t2, pg, pt7, pc0, w->epair,
-                                                               (R*)w->pt7T);
+  if ((rc = launch_pair_closure<R>(N, g2, t1, t2, pg, pt7, pc0, w->epair, (R*)w->pt7T, s))) return rc;
   ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
   size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl_ld(N), cl, (R*)w->clT);

@@ -213,6 +213,147 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict
   if (threadIdx.x == 0) epair[XW] = double(M[PPQ_EL00]) - double(h00);
 }
 
+// Persistent form of the same closure: each CTA stages the compact tables
+// (Hamiltonian CSR, per-sector sweep lists, output element lists) in shared
+// memory once and then loops over pairs XW.  Right multiplication by
+// (1 + t_o O_o) only mixes entries of one row and left multiplication only
+// entries of one column, so a thread takes one row through all 35 operators,
+// then one column, with no barrier between operators.  Threads are ordered by
+// sector, so the lanes of a warp walk the same list; the lists come in groups
+// of 4 entries of one operator (independent targets), loaded together.  The
+// shared copy of M pads every sector row to dim + 1 entries (no bank
+// conflicts between rows dim apart).  The gather multiplies by the five
+// coefficient values -1, -1/2, 1/2, 1, 2 through a pre-scaled copy of the
+// integrals (the products are exact).  Same result, element for element, as
+// k_pair_closure.
+struct ClosureSmem {
+  static constexpr int kM = PPQ_BLKP + 8;
+  static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2;   // pre-scaled integrals
+  template <typename R>
+  static __host__ __device__ constexpr size_t off_cj() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
+  template <typename R>
+  static __host__ __device__ constexpr size_t off_hel() { return off_cj<R>() + (PPQ_H2_NNZ * 2 + 15) / 16 * 16; }
+  template <typename R>
+  static __host__ __device__ constexpr size_t off_hptr() { return off_hel<R>() + (PPQ_H2_NEL * 2 + 15) / 16 * 16; }
+  template <typename R>
+  static __host__ __device__ constexpr size_t off_sl() { return off_hptr<R>() + ((PPQ_H2_NEL + 1) * 2 + 15) / 16 * 16; }
+  template <typename R>
+  static __host__ __device__ constexpr size_t off_oel() { return off_sl<R>() + (size_t)(PPQ_PSR_N + PPQ_PSL_N) * 4; }
+  template <typename R>
+  static __host__ __device__ constexpr size_t total() {
+    return off_oel<R>() + ((PPQ_NS36 + PPQ_NT7E + PPQ_NCOL0) * 2 + 15) / 16 * 16;
+  }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_pair_closure_p(int N, const R* __restrict__ g2,
+    const double* __restrict__ t1, const double* __restrict__ t2, R* __restrict__ pg,
+    R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair, R* __restrict__ pt7T) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* M = reinterpret_cast<R*>(smem_raw);
+  R* gsv = M + ClosureSmem::kM;                          // [code][j]
+  R* fac = gsv + ClosureSmem::kG;                        // [2 o + sign], slots 70, 71 = 0
+  uint16_t* cj = reinterpret_cast<uint16_t*>(smem_raw + ClosureSmem::off_cj<R>());
+  int16_t* hel = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_hel<R>());
+  int16_t* hptr = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_hptr<R>());
+  int32_t* srl = reinterpret_cast<int32_t*>(smem_raw + ClosureSmem::off_sl<R>());
+  int32_t* sll = srl + PPQ_PSR_N;
+  int16_t* oel = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_oel<R>());
+  const int tid = threadIdx.x;
+  for (int i = tid; i < PPQ_H2_NNZ; i += blockDim.x) cj[i] = ppq_h2_cj[i];
+  for (int i = tid; i < PPQ_H2_NEL; i += blockDim.x) { hel[i] = ppq_h2_elp[i]; hptr[i] = (int16_t)ppq_h2_ptr[i]; }
+  if (tid == 0) hptr[PPQ_H2_NEL] = (int16_t)ppq_h2_ptr[PPQ_H2_NEL];
+  for (int i = tid; i < PPQ_PSR_N; i += blockDim.x) srl[i] = ppq_ps_right[i];
+  for (int i = tid; i < PPQ_PSL_N; i += blockDim.x) sll[i] = ppq_ps_left[i];
+  for (int i = tid; i < PPQ_NS36; i += blockDim.x) oel[i] = ppq_g_elp[i];
+  for (int i = tid; i < PPQ_NT7E; i += blockDim.x) oel[PPQ_NS36 + i] = ppq_t7_elp[i];
+  for (int i = tid; i < PPQ_NCOL0; i += blockDim.x) oel[PPQ_NS36 + PPQ_NT7E + i] = ppq_col0_elp[i];
+  // this thread's row / column (blockDim.x == 256 two-site states, by sector)
+  const int st = ppq_th_state[tid];
+  const int q = ppq_st_sec[st], dp = ppq_sec_dim[q] + 1;
+  const int rowbase = ppq_sec_pbase[q] + ppq_st_pos[st] * dp;
+  const int colbase = ppq_sec_pbase[q] + ppq_st_pos[st];
+  const int r0 = ppq_ps_rptr[q], r1 = ppq_ps_rptr[q + 1], l0 = ppq_ps_lptr[q], l1 = ppq_ps_lptr[q + 1];
+  const int NN = N * N;
+  for (int XW = blockIdx.x; XW < NN; XW += gridDim.x) {
+    const int X = XW / N, W = XW % N;
+    if (X == W) {
+      for (int i = tid; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = R(0);
+      for (int i = tid; i < PPQ_NT7E; i += blockDim.x) {
+        pt7[(size_t)XW * PPQ_NT7E + i] = R(0);
+        pt7T[(size_t)i * NN + XW] = R(0);
+      }
+      for (int i = tid; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = R(0);
+      if (tid == 0) epair[XW] = 0.0;
+      continue;
+    }
+    if (tid < 36) {
+      R to = tid == 35 ? R(0)
+                       : R(tid < 3 ? t1[X * 3 + tid] : (tid < 6 ? t1[W * 3 + tid - 3] : t2[(size_t)XW * PPQ_NA2 + tid - 6]));
+      fac[2 * tid] = to;
+      fac[2 * tid + 1] = -to;
+    }
+    const R* g = g2 + (size_t)XW * PPQ_NG2;
+    for (int i = tid; i < PPQ_NG2; i += blockDim.x) {
+      const R v = g[i];
+#pragma unroll
+      for (int c = 0; c < PPQ_H2_NCODE; ++c) gsv[c * PPQ_NG2 + i] = R(ppq_h2_code[c]) * v;
+    }
+    for (int i = tid; i < ClosureSmem::kM; i += blockDim.x) M[i] = R(0);
+    __syncthreads();
+    for (int el = tid; el < PPQ_H2_NEL; el += blockDim.x) {
+      R acc = R(0);
+      for (int p = hptr[el]; p < hptr[el + 1]; ++p) acc += gsv[cj[p]];
+      M[hel[el]] = acc;
+    }
+    __syncthreads();
+    const R h00 = M[PPQ_EL00P];
+    // right: M <- M exp(I), along this thread's row
+    for (int e = r0; e < r1; e += 4) {
+      int ti[4], si[4];
+      R f[4], mt[4], ms[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t w = srl[e + k];
+        ti[k] = rowbase + (w & 0xFFF);
+        si[k] = rowbase + ((w >> 12) & 0xFFF);
+        f[k] = fac[w >> 24];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { ms[k] = M[si[k]]; mt[k] = M[ti[k]]; }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) M[ti[k]] = mt[k] + f[k] * ms[k];
+    }
+    __syncthreads();
+    // left: M <- exp(-I) M, along this thread's column
+    for (int e = l0; e < l1; e += 4) {
+      int ti[4], si[4];
+      R f[4], mt[4], ms[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t w = sll[e + k];
+        ti[k] = colbase + (w & 0xFFF);
+        si[k] = colbase + ((w >> 12) & 0xFFF);
+        f[k] = fac[w >> 24];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { ms[k] = M[si[k]]; mt[k] = M[ti[k]]; }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) M[ti[k]] = mt[k] - f[k] * ms[k];
+    }
+    __syncthreads();
+    for (int i = tid; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = M[oel[i]];
+    for (int i = tid; i < PPQ_NT7E; i += blockDim.x) {
+      R v = M[oel[PPQ_NS36 + i]];
+      pt7[(size_t)XW * PPQ_NT7E + i] = v;
+      pt7T[(size_t)i * NN + (size_t)W * N + X] = v;  // stored [e][W][X]
+    }
+    for (int i = tid; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = M[oel[PPQ_NS36 + PPQ_NT7E + i]];
+    if (tid == 0) epair[XW] = double(M[PPQ_EL00P]) - double(h00);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- contractions
 template <typename R>
 __device__ __forceinline__ R block_sum(R v, R* red) {

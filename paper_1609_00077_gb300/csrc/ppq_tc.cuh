@@ -370,11 +370,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int16_t* c = ppq_c9q + 4 * ch;
           const float* cy = clT + (size_t)c[0] * NNp + Y;   // Cl[W,Y][c3] at W * N
           const float* cz = clT + (size_t)c[1] * NNp + Z;   // Cl[W,Z][c4] at W * N
+          // batches of 8 W: whole batches load all 16 values before use
           float v0 = 0.f, v1 = 0.f;
+          const float* py = cy;
+          const float* pz = cz;
 #pragma unroll
-          for (int W = 0; W < NW; W += 2) {
-            if (W < N) v0 = fmaf(D[W] * __ldg(cy + (size_t)W * N), __ldg(cz + (size_t)W * N), v0);
-            if (W + 1 < N) v1 = fmaf(D[W + 1] * __ldg(cy + (size_t)(W + 1) * N), __ldg(cz + (size_t)(W + 1) * N), v1);
+          for (int W0 = 0; W0 < NW; W0 += 8) {
+            if (W0 + 8 <= N) {
+              float a[8], bz[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) { a[i] = __ldg(py + i * N); bz[i] = __ldg(pz + i * N); }
+#pragma unroll
+              for (int i = 0; i < 8; i += 2) {
+                v0 = fmaf(D[W0 + i] * a[i], bz[i], v0);
+                v1 = fmaf(D[W0 + i + 1] * a[i + 1], bz[i + 1], v1);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                if (W0 + i < N) v0 = fmaf(D[W0 + i] * __ldg(py + i * N), __ldg(pz + i * N), v0);
+            }
+            py += 8 * N;
+            pz += 8 * N;
           }
           acc[c[2]] += 0.5f * float(c[3]) * (v0 + v1);
         }

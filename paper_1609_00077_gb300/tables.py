@@ -479,6 +479,55 @@ def pair_transform_lists(T, L):
             np.array(left, dtype=np.int64), np.array(lptr, dtype=np.int64))
 
 
+def pair_sector_lists(T, L, group=4):
+    """The pair closure's sweeps per sector: every row r of sector q goes
+    through the same sequence M[r, a] += t_o sg M[r, b] (right, exp(I)) and
+    every column c through M[b', c] -= t_o sg M[a', c] (left, exp(-I)), with
+    the positions a, b inside the sector.  Entries of one operator touch
+    distinct targets that are never sources (each O_o is nilpotent), so the
+    lists are cut into groups of `group` entries of one operator.  A group is
+    padded with entries whose target is the group's first source and whose
+    factor is zero (slot 70), which leave M unchanged.  Offsets are in the
+    padded shared layout (row stride dim + 1): right entries step along a
+    row, left entries along a column (offset = position * (dim + 1)).
+    Entry: target offset | source offset << 12 | factor slot << 24, factor
+    slot 2 o + (sign < 0)."""
+    ops = []
+    for k in range(3):
+        ops.append(T.site_ops2a[T.site_ops2a[:, 0] == k])
+    for k in range(3):
+        ops.append(T.site_ops2b[T.site_ops2b[:, 0] == k])
+    for k in range(29):
+        ops.append(T.pair_ops[T.pair_ops[:, 0] == k])
+    nq = len(L.sectors)
+    rl, ll = [[] for _ in range(nq)], [[] for _ in range(nq)]
+    enc = lambda tg, sc, f: tg | (sc << 12) | (f << 24)
+    for o, tab in enumerate(ops):
+        cur_r, cur_l = [[] for _ in range(nq)], [[] for _ in range(nq)]
+        for _, src, dst, sg in tab:
+            q = int(L.sec_of[src])
+            assert int(L.sec_of[dst]) == q
+            a, b, f = int(L.pos[src]), int(L.pos[dst]), 2 * o + (1 if sg < 0 else 0)
+            dp = L.dim[q] + 1
+            cur_r[q].append((a, b, f))             # M[r, a] += t sg M[r, b]
+            cur_l[q].append((b * dp, a * dp, f))   # M[b, c] -= t sg M[a, c]
+        for q in range(nq):
+            for cur, lst in ((cur_r[q], rl[q]), (cur_l[q], ll[q])):
+                for i in range(0, len(cur), group):
+                    chunk = cur[i:i + group]
+                    first_src = chunk[0][1]
+                    chunk = chunk + [(first_src, first_src, 70)] * (group - len(chunk))
+                    lst.extend(enc(*e) for e in chunk)
+    def flat(lists):
+        ptr = [0]
+        for x in lists:
+            ptr.append(ptr[-1] + len(x))
+        return np.array([e for x in lists for e in x], dtype=np.int64), np.array(ptr, dtype=np.int64)
+    r, rp = flat(rl)
+    l, lp = flat(ll)
+    return r, rp, l, lp
+
+
 def site_transform_lists(T):
     right, left, rptr, lptr = [], [], [0], [0]
     for k in range(3):
@@ -560,6 +609,42 @@ def emit_header(path):
     out += [f"#define PPQ_PR_N {len(pr)}", f"#define PPQ_PL_N {len(pl)}",
             _c_array("ppq_p_right", "int32_t", pr), _c_array("ppq_p_rptr", "int32_t", prp),
             _c_array("ppq_p_left", "int32_t", pl), _c_array("ppq_p_lptr", "int32_t", plp)]
+    # compact forms for the persistent pair-closure kernel: per-sector sweep
+    # lists (groups of 4), state -> (sector, position), sector base and size,
+    # and the Hamiltonian CSR with (j, 2c) packed in 16 bits
+    sr, srp, sl, slp = pair_sector_lists(T, L)
+    assert np.all(np.abs(2 * c2 - np.round(2 * c2)) == 0) and np.abs(2 * c2).max() <= 127
+    jc = np.asarray(j2)
+    PPQ_NG2_VALUE = defs["PPQ_NG2"]
+    assert int(max(j2)) < PPQ_NG2_VALUE
+    out += [f"#define PPQ_H2_NNZ {len(jc)}", f"#define PPQ_NSEC {len(L.sectors)}", f"#define PPQ_PSR_N {len(sr)}", f"#define PPQ_PSL_N {len(sl)}",
+            _c_array("ppq_ps_right", "int32_t", sr), _c_array("ppq_ps_rptr", "int16_t", srp),
+            _c_array("ppq_ps_left", "int32_t", sl), _c_array("ppq_ps_lptr", "int16_t", slp),
+            _c_array("ppq_st_sec", "int8_t", L.sec_of), _c_array("ppq_st_pos", "int8_t", L.pos),
+            _c_array("ppq_sec_dim", "int8_t", np.array(L.dim))]
+    # thread -> two-site state, grouped by sector (largest first) so that the
+    # lanes of a warp walk the same list
+    order = sorted(range(256), key=lambda st: (-L.dim[L.sec_of[st]], L.sec_of[st], L.pos[st]))
+    # gather terms as code * NG2 + j, code indexing the coefficients below
+    codes = [-1.0, -0.5, 0.5, 1.0, 2.0]
+    cidx = np.array([codes.index(float(x)) for x in c2], dtype=np.int64)
+    out += [_c_array("ppq_th_state", "int16_t", np.array(order)),
+            _c_array("ppq_h2_cj", "uint16_t", cidx * PPQ_NG2_VALUE + np.asarray(j2).astype(np.int64)),
+            "#define PPQ_H2_NCODE 5", _c_array("ppq_h2_code", "float", np.array(codes))]
+    # padded sector layout of the persistent kernel's shared-memory copy: rows
+    # of sector q are dim_q + 1 apart (odd or coprime strides, no bank
+    # conflicts when one thread walks each row)
+    pbase, off = [], 0
+    for dq in L.dim:
+        pbase.append(off)
+        off += dq * (dq + 1)
+    def padded(e):
+        q = int(np.searchsorted(np.array(L.base), e, side="right") - 1)
+        r, c = divmod(int(e) - L.base[q], L.dim[q])
+        return pbase[q] + r * (L.dim[q] + 1) + c
+    out += [f"#define PPQ_BLKP {off}", _c_array("ppq_sec_pbase", "int16_t", np.array(pbase)),
+            _c_array("ppq_h2_elp", "int16_t", np.array([padded(e) for e in e2]))]
+    padded_of = padded
     # outputs of the pair closure: G row, T7 entries, column-0 entries, element (0,0)
     g_el = [L.elem(0, 16 * a + b) for a, b in st]
     t7 = t7_channels(T)
@@ -571,6 +656,10 @@ def emit_header(path):
             f"#define PPQ_EL00 {L.elem(0, 0)}",
             _c_array("ppq_g_el", "int16_t", g_el), _c_array("ppq_t7_el", "int16_t", t7_el),
             _c_array("ppq_col0_el", "int16_t", col0)]
+    out += [f"#define PPQ_EL00P {padded_of(L.elem(0, 0))}",
+            _c_array("ppq_g_elp", "int16_t", np.array([padded_of(e) for e in g_el])),
+            _c_array("ppq_t7_elp", "int16_t", np.array([padded_of(e) for e in t7_el])),
+            _c_array("ppq_col0_elp", "int16_t", np.array([padded_of(e) for e in col0]))]
     # link / transform operators on the 36-state sector
     sop = sector_pair_ops(T)
     sptr = [0]
