@@ -19,9 +19,10 @@
 // 16-byte core matrices, K-adjacent cores 128 B apart (leading byte offset),
 // 8-row groups 256 B apart (stride byte offset); one K stage is 8 TF32 values.
 //
-// Roles (288 threads): warps 0-3 epilogue (TMEM lane quarter = warp), warps
-// 4-7 producers (A generation; thread 128 also issues the bulk copies of B
-// and of the Cl slices), warp 8 TMEM allocation and MMA issue (lane 0).
+// Roles (416 threads): warps 0-7 epilogue (TMEM lane quarter = warp % 4; the
+// two warps of a quarter take alternate channels into separate row sums),
+// warps 8-11 producers (A generation; thread 256 also issues the bulk copies
+// of B and of the Cl slices), warp 12 TMEM allocation and MMA issue (lane 0).
 // Each CTA writes the sums of its rows (all 29 outputs) to its own slot of
 // a partial buffer, part[slot][p][o]; k_t9_reduce adds the slots in a fixed
 // order, so the result does not depend on scheduling.
@@ -37,7 +38,10 @@ namespace tc {
 constexpr int kStages = 4;
 constexpr int kRows = 128;                 // MMA M, rows per tile
 constexpr int kMaxCols = 256;              // TMEM columns per accumulator buffer
-constexpr int kThreads = 288;
+constexpr int kThreads = 416;
+constexpr int kEpiThreads = 256;           // warps 0-7
+constexpr int kProdBase = 256;             // warps 8-11
+constexpr int kMmaWarp = 12;
 constexpr long long kWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
 constexpr int kChunkFields = 12;           // c1, c2, n_g, n_cols, g[4], q[4]
 
@@ -163,7 +167,7 @@ struct Smem {
   static constexpr int kNBars = 4 * kStages + 9;
   static size_t __host__ __device__ slices() { return (size_t)kStages * kStageBytes; }
   static size_t __host__ __device__ t9(int NNp) { return slices() + 2 * 2 * (size_t)NNp * 4; }
-  static size_t __host__ __device__ rows(int NNp) { return t9(NNp) + (size_t)kRows * PPQ_NA2 * 4; }
+  static size_t __host__ __device__ rows(int NNp) { return t9(NNp) + 2 * (size_t)kRows * PPQ_NA2 * 4; }
   static size_t __host__ __device__ bars(int NNp) { return rows(NNp) + (size_t)kRows * 2 * 4; }
   static size_t __host__ __device__ total(int NNp) { return bars(NNp) + kNBars * 8 + 16; }
 };
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* sA = reinterpret_cast<float*>(sm);                              // [S][2][128 x 8]
   float* sB = reinterpret_cast<float*>(sm + kStages * 2 * Smem::kA);     // [S][2][256 x 8]
   float* sCl = reinterpret_cast<float*>(sm + Smem::slices());            // [2][2][NNp]
-  float* st9 = reinterpret_cast<float*>(sm + Smem::t9(NNp));             // [128][29]
+  float* st9 = reinterpret_cast<float*>(sm + Smem::t9(NNp));             // [2][128][29]
   int* rowYZ = reinterpret_cast<int*>(sm + Smem::rows(NNp));             // [128][2]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars(NNp));
   uint64_t* fullA = bars;                     // [S] producers wrote A (count 128)
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* slf = bars + 4 * kStages;         // [2] Cl slices landed (count 1 + tx)
   uint64_t* sle = slf + 2;                    // [2] producers done with the slices (count 128)
   uint64_t* tmf = sle + 2;                    // [2] accumulator buffer ready (commit)
-  uint64_t* tme = tmf + 2;                    // [2] epilogue done with the buffer (count 128)
+  uint64_t* tme = tmf + 2;                    // [2] epilogue done with the buffer (count 256)
   uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + Smem::kNBars);
   volatile int* abort = reinterpret_cast<volatile int*>(tbase + 1);
 
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&slf[b], 1);
       mbar_init(&sle[b], 128);
       mbar_init(&tmf[b], 1);
-      mbar_init(&tme[b], 128);
+      mbar_init(&tme[b], kEpiThreads);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,9 +230,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     rowYZ[2 * tid] = Y;
     rowYZ[2 * tid + 1] = Z;
-    for (int o = 0; o < PPQ_NA2; ++o) st9[tid * PPQ_NA2 + o] = 0.f;
   }
-  if (warp == 8) {
+  if (tid < kEpiThreads)
+    for (int o = 0; o < PPQ_NA2; ++o) st9[tid * PPQ_NA2 + o] = 0.f;
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase)),
                  "r"(2 * kMaxCols)
                  : "memory");
@@ -239,9 +244,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_after();
   const uint32_t tmem = *tbase;
 
-  if (warp >= 4 && warp < 8) {
+  if (warp >= 8 && warp < kMmaWarp) {
     // ------------------------------------------------------------ producers
-    const int r = tid - 128;
+    const int r = tid - kProdBase;
     const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
     const bool lead = (r == 0);
     int issued_b = 0, issued_s = 0;  // stage / slice fills issued by the lead thread
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_drain(&fullB[k % kStages], (k / kStages) & 1);
       for (int k = (issued_s > 2 ? issued_s - 2 : 0); k < issued_s; ++k) mbar_drain(&slf[k & 1], (k >> 1) & 1);
     }
-  } else if (warp == 8) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
       int it = 0;
@@ -347,10 +352,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int r = tid;
+    const int r = tid & (kRows - 1), half = tid >> 7;
     const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    float* acc = st9 + r * PPQ_NA2;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    float* acc = st9 + ((size_t)half * kRows + r) * PPQ_NA2;
     for (int l = 0; l < nloc; ++l) {
       const int16_t* h = chunks + (size_t)(cb + l) * kChunkFields;
       const int ng = h[2];
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld16(tmem + lane_base + (uint32_t)(b * kMaxCols + j * Npad + 16 * i), D + 16 * i);
         if (Y < 0) continue;
         const int q = h[8 + j];
-        for (int ch = ppq_c9qp[q]; ch < ppq_c9qp[q + 1]; ++ch) {
+        for (int ch = ppq_c9qp[q] + half; ch < ppq_c9qp[q + 1]; ch += 2) {
           const int16_t* c = ppq_c9q + 4 * ch;
           const float* cy = clT + (size_t)c[0] * NNp + Y;   // Cl[W,Y][c3] at W * N
           const float* cz = clT + (size_t)c[1] * NNp + Z;   // Cl[W,Z][c4] at W * N
@@ -399,18 +404,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_before();
       mbar_arrive(&tme[b]);
     }
-    if (Y >= 0) {
-      float* dst = part + ((size_t)(blockIdx.x % nslot) * P + (size_t)tile * kRows + r) * PPQ_NA2;
-      for (int o = 0; o < PPQ_NA2; ++o) dst[o] = acc[o];
-    }
   }
   tc_before();
+  __syncthreads();
+  if (tid < kRows) {
+    // both halves' sums, in a fixed order
+    const int p = tile * kRows + tid;
+    if (p < P) {
+      float* dst = part + ((size_t)(blockIdx.x % nslot) * P + p) * PPQ_NA2;
+      for (int o = 0; o < PPQ_NA2; ++o) dst[o] = st9[tid * PPQ_NA2 + o] + st9[(kRows + tid) * PPQ_NA2 + o];
+    }
+  }
   __syncthreads();
   if (*abort && tid == 0) {
     atomicExch(err, 1);
     part[((size_t)(blockIdx.x % nslot) * P + (size_t)tile * kRows) * PPQ_NA2] = __int_as_float(0x7fc00000);  // NaN
   }
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     tc_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kMaxCols)
                  : "memory");
