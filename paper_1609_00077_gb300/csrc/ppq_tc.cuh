@@ -19,10 +19,12 @@
 // 16-byte core matrices, K-adjacent cores 128 B apart (leading byte offset),
 // 8-row groups 256 B apart (stride byte offset); one K stage is 8 TF32 values.
 //
-// Roles (416 threads): warps 0-7 epilogue (TMEM lane quarter = warp % 4; the
-// two warps of a quarter take alternate channels into separate row sums),
-// warps 8-11 producers (A generation; thread 256 also issues the bulk copies
-// of B and of the Cl slices), warp 12 TMEM allocation and MMA issue (lane 0).
+// Roles (672 threads): warps 0-15 epilogue (TMEM lane quarter = warp % 4; the
+// four warps of a quarter take the channels of output o = warp / 4 mod 4, so
+// every (row, o) sum has one owner and a fixed order; D is read from TMEM
+// eight columns at a time next to the loads of the Cl factors), warps 16-19
+// producers (A generation; thread 512 also issues the bulk copies of B and of
+// the Cl slices), warp 20 TMEM allocation and MMA issue (lane 0).
 // Each CTA writes the sums of its rows (all 29 outputs) to its own slot of
 // a partial buffer, part[slot][p][o]; k_t9_reduce adds the slots in a fixed
 // order, so the result does not depend on scheduling.
@@ -38,10 +40,13 @@ namespace tc {
 constexpr int kStages = 4;
 constexpr int kRows = 128;                 // MMA M, rows per tile
 constexpr int kMaxCols = 256;              // TMEM columns per accumulator buffer
-constexpr int kThreads = 416;
-constexpr int kEpiThreads = 256;           // warps 0-7
-constexpr int kProdBase = 256;             // warps 8-11
-constexpr int kMmaWarp = 12;
+constexpr int kEpiThreads = 512;           // warps 0-15
+constexpr int kProdBase = kEpiThreads;     // warps 16-19
+constexpr int kProdWarp0 = kProdBase / 32;
+constexpr int kMmaWarp = kProdWarp0 + kRows / 32;
+constexpr int kThreads = (kMmaWarp + 1) * 32;
+static_assert(kEpiThreads % kRows == 0 && kEpiThreads / kRows == 4, "four epilogue groups of 128 rows");
+static_assert(kThreads == 672, "20 role warps + the MMA warp");
 constexpr long long kWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
 constexpr int kChunkFields = 12;           // c1, c2, n_g, n_cols, g[4], q[4]
 
@@ -134,6 +139,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 8 consecutive TMEM columns of this thread's lane, waited on before return
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -167,7 +184,7 @@ struct Smem {
   static constexpr int kNBars = 4 * kStages + 9;
   static size_t __host__ __device__ slices() { return (size_t)kStages * kStageBytes; }
   static size_t __host__ __device__ t9(int NNp) { return slices() + 2 * 2 * (size_t)NNp * 4; }
-  static size_t __host__ __device__ rows(int NNp) { return t9(NNp) + 2 * (size_t)kRows * PPQ_NA2 * 4; }
+  static size_t __host__ __device__ rows(int NNp) { return t9(NNp) + (size_t)kRows * PPQ_NA2 * 4; }
   static size_t __host__ __device__ bars(int NNp) { return rows(NNp) + (size_t)kRows * 2 * 4; }
   static size_t __host__ __device__ total(int NNp) { return bars(NNp) + kNBars * 8 + 16; }
 };
@@ -185,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* sA = reinterpret_cast<float*>(sm);                              // [S][2][128 x 8]
   float* sB = reinterpret_cast<float*>(sm + kStages * 2 * Smem::kA);     // [S][2][256 x 8]
   float* sCl = reinterpret_cast<float*>(sm + Smem::slices());            // [2][2][NNp]
-  float* st9 = reinterpret_cast<float*>(sm + Smem::t9(NNp));             // [2][128][29]
+  float* st9 = reinterpret_cast<float*>(sm + Smem::t9(NNp));             // [128][29]
   int* rowYZ = reinterpret_cast<int*>(sm + Smem::rows(NNp));             // [128][2]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars(NNp));
   uint64_t* fullA = bars;                     // [S] producers wrote A (count 128)
@@ -195,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* slf = bars + 4 * kStages;         // [2] Cl slices landed (count 1 + tx)
   uint64_t* sle = slf + 2;                    // [2] producers done with the slices (count 128)
   uint64_t* tmf = sle + 2;                    // [2] accumulator buffer ready (commit)
-  uint64_t* tme = tmf + 2;                    // [2] epilogue done with the buffer (count 256)
+  uint64_t* tme = tmf + 2;                    // [2] epilogue done with the buffer (count 512)
   uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + Smem::kNBars);
   volatile int* abort = reinterpret_cast<volatile int*>(tbase + 1);
 
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     rowYZ[2 * tid] = Y;
     rowYZ[2 * tid + 1] = Z;
   }
-  if (tid < kEpiThreads)
+  if (tid < kRows)
     for (int o = 0; o < PPQ_NA2; ++o) st9[tid * PPQ_NA2 + o] = 0.f;
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase)),
@@ -244,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_after();
   const uint32_t tmem = *tbase;
 
-  if (warp >= 8 && warp < kMmaWarp) {
+  if (warp >= kProdWarp0 && warp < kMmaWarp) {
     // ------------------------------------------------------------ producers
     const int r = tid - kProdBase;
     const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
@@ -352,10 +369,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int r = tid & (kRows - 1), half = tid >> 7;
-    const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
+    const int r = tid & (kRows - 1), grp = tid >> 7;   // grp = warp / 4
+    const bool valid = rowYZ[2 * r] >= 0;
+    const int Y = valid ? rowYZ[2 * r] : 0, Z = valid ? rowYZ[2 * r + 1] : 0;  // safe addresses
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    float* acc = st9 + ((size_t)half * kRows + r) * PPQ_NA2;
+    float* acc = st9 + (size_t)r * PPQ_NA2;
     for (int l = 0; l < nloc; ++l) {
       const int16_t* h = chunks + (size_t)(cb + l) * kChunkFields;
       const int ng = h[2];
@@ -365,40 +383,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_after();
       for (int j = 0; j < ng; ++j) {
-        float D[NW];
-#pragma unroll
-        for (int i = 0; i < NW / 16; ++i)
-          tmem_ld16(tmem + lane_base + (uint32_t)(b * kMaxCols + j * Npad + 16 * i), D + 16 * i);
-        if (Y < 0) continue;
         const int q = h[8 + j];
-        for (int ch = ppq_c9qp[q] + half; ch < ppq_c9qp[q + 1]; ch += 2) {
+        const uint32_t col = tmem + lane_base + (uint32_t)(b * kMaxCols + j * Npad);
+        for (int ch = ppq_c9qp[q]; ch < ppq_c9qp[q + 1]; ++ch) {
           const int16_t* c = ppq_c9q + 4 * ch;
-          const float* cy = clT + (size_t)c[0] * NNp + Y;   // Cl[W,Y][c3] at W * N
-          const float* cz = clT + (size_t)c[1] * NNp + Z;   // Cl[W,Z][c4] at W * N
-          // batches of 8 W: whole batches load all 16 values before use
+          if ((c[2] & 3) != grp) continue;                    // warp-uniform
+          const float* py = clT + (size_t)c[0] * NNp + Y;     // Cl[W,Y][c3] at W * N
+          const float* pz = clT + (size_t)c[1] * NNp + Z;     // Cl[W,Z][c4] at W * N
           float v0 = 0.f, v1 = 0.f;
-          const float* py = cy;
-          const float* pz = cz;
 #pragma unroll
           for (int W0 = 0; W0 < NW; W0 += 8) {
+            float a[8], bz[8], D[8];
             if (W0 + 8 <= N) {
-              float a[8], bz[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) { a[i] = __ldg(py + i * N); bz[i] = __ldg(pz + i * N); }
-#pragma unroll
-              for (int i = 0; i < 8; i += 2) {
-                v0 = fmaf(D[W0 + i] * a[i], bz[i], v0);
-                v1 = fmaf(D[W0 + i + 1] * a[i + 1], bz[i + 1], v1);
-              }
             } else {
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (W0 + i < N) v0 = fmaf(D[W0 + i] * __ldg(py + i * N), __ldg(pz + i * N), v0);
+              for (int i = 0; i < 8; ++i) {
+                a[i] = W0 + i < N ? __ldg(py + i * N) : 0.f;
+                bz[i] = W0 + i < N ? __ldg(pz + i * N) : 0.f;
+              }
+            }
+            tmem_ld8(col + (uint32_t)W0, D);
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+              v0 = fmaf(D[i] * a[i], bz[i], v0);
+              v1 = fmaf(D[i + 1] * a[i + 1], bz[i + 1], v1);
             }
             py += 8 * N;
             pz += 8 * N;
           }
-          acc[c[2]] += 0.5f * float(c[3]) * (v0 + v1);
+          if (valid) acc[c[2]] += 0.5f * float(c[3]) * (v0 + v1);
         }
       }
       tc_before();
@@ -408,11 +423,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_before();
   __syncthreads();
   if (tid < kRows) {
-    // both halves' sums, in a fixed order
+    // this CTA's row sums to its slot
     const int p = tile * kRows + tid;
     if (p < P) {
       float* dst = part + ((size_t)(blockIdx.x % nslot) * P + p) * PPQ_NA2;
-      for (int o = 0; o < PPQ_NA2; ++o) dst[o] = st9[tid * PPQ_NA2 + o] + st9[(kRows + tid) * PPQ_NA2 + o];
+      for (int o = 0; o < PPQ_NA2; ++o) dst[o] = st9[tid * PPQ_NA2 + o];
     }
   }
   __syncthreads();
