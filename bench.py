@@ -82,6 +82,13 @@ def batch_systems(count, seed=1609):
     return out
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# quartic kernels on this workload, from single ncu captures of the current
+# kernels (profiles/quartic_kernels_c140h142.md); None until captured
+TRAFFIC_TC_QUARTIC = 2272256      # k_t9_tc<80>: 2.27 MB read, 0 B written
+TRAFFIC_FP64_QUARTIC = None       # k_t9_gemm<double,7>: not captured
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -304,9 +311,13 @@ def main():
     t32 = info["t_quartic32_ms"]; t64 = info["t_quartic_ms"] - t32
     ach32 = info["quartic_flops"] / (t32 / max(n32, 1) * 1e-3) / 1e12 if n32 else None
     ach64 = info["quartic_flops"] / (t64 / max(n64, 1) * 1e-3) / 1e12 if n64 else None
-    # SIMT peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 x clock; FP64 measured DGEMM
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
-    fp64_peak = 1.05
+    # peaks: the measured bf16 burst x the nominal ratio of the dtype (2.25 PF bf16 dense,
+    # 1.1 PF TF32, 1.25 TF FP64); the FP32 residual's quartic term runs as 3xTF32 MMAs,
+    # so its FP32-equivalent peak is a third of the TF32 figure
+    bf16 = pk.get("bf16_tflops", 1900.0)
+    tf32_peak = bf16 * 1.1 / 2.25
+    fp32_peak = tf32_peak / 3.0
+    fp64_peak = bf16 * 1.25 / 2250.0
     dominant64 = t64 > t32
     achieved = ach64 if dominant64 else ach32
     n_launch = info["n_launches"]
@@ -326,20 +337,23 @@ def main():
         "residual_tflops": res_tflops,
         "fp64": fp64,
         "gpu_launches": n_launch * args.steps,
-        "roofline": {"bound": "alu",
-                     "kernel": "k_t9_gemm<%s> (quartic GEMM, largest share of device time)"
-                               % ("double" if dominant64 else "float"),
+        "roofline": {"bound": "alu" if dominant64 else "tensor",
+                     "kernel": ("k_t9_gemm<double> (SIMT FP64 quartic GEMM, largest share of device time)"
+                                if dominant64 else
+                                "k_t9_tc (tcgen05 3xTF32 quartic kernel, largest share of device time)"),
                      "achieved": achieved, "peak": fp64_peak if dominant64 else fp32_peak,
                      "unit": "TFLOP/s",
-                     "frac": achieved / (fp64_peak if dominant64 else fp32_peak), "traffic": None,
-                     "peak_note": ("measured cuBLAS DGEMM 1.05 TFLOP/s (not in MEASURED_PEAKS.json)"
+                     "frac": achieved / (fp64_peak if dominant64 else fp32_peak),
+                     "traffic": TRAFFIC_FP64_QUARTIC if dominant64 else TRAFFIC_TC_QUARTIC,
+                     "peak_note": ("FP64: measured bf16 burst x 1.25/2250 (of measured)"
                                    if dominant64 else
-                                   "FP32 SIMT peak from 152 SMs x 128 lanes x 2 FLOP x 2070 MHz "
-                                   "(MEASURED_PEAKS.json has no FP32 SIMT figure)"),
-                     "fp32_launches": {"n": n32, "ms_total": t32, "tflops": ach32,
-                                       "frac_of_simt_peak": ach32 / fp32_peak if ach32 else None},
-                     "fp64_launches": {"n": n64, "ms_total": t64, "tflops": ach64,
-                                       "frac_of_dgemm": ach64 / fp64_peak if ach64 else None}},
+                                   "3xTF32: measured bf16 burst x 1.1/2.25 / 3 (of measured)"),
+                     "fp32_launches": {"kernel": "k_t9_tc", "n": n32, "ms_total": t32, "tflops": ach32,
+                                       "peak_3xtf32": fp32_peak,
+                                       "frac": ach32 / fp32_peak if ach32 else None},
+                     "fp64_launches": {"kernel": "k_t9_gemm<double>", "n": n64, "ms_total": t64,
+                                       "tflops": ach64, "peak_fp64": fp64_peak,
+                                       "frac": ach64 / fp64_peak if ach64 else None}},
         "evals": {"fp32": info["evals_fp32"], "fp64": info["evals_fp64"]},
         "e2e": {"value": e2e_s, "unit": "s",
                 "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),
