@@ -53,7 +53,10 @@ typedef struct {
                       /*     ||R|| <= switch_tol or stagnation, then FP64      */
   double switch_tol;  /* 1e-5                                                  */
   double r_tol;       /* converged when ||R||_2 <= r_tol ...  (1e-10)           */
-  double e_tol;       /* ... and |dE| <= e_tol (1e-12)                          */
+  double e_tol;       /* ... and |dE| <= e_tol (1e-10): dE between successive   */
+                      /*     FP64 iterates, or (defect-correction polish) the   */
+                      /*     energy change of one more Jacobi step, evaluated   */
+                      /*     from the closures alone                            */
   int max_iter;       /* 200                                                   */
   int diis_dim;       /* 8 (0 disables DIIS)                                    */
   int diis_start;     /* 3                                                     */

@@ -1022,6 +1022,26 @@ struct Solver {
 
   int step_plain(Diis& d, int it) { return diis_step(d, w->t, w->r, it); }
 
+  // Energy after one plain Jacobi step t + R / D (w->r holds R(t)), from the
+  // closures alone: the site and pair closures in FP64 and the FP64 sum, about
+  // a twentieth of a full FP64 residual.  Scratch: w->tb, w->del and the
+  // closure buffers, all rewritten by the next evaluation.
+  int jacobi_energy(double* e_next) {
+    double* tn = w->tb;
+    ppq::k_jacobi<<<lb, 256, 0, s>>>(L, N, w->t, w->r, w->fo, w->fv, o.level_shift, tn, w->del);
+    ppq::k_site_closure<double><<<N, 64, 0, s>>>(N, w->g1d, tn, (double*)w->hs, w->esite);
+    int rc = launch_pair_closure<double>(N, w->g2d, tn, tn + 3 * N, (double*)w->pg, (double*)w->pt7,
+                                         (double*)w->pc0, w->epair, (double*)w->pt7T, s);
+    if (rc) return rc;
+    k_rowsum<<<1, 256, 0, s>>>(0, 0, w->part, N, w->esite, w->epair, w->scal);
+    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    w->n_launches += 4;
+    *e_next = w->host[0];
+    if (trace_on()) fprintf(stderr, "ppq jacobi-step energy %.12f\n", *e_next);
+    return 0;
+  }
+
   // Lambda equations at the converged t in w->t: grad_t L(t, lambda) = 0 by
   // Jacobi steps lambda += grad / D with DIIS (FP64)
   int solve_lambda(double tol, int max_iter, double* res_out, int* iters_out) {
@@ -1049,11 +1069,13 @@ struct Solver {
   }
 
   // FP64 defect correction: w->r holds R_64(t) on entry.  Solves
-  // r + J delta = 0 to a relative accuracy of ~3e-4 with forward-difference
-  // Jacobian products of FP32 residuals (perturbation eta = 3e-4 in max norm,
-  // far above the FP32 resolution of t), then t <- t + delta.
+  // r + J delta = 0 to a relative accuracy of 1e-3 with forward-difference
+  // Jacobian products of FP32 residuals (perturbation eta = 1e-3 in max norm,
+  // far above the FP32 resolution of t), then t <- t + delta.  The
+  // finite-difference model itself is good to about 2e-3 on the PPP
+  // workloads, so a tighter inner solve gains nothing per outer step.
   int defect_correction(int* inner_out, int* it_io) {
-    const double eta = 1e-3, tol = 3e-4;
+    const double eta = 1e-3, tol = 1e-3;
     double* tb = w->tb;
     double* r64 = w->r64;
     double* rb = w->rb;
@@ -1110,7 +1132,7 @@ extern "C" {
 int ppq_default_opts(ppq_opts* o) {
   if (!o) return fail(-2, "null opts");
   o->K = 2; o->K_H = 0; o->precision = 0;
-  o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-12;
+  o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-10;
   o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
   o->level_shift = 0.0; o->guess = 0; o->profile = 0; o->polish = 1;
   return 0;
@@ -1261,7 +1283,11 @@ int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o
       e_old = e;
       have_old = true;
       if (res <= o.r_tol) {
-        // only the energy test is left: a Jacobi step changes E by O(|R|^2)
+        // only the energy test is left: converged if one more Jacobi step
+        // would change E by at most e_tol (energy from the closures alone)
+        double e_next = 0.0;
+        if ((rc = S.jacobi_energy(&e_next)) != 0) return rc;
+        if (fabs(e_next - e) <= o.e_tol) { status = 0; break; }
         D.reset();
         if ((rc = S.step_plain(D, 1)) != 0) return rc;
         continue;
