@@ -86,7 +86,7 @@ def batch_systems(count, seed=1609):
 # quartic kernels on this workload, from single ncu captures of the current
 # kernels (profiles/quartic_kernels_c140h142.md); None until captured
 TRAFFIC_TC_QUARTIC = 2272256      # k_t9_tc<80>: 2.27 MB read, 0 B written
-TRAFFIC_FP64_QUARTIC = None       # k_t9_gemm<double,7>: not captured
+TRAFFIC_FP64_QUARTIC = None       # k_t9_tc64<80>: not captured yet
 
 
 def peaks():
@@ -317,7 +317,10 @@ def main():
     bf16 = pk.get("bf16_tflops", 1900.0)
     tf32_peak = bf16 * 1.1 / 2.25
     fp32_peak = tf32_peak / 3.0
-    fp64_peak = bf16 * 1.25 / 2250.0
+    fp64_alu_peak = bf16 * 1.25 / 2250.0
+    # the FP64 residual's quartic term runs as exact integer splitting on the
+    # tensor cores: 21 TF32 MMAs per FP64 product
+    fp64_peak = tf32_peak / 21.0
     dominant64 = t64 > t32
     achieved = ach64 if dominant64 else ach32
     n_launch = info["n_launches"]
@@ -338,23 +341,25 @@ def main():
         "residual_tflops": res_tflops,
         "fp64": fp64,
         "gpu_launches": n_launch * args.steps,
-        "roofline": {"bound": "alu" if dominant64 else "tensor",
-                     "kernel": ("k_t9_gemm<double> (SIMT FP64 quartic GEMM, largest share of device time)"
-                                if dominant64 else
-                                "k_t9_tc (tcgen05 3xTF32 quartic kernel, largest share of device time)"),
+        "roofline": {"bound": "tensor",
+                     "kernel": ("k_t9_tc64 (FP64 quartic term, exact splitting on tcgen05; largest share"
+                                " of device time)" if dominant64 else
+                                "k_t9_tc (FP32 quartic term, 3xTF32 on tcgen05; largest share of device time)"),
                      "achieved": achieved, "peak": fp64_peak if dominant64 else fp32_peak,
                      "unit": "TFLOP/s",
                      "frac": achieved / (fp64_peak if dominant64 else fp32_peak),
                      "traffic": TRAFFIC_FP64_QUARTIC if dominant64 else TRAFFIC_TC_QUARTIC,
-                     "peak_note": ("FP64: measured bf16 burst x 1.25/2250 (of measured)"
+                     "peak_note": ("measured bf16 burst x 1.1/2.25 (TF32) / 21 slice products (of measured)"
                                    if dominant64 else
-                                   "3xTF32: measured bf16 burst x 1.1/2.25 / 3 (of measured)"),
+                                   "measured bf16 burst x 1.1/2.25 (TF32) / 3 (of measured)"),
                      "fp32_launches": {"kernel": "k_t9_tc", "n": n32, "ms_total": t32, "tflops": ach32,
                                        "peak_3xtf32": fp32_peak,
                                        "frac": ach32 / fp32_peak if ach32 else None},
-                     "fp64_launches": {"kernel": "k_t9_gemm<double>", "n": n64, "ms_total": t64,
-                                       "tflops": ach64, "peak_fp64": fp64_peak,
-                                       "frac": ach64 / fp64_peak if ach64 else None}},
+                     "fp64_launches": {"kernel": "k_t9_tc64", "n": n64, "ms_total": t64,
+                                       "tflops": ach64, "peak_split_tf32": fp64_peak,
+                                       "frac": ach64 / fp64_peak if ach64 else None,
+                                       "fp64_alu_peak": fp64_alu_peak,
+                                       "of_fp64_alu_peak": ach64 / fp64_alu_peak if ach64 else None}},
         "evals": {"fp32": info["evals_fp32"], "fp64": info["evals_fp64"]},
         "e2e": {"value": e2e_s, "unit": "s",
                 "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),

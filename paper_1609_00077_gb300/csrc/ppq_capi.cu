@@ -23,6 +23,7 @@
 #include "ppq_kernels.cuh"
 #include "ppq_adjoint.cuh"
 #include "ppq_tc.cuh"
+#include "ppq_tc64.cuh"
 
 namespace {
 
@@ -87,6 +88,14 @@ struct Workspace {
   int* tc_err = nullptr;
   int tc_nslot = 0;
   float* tc_part = nullptr;   // per-CTA row sums, [slot][p][29]
+  // the same for the FP64 residual (exact-splitting tensor-core kernel)
+  int tc64_N = 0, tc64_Npad = 0, tc64_Kc = 0, tc64_nctas = 0, tc64_nslot = 0;
+  size_t tc64_smem = 0;
+  float* bpre64 = nullptr;
+  int* fexp64 = nullptr;
+  int16_t* tc64_chunk = nullptr;
+  int* tc64_cta = nullptr;
+  double* tc64_part = nullptr;
   double* t9part = nullptr;   // per-work-item row sums of the SIMT kernel, [item][p][29]
   double* t9 = nullptr;
   double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;
@@ -142,7 +151,8 @@ void free_ws(Workspace* w) {
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
                 w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
                 w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
-                w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part};
+                w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part,
+                w->bpre64, w->fexp64, w->tc64_chunk, w->tc64_cta, w->tc64_part};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -194,6 +204,12 @@ int grow(Workspace* w, int N, int diis) {
     AL(w->tc_cta, sizeof(int) * 3 * kTcMaxCtas);
     AL(w->tc_err, sizeof(int));
     AL(w->tc_part, sizeof(float) * kTcPartRows * PPQ_NA2);
+    AL(w->bpre64, sizeof(float) * PPQ_NS36 * ppq::tc::kSl * kc * npad * 8);
+    AL(w->fexp64, sizeof(int) * PPQ_NS36 * npad);
+    AL(w->tc64_chunk, sizeof(int16_t) * ppq::tc::kChunkFields * PPQ_NQ9);
+    AL(w->tc64_cta, sizeof(int) * 3 * kTcMaxCtas);
+    AL(w->tc64_part, sizeof(double) * kTcPartRows * PPQ_NA2);
+    w->tc64_N = 0;
     CK(cudaMemset(w->tc_err, 0, sizeof(int)));
     w->tc_allowed = true;
     w->tc_N = 0;
@@ -416,10 +432,10 @@ struct TcPlan {
   std::vector<int> cta;        // tile, first chunk, end chunk
 };
 
-int plan_tc(int N, TcPlan* pl) {
+int plan_tc(int N, TcPlan* pl, int g_cap = 4) {
   if (N < 1 || N > kTcMaxN) return fail(-5, "no tensor-core quartic kernel for n_pairs = %d", N);
   const int Npad = (N + 15) / 16 * 16, Kc = (N + 7) / 8;
-  const int max_g = std::max(1, std::min(4, ppq::tc::kMaxCols / Npad));
+  const int max_g = std::max(1, std::min(g_cap, ppq::tc::kMaxCols / Npad));
   pl->chunk.clear();
   pl->cta.clear();
   std::vector<double> cost;
@@ -520,6 +536,58 @@ int launch_t9_tc(Workspace* w, int N, cudaStream_t s) {
   }
 }
 
+// FP64 residual: one g per chunk (six accumulator groups fill TMEM)
+int prepare_tc64(Workspace* w, int N, cudaStream_t s) {
+  TcPlan pl;
+  int rc = plan_tc(N, &pl, 1);
+  if (rc) return rc;
+  if (!pl.cta.empty())
+    CK(cudaMemcpyAsync(w->tc64_cta, pl.cta.data(), sizeof(int) * pl.cta.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->tc64_chunk, pl.chunk.data(), sizeof(int16_t) * pl.chunk.size(), cudaMemcpyHostToDevice,
+                     s));
+  CK(cudaStreamSynchronize(s));
+  w->tc64_Npad = pl.Npad;
+  w->tc64_Kc = pl.Kc;
+  w->tc64_nctas = (int)pl.cta.size() / 3;
+  const int P = N * (N - 1) / 2, ntiles = (P + ppq::tc::kRows - 1) / ppq::tc::kRows;
+  w->tc64_nslot = ntiles > 0 ? w->tc64_nctas / ntiles : 0;
+  if (w->tc64_nslot * ntiles != w->tc64_nctas || (size_t)w->tc64_nslot * P > (size_t)kTcPartRows)
+    return fail(-5, "tensor-core work list does not fit its partial buffer");
+  w->tc64_smem = std::max(ppq::tc::Smem64::total(cl_ld(N)), (size_t)120 * 1024);
+  w->tc64_N = N;
+  return 0;
+}
+
+template <int NW>
+int launch_t9_tc64_nw(Workspace* w, int N, cudaStream_t s) {
+  static std::once_flag attr[64];  // per device
+  int dev;
+  CK(cudaGetDevice(&dev));
+  cudaError_t e = cudaSuccess;
+  std::call_once(attr[dev & 63], [&] {
+    e = cudaFuncSetAttribute(ppq::tc::k_t9_tc64<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ppq::tc::Smem64::total(cl_ld(kTcMaxN)));
+  });
+  if (e != cudaSuccess) return fail(-100, "k_t9_tc64 attribute: %s", cudaGetErrorString(e));
+  const int P = N * (N - 1) / 2;
+  ppq::tc::k_t9_tc64<NW><<<w->tc64_nctas, ppq::tc::kThreads, w->tc64_smem, s>>>(
+      N, P, w->tc64_Kc, cl_ld(N), (const double*)w->clT, w->bpre64, w->fexp64, w->tc64_cta, w->tc64_chunk,
+      w->tc64_nslot, w->tc64_part, w->tc_err);
+  return 0;
+}
+
+int launch_t9_tc64(Workspace* w, int N, cudaStream_t s) {
+  if (w->tc64_nctas == 0) return 0;  // no unordered pairs
+  switch (w->tc64_Npad) {
+    case 16: return launch_t9_tc64_nw<16>(w, N, s);
+    case 32: return launch_t9_tc64_nw<32>(w, N, s);
+    case 48: return launch_t9_tc64_nw<48>(w, N, s);
+    case 64: return launch_t9_tc64_nw<64>(w, N, s);
+    case 80: return launch_t9_tc64_nw<80>(w, N, s);
+    default: return fail(-5, "no tensor-core quartic kernel for n_pairs = %d", N);
+  }
+}
+
 // Tile autotuner: the micro-tile MT of k_t9_gemm (thread grid ceil(N/MT)^2,
 // at most 256 threads) is chosen per (N, precision) by timing every candidate
 // once on the stream, the first time that size is seen on this device.
@@ -600,6 +668,15 @@ int residual(Workspace* w, int N, cudaStream_t s) {
     if (w->profile) CK(cudaEventRecord(w->evq1, s));
     ppq::k_t9_reduce<float><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc_nslot, w->tc_part,
                                                                                    w->t9);
+  } else if (std::is_same<R, double>::value && w->tc64_N == N) {
+    // tensor cores, exact splitting: split B operands, then the MMA + W-contraction kernel
+    ppq::tc::k_t9_bprep64<<<PPQ_NS36, 128, 0, s>>>(
+        N, w->tc64_Npad, w->tc64_Kc, (const double*)pg, w->bpre64, w->fexp64);
+    if (w->profile) CK(cudaEventRecord(w->evq0, s));
+    if ((rc = launch_t9_tc64(w, N, s))) return rc;
+    if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc64_nslot,
+                                                                                    w->tc64_part, w->t9);
   } else {
     // SIMT: transposed operands, GEMM, W-contraction
     ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
@@ -623,6 +700,8 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   int p = precision ? 1 : 0;
   if (precision && w->tc_allowed && N <= kTcMaxN) {
     if (w->tc_N != N && (rc = prepare_tc(w, N, s))) return rc;
+  } else if (!precision && w->tc_allowed && N <= kTcMaxN) {
+    if (w->tc64_N != N && (rc = prepare_tc64(w, N, s))) return rc;
   } else if (precision) {
     if ((rc = tuned_mt<float>(w, N, s, &w->mt[1]))) return rc;
   } else {
