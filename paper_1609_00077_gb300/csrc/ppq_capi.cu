@@ -97,6 +97,7 @@ struct Workspace {
   int* tc64_cta = nullptr;
   double* tc64_part = nullptr;
   double* t9part = nullptr;   // per-work-item row sums of the SIMT kernel, [item][p][29]
+  double* r1part = nullptr;   // k_r1 partial sums, [split][N][3]
   double* t9 = nullptr;
   double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;
   unsigned long long* amax = nullptr;
@@ -143,6 +144,7 @@ size_t amp_len(int N) { return (size_t)3 * N + (size_t)PPQ_NA2 * N * N; }
 inline int cl_ld(int N) { return (N * N + 3) & ~3; }
 
 constexpr int kTcMaxN = 80;      // largest N of the tensor-core quartic kernel
+constexpr int kR1Split = 8;      // blocks per output pair label in k_r1
 constexpr int kTcMaxCtas = 1024;
 constexpr int kTcPartRows = 152 * 128;  // slots x unordered pairs of the partial buffer
 
@@ -152,7 +154,7 @@ void free_ws(Workspace* w) {
                 w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
                 w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
                 w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part,
-                w->bpre64, w->fexp64, w->tc64_chunk, w->tc64_cta, w->tc64_part};
+                w->bpre64, w->fexp64, w->tc64_chunk, w->tc64_cta, w->tc64_part, w->r1part};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (w->host) cudaFreeHost(w->host);
@@ -225,6 +227,7 @@ int grow(Workspace* w, int N, int diis) {
     AL(w->work9, sizeof(int) * wk.size());
     CK(cudaMemcpy(w->work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice));
     AL(w->t9part, sizeof(double) * w->n_work9 * (NN - Nc) / 2 * PPQ_NA2);
+    AL(w->r1part, sizeof(double) * kR1Split * 3 * Nc);
   }
   AL(w->esite, sizeof(double) * Nc); AL(w->epair, sizeof(double) * NN);
   AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
@@ -416,7 +419,15 @@ int launch_pair_closure(int N, const R* g2, const double* t1, const double* t2, 
     e = cudaFuncSetAttribute(ppq::k_pair_closure_p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return fail(-100, "k_pair_closure_p attribute: %s", cudaGetErrorString(e));
-  const int grid = std::min(N * N, kRedBlocks);
+  static int per_sm[2][64] = {};  // resident CTAs per SM, per precision and device
+  int& ps = per_sm[sizeof(R) == 4][dev & 63];
+  if (ps == 0) {
+    int nb = 0, nsm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ppq::k_pair_closure_p<R>, 256, smem));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    ps = std::max(1, nb) * std::max(1, nsm);
+  }
+  const int grid = std::min(N * N, ps);
   ppq::k_pair_closure_p<R><<<grid, 256, smem, s>>>(N, g2, t1, t2, pg, pt7, pc0, epair, pt7T);
   return 0;
 }
@@ -648,7 +659,8 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   ppq::k_links<R><<<(NN + 63) / 64, 64, 0, s>>>(N, t2, cl);
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
   if ((rc = launch_pair_closure<R>(N, g2, t1, t2, pg, pt7, pc0, w->epair, (R*)w->pt7T, s))) return rc;
-  ppq::k_r1<R><<<N, 256, 0, s>>>(N, hs, pc0, cl, pg, w->r);
+  ppq::k_r1<R><<<dim3(N, kR1Split), 256, 0, s>>>(N, hs, pc0, cl, pg, w->r1part);
+  ppq::k_r1_reduce<R><<<(3 * N + 127) / 128, 128, 0, s>>>(N, kR1Split, hs, w->r1part, w->r);
   size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl_ld(N), cl, (R*)w->clT);
   {
@@ -689,7 +701,7 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
   CK(cudaGetLastError());
-  w->n_launches += 11;
+  w->n_launches += 12;
   return 0;
 }
 
@@ -724,7 +736,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
     w->n_launches = nl;
   }
   CK(cudaGraphLaunch(w->graph[p], s));
-  w->n_launches += 11;
+  w->n_launches += 12;
   return 0;
 }
 
@@ -1729,6 +1741,7 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   w.n_work9 = (int)wk.size() / 3;
   w.work9 = cv.take<int>(wk.size());
   w.t9part = cv.take<double>((size_t)w.n_work9 * (NN - N) / 2 * PPQ_NA2);
+  w.r1part = cv.take<double>((size_t)kR1Split * 3 * N);
   if (cv.off > kStaticScratchBytes)
     return fail(-6, "pq_residual_static: %zu bytes of scratch needed, %zu available", cv.off,
                 kStaticScratchBytes);

@@ -214,8 +214,8 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict
 }
 
 // Persistent form of the same closure: each CTA stages the compact tables
-// (Hamiltonian CSR, per-sector sweep lists, output element lists) in shared
-// memory once and then loops over pairs XW.  Right multiplication by
+// (per-sector sweep lists, output element lists) in shared memory once, reads
+// the Hamiltonian CSR through L1, and then loops over pairs XW.  Right multiplication by
 // (1 + t_o O_o) only mixes entries of one row and left multiplication only
 // entries of one column, so a thread takes one row through all 35 operators,
 // then one column, with no barrier between operators.  Threads are ordered by
@@ -230,13 +230,7 @@ struct ClosureSmem {
   static constexpr int kM = PPQ_BLKP + 8;
   static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2;   // pre-scaled integrals
   template <typename R>
-  static __host__ __device__ constexpr size_t off_cj() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
-  template <typename R>
-  static __host__ __device__ constexpr size_t off_hel() { return off_cj<R>() + (PPQ_H2_NNZ * 2 + 15) / 16 * 16; }
-  template <typename R>
-  static __host__ __device__ constexpr size_t off_hptr() { return off_hel<R>() + (PPQ_H2_NEL * 2 + 15) / 16 * 16; }
-  template <typename R>
-  static __host__ __device__ constexpr size_t off_sl() { return off_hptr<R>() + ((PPQ_H2_NEL + 1) * 2 + 15) / 16 * 16; }
+  static __host__ __device__ constexpr size_t off_sl() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
   template <typename R>
   static __host__ __device__ constexpr size_t off_oel() { return off_sl<R>() + (size_t)(PPQ_PSR_N + PPQ_PSL_N) * 4; }
   template <typename R>
@@ -246,23 +240,17 @@ struct ClosureSmem {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(256, 2) k_pair_closure_p(int N, const R* __restrict__ g2,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(int N, const R* __restrict__ g2,
     const double* __restrict__ t1, const double* __restrict__ t2, R* __restrict__ pg,
     R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair, R* __restrict__ pt7T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* M = reinterpret_cast<R*>(smem_raw);
   R* gsv = M + ClosureSmem::kM;                          // [code][j]
   R* fac = gsv + ClosureSmem::kG;                        // [2 o + sign], slots 70, 71 = 0
-  uint16_t* cj = reinterpret_cast<uint16_t*>(smem_raw + ClosureSmem::off_cj<R>());
-  int16_t* hel = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_hel<R>());
-  int16_t* hptr = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_hptr<R>());
   int32_t* srl = reinterpret_cast<int32_t*>(smem_raw + ClosureSmem::off_sl<R>());
   int32_t* sll = srl + PPQ_PSR_N;
   int16_t* oel = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_oel<R>());
   const int tid = threadIdx.x;
-  for (int i = tid; i < PPQ_H2_NNZ; i += blockDim.x) cj[i] = ppq_h2_cj[i];
-  for (int i = tid; i < PPQ_H2_NEL; i += blockDim.x) { hel[i] = ppq_h2_elp[i]; hptr[i] = (int16_t)ppq_h2_ptr[i]; }
-  if (tid == 0) hptr[PPQ_H2_NEL] = (int16_t)ppq_h2_ptr[PPQ_H2_NEL];
   for (int i = tid; i < PPQ_PSR_N; i += blockDim.x) srl[i] = ppq_ps_right[i];
   for (int i = tid; i < PPQ_PSL_N; i += blockDim.x) sll[i] = ppq_ps_left[i];
   for (int i = tid; i < PPQ_NS36; i += blockDim.x) oel[i] = ppq_g_elp[i];
@@ -302,9 +290,11 @@ __global__ void __launch_bounds__(256, 2) k_pair_closure_p(int N, const R* __res
     for (int i = tid; i < ClosureSmem::kM; i += blockDim.x) M[i] = R(0);
     __syncthreads();
     for (int el = tid; el < PPQ_H2_NEL; el += blockDim.x) {
+      // the Hamiltonian CSR is read through L1 (the same 52 KB for every pair)
       R acc = R(0);
-      for (int p = hptr[el]; p < hptr[el + 1]; ++p) acc += gsv[cj[p]];
-      M[hel[el]] = acc;
+      const int p1 = __ldg(ppq_h2_ptr + el + 1);
+      for (int p = __ldg(ppq_h2_ptr + el); p < p1; ++p) acc += gsv[__ldg(ppq_h2_cj + p)];
+      M[__ldg(ppq_h2_elp + el)] = acc;
     }
     __syncthreads();
     const R h00 = M[PPQ_EL00P];
@@ -372,11 +362,13 @@ __device__ __forceinline__ R block_sum(R v, R* red) {
 // X linked to Y), T8 (pair piece on X,W, both linked to Y)
 template <typename R>
 __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
-                     const R* __restrict__ cl, const R* __restrict__ pg, double* __restrict__ r1) {
+                     const R* __restrict__ cl, const R* __restrict__ pg, double* __restrict__ part) {
+  // block (Y, split): the T3 / column-0 part in split 0, the T8 sum over
+  // XW = split, split + nsplit, ... ; partial sums to part[split][Y][3]
   __shared__ R red[32];
-  int Y = blockIdx.x;
+  int Y = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
   R acc[3] = {R(0), R(0), R(0)};
-  for (int X = threadIdx.x; X < N; X += blockDim.x) {
+  for (int X = threadIdx.x; sp == 0 && X < N; X += blockDim.x) {
     if (X == Y) continue;
     const R* c = cl + ((size_t)X * N + Y) * PPQ_NS36;
     const R* h0 = hs + (size_t)X * 256;  // row 0 of Ht_X
@@ -386,7 +378,7 @@ __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
     const R* p0 = pc0 + ((size_t)Y * N + X) * PPQ_NCOL0;
     for (int k = 0; k < 3; ++k) acc[k] += p0[29 + k];
   }
-  for (int XW = threadIdx.x; XW < N * N; XW += blockDim.x) {
+  for (int XW = sp * blockDim.x + threadIdx.x; XW < N * N; XW += nsp * blockDim.x) {
     int X = XW / N, W = XW % N;
     if (X == W || X == Y || W == Y) continue;
     const R* cx = cl + ((size_t)X * N + Y) * PPQ_NS36;
@@ -400,8 +392,20 @@ __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
   }
   for (int k = 0; k < 3; ++k) {
     R s = block_sum(acc[k], red);
-    if (threadIdx.x == 0) r1[Y * 3 + k] = double(s) + double(hs[(size_t)Y * 256 + ppq_A1[k] * 16]);
+    if (threadIdx.x == 0) part[((size_t)sp * N + Y) * 3 + k] = double(s);
   }
+}
+
+// r1[Y][k] = site element + sum of the k_r1 partial sums in split order
+template <typename R>
+__global__ void k_r1_reduce(int N, int nsp, const R* __restrict__ hs, const double* __restrict__ part,
+                            double* __restrict__ r1) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * N) return;
+  int Y = i / 3, k = i % 3;
+  double v = 0.0;
+  for (int s = 0; s < nsp; ++s) v += part[(size_t)s * 3 * N + i];
+  r1[i] = v + double(hs[(size_t)Y * 256 + ppq_A1[k] * 16]);
 }
 
 // r2 for ordered (Y,Z): T5, T4 directly (dir) and T2+T7 through the
