@@ -148,74 +148,11 @@ __global__ void k_site_closure(int N, const R* __restrict__ g1, const double* __
 }
 
 // two-site closure Ht_XW = exp(-I) H_XW exp(I), I = T_X + T_W + T_XW, on the
-// charge/S_z block layout (4900 entries); writes the entries the topologies use
-template <typename R>
-__global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict__ g2,
-    const double* __restrict__ t1, const double* __restrict__ t2, R* __restrict__ pg,
-    R* __restrict__ pt7, R* __restrict__ pc0, double* __restrict__ epair, R* __restrict__ pt7T) {
-  extern __shared__ unsigned char smem_raw[];
-  R* M = reinterpret_cast<R*>(smem_raw);
-  __shared__ R h00;
-  __shared__ double tops[35];
-  int XW = blockIdx.x;
-  int X = XW / N, W = XW % N;
-  if (X == W) {
-    for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = R(0);
-    for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) {
-      pt7[(size_t)XW * PPQ_NT7E + i] = R(0);
-      pt7T[(size_t)i * N * N + XW] = R(0);  // diagonal: [W][X] = [X][W]
-    }
-    for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = R(0);
-    if (threadIdx.x == 0) epair[XW] = 0.0;
-    return;
-  }
-  if (threadIdx.x < 35) {
-    int o = threadIdx.x;
-    tops[o] = o < 3 ? t1[X * 3 + o] : (o < 6 ? t1[W * 3 + o - 3] : t2[(size_t)XW * PPQ_NA2 + o - 6]);
-  }
-  for (int i = threadIdx.x; i < PPQ_BLK; i += blockDim.x) M[i] = R(0);
-  __syncthreads();
-  const R* g = g2 + (size_t)XW * PPQ_NG2;
-  for (int el = threadIdx.x; el < PPQ_H2_NEL; el += blockDim.x) {
-    R s = R(0);
-    for (int p = ppq_h2_ptr[el]; p < ppq_h2_ptr[el + 1]; ++p) s += R(ppq_h2_c[p]) * g[ppq_h2_j[p]];
-    M[ppq_h2_el[el]] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) h00 = M[PPQ_EL00];
-  for (int o = 0; o < 35; ++o) {
-    R to = R(tops[o]);
-    if (to != R(0)) {
-      for (int e = ppq_p_rptr[o] + threadIdx.x; e < ppq_p_rptr[o + 1]; e += blockDim.x) {
-        int32_t w = ppq_p_right[e];
-        M[unpack_t(w)] += to * unpack_sign<R>(w) * M[unpack_s(w)];
-      }
-    }
-    __syncthreads();
-  }
-  for (int o = 0; o < 35; ++o) {
-    R to = R(tops[o]);
-    if (to != R(0)) {
-      for (int e = ppq_p_lptr[o] + threadIdx.x; e < ppq_p_lptr[o + 1]; e += blockDim.x) {
-        int32_t w = ppq_p_left[e];
-        M[unpack_t(w)] -= to * unpack_sign<R>(w) * M[unpack_s(w)];
-      }
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = M[ppq_g_el[i]];
-  for (int i = threadIdx.x; i < PPQ_NT7E; i += blockDim.x) {
-    R v = M[ppq_t7_el[i]];
-    pt7[(size_t)XW * PPQ_NT7E + i] = v;
-    pt7T[(size_t)i * N * N + (size_t)W * N + X] = v;  // stored [e][W][X]
-  }
-  for (int i = threadIdx.x; i < PPQ_NCOL0; i += blockDim.x) pc0[(size_t)XW * PPQ_NCOL0 + i] = M[ppq_col0_el[i]];
-  if (threadIdx.x == 0) epair[XW] = double(M[PPQ_EL00]) - double(h00);
-}
-
-// Persistent form of the same closure: each CTA stages the compact tables
-// (per-sector sweep lists, output element lists) in shared memory once, reads
-// the Hamiltonian CSR through L1, and then loops over pairs XW.  Right multiplication by
+// charge/S_z block layout (4900 entries); writes the entries the topologies
+// use (G row, T7 entries and their transpose, column 0) and the pair energy.
+// Persistent: each CTA stages the compact tables (per-sector sweep lists,
+// output element lists) in shared memory once, reads the Hamiltonian CSR
+// through L1, and then loops over pairs XW.  Right multiplication by
 // (1 + t_o O_o) only mixes entries of one row and left multiplication only
 // entries of one column, so a thread takes one row through all 35 operators,
 // then one column, with no barrier between operators.  Threads are ordered by
@@ -224,8 +161,9 @@ __global__ void __launch_bounds__(256) k_pair_closure(int N, const R* __restrict
 // shared copy of M pads every sector row to dim + 1 entries (no bank
 // conflicts between rows dim apart).  The gather multiplies by the five
 // coefficient values -1, -1/2, 1/2, 1, 2 through a pre-scaled copy of the
-// integrals (the products are exact).  Same result, element for element, as
-// k_pair_closure.
+// integrals (the products are exact).  Element for element the arithmetic of
+// the flat operator-by-operator sweeps (ppq_p_right / ppq_p_left, used by the
+// adjoint's forward recomputation).
 struct ClosureSmem {
   static constexpr int kM = PPQ_BLKP + 8;
   static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2;   // pre-scaled integrals
@@ -409,7 +347,8 @@ __global__ void k_r1_reduce(int N, int nsp, const R* __restrict__ hs, const doub
 }
 
 // r2 for ordered (Y,Z): T5, T4 directly (dir) and T2+T7 through the
-// exp(-T_YZ) transform (abuf, mirrored later); T9 is k_t9_gemm + k_t9_epi
+// exp(-T_YZ) transform (abuf, mirrored later); T9 is the quartic kernels
+// (tc::k_t9_tc, tc::k_t9_tc64, k_t9_gemm) and k_t9_reduce
 template <typename R>
 __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
     const R* __restrict__ m7, const R* __restrict__ pg, const R* __restrict__ cl,
@@ -553,30 +492,6 @@ __device__ __forceinline__ double denom(size_t i, int N, const double* fo, const
   return d - shift;
 }
 
-// partial sums over blocks of sum_i w_i x_i y_i (x == y for norms)
-__global__ void k_wdot(size_t L, int N, const double* __restrict__ x, const double* __restrict__ y,
-                       double* __restrict__ part) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
-    s += amp_weight(i, N) * x[i] * y[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// final reduction of block partials and of the energy pieces, in FP64
-__global__ void k_finalize(int nb, const double* __restrict__ part, int N, const double* __restrict__ esite,
-                           const double* __restrict__ epair, double* __restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0, e = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) e += esite[i];
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) e += 0.5 * epair[i];
-  s = block_sum(s, red);
-  double es = block_sum(e, red);
-  if (threadIdx.x == 0) { out[0] = s; out[1] = es; }
-}
-
 // Jacobi step: tn = t + r / D, e = tn - t; written to DIIS slot
 __global__ void k_jacobi(size_t L, int N, const double* __restrict__ t, const double* __restrict__ r,
                          const double* __restrict__ fo, const double* __restrict__ fv, double shift,
@@ -592,49 +507,6 @@ __global__ void k_jacobi(size_t L, int N, const double* __restrict__ t, const do
   }
   tn[i] = t[i] + e;
   en[i] = e;
-}
-
-// DIIS: B[i][j] = <e_i, e_j> (weighted); solve [B -1; -1 0][c; l] = [0; -1]
-// by Gaussian elimination with partial pivoting (FP64, one thread).
-__global__ void k_diis_solve(int m, const double* __restrict__ bmat, int ld, double* __restrict__ coef,
-                             int* __restrict__ ok) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double A[17][18];
-  int n = m + 1;
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i][j] = bmat[i * ld + j];
-    A[i][m] = -1.0;
-    A[i][n] = 0.0;
-  }
-  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
-  A[m][m] = 0.0;
-  A[m][n] = -1.0;
-  // scale the error block for conditioning (solution for c is unchanged)
-  double sc = 0.0;
-  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(A[i][i]));
-  if (sc > 0.0)
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) A[i][j] /= sc;
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < n; ++r)
-      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-    if (fabs(A[piv][c]) < 1e-300) { *ok = 0; return; }
-    if (piv != c)
-      for (int k = 0; k <= n; ++k) { double tmp = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = tmp; }
-    for (int r = c + 1; r < n; ++r) {
-      double f = A[r][c] / A[c][c];
-      for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
-    }
-  }
-  double x[17];
-  for (int r = n - 1; r >= 0; --r) {
-    double s = A[r][n];
-    for (int k = r + 1; k < n; ++k) s -= A[r][k] * x[k];
-    x[r] = s / A[r][r];
-  }
-  for (int i = 0; i < m; ++i) coef[i] = x[i];
-  *ok = 1;
 }
 
 __global__ void k_extrapolate(size_t L, int m, const double* __restrict__ coef, const int* __restrict__ ok,
@@ -784,40 +656,6 @@ __global__ void k_t9_reduce(int N, int nslot, const P_* __restrict__ part, doubl
     for (int k = 0; k < nslot; ++k) v += double(src[(size_t)k * P * PPQ_NA2]);
   }
   t9[i] = v;
-}
-
-// Stage 2: t9[Y,Z][o] = 1/2 sum_W sum_{ch -> o} s B[Y][q][Z][W] Cl[W,Y][c3] Cl[W,Z][c4], Y < Z
-template <typename R>
-__global__ void __launch_bounds__(256) k_t9_epi(int N, const R* __restrict__ B, const R* __restrict__ cl,
-                                                double* __restrict__ t9) {
-  extern __shared__ unsigned char smem_raw[];
-  R* cy = reinterpret_cast<R*>(smem_raw);
-  R* cz = cy + N * PPQ_NS36;
-  int YZ = blockIdx.x;
-  int Y = YZ / N, Z = YZ % N;
-  if (Y >= Z) return;
-  for (int e = threadIdx.x; e < N * PPQ_NS36; e += blockDim.x) {
-    int W = e / PPQ_NS36, c = e % PPQ_NS36;
-    cy[e] = cl[((size_t)W * N + Y) * PPQ_NS36 + c];
-    cz[e] = cl[((size_t)W * N + Z) * PPQ_NS36 + c];
-  }
-  __syncthreads();
-  const R* bb = B + ((size_t)Y * PPQ_NQ9 * N + Z) * N;   // + q * N * N + W
-  size_t qs = (size_t)N * N;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int o = warp; o < PPQ_NA2; o += nw) {
-    R acc = R(0);
-    for (int e = ppq_c9p[o]; e < ppq_c9p[o + 1]; ++e) {
-      const int16_t* c = ppq_c9 + 5 * e;
-      const R* bq = bb + c[0] * qs;
-      R sg = R(c[4]);
-      int c3 = c[1], c4 = c[2];
-      for (int W = lane; W < N; W += 32) acc += sg * bq[W] * cy[W * PPQ_NS36 + c3] * cz[W * PPQ_NS36 + c4];
-    }
-    double v = double(acc);
-    for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
-    if (lane == 0) t9[(size_t)YZ * PPQ_NA2 + o] = 0.5 * v;
-  }
 }
 
 // transposed link coefficients clT[c][X][Y] = Cl[X,Y][c]; slices ldc apart
