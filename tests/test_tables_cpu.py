@@ -1,0 +1,108 @@
+"""Host-side pins of the generated tables and of the arithmetic the tensor-core
+kernels rely on (no GPU needed).
+
+* The pair closure's per-sector sweep lists (groups of four entries of one
+  operator, padded with no-op entries, offsets in the padded sector layout)
+  reproduce the flat operator-by-operator sweeps exactly, stay inside their
+  sector block, and give every thread of a sector a row start in its own
+  shared-memory bank.
+* The exact integer splitting of the FP64 quartic kernel (six 7-bit slices,
+  K <= 80): every grouped slice-product sum is an exact FP32 integer below
+  2^23, and the recombined product is within 3e-12 of row-max x column-max x K.
+"""
+import numpy as np
+import pytest
+
+from paper_1609_00077_gb300 import tables as T
+
+
+@pytest.fixture(scope="module")
+def layout():
+    Tb = T.Tables()
+    return Tb, T.BlockLayout(Tb)
+
+
+def test_sector_lists_reproduce_flat_sweeps(layout):
+    Tb, L = layout
+    pr, prp, pl, plp = T.pair_transform_lists(Tb, L)
+    sr, srp, sl, slp = T.pair_sector_lists(Tb, L)
+    rng = np.random.default_rng(3)
+    M0 = rng.standard_normal(L.size)
+    t = rng.standard_normal(35) * 0.3
+    # flat lists, operator by operator
+    M = M0.copy()
+    for o in range(35):
+        for w in pr[prp[o]:prp[o + 1]]:
+            M[w >> 17] += t[o] * (-1 if w & 1 else 1) * M[(w >> 1) & 0xFFFF]
+    for o in range(35):
+        for w in pl[plp[o]:plp[o + 1]]:
+            M[w >> 17] -= t[o] * (-1 if w & 1 else 1) * M[(w >> 1) & 0xFFFF]
+    # per-sector lists in the padded layout (row stride dim + 1)
+    pbase, off = [], 0
+    for d in L.dim:
+        pbase.append(off)
+        off += d * (d + 1)
+    P = np.zeros(off)
+    for q, ss in enumerate(L.sectors):
+        for r in ss:
+            for c in ss:
+                P[pbase[q] + L.pos[r] * (L.dim[q] + 1) + L.pos[c]] = M0[L.elem(r, c)]
+    fac = np.zeros(72)
+    fac[0:70:2], fac[1:70:2] = t, -t
+    for lst, lp, rows, sgn in ((sr, srp, True, 1.0), (sl, slp, False, -1.0)):
+        for st in range(256):
+            q = L.sec_of[st]
+            d, dp = L.dim[q], L.dim[q] + 1
+            base = pbase[q] + (L.pos[st] * dp if rows else L.pos[st])
+            lo, hi = pbase[q], pbase[q] + d * dp
+            for e in range(lp[q], lp[q + 1], 4):
+                grp = lst[e:e + 4]
+                ti = [base + (w & 0xFFF) for w in grp]
+                si = [base + ((w >> 12) & 0xFFF) for w in grp]
+                assert all(lo <= x < hi for x in ti + si)
+                real = [x for x, w in zip(ti, grp) if (w >> 24) != 70]
+                assert len(set(real)) == len(real) and not set(real) & set(si)
+                vals = [P[a] + sgn * fac[w >> 24] * P[b] for a, b, w in zip(ti, si, grp)]
+                for a, v in zip(ti, vals):
+                    P[a] = v
+    for q, ss in enumerate(L.sectors):
+        for r in ss:
+            for c in ss:
+                assert P[pbase[q] + L.pos[r] * (L.dim[q] + 1) + L.pos[c]] == M[L.elem(r, c)]
+    # row starts of the threads of one sector fall in distinct banks
+    for q, ss in enumerate(L.sectors):
+        banks = [(pbase[q] + L.pos[r] * (L.dim[q] + 1)) % 32 for r in ss[:32]]
+        assert len(set(banks)) == len(banks)
+
+
+def _split(M, bits=7, nsl=6):
+    mx = np.abs(M).max(axis=1, keepdims=True)
+    e = np.where(mx > 0, np.frexp(mx)[1], 0)
+    xi = np.rint(np.ldexp(M, bits * nsl - e)).astype(np.int64)
+    out, rem = [], xi
+    for i in range(nsl):
+        sh = bits * (nsl - 1 - i)
+        a = rem >> sh
+        rem = rem - (a << sh)
+        out.append(a)
+    assert (rem == 0).all()
+    return out, e
+
+
+@pytest.mark.parametrize("K", [8, 70, 80])
+def test_exact_splitting_is_exact_and_bounded(K):
+    rng = np.random.default_rng(K)
+    A = rng.standard_normal((128, K)) * np.exp(rng.standard_normal((128, 1)) * 3)
+    B = rng.standard_normal((80, K)) * np.exp(rng.standard_normal((80, 1)) * 2)
+    As, ea = _split(A)
+    Bs, eb = _split(B)
+    assert np.abs(As[0]).max() <= 128 and all(0 <= a.min() and a.max() < 128 for a in As[1:])
+    Dint = np.zeros((128, 80), dtype=np.int64)
+    for g in range(6):
+        S = sum(As[i].astype(np.float64) @ Bs[g - i].astype(np.float64).T for i in range(g + 1))
+        assert np.abs(S).max() < 2 ** 23
+        assert (S.astype(np.float32).astype(np.float64) == S).all()   # exact in the FP32 accumulator
+        Dint += S.astype(np.int64) << (7 * (5 - g))
+    D = np.ldexp(Dint.astype(np.float64), ea + eb.T - 49)
+    scale = np.abs(A).max(1, keepdims=True) * np.abs(B).max(1, keepdims=True).T * K
+    assert (np.abs(D - A @ B.T) / scale).max() < 3e-12
