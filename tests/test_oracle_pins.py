@@ -8,8 +8,9 @@ independent of the oracle's own formulas.
 * Size consistency (inherited from CC, Theory section): a direct sum of two
   non-interacting fragments has the sum of the fragment energies.
 * Invariance to swapping pairs (Theory section) and to MO sign changes;
-  non-invariance of PQ to occupied-occupied rotations (Theory section) while
-  FCI is invariant (negative control).
+  non-invariance of PQ to occupied-occupied rotations and to the choice of
+  which virtual is paired with which occupied orbital (Theory section), while
+  FCI is invariant (negative control); at 4e/4o every pairing is exact.
 * Residual at random amplitudes against an independent Jordan-Wigner matrix
   construction of exp(-T) H exp(T) (scipy expm), and O-loc against O-det.
 * Manifold sizes against the closed form derived from Eq. decompose.
@@ -147,6 +148,25 @@ def test_occupied_rotation_changes_pq_not_fci():
     e1, _, _ = solve_total(Hr, K=2)
     assert abs(e0 - e1) > 1e-5
     assert abs(fci_energy(H.h, H.eri, 3) - fci_energy(Hr.h, Hr.eri, 3)) < 1e-10
+
+
+def _repair(H, perm):
+    vir = np.asarray(H.vir_of_pair)[perm]
+    return Hamiltonian(H.name, H.h, H.eri, H.e_const, H.occ_of_pair, vir, H.mo_energy)
+
+
+def test_pairing_choice_changes_pq_but_not_exactness():
+    # 6e/6o: the energy depends on the occupied-virtual pairing
+    H = build_ppp('polyene', 6)
+    e0, _, _ = solve_total(H, K=2)
+    e1, _, _ = solve_total(_repair(H, np.array([2, 0, 1])), K=2)
+    assert abs(e0 - e1) > 1e-5
+    # 4e/4o: PQ is exact for any pairing
+    B = build_ppp('polyene', 4)
+    efci = fci_energy(B.h, B.eri, 2) + B.e_const
+    for perm in ([0, 1], [1, 0]):
+        e, _, _ = solve_total(_repair(B, np.array(perm)), K=2)
+        assert abs(e - efci) < 1e-9
 
 
 def test_manifold_counts_closed_form_and_tables():
