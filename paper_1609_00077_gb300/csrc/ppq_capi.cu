@@ -419,13 +419,17 @@ int launch_pair_closure(int N, const R* g2, const double* t1, const double* t2, 
     e = cudaFuncSetAttribute(ppq::k_pair_closure_p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return fail(-100, "k_pair_closure_p attribute: %s", cudaGetErrorString(e));
-  static int per_sm[2][64] = {};  // resident CTAs per SM, per precision and device
-  int& ps = per_sm[sizeof(R) == 4][dev & 63];
+  // resident CTAs on the device, per precision and device (threads of the
+  // batched solver may fill an entry concurrently with the same value)
+  static std::atomic<int> per_dev[2][64];
+  std::atomic<int>& slot = per_dev[sizeof(R) == 4][dev & 63];
+  int ps = slot.load(std::memory_order_relaxed);
   if (ps == 0) {
     int nb = 0, nsm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ppq::k_pair_closure_p<R>, 256, smem));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     ps = std::max(1, nb) * std::max(1, nsm);
+    slot.store(ps, std::memory_order_relaxed);
   }
   const int grid = std::min(N * N, ps);
   ppq::k_pair_closure_p<R><<<grid, 256, smem, s>>>(N, g2, t1, t2, pg, pt7, pc0, epair, pt7T);
