@@ -36,7 +36,19 @@
  *   - work runs on `stream` (a cudaStream_t, 0 = legacy default stream); the
  *     call returns after the stream has finished the work;
  *   - the library keeps a per-device workspace between calls (released by
- *     ppq_release); calls on one device are serialised by a mutex.
+ *     ppq_release); calls on one device are serialised by a mutex;
+ *   - results are bit-reproducible: every reduction adds its partial sums in
+ *     a fixed order.
+ *
+ * Arithmetic of the residual
+ *   - precision 0 ("FP64"): every term in FP64, except that for n_pairs <= 80
+ *     the quartic four-link term (Table V's heaviest class) runs on the tensor
+ *     cores by exact integer splitting of its FP64 operands (42-bit fixed
+ *     point per row / per integral block, 21 TF32 slice products with exact
+ *     FP32 sums); its error is below ~3e-12 of (largest operand of the row) x
+ *     (largest integral of the block) x n_pairs per element;
+ *   - precision 1 ("FP32"): FP32 throughout, the quartic term as three TF32
+ *     products (hi*hi + hi*lo + lo*hi), i.e. FP32 accuracy.
  */
 #ifndef PPQ_H
 #define PPQ_H
