@@ -1,5 +1,5 @@
-"""The FP32 residual with the quartic topology on the tensor cores (tcgen05,
-3xTF32 split) beyond one 128-row tile.
+"""The residual with the quartic topology on the tensor cores (tcgen05: FP32
+by 3xTF32 products, FP64 by exact integer splitting) beyond one 128-row tile.
 
 * N = 20 (190 unordered pairs: a full tile and a ragged one of 62 rows):
   every pair-amplitude element of two sampled pairs of the second tile
@@ -7,8 +7,9 @@
   contain the pair (exact for those elements), FP32 within 2e-5 * max|R|,
   FP64 within 1e-11;
 * N = 40 and 70 (7 and 19 tiles, 48 and 80 TMEM columns per g): the whole
-  FP32 residual against the FP64 one (SIMT path, oracle-pinned at small N)
-  within the same FP32 bound -- a property that holds at any size.
+  FP32 residual against the FP64 one (oracle-pinned at N <= 12 and on the
+  N = 20 samples above) within the same FP32 bound -- a property that holds
+  at any size.
 """
 from itertools import combinations
 
