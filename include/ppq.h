@@ -105,14 +105,20 @@ typedef struct {
   int n_quartic32;       /* number of FP32 launches among n_quartic             */
 } ppq_info;
 
-/* Fill *o with the defaults listed above.  Returns 0. */
+/* Fill *o with the defaults listed above (the solver of the Implementation
+   section: Jacobi steps with orbital-energy denominators and DIIS; the
+   thresholds are this library's, the paper gives none).  Returns 0. */
 int ppq_default_opts(ppq_opts* o);
 
-/* Number of amplitudes of the layout above for n_pairs pairs: 3N + 29N^2.
+/* Number of amplitudes of the layout above for n_pairs pairs: 3N + 29N^2
+   (the <= 2-label manifold of Eq. decompose and Tables I-II: 3N + 29 C(N,2)
+   unique amplitudes, each two-pair one stored for both orders).
    Returns 0, or -1 if K != 2 or n_pairs < 1. */
 int ppq_amp_count(int K, int n_pairs, size_t* n_amp);
 
-/* Describe the 32 channels (3 single-pair then 29 two-pair): desc[3*c+0] =
+/* Describe the 32 channels (3 single-pair then 29 two-pair blocks of the
+   block decomposition of T into pairing labels, Eq. decompose; pairs as in
+   Fig. 1): desc[3*c+0] =
    number of pairs (1 or 2), desc[3*c+1], desc[3*c+2] = 4-bit monomial masks of
    the first and second pair: bit 0 annihilates the alpha occupied orbital,
    bit 1 the beta occupied, bit 2 creates the alpha virtual, bit 3 the beta
@@ -130,7 +136,9 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
                 const double* h, const double* eri, const double* t,
                 double* r, double* e_corr, int precision, void* stream);
 
-/* Solve the PQ amplitude equations.  t_in (nullable unless guess == 1) and
+/* Solve the PQ amplitude equations (Theory section) by Jacobi steps with
+   orbital-energy denominators and DIIS (Implementation section); the energy
+   is Eq. Ec.  t_in (nullable unless guess == 1) and
    t_out use the layout above; e_corr / e_total / info are host pointers
    (nullable).  e_total = e_corr + E_ref + e_const with
    E_ref = sum_i (h_ii + f_ii) over the occupied orbitals. */
@@ -172,16 +180,18 @@ int pq_lagrangian_gradient(int n_pairs, const int* occ_of_pair, const int* vir_o
                            const double* lam, double* grad, double* e_corr, void* stream);
 
 /* Solve the Lambda (left) equations grad_t L(t, lambda) = 0 at converged
-   amplitudes t: Jacobi steps lambda += grad / D with DIIS, FP64, converged
-   when ||grad||_2 <= opts->r_tol (max_iter steps).  lam_out uses the amplitude
+   amplitudes t (the left-hand amplitudes live on the same truncated manifold
+   as t, Theory section and Table I): Jacobi steps lambda += grad / D with
+   DIIS, FP64, converged when ||grad||_2 <= opts->r_tol (max_iter steps).  lam_out uses the amplitude
    layout.  Returns 0, 1 (not converged) or 2 (diverged), or < 0 on errors. */
 int pq_lambda(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
               const double* eri, const double* t, const ppq_opts* opts, double* lam_out,
               ppq_info* info, void* stream);
 
-/* Energy gradients of the PQ model through the Lambda (left) equations:
-   solve the amplitudes (opts as pq_solve, from zero), solve Lambda (FP64),
-   then form dE_total/dh (n_orb^2), dE_total/d(pq|rs) (n_orb^4) and the
+/* Energy gradients of the PQ model (Theory section; the response of the
+   energy to h and (pq|rs) through the Lambda equations on the Table I
+   manifold): solve the amplitudes (opts as pq_solve, from zero), solve
+   Lambda (FP64), then form dE_total/dh (n_orb^2), dE_total/d(pq|rs) (n_orb^4) and the
    orbital-rotation gradient dE/dkappa (n_orb^2, antisymmetric) for
    C -> C exp(kappa) with the pairing kept by index.  The integral gradients
    are symmetrised: dE = sum G delta for symmetric perturbations delta (all
@@ -214,10 +224,12 @@ int pq_residual_static(int n_pairs, const int* occ_of_pair, const int* vir_of_pa
                        const double* h, const double* eri, const double* t,
                        double* r, double* e_corr, int precision, void* stream);
 
-/* Free the cached workspace of the current device.  Returns 0. */
+/* Free the cached workspace of the current device (library housekeeping;
+   the paper has no counterpart).  Returns 0. */
 int ppq_release(void);
 
-/* Thread-local message of the last failing call on this thread ("" if none). */
+/* Thread-local message of the last failing call on this thread ("" if none;
+   library housekeeping, the paper has no counterpart). */
 const char* ppq_last_error(void);
 
 /* Work list of the tensor-core form of the quartic topology (Sec. II, the
