@@ -1759,7 +1759,16 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   if ((rc = stage(&w, P, s))) return rc;
   w.t = const_cast<double*>(t);  // read only by the residual kernels
   w.r = r;
-  if ((rc = run_residual(&w, N, precision, s))) return rc;
+  // launched directly on any stream: capturing a graph here would instantiate
+  // (allocate) one per call
+  if (precision) {
+    if ((rc = tuned_mt<float>(&w, N, s, &w.mt[1]))) return rc;
+    rc = residual<float>(&w, N, s);
+  } else {
+    if ((rc = tuned_mt<double>(&w, N, s, &w.mt[0]))) return rc;
+    rc = residual<double>(&w, N, s);
+  }
+  if (rc) return rc;
   k_rowsum<<<1, 256, 0, s>>>(1, 0, w.part, N, w.esite, w.epair, w.scal);
   double e = 0.0;
   CK(cudaMemcpyAsync(&e, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
