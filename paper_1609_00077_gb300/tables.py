@@ -148,6 +148,25 @@ def amplitude_channels():
     return A1, A2
 
 
+def amplitude_channels3():
+    """Three-pair (PH) amplitude channels: triples of nonzero per-site
+    monomials with zero total charge and S_z (Eq. decompose with K = 3,
+    Table II); 303 of them per unordered triple of pairing labels."""
+    return [(a, b, c) for a in range(1, NS) for b in range(1, NS) for c in range(1, NS)
+            if qn(a)[0] + qn(b)[0] + qn(c)[0] == 0 and qn(a)[1] + qn(b)[1] + qn(c)[1] == 0]
+
+
+def triple_integral_keys():
+    """Three-label integrals of PH (K_H = 3, Table I: rank-3 subtensors of v):
+    (pq|rs) over the 6 spatial orbitals 0 = X_o, 1 = X_v, 2 = W_o, 3 = W_v,
+    4 = V_o, 5 = V_v whose orbitals touch all three sites; 6^4 - 3 4^4 + 3 2^4
+    = 576 of them per ordered triple.  (No one-body element touches three.)"""
+    keys = [("v", p, q, r, s) for p in range(6) for q in range(6) for r in range(6)
+            for s in range(6) if len({p // 2, q // 2, r // 2, s // 2}) == 3]
+    assert len(keys) == 576
+    return keys
+
+
 def _spin_orbital(site, x, sigma):
     return 4 * site + 2 * x + sigma
 

@@ -106,3 +106,37 @@ def test_exact_splitting_is_exact_and_bounded(K):
     D = np.ldexp(Dint.astype(np.float64), ea + eb.T - 49)
     scale = np.abs(A).max(1, keepdims=True) * np.abs(B).max(1, keepdims=True).T * K
     assert (np.abs(D - A @ B.T) / scale).max() < 3e-12
+
+
+def test_three_pair_channels_and_sector(layout):
+    # PH groundwork: the 303 three-pair channels, the three-label integral
+    # keys, and the zero-charge three-site sector they span with the lower
+    # ranks: 1 (reference) + 3 x 3 (one site) + 3 x 29 (two sites) + 303 = 400
+    import itertools
+    Tb, _ = layout
+    A3 = T.amplitude_channels3()
+    assert len(A3) == 303 and len(set(A3)) == 303
+    assert len(T.triple_integral_keys()) == 576
+    zero = sum(1 for st in itertools.product(range(16), repeat=3)
+               if all(sum(Tb.qn[m][i] for m in st) == 0 for i in range(len(Tb.qn[0]))))
+    assert zero == 1 + 3 * len(Tb.A1) + 3 * len(Tb.A2) + len(A3) == 400
+
+
+def test_three_pair_channels_match_the_oracle_manifold():
+    # the oracle enumerates the K = 3 manifold on its own; its excitations that
+    # touch all three labels of N = 3 pairs, written as per-site monomial
+    # masks, are exactly the 303 channels
+    from oracle.detcc import enumerate_manifold
+    occ, vir = [0, 1, 2], [3, 4, 5]
+    lab = {0: 0, 1: 1, 2: 2, 3: 0, 4: 1, 5: 2}
+    A3 = set(T.amplitude_channels3())
+    seen = set()
+    for ah, ap, bh, bp in enumerate_manifold(occ, vir, 3):
+        mono = [0, 0, 0]
+        for x in ah: mono[lab[x]] |= 1
+        for x in bh: mono[lab[x]] |= 2
+        for x in ap: mono[lab[x]] |= 4
+        for x in bp: mono[lab[x]] |= 8
+        if all(mono):
+            seen.add(tuple(mono))
+    assert seen == A3
