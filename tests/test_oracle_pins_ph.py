@@ -1,0 +1,197 @@
+"""Pins of the oracle's three-pair (PH) path, independent of its formulas.
+
+* Residual and energy at random amplitudes for K = 3 (every excitation of
+  three pairs, up to hextuples) against a Jordan-Wigner construction of
+  exp(-T) H exp(T) with scipy's expm, in the six-electron sector of twelve
+  spin orbitals, with the integrals truncated to three labels (all kept at
+  N = 3) and to two labels (Table I, Implementation section).
+* The truncated bare Hamiltonian against the Slater-Condon rules: its
+  normal-ordered one-body part is the full Fock matrix and its two-body part
+  keeps an integral exactly when its orbitals carry at most K_H labels.
+* Size consistency of PH (Theory section): a direct sum of a three-pair and a
+  one-pair fragment, pairs interleaved, has the sum of the fragment FCI
+  energies (PH is exact for each fragment).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.linalg import expm
+
+from workloads import build_ppp, build_hchain
+from oracle.detcc import Problem
+from oracle.fci import fci_energy
+from tests.test_oracle_pins import _direct_sum
+
+
+def _jw_sparse(nso):
+    """Annihilators a_k on nso spin orbitals (basis bit k is the k-th kron
+    factor; 0 = empty), as sparse matrices."""
+    I = sp.identity(2, format="csr")
+    Z = sp.csr_matrix(np.diag([1.0, -1.0]))
+    a = sp.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))
+    ops = []
+    for k in range(nso):
+        m = sp.csr_matrix(np.array([[1.0]]))
+        for j in range(nso):
+            m = sp.kron(m, Z if j < k else (a if j == k else I), format="csr")
+        ops.append(m)
+    return ops
+
+
+def _occupations(nso):
+    idx = np.arange(2 ** nso)
+    return np.array([[(i >> (nso - 1 - k)) & 1 for k in range(nso)] for i in idx])
+
+
+class JW:
+    """Fermion operators of n spatial orbitals (spin orbital p + n*s) in the
+    sector of n_el electrons."""
+
+    def __init__(self, n, n_el):
+        self.n = n
+        self.a = _jw_sparse(2 * n)
+        self.ad = [x.T.tocsr() for x in self.a]
+        occ = _occupations(2 * n)
+        self.sector = np.flatnonzero(occ.sum(1) == n_el)
+        self.vac = np.zeros(2 ** (2 * n))
+        self.vac[0] = 1.0
+
+    def restrict(self, m):
+        return m.tocsr()[self.sector][:, self.sector]
+
+    def det(self, alpha, beta):
+        """a+ (alpha ascending) a+ (beta ascending) |vac>."""
+        v = self.vac.copy()
+        for c in reversed([self.ad[x] for x in sorted(alpha)]
+                          + [self.ad[x + self.n] for x in sorted(beta)]):
+            v = c @ v
+        return v
+
+    def hamiltonian(self, h1, v2):
+        n, a, ad = self.n, self.a, self.ad
+        H = sp.csr_matrix((2 ** (2 * n), 2 ** (2 * n)))
+        for p in range(n):
+            for q in range(n):
+                if h1[p, q] != 0.0:
+                    for s in range(2):
+                        H = H + h1[p, q] * (ad[p + n * s] @ a[q + n * s])
+        for p, q, r, u in zip(*np.nonzero(v2)):
+            for s1 in range(2):
+                for s2 in range(2):
+                    H = H + 0.5 * v2[p, q, r, u] * (
+                        ad[p + n * s1] @ ad[r + n * s2] @ a[u + n * s2] @ a[q + n * s1])
+        return H
+
+
+def _labels(H):
+    lab = np.empty(H.n_orb, dtype=np.int64)
+    lab[H.occ_of_pair] = np.arange(H.n_pairs)
+    lab[H.vir_of_pair] = np.arange(H.n_pairs)
+    return lab
+
+
+@pytest.mark.parametrize("K_H", [3, 2])
+def test_ph_residual_random_t_against_jordan_wigner_expm(K_H):
+    """N = 3 (hexatriene PPP, 12 spin orbitals, 924 six-electron states):
+    every tau_D of the 399 three-pair amplitudes and H as sparse Jordan-Wigner
+    products, exp(+-T) by scipy expm; linked residual and energy compared."""
+    H = build_ppp('polyene', 6)
+    n = H.n_orb
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=K_H)
+    assert P.cc.n_amp == 3 * 3 + 29 * 3 + 303
+    t = np.random.default_rng(4242).uniform(-0.1, 0.1, P.cc.n_amp)
+    R, e = P.residual(t)
+
+    jw = JW(n, n)
+    a, ad = jw.a, jw.ad
+    occ = sorted(int(i) for i in H.occ_of_pair)
+    ref = jw.det(occ, occ)
+    T = sp.csr_matrix((2 ** (2 * n), 2 ** (2 * n)))
+    dets = []
+    for tk, (ah, ap, bh, bp) in zip(t, P.cc.manifold):
+        op = sp.identity(2 ** (2 * n), format="csr")
+        for m in ([ad[x] for x in ap] + [a[x] for x in reversed(ah)]
+                  + [ad[x + n] for x in bp] + [a[x + n] for x in reversed(bh)]):
+            op = op @ m
+        det = jw.det(sorted(set(occ) - set(ah) | set(ap)), sorted(set(occ) - set(bh) | set(bp)))
+        sgn = float(det @ (op @ ref))
+        assert abs(abs(sgn) - 1.0) < 1e-12
+        T = T + (tk * sgn) * op
+        dets.append(det[jw.sector])
+    Hm = jw.restrict(jw.hamiltonian(P.hp, P.vt)).toarray()
+    Tm = jw.restrict(T).toarray()
+    ref_s = ref[jw.sector]
+    Hbar = expm(-Tm) @ Hm @ expm(Tm)
+    R_jw = np.array([d @ Hbar @ ref_s for d in dets])
+    e_jw = ref_s @ Hbar @ ref_s - ref_s @ Hm @ ref_s
+    assert np.abs(R - R_jw).max() < 1e-12
+    assert abs(e - e_jw) < 1e-12
+
+
+@pytest.mark.parametrize("K_H", [3, 2])
+def test_truncated_hamiltonian_slater_condon(K_H):
+    """N = 3: the oracle's bare (h', v') as a Jordan-Wigner operator.  Its
+    reference expectation is the full E_ref, its singles-reference elements
+    are the full Fock matrix, and its doubles-reference and opposite-spin
+    singles-singles elements are the integrals (ai|bj) and (ai|jb) when
+    a, i, b, j carry at most K_H labels and zero otherwise."""
+    H = build_ppp('polyene', 6)
+    n = H.n_orb
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=K_H)
+    jw = JW(n, n)
+    a, ad = jw.a, jw.ad
+    Hm = jw.hamiltonian(P.hp, P.vt)
+    occ = sorted(int(i) for i in H.occ_of_pair)
+    vir = sorted(int(x) for x in H.vir_of_pair)
+    ref = jw.det(occ, occ)
+    Href = Hm @ ref
+    eri, h = H.eri, H.h
+    f = h + 2.0 * np.einsum('pqii->pq', eri[:, :, occ][:, :, :, occ]) \
+        - np.einsum('piiq->pq', eri[:, occ][:, :, occ])
+    assert abs(ref @ Href - sum(h[i, i] + f[i, i] for i in occ)) < 1e-12
+
+    lab = _labels(H)
+
+    def kept(*orbs):
+        return len({lab[o] for o in orbs}) <= K_H
+
+    al = lambda p: p
+    be = lambda p: p + n
+    n_masked = 0
+    for i in occ:
+        for x in vir:
+            for s in (al, be):
+                v = ad[s(x)] @ (a[s(i)] @ ref)
+                assert abs(v @ Href - f[x, i]) < 1e-12
+            for j in occ:
+                for y in vir:
+                    d = ad[al(x)] @ (ad[be(y)] @ (a[be(j)] @ (a[al(i)] @ ref)))
+                    want = eri[x, i, y, j] if kept(x, i, y, j) else 0.0
+                    assert abs(d @ Href - want) < 1e-12
+                    n_masked += not kept(x, i, y, j)
+                    s1 = ad[al(x)] @ (a[al(i)] @ ref)
+                    s2 = ad[be(y)] @ (a[be(j)] @ ref)
+                    want = eri[x, i, j, y] if kept(x, i, j, y) else 0.0
+                    assert abs(s1 @ (Hm @ s2) - want) < 1e-12
+                    if i < j and x < y:
+                        d = ad[al(x)] @ (ad[al(y)] @ (a[al(j)] @ (a[al(i)] @ ref)))
+                        want = ((eri[x, i, y, j] if kept(x, i, y, j) else 0.0)
+                                - (eri[x, j, y, i] if kept(x, j, y, i) else 0.0))
+                        assert abs(d @ Href - want) < 1e-12
+    # the two-label truncation really removes three-label integrals here
+    assert (n_masked > 0) == (K_H == 2)
+    assert np.abs(eri[np.ix_(vir, occ, vir, occ)]).max() > 1e-3
+
+
+def test_ph_size_consistency_three_plus_one_pairs():
+    """Hexatriene PPP (3 pairs) and H2 (1 pair) as one non-interacting system,
+    pairs interleaved: E_PH(A+B) = E_FCI(A) + E_FCI(B)."""
+    A = build_ppp('polyene', 6)
+    B = build_hchain(2, 1.4)
+    AB = _direct_sum(A, B)
+    P = Problem(AB.h, AB.eri, AB.occ_of_pair, AB.vir_of_pair, K=3, e_const=AB.e_const)
+    r = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    assert r['converged']
+    fa = fci_energy(A.h, A.eri, 3, A.e_const)
+    fb = fci_energy(B.h, B.eri, 1, B.e_const)
+    assert abs(r['e_corr'] + P.e_ref - (fa + fb)) < 1e-9
