@@ -6,7 +6,8 @@ independent of the oracle's own formulas.
   FCI, and PQ equals PH at 4e/4o.
 * A complete manifold (K >= number of pairs) with untruncated integrals is FCI.
 * Size consistency (inherited from CC, Theory section): a direct sum of two
-  non-interacting fragments has the sum of the fragment energies.
+  non-interacting fragments has the sum of the fragment energies, and two
+  H chains 100 A apart (one RHF, fragment-local pairs) nearly so.
 * Invariance to swapping pairs (Theory section) and to MO sign changes;
   non-invariance of PQ to occupied-occupied rotations and to the choice of
   which virtual is paired with which occupied orbital (Theory section), while
@@ -111,6 +112,38 @@ def test_fragment_additivity_pq_nontrivial_fragments():
     r = jacobi_diis(P.residual, d, len(P.manifold), r_tol=1e-11, e_tol=1e-13, max_iter=400)
     assert r['converged']
     assert abs(r['e_corr'] + P.e_ref + AB.e_const - (ea + eb)) < 1e-9
+
+
+def test_far_separated_chains_size_consistency():
+    """Physical, not block-diagonal: H4 (1.5 A spacing) and H2 (0.74 A) on one
+    line 100 A apart, one RHF for all six atoms (every cross integral kept),
+    pairs formed inside each fragment.  The neutral fragments interact through
+    multipoles (quadrupole-quadrupole, R^-5) and dispersion (R^-6), about 1e-12
+    Eh here, so E_PQ(A+B) = E_PQ(A) + E_PQ(B) to 5e-11."""
+    from workloads.hchain import ao_integrals_at, chain_positions, BOHR_PER_ANGSTROM
+    from workloads.scf import rhf, mo_integrals
+    zA = chain_positions(4, 1.5)
+    zB = chain_positions(2, 0.74) + zA[-1] + 100.0 * BOHR_PER_ANGSTROM
+    S, h, eri, e_nuc = ao_integrals_at(np.concatenate([zA, zB]))
+    n = len(zA) + len(zB)
+
+    def jk(P):
+        J = (eri.reshape(n * n, n * n) @ P.ravel()).reshape(n, n)
+        K = (eri.transpose(0, 2, 1, 3).reshape(n * n, n * n) @ P.ravel()).reshape(n, n)
+        return J, K
+    e, C, _ = rhf(S, h, n // 2, jk)
+    on_a = (C[:len(zA)] ** 2).sum(0) / (C ** 2).sum(0)
+    assert np.all(np.minimum(on_a, 1.0 - on_a) < 1e-10)      # every MO on one fragment
+    occ, vir = [], []
+    for frag in (on_a > 0.5, on_a < 0.5):
+        occ += sorted((k for k in range(n // 2) if frag[k]), key=lambda k: -e[k])
+        vir += sorted((k for k in range(n // 2, n) if frag[k]), key=lambda k: e[k])
+    h_mo, eri_mo = mo_integrals(C, h, eri_ao=eri)
+    AB = Hamiltonian("H4 + H2", h_mo, eri_mo, e_nuc, np.array(occ), np.array(vir), e)
+    e_ab, _, _ = solve_total(AB, K=2)
+    e_a, _, _ = solve_total(build_hchain(4, 1.5), K=2)
+    e_b, _, _ = solve_total(build_hchain(2, 0.74), K=2)
+    assert abs(e_ab - (e_a + e_b)) < 5e-11
 
 
 def _permute_pairs(H, perm):

@@ -32,14 +32,20 @@ def chain_positions(n_atoms, spacing_angstrom, bond_bohr=None):
 
 
 def hchain_ao_integrals(n_atoms, spacing_angstrom, bond_bohr=None):
-    z = chain_positions(n_atoms, spacing_angstrom, bond_bohr)
+    return ao_integrals_at(chain_positions(n_atoms, spacing_angstrom, bond_bohr))
+
+
+def ao_integrals_at(z):
+    """(S, T+V, ERI, E_nuc) for hydrogen atoms at the z coordinates z (bohr)
+    on one line, one contracted s function each."""
+    z = np.asarray(z, dtype=float)
     a = STO3G_EXPONENTS
     c = STO3G_COEFFS * (2.0 * a / np.pi) ** 0.75
     # renormalise the contraction exactly
     pab = a[:, None] + a[None, :]
     s_self = (c[:, None] * c[None, :] * (np.pi / pab) ** 1.5).sum()
     c = c / np.sqrt(s_self)
-    n, k = n_atoms, len(a)
+    n, k = len(z), len(a)
     # primitive pair quantities for every AO pair (mu, nu) and primitives (i, j)
     A = z[:, None, None, None]; B = z[None, :, None, None]
     al = a[None, None, :, None]; be = a[None, None, None, :]
