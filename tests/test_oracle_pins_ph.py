@@ -2,8 +2,8 @@
 
 * Residual and energy at random amplitudes for K = 3 (every excitation of
   three pairs, up to hextuples) against a Jordan-Wigner construction of
-  exp(-T) H exp(T) with scipy's expm, in the six-electron sector of twelve
-  spin orbitals, with the integrals truncated to three labels (all kept at
+  exp(-T) H exp(T) with scipy's expm, in the 400-state sector of three
+  alpha and three beta electrons in twelve spin orbitals, with the integrals truncated to three labels (all kept at
   N = 3) and to two labels (Table I, Implementation section).
 * The truncated bare Hamiltonian against the Slater-Condon rules: its
   normal-ordered one-body part is the full Fock matrix and its two-body part
@@ -14,73 +14,13 @@
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 from scipy.linalg import expm
 
 from workloads import build_ppp, build_hchain
 from oracle.detcc import Problem
 from oracle.fci import fci_energy
 from tests.test_oracle_pins import _direct_sum
-
-
-def _jw_sparse(nso):
-    """Annihilators a_k on nso spin orbitals (basis bit k is the k-th kron
-    factor; 0 = empty), as sparse matrices."""
-    I = sp.identity(2, format="csr")
-    Z = sp.csr_matrix(np.diag([1.0, -1.0]))
-    a = sp.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))
-    ops = []
-    for k in range(nso):
-        m = sp.csr_matrix(np.array([[1.0]]))
-        for j in range(nso):
-            m = sp.kron(m, Z if j < k else (a if j == k else I), format="csr")
-        ops.append(m)
-    return ops
-
-
-def _occupations(nso):
-    idx = np.arange(2 ** nso)
-    return np.array([[(i >> (nso - 1 - k)) & 1 for k in range(nso)] for i in idx])
-
-
-class JW:
-    """Fermion operators of n spatial orbitals (spin orbital p + n*s) in the
-    sector of n_el electrons."""
-
-    def __init__(self, n, n_el):
-        self.n = n
-        self.a = _jw_sparse(2 * n)
-        self.ad = [x.T.tocsr() for x in self.a]
-        occ = _occupations(2 * n)
-        self.sector = np.flatnonzero(occ.sum(1) == n_el)
-        self.vac = np.zeros(2 ** (2 * n))
-        self.vac[0] = 1.0
-
-    def restrict(self, m):
-        return m.tocsr()[self.sector][:, self.sector]
-
-    def det(self, alpha, beta):
-        """a+ (alpha ascending) a+ (beta ascending) |vac>."""
-        v = self.vac.copy()
-        for c in reversed([self.ad[x] for x in sorted(alpha)]
-                          + [self.ad[x + self.n] for x in sorted(beta)]):
-            v = c @ v
-        return v
-
-    def hamiltonian(self, h1, v2):
-        n, a, ad = self.n, self.a, self.ad
-        H = sp.csr_matrix((2 ** (2 * n), 2 ** (2 * n)))
-        for p in range(n):
-            for q in range(n):
-                if h1[p, q] != 0.0:
-                    for s in range(2):
-                        H = H + h1[p, q] * (ad[p + n * s] @ a[q + n * s])
-        for p, q, r, u in zip(*np.nonzero(v2)):
-            for s1 in range(2):
-                for s2 in range(2):
-                    H = H + 0.5 * v2[p, q, r, u] * (
-                        ad[p + n * s1] @ ad[r + n * s2] @ a[u + n * s2] @ a[q + n * s1])
-        return H
+from tests.jw import JW
 
 
 def _labels(H):
@@ -92,7 +32,7 @@ def _labels(H):
 
 @pytest.mark.parametrize("K_H", [3, 2])
 def test_ph_residual_random_t_against_jordan_wigner_expm(K_H):
-    """N = 3 (hexatriene PPP, 12 spin orbitals, 924 six-electron states):
+    """N = 3 (hexatriene PPP, 12 spin orbitals, 400 states of 3 + 3 electrons):
     every tau_D of the 399 three-pair amplitudes and H as sparse Jordan-Wigner
     products, exp(+-T) by scipy expm; linked residual and energy compared."""
     H = build_ppp('polyene', 6)
@@ -102,28 +42,20 @@ def test_ph_residual_random_t_against_jordan_wigner_expm(K_H):
     t = np.random.default_rng(4242).uniform(-0.1, 0.1, P.cc.n_amp)
     R, e = P.residual(t)
 
-    jw = JW(n, n)
-    a, ad = jw.a, jw.ad
+    jw = JW(n, n // 2, n // 2)
     occ = sorted(int(i) for i in H.occ_of_pair)
     ref = jw.det(occ, occ)
-    T = sp.csr_matrix((2 ** (2 * n), 2 ** (2 * n)))
+    T = 0.0
     dets = []
     for tk, (ah, ap, bh, bp) in zip(t, P.cc.manifold):
-        op = sp.identity(2 ** (2 * n), format="csr")
-        for m in ([ad[x] for x in ap] + [a[x] for x in reversed(ah)]
-                  + [ad[x + n] for x in bp] + [a[x + n] for x in reversed(bh)]):
-            op = op @ m
-        det = jw.det(sorted(set(occ) - set(ah) | set(ap)), sorted(set(occ) - set(bh) | set(bp)))
-        sgn = float(det @ (op @ ref))
-        assert abs(abs(sgn) - 1.0) < 1e-12
-        T = T + (tk * sgn) * op
-        dets.append(det[jw.sector])
-    Hm = jw.restrict(jw.hamiltonian(P.hp, P.vt)).toarray()
-    Tm = jw.restrict(T).toarray()
-    ref_s = ref[jw.sector]
+        tau, D = jw.excitation(ah, ap, bh, bp, occ)
+        T = T + tk * tau
+        dets.append(D)
+    Hm = jw.hamiltonian(P.hp, P.vt).toarray()
+    Tm = T.toarray()
     Hbar = expm(-Tm) @ Hm @ expm(Tm)
-    R_jw = np.array([d @ Hbar @ ref_s for d in dets])
-    e_jw = ref_s @ Hbar @ ref_s - ref_s @ Hm @ ref_s
+    R_jw = np.array([d @ Hbar @ ref for d in dets])
+    e_jw = ref @ Hbar @ ref - ref @ Hm @ ref
     assert np.abs(R - R_jw).max() < 1e-12
     assert abs(e - e_jw) < 1e-12
 
@@ -138,7 +70,7 @@ def test_truncated_hamiltonian_slater_condon(K_H):
     H = build_ppp('polyene', 6)
     n = H.n_orb
     P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=K_H)
-    jw = JW(n, n)
+    jw = JW(n, n // 2, n // 2)
     a, ad = jw.a, jw.ad
     Hm = jw.hamiltonian(P.hp, P.vt)
     occ = sorted(int(i) for i in H.occ_of_pair)
@@ -161,20 +93,20 @@ def test_truncated_hamiltonian_slater_condon(K_H):
     for i in occ:
         for x in vir:
             for s in (al, be):
-                v = ad[s(x)] @ (a[s(i)] @ ref)
+                v = jw.product([ad[s(x)], a[s(i)]]) @ ref
                 assert abs(v @ Href - f[x, i]) < 1e-12
             for j in occ:
                 for y in vir:
-                    d = ad[al(x)] @ (ad[be(y)] @ (a[be(j)] @ (a[al(i)] @ ref)))
+                    d = jw.product([ad[al(x)], ad[be(y)], a[be(j)], a[al(i)]]) @ ref
                     want = eri[x, i, y, j] if kept(x, i, y, j) else 0.0
                     assert abs(d @ Href - want) < 1e-12
                     n_masked += not kept(x, i, y, j)
-                    s1 = ad[al(x)] @ (a[al(i)] @ ref)
-                    s2 = ad[be(y)] @ (a[be(j)] @ ref)
+                    s1 = jw.product([ad[al(x)], a[al(i)]]) @ ref
+                    s2 = jw.product([ad[be(y)], a[be(j)]]) @ ref
                     want = eri[x, i, j, y] if kept(x, i, j, y) else 0.0
                     assert abs(s1 @ (Hm @ s2) - want) < 1e-12
                     if i < j and x < y:
-                        d = ad[al(x)] @ (ad[al(y)] @ (a[al(j)] @ (a[al(i)] @ ref)))
+                        d = jw.product([ad[al(x)], ad[al(y)], a[al(j)], a[al(i)]]) @ ref
                         want = ((eri[x, i, y, j] if kept(x, i, y, j) else 0.0)
                                 - (eri[x, j, y, i] if kept(x, j, y, i) else 0.0))
                         assert abs(d @ Href - want) < 1e-12
