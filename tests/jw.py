@@ -58,45 +58,49 @@ class JW:
         return self._E[key]
 
     def det(self, alpha, beta):
-        """a+ (alpha ascending) a+ (beta ascending) |vac>, as a sector vector."""
+        """a+ (alpha ascending) a+ (beta ascending) |vac>, as a sector vector.
+        Creators applied in descending spin-orbital order never pass an
+        occupied orbital, so the state is +1 on its basis vector."""
         nso = 2 * self.n
-        v = np.zeros(2 ** nso)
-        v[0] = 1.0
-        for c in reversed([self.ad[x] for x in sorted(alpha)]
-                          + [self.ad[x + self.n] for x in sorted(beta)]):
-            v = c @ v
-        return v[self.sector]
+        idx = 0
+        for x in list(alpha) + [b + self.n for b in beta]:
+            idx |= 1 << (nso - 1 - x)
+        v = np.zeros(self.dim)
+        pos = np.searchsorted(self.sector, idx)
+        if pos == self.dim or self.sector[pos] != idx:
+            raise ValueError("determinant outside the sector")
+        v[pos] = 1.0
+        return v
+
+    def _lincomb(self, terms):
+        """sum of coef * matrix over (coef, matrix) pairs, in one pass."""
+        rows, cols, vals = [], [], []
+        for c, m in terms:
+            m = m.tocoo()
+            rows.append(m.row); cols.append(m.col); vals.append(c * m.data)
+        if not rows:
+            return sp.csr_matrix((self.dim, self.dim))
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.dim, self.dim))
 
     def hamiltonian(self, h1, v2):
         """sum h1[p,q] E_pq + 1/2 sum v2[p,q,r,s] (E_pq E_rs - delta_qr E_ps),
         spin-summed; v2 in chemists' notation."""
         n = self.n
-        H = sp.csr_matrix((self.dim, self.dim))
-        for s in range(2):
-            for p in range(n):
-                for q in range(n):
-                    if h1[p, q] != 0.0:
-                        H = H + h1[p, q] * self.E(p, q, s)
-        if not np.any(v2):
-            return H
+        terms = [(h1[p, q], self.E(p, q, s)) for s in range(2) for p in range(n)
+                 for q in range(n) if h1[p, q] != 0.0]
         for s1 in range(2):
             for p in range(n):
                 for q in range(n):
                     blk = v2[p, q]
                     if not np.any(blk):
                         continue
-                    inner = sp.csr_matrix((self.dim, self.dim))
-                    for s2 in range(2):
-                        for r in range(n):
-                            for u in range(n):
-                                if blk[r, u] != 0.0:
-                                    inner = inner + blk[r, u] * self.E(r, u, s2)
-                    H = H + 0.5 * (self.E(p, q, s1) @ inner)
+                    inner = self._lincomb([(blk[r, u], self.E(r, u, s2)) for s2 in range(2)
+                                           for r in range(n) for u in range(n) if blk[r, u] != 0.0])
+                    terms.append((0.5, self.E(p, q, s1) @ inner))
                     # the delta_qr E_ps term (same spin only)
-                    for u in range(n):
-                        if blk[q, u] != 0.0:
-                            H = H - 0.5 * blk[q, u] * self.E(p, u, s1)
-        return H
+                    terms += [(-0.5 * blk[q, u], self.E(p, u, s1)) for u in range(n) if blk[q, u] != 0.0]
+        return self._lincomb(terms)
 
     def excitation(self, holes_a, parts_a, holes_b, parts_b, occ):
         """tau with tau|Phi> = +|D>: the particle creators then the hole
@@ -106,7 +110,7 @@ class JW:
         seq = ([self.ad[x] for x in parts_a] + [self.a[x] for x in reversed(holes_a)]
                + [self.ad[x + n] for x in parts_b] + [self.a[x + n] for x in reversed(holes_b)])
         op = self.product(seq)
-        ref = self.det(occ, occ)
+        ref = self.det(sorted(occ), sorted(occ))
         D = self.det(sorted(set(occ) - set(holes_a) | set(parts_a)),
                      sorted(set(occ) - set(holes_b) | set(parts_b)))
         sgn = float(D @ (op @ ref))
