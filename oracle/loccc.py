@@ -36,17 +36,20 @@ def _moebius_coeff(N, k, kmax):
 class LocalAssembly:
     """Residual and energy of a PQ/PH problem by local inclusion-exclusion."""
 
-    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0, subsets=None):
+    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0, subsets=None, truncated=None):
         """subsets: optional list of label subsets; when given, only those local
         problems are built and residual() returns their partial sum (used to
-        time a bounded sample of a large problem)."""
+        time a bounded sample of a large problem, and to split one residual
+        over processes).  truncated: optional result of truncated_hamiltonian
+        for these integrals, pairing and K_H, computed once by the caller (h
+        and eri are then not read)."""
         self.K = K
         self.K_H = K if K_H == 0 else K_H
         self.occ = np.asarray(occ_of_pair); self.vir = np.asarray(vir_of_pair)
         self.N = len(self.occ)
-        n = h.shape[0]
-        self.hp, self.vt, self.f, self.e_ref = truncated_hamiltonian(
-            h, eri, self.occ, self.vir, self.K_H)
+        if truncated is None:
+            truncated = truncated_hamiltonian(h, eri, self.occ, self.vir, self.K_H)
+        self.hp, self.vt, self.f, self.e_ref = truncated
         self.manifold = enumerate_manifold(self.occ, self.vir, K)
         self.index = {d: k for k, d in enumerate(self.manifold)}
         self.global_ref = sum(1 << int(i) for i in self.occ)

@@ -6,11 +6,23 @@ by 3xTF32 products, FP64 by exact integer splitting) beyond one 128-row tile.
   against the oracle's local assembly restricted to the label subsets that
   contain the pair (exact for those elements), FP32 within 2e-5 * max|R|,
   FP64 within 1e-11;
+* N = 70, the time-to-solution workload (PPP C140H142, Boys-localised
+  pairs; 2415 unordered pairs in 19 tiles, the last one ragged): every
+  pair-amplitude element of a pair in a middle tile and of the last pair
+  against the oracle's local assembly over the 2347 label sets containing
+  each pair, run as a separate process split over the host cores
+  (tests/oloc_sampled.py).  FP64 within 1e-9: the exact slicing drops
+  products below about 2^-41 of the row and block scales, and each element
+  sums a few 10^4 such products over X, W and the channels (below 1e-11 at
+  N = 20); FP32 within 2e-5 * max|R| as above;
 * N = 40 and 70 (7 and 19 tiles, 48 and 80 TMEM columns per g): the whole
   FP32 residual against the FP64 one (oracle-pinned at N <= 12 and on the
-  N = 20 samples above) within the same FP32 bound -- a property that holds
-  at any size.
+  N = 20 and N = 70 samples) within the same FP32 bound -- a property that
+  holds at any size.
 """
+import os
+import subprocess
+import sys
 from itertools import combinations
 
 import numpy as np
@@ -27,6 +39,9 @@ from workloads import build_ppp, ppp_eri_device, random_pair_amplitude_seed
 from oracle.loccc import LocalAssembly
 from oracle.detcc import enumerate_manifold
 from tests.layout import LayoutMap
+from tests.oloc_sampled import amplitudes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def dev(x):
@@ -86,3 +101,33 @@ def test_fp32_tensor_core_residual_matches_fp64(size):
     scale = np.abs(r64).max()
     assert np.abs(r32 - r64).max() < 2e-5 * scale
     assert abs(e32 - e64) < 2e-5 * max(1.0, abs(e64))
+
+
+def test_bench_workload_sampled_pairs_match_oracle(tmp_path):
+    out = tmp_path / "sampled.npz"
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    oracle = subprocess.Popen([sys.executable, "-m", "tests.oloc_sampled", "--size", "140",
+                               "--orbitals", "local", "--pairs", "33,34", "68,69", "--tag", "0",
+                               "--out", str(out)], cwd=ROOT, env=env)
+    try:
+        H = build_ppp('polyene', 140, orbitals='local', with_eri=False)
+        N = H.n_pairs
+        assert N == 70
+        eri = ppp_eri_device(H, torch)
+        man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+        lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+        res = residuals(H, lm.to_layout(amplitudes(len(man), N, 0)), eri)
+        del eri
+        assert oracle.wait(timeout=1800) == 0
+    finally:
+        if oracle.poll() is None:
+            oracle.kill()
+    got = np.load(out)
+    idx, R_ref = got["idx"], got["vals"]
+    assert len(idx) == 2 * 29
+    R64 = lm.from_layout(res[0][0])
+    R32 = lm.from_layout(res[1][0])
+    assert np.abs(R_ref).max() > 1e-2
+    assert np.abs(R64[idx] - R_ref).max() < 1e-9
+    scale = max(np.abs(R_ref).max(), np.abs(R64).max())
+    assert np.abs(R32[idx] - R_ref).max() < 2e-5 * scale

@@ -1,0 +1,36 @@
+"""The process-split sampled oracle (tests/oloc_sampled.py) as GPU tests run
+it -- a command in a fresh process -- against the oracle's serial local
+assembly over every label set, at N = 6."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+from oracle.detcc import enumerate_manifold
+from oracle.loccc import LocalAssembly
+from tests.oloc_sampled import workload, amplitudes, pair_subsets
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_pair_subsets_count():
+    # 1 + (N - 2) + C(N - 2, 2) label sets per pair for PQ; shared ones once
+    assert len(pair_subsets(70, [(33, 34)], 4)) == 1 + 68 + 68 * 67 // 2
+    assert len(pair_subsets(6, [(0, 1), (0, 1)], 4)) == 1 + 4 + 6
+
+
+def test_sampled_command_matches_serial_oracle(tmp_path):
+    out = tmp_path / "s.npz"
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "12", "--pairs", "0,1", "2,5",
+                    "--tag", "3", "--workers", "2", "--out", str(out)],
+                   cwd=ROOT, env=env, check=True, timeout=600)
+    got = np.load(out)
+    H = workload("polyene", 12, "canonical")
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    t = amplitudes(len(man), H.n_pairs, 3)
+    R, _ = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2).residual(t)
+    assert len(got["idx"]) == 2 * 29
+    assert np.abs(R[got["idx"]]).max() > 1e-3
+    assert np.abs(got["vals"] - R[got["idx"]]).max() < 1e-13
