@@ -12,9 +12,10 @@ run this module as a command in a fresh process:
         --pairs 33,34 68,69 --tag 0 --workers 16 --out sampled.npz
 
 The amplitudes are uniform(-0.1, 0.1) over the oracle's manifold from
-random_pair_amplitude_seed(N, tag), so the caller can draw the same ones.
-The output holds the manifold indices of the sampled pairs' elements and
-their exact residual values.
+random_pair_amplitude_seed(N, tag), so the caller can draw the same ones, or
+are read from --t-in.  The output holds the manifold indices of the sampled
+pairs' elements and their exact residual values, the reference energy and
+constant and, with --energy, the correlation energy at those amplitudes.
 """
 import argparse
 import multiprocessing as mp
@@ -24,7 +25,7 @@ from itertools import combinations
 import numpy as np
 
 from workloads import build_ppp, build_hchain, random_pair_amplitude_seed
-from oracle.detcc import truncated_hamiltonian
+from oracle.detcc import truncated_hamiltonian, enumerate_manifold
 from oracle.loccc import LocalAssembly
 
 _SHARED = {}
@@ -45,27 +46,36 @@ def _chunk_residual(subsets):
     d = _SHARED
     L = LocalAssembly(None, None, d["occ"], d["vir"], d["K"], d["K_H"], subsets=subsets,
                       truncated=d["truncated"])
-    return L.residual(d["t"])[0]
+    return L.residual(d["t"])
 
 
-def sampled_residual(h, eri, occ, vir, pairs, t, K=2, K_H=2, workers=2):
-    """(indices, values): the oracle's residual elements of the given pairs at
-    amplitudes t (over the oracle's manifold), exact.  Uses a fork pool."""
+def sampled_residual(h, eri, occ, vir, pairs, t, K=2, K_H=2, workers=2, energy=False):
+    """(indices, values, e_c, e_ref): the oracle's residual elements of the
+    given pairs at amplitudes t (over the oracle's manifold), exact; with
+    energy=True also the correlation energy at t (every label set of at most
+    K_H labels is added), else None; e_ref is the reference energy without
+    the constant.  Uses a fork pool."""
     occ = np.asarray(occ)
     vir = np.asarray(vir)
     truncated = truncated_hamiltonian(h, eri, occ, vir, K_H)
-    subsets = pair_subsets(len(occ), pairs, K + K_H)
+    subsets = set(pair_subsets(len(occ), pairs, K + K_H))
+    if energy:
+        for m in range(1, K_H + 1):
+            subsets.update(combinations(range(len(occ)), m))
+    subsets = sorted(subsets)
     _SHARED.update(occ=occ, vir=vir, K=K, K_H=K_H, truncated=truncated, t=np.asarray(t, float))
     chunks = [subsets[i::workers] for i in range(workers)]
     try:
         with mp.get_context("fork").Pool(workers) as pool:
-            R = sum(pool.map(_chunk_residual, [c for c in chunks if c]))
+            parts = pool.map(_chunk_residual, [c for c in chunks if c])
     finally:
         _SHARED.clear()
+    R = sum(p[0] for p in parts)
+    e_c = sum(p[1] for p in parts) if energy else None
     probe = LocalAssembly(None, None, occ, vir, K, K_H, subsets=[], truncated=truncated)
     want = [set(p) for p in pairs]
     idx = np.array([k for k, d in enumerate(probe.manifold) if probe._labels(d) in want], dtype=np.int64)
-    return idx, R[idx]
+    return idx, R[idx], e_c, truncated[3]
 
 
 def workload(kind, size, orbitals):
@@ -87,16 +97,20 @@ def main(argv=None):
     ap.add_argument("--tag", type=int, default=0)
     ap.add_argument("--K", type=int, default=2)
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--t-in", default=None, help="amplitudes over the oracle's manifold (.npy)")
+    ap.add_argument("--energy", action="store_true", help="also the correlation energy at t")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     H = workload(a.kind, a.size, a.orbitals)
     pairs = [tuple(int(x) for x in p.split(",")) for p in a.pairs]
-    from oracle.detcc import enumerate_manifold
-    n_amp = len(enumerate_manifold(H.occ_of_pair, H.vir_of_pair, a.K))
-    t = amplitudes(n_amp, H.n_pairs, a.tag)
-    idx, vals = sampled_residual(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, pairs, t,
-                                 K=a.K, K_H=a.K, workers=a.workers)
-    np.savez(a.out, idx=idx, vals=vals)
+    if a.t_in:
+        t = np.load(a.t_in)
+    else:
+        t = amplitudes(len(enumerate_manifold(H.occ_of_pair, H.vir_of_pair, a.K)), H.n_pairs, a.tag)
+    idx, vals, e_c, e_ref = sampled_residual(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, pairs, t,
+                                             K=a.K, K_H=a.K, workers=a.workers, energy=a.energy)
+    np.savez(a.out, idx=idx, vals=vals, e_c=np.nan if e_c is None else e_c, e_ref=e_ref,
+             e_const=H.e_const)
 
 
 if __name__ == "__main__":

@@ -1,6 +1,11 @@
 """Batched solve: many Hamiltonians of different pair counts in one call give
 the same energies and amplitudes as one-by-one solves (and, for the small
-members, as the oracle)."""
+members, as the oracle).  The largest member (N = 20) is checked by the
+oracle at the amplitudes the batched mixed-precision solve returns."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -12,7 +17,10 @@ if not torch.cuda.is_available():
 
 import paper_1609_00077_gb300 as ppq
 from workloads import build_hchain, build_ppp
-from oracle.detcc import Problem
+from oracle.detcc import Problem, enumerate_manifold
+from tests.layout import LayoutMap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _systems():
@@ -59,3 +67,29 @@ def test_batched_reports_per_system_status():
     rc, e_b, infos = ppq.pq_solve_batched(syst, max_iter=2)
     assert rc == 1 and all(i['status'] == 1 for i in infos)
     assert np.all(e_b == e_b[0])
+
+
+def test_batched_largest_member_against_oracle(tmp_path):
+    """PPP C40H42 with Boys-localised pairs (N = 20) inside a mixed-precision
+    batch: at the returned amplitudes the oracle's energy (every label set of
+    at most two labels) equals the batched energy to 1e-8 Eh, and the oracle's
+    residual elements of two sampled pairs, one per 128-row tile, vanish to
+    1e-8 (the solve stops at ||R|| <= 1e-10 in FP64)."""
+    Hs = _systems()
+    syst = [(H.occ_of_pair, H.vir_of_pair, torch.from_numpy(H.h).cuda(),
+             torch.from_numpy(H.eri).cuda(), H.e_const) for H in Hs]
+    rc, e_b, infos, amps = ppq.pq_solve_batched(syst, precision=1, max_iter=400, with_amplitudes=True)
+    k = len(Hs) - 1
+    H = Hs[k]
+    assert H.n_pairs == 20 and infos[k]['status'] == 0
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+    np.save(tmp_path / "t.npy", lm.from_layout(amps[k]))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "40", "--orbitals", "local",
+                    "--pairs", "0,1", "18,19", "--t-in", str(tmp_path / "t.npy"), "--energy",
+                    "--out", str(tmp_path / "o.npz")], cwd=ROOT, env=env, check=True, timeout=1800)
+    got = np.load(tmp_path / "o.npz")
+    assert len(got["idx"]) == 2 * 29
+    assert abs(float(got["e_c"] + got["e_ref"] + got["e_const"]) - e_b[k]) < 1e-8
+    assert np.abs(got["vals"]).max() < 1e-8

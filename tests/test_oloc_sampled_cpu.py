@@ -20,17 +20,31 @@ def test_pair_subsets_count():
     assert len(pair_subsets(6, [(0, 1), (0, 1)], 4)) == 1 + 4 + 6
 
 
-def test_sampled_command_matches_serial_oracle(tmp_path):
-    out = tmp_path / "s.npz"
+def _run(args, cwd):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "12", "--pairs", "0,1", "2,5",
-                    "--tag", "3", "--workers", "2", "--out", str(out)],
-                   cwd=ROOT, env=env, check=True, timeout=600)
-    got = np.load(out)
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled"] + args, cwd=cwd, env=env,
+                   check=True, timeout=600)
+
+
+def test_sampled_command_matches_serial_oracle(tmp_path):
     H = workload("polyene", 12, "canonical")
     man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
-    t = amplitudes(len(man), H.n_pairs, 3)
-    R, _ = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2).residual(t)
+    L = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2)
+    # seeded amplitudes
+    out = tmp_path / "s.npz"
+    _run(["--size", "12", "--pairs", "0,1", "2,5", "--tag", "3", "--workers", "2", "--out", str(out)], ROOT)
+    got = np.load(out)
+    R, _ = L.residual(amplitudes(len(man), H.n_pairs, 3))
     assert len(got["idx"]) == 2 * 29
     assert np.abs(R[got["idx"]]).max() > 1e-3
     assert np.abs(got["vals"] - R[got["idx"]]).max() < 1e-13
+    assert np.isnan(got["e_c"]) and abs(got["e_ref"] - L.e_ref) < 1e-12
+    # given amplitudes, with the energy
+    t = np.random.default_rng(11).uniform(-0.05, 0.05, len(man))
+    np.save(tmp_path / "t.npy", t)
+    _run(["--size", "12", "--pairs", "1,4", "--t-in", str(tmp_path / "t.npy"), "--energy",
+          "--workers", "3", "--out", str(out)], ROOT)
+    got = np.load(out)
+    R, e = L.residual(t)
+    assert np.abs(got["vals"] - R[got["idx"]]).max() < 1e-13
+    assert abs(got["e_c"] - e) < 1e-12 and abs(e) > 1e-3
