@@ -131,3 +131,27 @@ def test_bench_workload_sampled_pairs_match_oracle(tmp_path):
     assert np.abs(R64[idx] - R_ref).max() < 1e-9
     scale = max(np.abs(R_ref).max(), np.abs(R64).max())
     assert np.abs(R32[idx] - R_ref).max() < 2e-5 * scale
+
+
+def test_bench_workload_solution_against_oracle(tmp_path):
+    """The time-to-solution solve itself (C140H142, mixed precision, default
+    tolerances): at the amplitudes it returns, the oracle's energy (all 2485
+    label sets of at most two labels) equals the returned energy to 1e-8 Eh,
+    and the oracle's residual elements of the last pair (the ragged tile)
+    vanish to 1e-8 (the solve stops at ||R|| <= 1e-10 in FP64)."""
+    H = build_ppp('polyene', 140, orbitals='local', with_eri=False)
+    eri = ppp_eri_device(H, torch)
+    rc, e, t, info = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), eri, H.e_const, precision=1)
+    del eri
+    assert rc == 0 and info['polish_iters'] > 0
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
+    np.save(tmp_path / "t.npy", lm.from_layout(t))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "140", "--orbitals", "local",
+                    "--pairs", "68,69", "--t-in", str(tmp_path / "t.npy"), "--energy",
+                    "--out", str(tmp_path / "o.npz")], cwd=ROOT, env=env, check=True, timeout=1800)
+    got = np.load(tmp_path / "o.npz")
+    assert len(got["idx"]) == 29
+    assert abs(float(got["e_c"] + got["e_ref"] + got["e_const"]) - e) < 1e-8
+    assert np.abs(got["vals"]).max() < 1e-8
