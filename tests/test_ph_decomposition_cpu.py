@@ -7,13 +7,17 @@ H_S reproduces every residual element and the energy to FP64 rounding, for
 PH with three- and two-label integrals and for PQ.  Controls: without the
 exp(-B) transform, or with A cut down to the clusters inside S, the sum is
 wrong; with A widened to clusters that leave U, it is unchanged (those
-clusters leave a label excited).
+clusters leave a label excited).  With PPQ_LONG_CHECKS=1 the same holds at
+N = 5 (H10), where terms reach five labels (about 4 min per case; both cases
+agreed to 4e-15 when last run).
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from workloads import build_ppp
+from workloads import build_ppp, build_hchain
 from oracle.detcc import Problem
 from tests.ph_decomposition import Decomposed, _expv
 
@@ -83,3 +87,17 @@ def test_decomposition_controls(system, mode, exact):
         assert err < 1e-12
     else:
         assert err > 1e-3
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("PPQ_LONG_CHECKS") != "1",
+                    reason="about 4 min per case; set PPQ_LONG_CHECKS=1")
+@pytest.mark.parametrize("K_H", [3, 2])
+def test_pieces_sum_to_the_residual_n5(K_H):
+    """N = 5 (H10): terms of up to five labels (|M| = 3 with two extra labels)."""
+    H = build_hchain(10, 1.6)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=K_H)
+    t = np.random.default_rng(9).uniform(-0.1, 0.1, P.cc.n_amp)
+    R, e = P.residual(t)
+    R2, e2 = Decomposed(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K_H, P.cc.manifold).residual(t)
+    assert np.abs(R2 - R).max() < 1e-12 and abs(e2 - e) < 1e-12
