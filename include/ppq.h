@@ -23,7 +23,8 @@
  *
  * Conventions of every entry point
  *   - return 0 on success; < 0 on invalid arguments (nothing written, message
- *     in ppq_last_error); > 0 numerical status (1 not converged within
+ *     in ppq_last_error; -6 for an entry point that this version declares
+ *     but does not implement); > 0 numerical status (1 not converged within
  *     max_iter, 2 diverged, 3 non-finite input) with outputs written;
  *   - n_pairs >= 2; occ_of_pair / vir_of_pair are HOST int32 arrays of length
  *     n_pairs that together list every one of the 2 n_pairs active orbitals
@@ -143,6 +144,16 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
    (nullable).  e_total = e_corr + E_ref + e_const with
    E_ref = sum_i (h_ii + f_ii) over the occupied orbitals. */
 int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+             const double* h, const double* eri, double e_const,
+             const ppq_opts* opts, const double* t_in, double* t_out,
+             double* e_corr, double* e_total, ppq_info* info, void* stream);
+
+/* Solve the PH amplitude equations: the three-pair truncation (K = 3,
+   singles through hextuples over at most three pairing labels; Theory
+   section, Table II), with the same arguments and layout conventions as
+   pq_solve.  Not implemented in this version: returns -6, writes nothing
+   and sets ppq_last_error. */
+int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const double* h, const double* eri, double e_const,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);

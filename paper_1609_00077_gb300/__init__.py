@@ -65,6 +65,7 @@ def lib():
         L.pq_residual_static.argtypes = [I, P, P, P, P, P, P, P, I, P]
         L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
                                ctypes.POINTER(Info), P]
+        L.ph_solve.argtypes = L.pq_solve.argtypes
         L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
         L.pq_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, P, P, P]
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
@@ -73,7 +74,8 @@ def lib():
         L.ppq_tc_plan.argtypes = [I, P, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
-                  L.pq_residual_static, L.pq_solve, L.pq_solve_batched, L.pq_lagrangian_gradient,
+                  L.pq_residual_static, L.pq_solve, L.ph_solve, L.pq_solve_batched,
+                  L.pq_lagrangian_gradient,
                   L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan):
             f.restype = ctypes.c_int
         _lib = L
@@ -81,7 +83,7 @@ def lib():
 
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
-            "pq_residual_static", "pq_solve", "pq_solve_batched", "pq_lagrangian_gradient",
+            "pq_residual_static", "pq_solve", "ph_solve", "pq_solve_batched", "pq_lagrangian_gradient",
             "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error", "ppq_tc_plan"]
 
 
@@ -200,6 +202,18 @@ def pq_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=Non
                         ctypes.byref(info), _stream(stream))
     _check(rc, "pq_solve")
     return rc, et.value, t_out, info.as_dict()
+
+
+def ph_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, **opts):
+    """The three-pair (PH) model.  The library declares it but has no kernels
+    for it yet, so this raises PPQError with the library's message."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    o = default_opts(**opts)
+    rc = lib().ph_solve(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
+                        float(e_const), ctypes.byref(o), None, None, None, None, None,
+                        _stream(stream))
+    _check(rc, "ph_solve")
+    raise PPQError(f"ph_solve returned {rc}")
 
 
 def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):

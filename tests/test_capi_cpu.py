@@ -53,6 +53,15 @@ def test_bad_pairing_rejected_without_gpu():
         ppq.pq_solve([0], [1], np.zeros((2, 2)), np.zeros((2,) * 4))
 
 
+def test_ph_solve_is_declared_and_refuses_loudly():
+    # the three-pair model is part of the boundary but has no kernels yet: the
+    # call fails with its own code and message, before touching a GPU
+    n = 6
+    h = np.zeros((n, n)); eri = np.zeros((n,) * 4)
+    with pytest.raises(ppq.PPQError, match=r"ph_solve failed \(-6\).*three-pair"):
+        ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri)
+
+
 def test_layout_map_round_trip():
     from oracle.detcc import enumerate_manifold
     from tests.layout import LayoutMap
