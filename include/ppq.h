@@ -20,6 +20,13 @@
  *                           zero when P == Q (the paper's vanishing-diagonal
  *                           convention).
  * offset of t2 = 3N; ppq_amp_layout describes the excitation of each channel.
+ * The three-pair (PH, K = 3) layout appends
+ *   t3[P][Q][R][k]  k = 0..302  three-pair excitations at offset 3N + 29N^2,
+ *                           stored for all six orders of the triple; a copy
+ *                           with the labels and the channel's monomials
+ *                           permuted alike carries (-1) for every transposed
+ *                           pair of odd monomials; zero when two of P, Q, R
+ *                           coincide.
  *
  * Conventions of every entry point
  *   - return 0 on success; < 0 on invalid arguments (nothing written, message
@@ -112,21 +119,27 @@ typedef struct {
 int ppq_default_opts(ppq_opts* o);
 
 /* Number of amplitudes of the layout above for n_pairs pairs: 3N + 29N^2
-   (the <= 2-label manifold of Eq. decompose and Tables I-II: 3N + 29 C(N,2)
-   unique amplitudes, each two-pair one stored for both orders).
-   Returns 0, or -1 if K != 2 or n_pairs < 1. */
+   for K = 2 (the <= 2-label manifold of Eq. decompose and Tables I-II:
+   3N + 29 C(N,2) unique amplitudes, each two-pair one stored for both
+   orders); 3N + 29N^2 + 303N^3 for K = 3 (plus 303 C(N,3) unique three-pair
+   amplitudes, stored for all six orders).
+   Returns 0, or -1 if K is not 2 or 3, or n_pairs < 1. */
 int ppq_amp_count(int K, int n_pairs, size_t* n_amp);
 
-/* Describe the 32 channels (3 single-pair then 29 two-pair blocks of the
-   block decomposition of T into pairing labels, Eq. decompose; pairs as in
-   Fig. 1): desc[3*c+0] =
-   number of pairs (1 or 2), desc[3*c+1], desc[3*c+2] = 4-bit monomial masks of
-   the first and second pair: bit 0 annihilates the alpha occupied orbital,
+/* Describe the channels of the block decomposition of T into pairing labels
+   (Eq. decompose; pairs as in Fig. 1), K + 1 ints per channel.  K = 2: the
+   32 channels (3 single-pair, then 29 two-pair), desc[3*c+0] = number of
+   pairs (1 or 2), desc[3*c+1], desc[3*c+2] = 4-bit monomial masks of the
+   first and second pair: bit 0 annihilates the alpha occupied orbital,
    bit 1 the beta occupied, bit 2 creates the alpha virtual, bit 3 the beta
    virtual.  The excitation operator of t1[P][k] is E_P^{m}; that of
    t2[P][Q][k] is E_P^{a} E_Q^{b}, with E^m = (a+_{v,alpha})^{b2}
    (a+_{v,beta})^{b3} (a_{o,beta})^{b1} (a_{o,alpha})^{b0} on one pair.
-   desc must hold 96 ints.  Returns 0, -1 for K != 2. */
+   K = 3: the same 32 channels then the 303 three-pair ones (Table II's
+   three-label blocks), desc[4*c+0] = number of pairs (1, 2 or 3) and three
+   monomials; t3[P][Q][R][k] has the operator E_P^{a} E_Q^{b} E_R^{c}.
+   desc must hold 96 ints for K = 2 and 1340 for K = 3.  Returns 0, or -1
+   if K is not 2 or 3. */
 int ppq_amp_layout(int K, int* desc);
 
 /* One residual evaluation R(T) and correlation energy at amplitudes t (both

@@ -115,17 +115,19 @@ def _check(rc, what):
     return rc
 
 
-def amp_count(n_pairs):
+def amp_count(n_pairs, K=2):
     n = ctypes.c_size_t()
-    _check(lib().ppq_amp_count(2, n_pairs, ctypes.byref(n)), "ppq_amp_count")
+    _check(lib().ppq_amp_count(K, n_pairs, ctypes.byref(n)), "ppq_amp_count")
     return n.value
 
 
-def amp_layout():
-    """(kind, first monomial, second monomial) for the 32 channels."""
-    d = np.zeros(96, dtype=np.int32)
-    _check(lib().ppq_amp_layout(2, d.ctypes.data), "ppq_amp_layout")
-    return d.reshape(32, 3)
+def amp_layout(K=2):
+    """(number of pairs, monomials...) per channel: 32 rows of 3 for K = 2,
+    335 rows of 4 for K = 3."""
+    rows = 32 if K == 2 else 32 + 303
+    d = np.zeros(rows * (K + 1), dtype=np.int32)
+    _check(lib().ppq_amp_layout(K, d.ctypes.data), "ppq_amp_layout")
+    return d.reshape(rows, K + 1)
 
 
 def tc_plan(n_pairs):

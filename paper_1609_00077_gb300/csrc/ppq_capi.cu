@@ -1234,14 +1234,19 @@ int ppq_default_opts(ppq_opts* o) {
 }
 
 int ppq_amp_count(int K, int n_pairs, size_t* n_amp) {
-  if (K != 2 || n_pairs < 1 || !n_amp) return fail(-1, "ppq_amp_count: K must be 2 and n_pairs >= 1");
-  *n_amp = amp_len(n_pairs);
+  if ((K != 2 && K != 3) || n_pairs < 1 || !n_amp)
+    return fail(-1, "ppq_amp_count: K must be 2 or 3 and n_pairs >= 1");
+  size_t N = (size_t)n_pairs;
+  *n_amp = amp_len(n_pairs) + (K == 3 ? (size_t)PPQ_NA3 * N * N * N : 0);
   return 0;
 }
 
 int ppq_amp_layout(int K, int* desc) {
-  if (K != 2 || !desc) return fail(-1, "ppq_amp_layout: K must be 2");
-  for (int i = 0; i < 96; ++i) desc[i] = ppq_layout_desc[i];
+  if ((K != 2 && K != 3) || !desc) return fail(-1, "ppq_amp_layout: K must be 2 or 3");
+  if (K == 2)
+    for (int i = 0; i < 3 * (PPQ_NA1 + PPQ_NA2); ++i) desc[i] = ppq_layout_desc[i];
+  else
+    for (int i = 0; i < 4 * (PPQ_NA1 + PPQ_NA2 + PPQ_NA3); ++i) desc[i] = ppq_layout_desc3[i];
   return 0;
 }
 

@@ -758,6 +758,12 @@ def emit_header(path):
     # amplitude layout descriptor for the C-ABI: kind, first monomial, second
     desc = [(1, m, 0) for m in T.A1] + [(2, a, b) for a, b in T.A2]
     out.append(_c_array("ppq_layout_desc", "int8_t", np.array(desc)).replace("static __device__ const", "static const"))
+    # the three-pair (PH) layout: one more column, then the 303 triple channels
+    A3 = amplitude_channels3()
+    desc3 = ([(1, m, 0, 0) for m in T.A1] + [(2, a, b, 0) for a, b in T.A2]
+             + [(3, a, b, c) for a, b, c in A3])
+    out.append(f"#define PPQ_NA3 {len(A3)}")
+    out.append(host(_c_array("ppq_layout_desc3", "int8_t", np.array(desc3))))
     text = "\n".join(out) + "\n"
     with open(path, "w") as fh:
         fh.write(text)
