@@ -31,3 +31,27 @@ def test_localised_pairing_preserves_reference_energy():
     f = B.h + 2 * B.eri[:, :, occ, occ].sum(-1) - B.eri[:, occ, occ, :].sum(1)
     e_ref = np.sum(B.h[occ, occ]) + np.sum(f[occ, occ]) + B.e_const
     assert abs(e_ref - A.e_rhf) < 1e-10
+
+
+def test_acene_geometry_hueckel_spectra():
+    """The acene builder (the PH workloads: fused hexagons, C-C 1.40 A): 4n+2
+    sites, 5n+1 bonds of 1.40 A, and the bond graph's spectrum equals the
+    textbook Hueckel values -- benzene 2, 1, 1, -1, -1, -2 and naphthalene
+    +-(1+sqrt(13))/2, +-(1+sqrt(5))/2, +-(-1+sqrt(13))/2, +-1, +-(sqrt(5)-1)/2
+    (in units of |beta|)."""
+    from workloads import acene_geometry
+    for n in range(1, 8):
+        xyz, bonds = acene_geometry(n)
+        assert len(xyz) == 4 * n + 2 and len(bonds) == 5 * n + 1
+        d = [np.linalg.norm(xyz[i] - xyz[j]) for i, j in bonds]
+        assert np.allclose(d, 1.40, atol=1e-5)
+    for n, want in ((1, [2, 1, 1, -1, -1, -2]),
+                    (2, [(1 + 13 ** .5) / 2, (1 + 5 ** .5) / 2, (-1 + 13 ** .5) / 2, 1, (5 ** .5 - 1) / 2])):
+        xyz, bonds = acene_geometry(n)
+        A = np.zeros((len(xyz), len(xyz)))
+        for i, j in bonds:
+            A[i, j] = A[j, i] = 1.0
+        ev = np.sort(np.linalg.eigvalsh(A))
+        if n == 2:
+            want = want + [-w for w in want]
+        assert np.allclose(ev, np.sort(want), atol=1e-12)
