@@ -195,8 +195,8 @@ class SiteInterp:
         return self.sector(k).matrix(R, C, V * vals[J])
 
     # ------------------------------------------------------------ residual
-    def residual(self, v):
-        """R (same layout, sorted-order slots filled) and E_c at layout amplitudes v."""
+    def amplitudes(self, v):
+        """Cluster amplitudes by sorted label tuple from the layout vector."""
         N = self.N
         t1 = v[:3 * N].reshape(N, 3)
         t2 = v[3 * N:3 * N + 29 * N * N].reshape(N, N, 29)
@@ -208,54 +208,106 @@ class SiteInterp:
             amp[(X, Y)] = t2[X, Y]
         for L in itertools.combinations(range(N), 3):
             amp[L] = t3[L]
+        return amp
+
+    def _ops(self, amp, U, select, mats):
+        """Sum of the clusters L inside U with select(L), on U's sector."""
+        k = len(U)
+        at = {X: i for i, X in enumerate(U)}
+        Sec = self.sector(k)
+        out = sp.csr_matrix((Sec.dim, Sec.dim))
+        for L, tl in amp.items():
+            if set(L) <= set(U) and select(set(L)):
+                pos = tuple(at[X] for X in L)
+                if (k, pos, L) not in mats:
+                    mats[(k, pos, L)] = self.cluster(k, pos, tl)
+                out = out + mats[(k, pos, L)]
+        return out
+
+    def _ref(self, k):
+        Sec = self.sector(k)
+        ref = np.zeros(Sec.dim)
+        ref[Sec.index(np.zeros((1, k), dtype=np.int64))[0]] = 1.0
+        return ref
+
+    def _read(self, M, U, w):
+        """Components of a U-vector on the channels of M, reference elsewhere."""
+        at = {X: i for i, X in enumerate(U)}
+        chans = {1: [(m,) for m in self.A1], 2: self.A2, 3: self.A3}[len(M)]
+        st = np.zeros((len(chans), len(U)), dtype=np.int64)
+        for j, X in enumerate(M):
+            st[:, at[X]] = [c[j] for c in chans]
+        return w[self.sector(len(U)).index(st)]
+
+    def term(self, M, S, amp, mats):
+        """exp(-B) H_S exp(B) exp(A) |ref_U> on the sector of U = M + S."""
+        U = tuple(sorted(set(M) | set(S)))
+        at = {X: i for i, X in enumerate(U)}
+        E = set(S) - set(M)
+        A = self._ops(amp, U, lambda L: bool(L & E), mats)
+        B = self._ops(amp, U, lambda L: not (L & E) and L <= set(M) and bool(L & set(S)), mats)
+        H_S = self.piece(len(U), tuple(at[X] for X in S), S)
+        w = _expv(A, self._ref(len(U)))
+        w = _expv(B, w)
+        return U, _expv(B, H_S @ w, -1.0), H_S
+
+    def residual(self, v):
+        """R (same layout, sorted-order slots filled) and E_c at layout amplitudes v."""
+        N = self.N
+        amp = self.amplitudes(v)
         out = np.zeros_like(v)
         o1 = out[:3 * N].reshape(N, 3)
         o2 = out[3 * N:3 * N + 29 * N * N].reshape(N, N, 29)
         o3 = out[3 * N + 29 * N * N:].reshape(N, N, N, len(self.A3))
         pieces = [S for k in range(1, min(self.K_H, N) + 1) for S in itertools.combinations(range(N), k)]
         outputs = [M for k in range(1, min(3, N) + 1) for M in itertools.combinations(range(N), k)]
-        e = 0.0
         mats = {}
-        for M in [()] + outputs:
-            y = None
-            for S in pieces:
-                U = tuple(sorted(set(M) | set(S)))
-                k = len(U)
-                Sec = self.sector(k)
-                at = {X: i for i, X in enumerate(U)}
-                E = set(S) - set(M)
-                A = sp.csr_matrix((Sec.dim, Sec.dim))
-                B = sp.csr_matrix((Sec.dim, Sec.dim))
-                for L, tl in amp.items():
-                    if not set(L) <= set(U):
-                        continue
-                    pos = tuple(at[X] for X in L)
-                    if set(L) & E or (set(L) <= set(M) and set(L) & set(S)):
-                        if (k, pos, L) not in mats:
-                            mats[(k, pos, L)] = self.cluster(k, pos, tl)
-                        if set(L) & E:
-                            A = A + mats[(k, pos, L)]
-                        else:
-                            B = B + mats[(k, pos, L)]
-                H_S = self.piece(k, tuple(at[X] for X in S), S)
-                ref = np.zeros(Sec.dim)
-                ref[Sec.index(np.zeros((1, k), dtype=np.int64))[0]] = 1.0
-                w = _expv(A, ref)
-                w = _expv(B, w)
-                w = _expv(B, H_S @ w, -1.0)
-                if not M:
-                    e += w @ ref - ref @ (H_S @ ref)
-                    continue
-                # read the outputs: channel monomials on M, reference on E
-                chans = {1: [(m,) for m in self.A1], 2: self.A2, 3: self.A3}[len(M)]
-                st = np.zeros((len(chans), k), dtype=np.int64)
-                for j, X in enumerate(M):
-                    st[:, at[X]] = [c[j] for c in chans]
-                vals = w[Sec.index(st)]
-                y = vals if y is None else y + vals
-            if M:
-                (o1 if len(M) == 1 else o2 if len(M) == 2 else o3)[M] = y
+        e = 0.0
+        for S in pieces:
+            U, w, H_S = self.term((), S, amp, mats)
+            ref = self._ref(len(U))
+            e += w @ ref - ref @ (H_S @ ref)
+        for M in outputs:
+            y = sum(self._read(M, *self.term(M, S, amp, mats)[:2]) for S in pieces)
+            (o1 if len(M) == 1 else o2 if len(M) == 2 else o3)[M] = y
         return out, e
+
+    # ------------------------------------------------------------ disjoint class
+    def disjoint_term(self, M, S, amp, mats):
+        """The contribution of H_S to the outputs on M when S and M share no
+        label, as a closure row times link coefficients:
+
+            sum_{s'} G_S[s'] (-1)^{sum_{s in S} |s'_s| #odd(mu before s)} Lambda(mu, s'),
+            G_S[s'] = <ref_S| H_S exp(I_S) |s'>,   Lambda(mu, s') = <mu s'| exp(L) |ref_U>,
+
+        I_S the clusters inside S, L the clusters inside U = M + S meeting both,
+        s' over the zero-charge sector of S (mu has zero charge on M).  The
+        sign moves the per-site factors of H_S exp(I_S) past the odd monomials
+        of mu on the labels of M that precede them."""
+        assert not set(M) & set(S)
+        kS = len(S)
+        I_S = self._ops(amp, tuple(S), lambda L: True, mats)
+        H_S = self.piece(kS, tuple(range(kS)), S)
+        row = _expv(I_S.T.tocsr(), H_S.T @ self._ref(kS))         # G_S as a row on S's sector
+        U = tuple(sorted(set(M) | set(S)))
+        at = {X: i for i, X in enumerate(U)}
+        L = self._ops(amp, U, lambda L: bool(L & set(S)) and bool(L & set(M)), mats)
+        w = _expv(L, self._ref(len(U)))
+        SecS = self.sector(kS)
+        chans = {1: [(m,) for m in self.A1], 2: self.A2, 3: self.A3}[len(M)]
+        out = np.zeros(len(chans))
+        nz = np.flatnonzero(row)
+        for c, mu in enumerate(chans):
+            st = np.zeros((len(nz), len(U)), dtype=np.int64)
+            for j, X in enumerate(M):
+                st[:, at[X]] = mu[j]
+            sgn = np.ones(len(nz))
+            for j, X in enumerate(S):
+                st[:, at[X]] = SecS.states[nz, j]
+                odd_before = sum(PAR[mu[i]] for i, Y in enumerate(M) if Y < X) & 1
+                sgn *= np.where(PAR[SecS.states[nz, j]] & odd_before, -1.0, 1.0)
+            out[c] = np.sum(row[nz] * sgn * w[self.sector(len(U)).index(st)])
+        return out
 
 
 def _expv(X, v, sign=1.0):

@@ -55,3 +55,36 @@ def test_embedding_sign_control(monkeypatch):
     monkeypatch.setattr(psi.Sector, "_before", staticmethod(lambda st, j: np.zeros(len(st), dtype=np.int64)))
     R, e, R2, e2 = _run("C6H8", 3)
     assert np.abs(R2 - R).max() > 1e-3
+
+
+def test_disjoint_class_as_closure_row_times_links():
+    """Every (M, S) with no common label at N = 4 (all interleavings of the
+    labels, |M| + |S| <= 4): the generic term equals the closure row
+    G_S[s'] = <ref| H_S exp(I_S) |s'> times the link coefficients
+    <mu s'| exp(L) |ref> with the interleaving sign -- the form the six-label
+    PH class takes on the tensor cores.  G_S vanishes beyond two holes."""
+    import itertools
+    desc3 = _desc3()
+    H = SYSTEMS["C8H10"]()
+    N = H.n_pairs
+    si = psi.SiteInterp(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, desc3)
+    amp = si.amplitudes(np.random.default_rng(4).uniform(-0.1, 0.1, ppq.amp_count(N, 3)))
+    mats = {}
+    n = 0
+    for km in (1, 2, 3):
+        for M in itertools.combinations(range(N), km):
+            rest = [X for X in range(N) if X not in M]
+            for ks in range(1, len(rest) + 1):
+                for S in itertools.combinations(rest, ks):
+                    U, w, _ = si.term(M, S, amp, mats)
+                    want = si._read(M, U, w)
+                    got = si.disjoint_term(M, S, amp, mats)
+                    assert np.abs(got - want).max() < 1e-14 * max(1.0, np.abs(want).max())
+                    n += 1
+    assert n == 50
+    # the closure row of a three-label piece has no entry beyond two holes
+    S = (0, 1, 3)
+    I_S = si._ops(amp, S, lambda L: True, mats)
+    row = psi._expv(I_S.T.tocsr(), si.piece(3, (0, 1, 2), S).T @ si._ref(3))
+    holes = (si.sector(3).states & 1).astype(bool).sum(1) + (si.sector(3).states & 2).astype(bool).sum(1)
+    assert np.abs(row).max() > 1e-3 and np.all(row[holes > 2] == 0.0)
