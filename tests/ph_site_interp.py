@@ -122,6 +122,9 @@ class SiteInterp:
         self.N = len(self.occ)
         self.K_H = K_H
         self.hp, self.v, _ = bare_truncated_hamiltonian(h, eri, np.array(self.occ), np.array(self.vir), K_H)
+        o = self.occ
+        self.f = h + 2.0 * np.einsum('pqii->pq', eri[:, :, o][:, :, :, o]) \
+            - np.einsum('piiq->pq', eri[:, o][:, :, o])
         self.A1 = [int(d[1]) for d in desc3 if d[0] == 1]
         self.A2 = [(int(d[1]), int(d[2])) for d in desc3 if d[0] == 2]
         self.A3 = [tuple(int(x) for x in d[1:4]) for d in desc3 if d[0] == 3]
@@ -319,3 +322,66 @@ def _expv(X, v, sign=1.0):
             return out
         out = out + term
     raise RuntimeError("series did not terminate")
+
+
+# ---------------------------------------------------------------- solver
+def layout_denominators(si, f):
+    """D for every sorted slot of the K = 3 layout: sum over the labels of
+    (holes x f_ii - particles x f_aa), diagonal Fock (Jacobi update of the
+    Implementation section); 1 on the unused copies."""
+    N = si.N
+    nh = np.array([bin(m & 3).count("1") for m in range(16)])
+    npart = np.array([bin(m & 12).count("1") for m in range(16)])
+    fo = np.array([f[i, i] for i in si.occ])
+    fv = np.array([f[a, a] for a in si.vir])
+
+    def d(labels, monos):
+        return sum(nh[m] * fo[X] - npart[m] * fv[X] for X, m in zip(labels, monos))
+
+    D = np.ones(3 * N + 29 * N * N + len(si.A3) * N ** 3)
+    D1 = D[:3 * N].reshape(N, 3)
+    D2 = D[3 * N:3 * N + 29 * N * N].reshape(N, N, 29)
+    D3 = D[3 * N + 29 * N * N:].reshape(N, N, N, len(si.A3))
+    mask = np.zeros(D.shape, dtype=bool)
+    m1 = mask[:3 * N].reshape(N, 3)
+    m2 = mask[3 * N:3 * N + 29 * N * N].reshape(N, N, 29)
+    m3 = mask[3 * N + 29 * N * N:].reshape(N, N, N, len(si.A3))
+    for X in range(N):
+        D1[X] = [d((X,), (m,)) for m in si.A1]
+        m1[X] = True
+    for L in itertools.combinations(range(N), 2):
+        D2[L] = [d(L, ab) for ab in si.A2]
+        m2[L] = True
+    for L in itertools.combinations(range(N), 3):
+        D3[L] = [d(L, abc) for abc in si.A3]
+        m3[L] = True
+    return D, mask
+
+
+def solve(si, f, r_tol=1e-10, e_tol=1e-12, max_iter=200, diis_dim=8, diis_start=3):
+    """Jacobi steps t <- t + R/D on the sorted slots with Pulay DIIS on the
+    steps.  Returns (t layout, E_c, ||R||, iterations, converged)."""
+    D, mask = layout_denominators(si, f)
+    t = np.zeros(D.shape)
+    ts, es, e_old = [], [], None
+    for it in range(1, max_iter + 1):
+        R, e = si.residual(t)
+        rn = float(np.linalg.norm(R[mask]))
+        if e_old is not None and rn <= r_tol and abs(e - e_old) <= e_tol:
+            return t, e, rn, it, True
+        e_old = e
+        step = np.where(mask, R / D, 0.0)
+        ts.append(t + step); es.append(step[mask])
+        ts, es = ts[-diis_dim:], es[-diis_dim:]
+        t = ts[-1]
+        if it >= diis_start and len(ts) > 1:
+            m = len(ts)
+            B = -np.ones((m + 1, m + 1))
+            B[m, m] = 0.0
+            G = np.array([[a @ b for b in es] for a in es])
+            B[:m, :m] = G / np.abs(np.diag(G)).max()
+            rhs = np.zeros(m + 1)
+            rhs[m] = -1.0
+            c = np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
+            t = sum(ci * ti for ci, ti in zip(c, ts))
+    return t, e, rn, max_iter, False

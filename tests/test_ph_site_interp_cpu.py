@@ -88,3 +88,34 @@ def test_disjoint_class_as_closure_row_times_links():
     row = psi._expv(I_S.T.tocsr(), si.piece(3, (0, 1, 2), S).T @ si._ref(3))
     holes = (si.sector(3).states & 1).astype(bool).sum(1) + (si.sector(3).states & 2).astype(bool).sum(1)
     assert np.abs(row).max() > 1e-3 and np.all(row[holes > 2] == 0.0)
+
+
+def test_site_formulation_ph_solve_is_fci_at_6e6o():
+    """Jacobi/DIIS on the K = 3 layout with the site-formulation residual and
+    the layout's orbital-energy denominators: for hexatriene (6 electrons in
+    6 orbitals) PH converges to the FCI energy (Abstract: PH is exact there)."""
+    from oracle.fci import fci_energy
+    desc3 = _desc3()
+    H = SYSTEMS["C6H8"]()
+    si = psi.SiteInterp(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, desc3)
+    t, e, rn, it, ok = psi.solve(si, si.f, r_tol=1e-11, e_tol=1e-13)
+    assert ok
+    e_ref = sum(H.h[i, i] + si.f[i, i] for i in H.occ_of_pair) + H.e_const
+    assert abs(e + e_ref - fci_energy(H.h, H.eri, 3, H.e_const)) < 1e-9
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(__import__("os").environ.get("PPQ_LONG_CHECKS") != "1",
+                    reason="about 2 min; set PPQ_LONG_CHECKS=1")
+def test_site_formulation_ph_solve_matches_oracle_n4():
+    """Octatetraene (N = 4, where PH is not exact): the site-formulation PH
+    solve reaches the oracle's PH energy."""
+    from oracle.detcc import Problem
+    desc3 = _desc3()
+    H = SYSTEMS["C8H10"]()
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, e_const=H.e_const)
+    r = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    si = psi.SiteInterp(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, desc3)
+    t, e, rn, it, ok = psi.solve(si, si.f, r_tol=1e-11, e_tol=1e-13)
+    assert r['converged'] and ok
+    assert abs(e - r['e_corr']) < 1e-9
