@@ -56,9 +56,9 @@ def solve_lambda(P, t):
     return np.linalg.solve(J.T, -b)
 
 
-def fci_one_rdm(h, eri, n_alpha):
-    """Spin-summed FCI 1-RDM gamma_pq = <Psi| sum_s a+_ps a_qs |Psi> of the
-    lowest state (dense diagonalisation, small spaces)."""
+def _fci_ground(h, eri, n_alpha):
+    """(strings, C[I_alpha, I_beta]) of the lowest FCI state (dense
+    diagonalisation, small spaces)."""
     n = h.shape[0]
     S = Strings(n, n_alpha)
     dim = S.n * S.n
@@ -67,14 +67,39 @@ def fci_one_rdm(h, eri, n_alpha):
         c = np.zeros(dim); c[j] = 1.0
         Hm[:, j] = sigma(S, h, eri, c.reshape(S.n, S.n)).ravel()
     w, v = np.linalg.eigh(0.5 * (Hm + Hm.T))
-    C = v[:, 0].reshape(S.n, S.n)
+    return S, v[:, 0].reshape(S.n, S.n)
+
+
+def _spin_summed(S, C):
+    """E_pq C for every p, q (spin-summed one-body operators on C)."""
     E = S.E()
-    g = np.empty((n, n))
-    for p in range(n):
-        for q in range(n):
-            D = E[p][q] @ C + (E[p][q] @ C.T).T
-            g[p, q] = np.sum(C * D)
-    return g
+    n = len(E)
+    return [[E[p][q] @ C + (E[p][q] @ C.T).T for q in range(n)] for p in range(n)]
+
+
+def fci_one_rdm(h, eri, n_alpha):
+    """Spin-summed FCI 1-RDM gamma_pq = <Psi| sum_s a+_ps a_qs |Psi> of the
+    lowest state (dense diagonalisation, small spaces)."""
+    S, C = _fci_ground(h, eri, n_alpha)
+    X = _spin_summed(S, C)
+    n = h.shape[0]
+    return np.array([[np.sum(C * X[p][q]) for q in range(n)] for p in range(n)])
+
+
+def fci_two_rdm(h, eri, n_alpha):
+    """Spin-summed FCI 2-RDM in the chemists' order of the Hamiltonian,
+    Gamma_pqrs = sum_{s,t} <Psi| a+_ps a+_rt a_st a_qs |Psi>
+               = <Psi| E_pq E_rs |Psi> - delta_qr gamma_ps,
+    so that E = sum h_pq gamma_pq + 1/2 sum (pq|rs) Gamma_pqrs."""
+    S, C = _fci_ground(h, eri, n_alpha)
+    X = _spin_summed(S, C)
+    n = h.shape[0]
+    V = np.array([[X[p][q].ravel() for q in range(n)] for p in range(n)])   # E_pq Psi
+    g = np.einsum('i,pqi->pq', C.ravel(), V)
+    # <Psi| E_pq E_rs |Psi> = (E_qp Psi) . (E_rs Psi)
+    G = np.einsum('qpi,rsi->pqrs', V, V)
+    G -= np.einsum('qr,ps->pqrs', np.eye(n), g)
+    return G
 
 
 def energy(h, eri, occ, vir, K, e_const=0.0, K_H=0, **kw):

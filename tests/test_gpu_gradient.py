@@ -2,7 +2,8 @@
 facts the paper and mathematics fix:
 
 * 4 electrons in 4 orbitals: PQ is FCI (Abstract), so by Hellmann-Feynman
-  dE/dh is the FCI one-particle density matrix and dE/dkappa vanishes (FCI is
+  dE/dh is the FCI one-particle density matrix, dE/d(pq|rs) half the FCI
+  two-particle one (both symmetrised) and dE/dkappa vanishes (FCI is
   invariant to orbital rotations);
 * central finite differences (step 1e-4) of converged oracle energies along
   random symmetric directions in h and (pq|rs), and along a random orbital
@@ -22,7 +23,7 @@ if not torch.cuda.is_available():
 
 import paper_1609_00077_gb300 as ppq
 from workloads import build_ppp, build_hchain
-from oracle.gradient import fci_one_rdm, energy
+from oracle.gradient import fci_one_rdm, fci_two_rdm, energy
 
 TIGHT = dict(r_tol=1e-12, e_tol=1e-14, max_iter=600)
 
@@ -52,6 +53,13 @@ def test_fci_hellmann_feynman_at_4e4o(which):
     g = fci_one_rdm(H.h, H.eri, 2)
     assert np.abs(dh.cpu().numpy() - g).max() < 1e-8
     assert np.abs(dk.cpu().numpy()).max() < 1e-8
+    # dE/d(pq|rs), averaged over the 8 index permutations, is half the FCI
+    # two-body density averaged the same way
+    G = 0.5 * fci_two_rdm(H.h, H.eri, 2)
+    G8 = (G + G.transpose(1, 0, 2, 3) + G.transpose(0, 1, 3, 2) + G.transpose(1, 0, 3, 2)
+          + G.transpose(2, 3, 0, 1) + G.transpose(3, 2, 0, 1) + G.transpose(2, 3, 1, 0)
+          + G.transpose(3, 2, 1, 0)) / 8.0
+    assert np.abs(dv.cpu().numpy() - G8).max() < 1e-8
 
 
 @pytest.mark.parametrize("which", ["C6H8", "H8"])

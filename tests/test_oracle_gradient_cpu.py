@@ -5,7 +5,9 @@ independent numerical and physical facts.
   residual.
 * The FCI one-particle density matrix is Hermitian with trace equal to the
   number of electrons, and (Hellmann-Feynman) its contraction with a
-  symmetric change of h is the derivative of the FCI energy.
+  symmetric change of h is the derivative of the FCI energy; the two-particle
+  one rebuilds the FCI energy with it, traces down to (n_el - 1) gamma, and
+  gives the derivative along a symmetric change of (pq|rs).
 * The Lambda amplitudes turn the Lagrangian into the total derivative of the
   converged energy: for a change of h and (pq|rs), the partial derivative of
   E_ref + E_c(t) + lambda . R(t) at the converged t equals the central
@@ -17,7 +19,7 @@ import numpy as np
 from workloads import build_ppp, build_hchain
 from oracle.detcc import Problem
 from oracle.fci import fci_energy
-from oracle.gradient import jacobian, fci_one_rdm, solve_lambda, energy
+from oracle.gradient import jacobian, fci_one_rdm, fci_two_rdm, solve_lambda, energy
 
 
 def _sym(n, rng):
@@ -52,6 +54,20 @@ def test_fci_one_rdm_trace_symmetry_and_hellmann_feynman():
     eps = 1e-5
     fd = (fci_energy(H.h + eps * dh, H.eri, 3) - fci_energy(H.h - eps * dh, H.eri, 3)) / (2 * eps)
     assert abs(fd - np.sum(g * dh)) < 1e-7
+
+
+def test_fci_two_rdm_energy_trace_and_hellmann_feynman():
+    H = build_hchain(6, 1.3)
+    g = fci_one_rdm(H.h, H.eri, 3)
+    G = fci_two_rdm(H.h, H.eri, 3)
+    e = fci_energy(H.h, H.eri, 3)
+    assert abs(np.sum(H.h * g) + 0.5 * np.sum(H.eri * G) - e) < 1e-10
+    assert np.abs(np.einsum('pqrr->pq', G) - 5.0 * g).max() < 1e-10
+    _, dv = _sym(H.n_orb, np.random.default_rng(4))
+    dv *= 0.01
+    eps = 1e-4
+    fd = (fci_energy(H.h, H.eri + eps * dv, 3) - fci_energy(H.h, H.eri - eps * dv, 3)) / (2 * eps)
+    assert abs(fd - 0.5 * np.sum(G * dv)) < 1e-7
 
 
 def test_lambda_makes_the_lagrangian_derivative_total():
