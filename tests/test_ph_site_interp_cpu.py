@@ -119,3 +119,37 @@ def test_site_formulation_ph_solve_matches_oracle_n4():
     t, e, rn, it, ok = psi.solve(si, si.f, r_tol=1e-11, e_tol=1e-13)
     assert r['converged'] and ok
     assert abs(e - r['e_corr']) < 1e-9
+
+
+def _disjoint_pairs(N, max_sites):
+    import itertools
+    for km in (1, 2, 3):
+        for M in itertools.combinations(range(N), km):
+            rest = [X for X in range(N) if X not in M]
+            for ks in range(1, len(rest) + 1):
+                for S in itertools.combinations(rest, ks):
+                    if km + ks <= max_sites:
+                        yield M, S
+
+
+@pytest.mark.parametrize("max_sites", [3, pytest.param(4, marks=[pytest.mark.slow, pytest.mark.skipif(
+    __import__("os").environ.get("PPQ_LONG_CHECKS") != "1", reason="about 3 min; set PPQ_LONG_CHECKS=1")])])
+def test_disjoint_class_from_configuration_tables(max_sites):
+    """The link coefficients expanded into configurations generated per
+    interleaving pattern (tests/ph_disjoint_tables.py) reproduce the
+    disjoint-class term: every disjoint (M, S) of at most three labels at
+    N = 4 (all 50, four labels included, with PPQ_LONG_CHECKS=1)."""
+    from tests.ph_disjoint_tables import disjoint_term_from_tables
+    desc3 = _desc3()
+    H = SYSTEMS["C8H10"]()
+    N = H.n_pairs
+    si = psi.SiteInterp(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, desc3)
+    amp = si.amplitudes(np.random.default_rng(4).uniform(-0.1, 0.1, ppq.amp_count(N, 3)))
+    mats, cache = {}, {}
+    n = 0
+    for M, S in _disjoint_pairs(N, max_sites):
+        want = si.disjoint_term(M, S, amp, mats)
+        got = disjoint_term_from_tables(si, M, S, amp, mats, cache)
+        assert np.abs(got - want).max() < 1e-14 * max(1.0, np.abs(want).max())
+        n += 1
+    assert n == (36 if max_sites == 3 else 50)
