@@ -122,3 +122,52 @@ def disjoint_term_from_tables(si, M, S, amp, mats, tables_cache):
             acc += row[n] * sig * lam
         out[c] = acc
     return out
+
+
+# ---------------------------------------------------------------- per-label factors
+def _merge_sign(w, x):
+    """E^w E^x = sign E^{w|x} for monomial strings w, x over the same sites
+    (canonical order site by site), 0 if they overlap on a site."""
+    s = 1
+    for j in range(len(w)):
+        if w[j] & x[j]:
+            return 0
+        s *= PROD[w[j], x[j]]
+        if PAR[x[j]]:
+            for i in range(j + 1, len(w)):
+                if PAR[w[i]]:
+                    s = -s
+    return s
+
+
+def merge(f, g):
+    """Product of two monomial-operator expansions {monomial string: coef}."""
+    out = {}
+    for w, cw in f.items():
+        for x, cx in g.items():
+            s = _merge_sign(w, x)
+            if s:
+                key = tuple(a | b for a, b in zip(w, x))
+                out[key] = out.get(key, 0.0) + s * cw * cx
+    return out
+
+
+def link_factors(si, M, S, amp, mats):
+    """exp(L) |ref> for the clusters joining S to M, grouped by the labels of
+    S they touch: one factor exp(L_a) per label a of S (clusters (a, y) and
+    (a, y, y')) and one exp(L_aa') per pair (clusters (a, a', y)), each as a
+    monomial-operator expansion over the sites of U = M + S.  The factors
+    commute, so exp(L)|ref> is their merged product; a factor depends only on
+    its own labels of S and on M, which is what lets a kernel share it across
+    every piece S that contains those labels."""
+    import tests.ph_site_interp as psi
+    U = tuple(sorted(set(M) | set(S)))
+    Sec = si.sector(len(U))
+    factors = []
+    groups = [({a},) for a in S] + [({a, b},) for a, b in itertools.combinations(S, 2)]
+    for (part,) in groups:
+        Lp = si._ops(amp, U, lambda L, part=part: (L & set(S)) == part and bool(L & set(M)), mats)
+        v = psi._expv(Lp, si._ref(len(U)))
+        nz = np.flatnonzero(v)
+        factors.append({tuple(int(m) for m in Sec.states[i]): v[i] for i in nz})
+    return U, factors

@@ -153,3 +153,33 @@ def test_disjoint_class_from_configuration_tables(max_sites):
         assert np.abs(got - want).max() < 1e-14 * max(1.0, np.abs(want).max())
         n += 1
     assert n == (36 if max_sites == 3 else 50)
+
+
+@pytest.mark.parametrize("max_sites", [3, pytest.param(4, marks=[pytest.mark.slow, pytest.mark.skipif(
+    __import__("os").environ.get("PPQ_LONG_CHECKS") != "1", reason="about 30 s; set PPQ_LONG_CHECKS=1")])])
+def test_link_factors_per_label_merge_to_exp_L(max_sites):
+    """exp(L)|ref> of the clusters joining S to M, built as the graded product
+    of one factor per label of S and one per pair of labels of S (each
+    shareable across pieces), equals exp(L)|ref> on the sector of U."""
+    from tests.ph_disjoint_tables import link_factors, merge
+    desc3 = _desc3()
+    H = SYSTEMS["C8H10"]()
+    N = H.n_pairs
+    si = psi.SiteInterp(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, desc3)
+    amp = si.amplitudes(np.random.default_rng(4).uniform(-0.1, 0.1, ppq.amp_count(N, 3)))
+    mats = {}
+    n = 0
+    for M, S in _disjoint_pairs(N, max_sites):
+        U, fs = link_factors(si, M, S, amp, mats)
+        prod = fs[0]
+        for f in fs[1:]:
+            prod = merge(prod, f)
+        L = si._ops(amp, U, lambda L: bool(L & set(S)) and bool(L & set(M)), mats)
+        w = psi._expv(L, si._ref(len(U)))
+        Sec = si.sector(len(U))
+        v = np.zeros(Sec.dim)
+        for st, c in prod.items():
+            v[Sec.index(np.array([st]))[0]] += c
+        assert np.abs(v - w).max() < 1e-14
+        n += 1
+    assert n == (36 if max_sites == 3 else 50)
