@@ -15,13 +15,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "ppq.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ppq_\w+|pq_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ppq_\w+|pq_\w+|ph_\w+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
     L = ppq.lib()
     names = _declared()
-    assert {"pq_solve", "pq_residual", "ppq_amp_count", "ppq_amp_layout"} <= set(names)
+    assert {"pq_solve", "ph_solve", "pq_residual", "ppq_amp_count", "ppq_amp_layout"} <= set(names)
     for name in names:
         assert hasattr(L, name), name
 
