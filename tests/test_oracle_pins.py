@@ -306,8 +306,8 @@ def test_residual_random_t_against_jordan_wigner_expm():
 @pytest.mark.parametrize("kind,size,K", [("hchain", 10, 2), ("polyene", 10, 2), ("hchain", 12, 2)])
 def test_local_assembly_equals_detcc(kind, size, K):
     H = build_hchain(size, 1.6) if kind == "hchain" else build_ppp('polyene', size)
-    if size > 10:
-        pytest.skip("full determinant space too large for O-det")
+    if size > 10 and os.environ.get("PPQ_LONG_CHECKS") != "1":
+        pytest.skip("853 776 determinants for O-det; set PPQ_LONG_CHECKS=1")
     P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=K)
     L = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=K)
     rng = np.random.default_rng(1234)
