@@ -24,7 +24,8 @@ from itertools import combinations
 
 import numpy as np
 
-from workloads import build_ppp, build_hchain, random_pair_amplitude_seed
+from workloads import (build_ppp, build_hchain, random_pair_amplitude_seed, polyene_geometry,
+                       acene_geometry, ppp_site_hamiltonian, mo_integrals, Hamiltonian)
 from oracle.detcc import truncated_hamiltonian, enumerate_manifold
 from oracle.loccc import LocalAssembly
 
@@ -78,10 +79,30 @@ def sampled_residual(h, eri, occ, vir, pairs, t, K=2, K_H=2, workers=2, energy=F
     return idx, R[idx], e_c, truncated[3]
 
 
-def workload(kind, size, orbitals):
+def workload(kind, size, orbitals, orbitals_from=None):
+    """The Hamiltonian; with orbitals_from (an .npz of C, occ_of_pair,
+    vir_of_pair written by the caller) a PPP model is transformed with the
+    caller's own orbitals instead of re-running RHF and the localisation: a
+    phase chosen by argmax can differ between processes when two coefficients
+    of an orbital agree to ~1e-11, and that would flip the sign convention of
+    the amplitudes."""
+    if orbitals_from is not None:
+        if kind not in ("polyene", "acene"):
+            raise ValueError("orbitals_from needs a PPP model")
+        xyz, bonds = polyene_geometry(size) if kind == "polyene" else acene_geometry(size)
+        h_site, gamma, e_const = ppp_site_hamiltonian(xyz, bonds)
+        d = np.load(orbitals_from)
+        h, eri = mo_integrals(d["C"], h_site, gamma_zdo=gamma)
+        return Hamiltonian(f"PPP {kind} {size} (given orbitals)", h, eri, e_const,
+                           d["occ_of_pair"], d["vir_of_pair"])
     if kind == "hchain":
         return build_hchain(size, 1.5, orbitals=orbitals)
     return build_ppp(kind, size, orbitals=orbitals)
+
+
+def save_orbitals(path, H):
+    """Write H's orbitals and pairing for workload(..., orbitals_from=path)."""
+    np.savez(path, C=H.C, occ_of_pair=H.occ_of_pair, vir_of_pair=H.vir_of_pair)
 
 
 def amplitudes(n_amp, N, tag):
@@ -97,11 +118,12 @@ def main(argv=None):
     ap.add_argument("--tag", type=int, default=0)
     ap.add_argument("--K", type=int, default=2)
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--orbitals-from", default=None, help="C and pairing of the caller (.npz)")
     ap.add_argument("--t-in", default=None, help="amplitudes over the oracle's manifold (.npy)")
     ap.add_argument("--energy", action="store_true", help="also the correlation energy at t")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
-    H = workload(a.kind, a.size, a.orbitals)
+    H = workload(a.kind, a.size, a.orbitals, a.orbitals_from)
     pairs = [tuple(int(x) for x in p.split(",")) for p in a.pairs]
     if a.t_in:
         t = np.load(a.t_in)

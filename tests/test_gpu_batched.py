@@ -19,6 +19,7 @@ import paper_1609_00077_gb300 as ppq
 from workloads import build_hchain, build_ppp
 from oracle.detcc import Problem, enumerate_manifold
 from tests.layout import LayoutMap
+from tests.oloc_sampled import save_orbitals
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -85,8 +86,10 @@ def test_batched_largest_member_against_oracle(tmp_path):
     man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
     lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
     np.save(tmp_path / "t.npy", lm.from_layout(amps[k]))
+    save_orbitals(tmp_path / "orb.npz", H)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "40", "--orbitals", "local",
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "40",
+                    "--orbitals-from", str(tmp_path / "orb.npz"),
                     "--pairs", "0,1", "18,19", "--t-in", str(tmp_path / "t.npy"), "--energy",
                     "--out", str(tmp_path / "o.npz")], cwd=ROOT, env=env, check=True, timeout=1800)
     got = np.load(tmp_path / "o.npz")

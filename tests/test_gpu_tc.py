@@ -11,7 +11,7 @@ by 3xTF32 products, FP64 by exact integer splitting) beyond one 128-row tile.
   pair-amplitude element of a pair in a middle tile and of the last pair
   against the oracle's local assembly over the 2347 label sets containing
   each pair, run as a separate process split over the host cores
-  (tests/oloc_sampled.py).  FP64 within 1e-9: the exact slicing drops
+  (tests/oloc_sampled.py, given this process's orbitals).  FP64 within 1e-9: the exact slicing drops
   products below about 2^-41 of the row and block scales, and each element
   sums a few 10^4 such products over X, W and the channels (below 1e-11 at
   N = 20); FP32 within 2e-5 * max|R| as above;
@@ -39,7 +39,7 @@ from workloads import build_ppp, ppp_eri_device, random_pair_amplitude_seed
 from oracle.loccc import LocalAssembly
 from oracle.detcc import enumerate_manifold
 from tests.layout import LayoutMap
-from tests.oloc_sampled import amplitudes
+from tests.oloc_sampled import amplitudes, save_orbitals
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -105,14 +105,15 @@ def test_fp32_tensor_core_residual_matches_fp64(size):
 
 def test_bench_workload_sampled_pairs_match_oracle(tmp_path):
     out = tmp_path / "sampled.npz"
+    H = build_ppp('polyene', 140, orbitals='local', with_eri=False)
+    N = H.n_pairs
+    assert N == 70
+    save_orbitals(tmp_path / "orb.npz", H)       # the oracle process uses these very orbitals
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     oracle = subprocess.Popen([sys.executable, "-m", "tests.oloc_sampled", "--size", "140",
-                               "--orbitals", "local", "--pairs", "33,34", "68,69", "--tag", "0",
-                               "--out", str(out)], cwd=ROOT, env=env)
+                               "--orbitals-from", str(tmp_path / "orb.npz"), "--pairs", "33,34", "68,69",
+                               "--tag", "0", "--out", str(out)], cwd=ROOT, env=env)
     try:
-        H = build_ppp('polyene', 140, orbitals='local', with_eri=False)
-        N = H.n_pairs
-        assert N == 70
         eri = ppp_eri_device(H, torch)
         man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
         lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
@@ -147,8 +148,10 @@ def test_bench_workload_solution_against_oracle(tmp_path):
     man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
     lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout())
     np.save(tmp_path / "t.npy", lm.from_layout(t))
+    save_orbitals(tmp_path / "orb.npz", H)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "140", "--orbitals", "local",
+    subprocess.run([sys.executable, "-m", "tests.oloc_sampled", "--size", "140",
+                    "--orbitals-from", str(tmp_path / "orb.npz"),
                     "--pairs", "68,69", "--t-in", str(tmp_path / "t.npy"), "--energy",
                     "--out", str(tmp_path / "o.npz")], cwd=ROOT, env=env, check=True, timeout=1800)
     got = np.load(tmp_path / "o.npz")

@@ -48,3 +48,21 @@ def test_sampled_command_matches_serial_oracle(tmp_path):
     R, e = L.residual(t)
     assert np.abs(got["vals"] - R[got["idx"]]).max() < 1e-13
     assert abs(got["e_c"] - e) < 1e-12 and abs(e) > 1e-3
+
+
+def test_sampled_command_with_the_callers_orbitals(tmp_path):
+    """--orbitals-from: the command transforms the PPP model with the
+    caller's orbitals and pairing (as the GPU tests pass them)."""
+    from workloads import build_ppp
+    from tests.oloc_sampled import save_orbitals
+    H = build_ppp('polyene', 12, orbitals='local')
+    save_orbitals(tmp_path / "orb.npz", H)
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    t = np.random.default_rng(12).uniform(-0.05, 0.05, len(man))
+    np.save(tmp_path / "t.npy", t)
+    _run(["--size", "12", "--orbitals-from", str(tmp_path / "orb.npz"), "--pairs", "2,3",
+          "--t-in", str(tmp_path / "t.npy"), "--energy", "--workers", "2", "--out", str(tmp_path / "o.npz")], ROOT)
+    got = np.load(tmp_path / "o.npz")
+    R, e = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2).residual(t)
+    assert np.abs(got["vals"] - R[got["idx"]]).max() < 1e-12
+    assert abs(got["e_c"] - e) < 1e-12 and abs(got["e_const"] - H.e_const) < 1e-12
