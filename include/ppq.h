@@ -30,8 +30,7 @@
  *
  * Conventions of every entry point
  *   - return 0 on success; < 0 on invalid arguments (nothing written, message
- *     in ppq_last_error; -6 for an entry point that this version declares
- *     but does not implement); > 0 numerical status (1 not converged within
+ *     in ppq_last_error); > 0 numerical status (1 not converged within
  *     max_iter, 2 diverged, 3 non-finite input) with outputs written;
  *   - n_pairs >= 2; occ_of_pair / vir_of_pair are HOST int32 arrays of length
  *     n_pairs that together list every one of the 2 n_pairs active orbitals
@@ -67,8 +66,10 @@ extern "C" {
 #endif
 
 typedef struct {
-  int K;              /* amplitude truncation: 2 = PQ (set by pq_solve)        */
-  int K_H;            /* integral truncation in labels: 0 = same as K; only 2  */
+  int K;              /* amplitude truncation: 2 = PQ (set by pq_solve; 3 by   */
+                      /*     ph_solve)                                         */
+  int K_H;            /* integral truncation in labels: 0 = same as K; pq_solve*/
+                      /*     takes 2, ph_solve 2 or 3                           */
   int precision;      /* 0 = FP64 throughout; 1 = mixed: FP32 residual until   */
                       /*     ||R|| <= switch_tol or stagnation, then FP64      */
   double switch_tol;  /* 1e-5                                                  */
@@ -161,15 +162,56 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);
 
-/* Solve the PH amplitude equations: the three-pair truncation (K = 3,
+/* One residual evaluation of the PH model (the three-pair truncation, K = 3:
    singles through hextuples over at most three pairing labels; Theory
-   section, Table II), with the same arguments and layout conventions as
-   pq_solve.  Not implemented in this version: returns -6, writes nothing
-   and sets ppq_last_error. */
+   section, Table II) at amplitudes t in the K = 3 layout above, with the
+   two-electron integrals truncated to at most K_H labels (K_H = 0 or 3: the
+   rank-3 subtensors of v of Table I; 2: two labels).  Only the sorted-label
+   entries of t (t2[P][Q] with P < Q, t3[P][Q][R] with P < Q < R) are read; r
+   receives every stored order (copies by the layout's rule, zero where labels
+   repeat).  Exact evaluation: the residual is assembled from local problems
+   over every label subset of at most K + K_H labels, each solved in its
+   site basis (psi = exp(T)|ref>, <kappa| H |psi>, back-substitution with
+   exp(-T)), with inclusion-exclusion coefficients; a linked term of the
+   projected equations never carries more than K + K_H labels.
+   h, eri, t, r host or device pointers (detected); e_corr host (nullable).
+   precision 0 = FP64, 1 = FP32 local problems (assembly and energy sums in
+   FP64).  n_pairs <= 127.  Returns 0 or < 0 on invalid arguments. */
+int ph_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                const double* h, const double* eri, const double* t, double* r,
+                double* e_corr, int precision, int K_H, void* stream);
+
+/* Solve the PH amplitude equations (Theory section, K = 3) by Jacobi steps
+   with orbital-energy denominators and Pulay DIIS (Implementation section),
+   with the arguments and conventions of pq_solve; t_in / t_out use the K = 3
+   layout.  opts->K is ignored (the entry point sets K = 3); opts->K_H = 0 or
+   3 keeps three-label integrals, 2 keeps two.  precision 1 runs FP32
+   residuals until ||R|| <= switch_tol or stagnation, then FP64 iterations to
+   the final tolerances (opts->polish is ignored).  The DIIS least-squares
+   problem is solved on the device; the host reads ||R|| and E_c once per
+   iteration.  info->residual_flops counts 2 FLOPs per table entry and label
+   subset of one residual evaluation.  n_pairs <= 127.
+   The first call for a subset size builds that size's structure tables on
+   the host (about 6 s and 0.7 GB for six labels) and keeps them on the device
+   (about 1 GB for six labels) until the process exits. */
 int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const double* h, const double* eri, double e_const,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);
+
+/* Host-only export of the structure tables that ph_residual generates for
+   local problems of k sites (amplitudes over at most K labels, integrals over
+   at most K_H): the zero-charge sector, the recursions of exp(+-T)|ref>, the
+   Hamiltonian rows and the back-substitution.  The paper has no counterpart:
+   this is how the library lays out the exact evaluation, exported so that a
+   CPU check can interpret the tables against the oracle.  ph_tables_counts
+   fills counts[0..25] (counts must hold 32) with the element count of each
+   table; ph_tables_copy copies table `which` (0..25) into dst (host memory of
+   counts[which] elements: uint32 codes; int32 pointers, indices and
+   descriptors; int16 slot / key fields; double coefficients).  No device
+   call.  Returns 0, or < 0 for k outside 1..6 or K, K_H outside 1..3. */
+int ph_tables_counts(int k, int K, int K_H, int64_t* counts);
+int ph_tables_copy(int k, int K, int K_H, int which, void* dst);
 
 /* Solve n_sys independent PQ problems of (possibly different) sizes in one
    call: the batched form of the paper's calculations, e.g. a bond-length scan

@@ -66,6 +66,9 @@ def lib():
         L.pq_solve.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P,
                                ctypes.POINTER(Info), P]
         L.ph_solve.argtypes = L.pq_solve.argtypes
+        L.ph_residual.argtypes = [I, P, P, P, P, P, P, P, I, I, P]
+        L.ph_tables_counts.argtypes = [I, I, I, P]
+        L.ph_tables_copy.argtypes = [I, I, I, I, P]
         L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
         L.pq_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, P, P, P]
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
@@ -76,15 +79,17 @@ def lib():
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
                   L.pq_residual_static, L.pq_solve, L.ph_solve, L.pq_solve_batched,
                   L.pq_lagrangian_gradient,
-                  L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan):
+                  L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan, L.ph_residual,
+                  L.ph_tables_counts, L.ph_tables_copy):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
-            "pq_residual_static", "pq_solve", "ph_solve", "pq_solve_batched", "pq_lagrangian_gradient",
-            "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error", "ppq_tc_plan"]
+            "pq_residual_static", "pq_solve", "ph_solve", "ph_residual", "pq_solve_batched",
+            "pq_lagrangian_gradient", "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error",
+            "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy"]
 
 
 def _ptr(x):
@@ -107,6 +112,29 @@ def _stream(stream):
     except ImportError:
         pass
     return None
+
+
+def _check_buf(x, n, name, device=None):
+    """Argument check before any launch: x must be FP64, C-contiguous and hold
+    at least n elements; with device set, a CUDA tensor on that device."""
+    if isinstance(x, np.ndarray):
+        if device is not None:
+            raise PPQError(f"{name} must be a CUDA tensor (device memory)")
+        ok = x.dtype == np.float64 and x.flags['C_CONTIGUOUS']
+        size = x.size
+    else:
+        ok = str(getattr(x, "dtype", "")) == "torch.float64" and x.is_contiguous()
+        size = x.numel()
+        if device is not None and (not x.is_cuda or x.device != device):
+            raise PPQError(f"{name} must be a CUDA tensor on {device}")
+    if not ok:
+        raise PPQError(f"{name} must be a contiguous float64 array")
+    if size < n:
+        raise PPQError(f"{name} holds {size} elements, {n} needed")
+
+
+def _device_of(x):
+    return x.device if hasattr(x, "is_cuda") and x.is_cuda else None
 
 
 def _check(rc, what):
@@ -164,6 +192,9 @@ def pq_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, stream
     N = len(occ)
     if r is None:
         r = np.zeros(amp_count(N)) if isinstance(t, np.ndarray) else t.new_zeros(amp_count(N))
+    n = 2 * N
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, amp_count(N), "t"), (r, amp_count(N), "r")):
+        _check_buf(x, cnt, name)
     e = ctypes.c_double()
     rc = lib().pq_residual(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t),
                            _ptr(r), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p),
@@ -177,6 +208,13 @@ def pq_residual_static(occ_of_pair, vir_of_pair, h, eri, t, r, precision=0, stre
     array, n_pairs <= 12).  For callers that cannot call cudaMalloc: h, eri, t
     and r must already be device tensors (torch CUDA).  Returns e_corr."""
     occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    n = 2 * N
+    dev = _device_of(t)
+    if dev is None:
+        raise PPQError("pq_residual_static: t must be a CUDA tensor (device memory)")
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, amp_count(N), "t"), (r, amp_count(N), "r")):
+        _check_buf(x, cnt, name, device=dev)
     e = ctypes.c_double()
     rc = lib().pq_residual_static(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
                                   _ptr(t), _ptr(r), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p),
@@ -206,16 +244,51 @@ def pq_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=Non
     return rc, et.value, t_out, info.as_dict()
 
 
-def ph_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, **opts):
-    """The three-pair (PH) model.  The library declares it but has no kernels
-    for it yet, so this raises PPQError with the library's message."""
+def ph_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, K_H=3, stream=None):
+    """R(T) and E_c of the three-pair (PH) model at amplitudes t (the K = 3
+    layout of include/ppq.h; only the sorted-label entries are read).  h, eri,
+    t, r may be torch CUDA tensors or numpy arrays (FP64, contiguous).
+    Returns (r, e_corr), r with every stored order filled."""
     occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    L = amp_count(N, 3)
+    if r is None:
+        r = np.zeros(L) if isinstance(t, np.ndarray) else t.new_zeros(L)
+    n = 2 * N
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, L, "t"), (r, L, "r")):
+        _check_buf(x, cnt, name)
+    e = ctypes.c_double()
+    rc = lib().ph_residual(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t), _ptr(r),
+                           ctypes.cast(ctypes.pointer(e), ctypes.c_void_p), precision, K_H, _stream(stream))
+    _check(rc, "ph_residual")
+    return r, e.value
+
+
+def ph_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=None, stream=None, **opts):
+    """Solve the three-pair (PH) equations.  Returns (status, e_total, t_out,
+    info dict); t_out uses the K = 3 layout."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    L = amp_count(N, 3)
     o = default_opts(**opts)
-    rc = lib().ph_solve(len(occ), occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri),
-                        float(e_const), ctypes.byref(o), None, None, None, None, None,
-                        _stream(stream))
+    if t_in is not None and 'guess' not in opts:
+        o.guess = 1
+    if t_out is None:
+        t_out = np.zeros(L)
+    n = 2 * N
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t_out, L, "t_out")):
+        _check_buf(x, cnt, name)
+    if t_in is not None:
+        _check_buf(t_in, L, "t_in")
+    ec, et = ctypes.c_double(), ctypes.c_double()
+    info = Info()
+    rc = lib().ph_solve(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), float(e_const),
+                        ctypes.byref(o), _ptr(t_in), _ptr(t_out),
+                        ctypes.cast(ctypes.pointer(ec), ctypes.c_void_p),
+                        ctypes.cast(ctypes.pointer(et), ctypes.c_void_p),
+                        ctypes.byref(info), _stream(stream))
     _check(rc, "ph_solve")
-    raise PPQError(f"ph_solve returned {rc}")
+    return rc, et.value, t_out, info.as_dict()
 
 
 def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):

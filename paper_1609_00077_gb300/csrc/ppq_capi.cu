@@ -1473,14 +1473,6 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   return solve_core(w, P, e_const, o, t_in, t_out, e_corr, e_total, info, s, wall0);
 }
 
-int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
-             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
-             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
-  (void)n_pairs; (void)occ_of_pair; (void)vir_of_pair; (void)h; (void)eri; (void)e_const;
-  (void)opts; (void)t_in; (void)t_out; (void)e_corr; (void)e_total; (void)info; (void)stream;
-  return fail(-6, "ph_solve: the three-pair (PH) model has no kernels in this version");
-}
-
 int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pair,
                      const int* const* vir_of_pair, const double* const* h,
                      const double* const* eri, const double* e_const, const ppq_opts* opts,
@@ -1789,3 +1781,5 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   if (e_corr) *e_corr = e;
   return 0;
 }
+
+#include "ph_engine.cuh"

@@ -53,13 +53,47 @@ def test_bad_pairing_rejected_without_gpu():
         ppq.pq_solve([0], [1], np.zeros((2, 2)), np.zeros((2,) * 4))
 
 
-def test_ph_solve_is_declared_and_refuses_loudly():
-    # the three-pair model is part of the boundary but has no kernels yet: the
-    # call fails with its own code and message, before touching a GPU
+def test_ph_entry_points_reject_bad_arguments_without_gpu():
+    # argument errors come back before any device work, with their own codes
     n = 6
     h = np.zeros((n, n)); eri = np.zeros((n,) * 4)
-    with pytest.raises(ppq.PPQError, match=r"ph_solve failed \(-6\).*three-pair"):
-        ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri)
+    with pytest.raises(ppq.PPQError, match=r"ph_solve failed \(-4\).*K_H"):
+        ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri, K_H=4)
+    with pytest.raises(ppq.PPQError, match="twice"):
+        ppq.ph_solve([2, 2, 0], [3, 4, 5], h, eri)
+    t = np.zeros(ppq.amp_count(3, 3))
+    with pytest.raises(ppq.PPQError, match=r"ph_residual failed \(-4\).*K_H"):
+        ppq.ph_residual([2, 1, 0], [3, 4, 5], h, eri, t, K_H=1)
+
+
+def test_amp_count_three_pair():
+    for N in (2, 3, 15):
+        assert ppq.amp_count(N, 3) == 3 * N + 29 * N * N + 303 * N ** 3
+
+
+def test_binding_checks_buffers_before_any_launch():
+    # a short, mistyped or non-contiguous buffer is refused in the binding,
+    # before the library could read or write past it
+    N, n = 3, 6
+    h = np.zeros((n, n)); eri = np.zeros((n,) * 4)
+    L = ppq.amp_count(N)
+    occ, vir = [2, 1, 0], [3, 4, 5]
+    with pytest.raises(ppq.PPQError, match="t holds"):
+        ppq.pq_residual(occ, vir, h, eri, np.zeros(L - 1))
+    with pytest.raises(ppq.PPQError, match="float64"):
+        ppq.pq_residual(occ, vir, h, eri, np.zeros(L, dtype=np.float32))
+    with pytest.raises(ppq.PPQError, match="eri holds"):
+        ppq.pq_residual(occ, vir, h, eri[:5], np.zeros(L))
+    with pytest.raises(ppq.PPQError, match="float64"):
+        ppq.pq_residual(occ, vir, h, eri, np.zeros((L, 2))[:, 0])
+    with pytest.raises(ppq.PPQError, match="r holds"):
+        ppq.pq_residual(occ, vir, h, eri, np.zeros(L), np.zeros(3))
+    with pytest.raises(ppq.PPQError, match="CUDA tensor"):
+        ppq.pq_residual_static(occ, vir, h, eri, np.zeros(L), np.zeros(L))
+    with pytest.raises(ppq.PPQError, match="t_out holds"):
+        ppq.ph_solve(occ, vir, h, eri, t_out=np.zeros(ppq.amp_count(N, 3) - 1))
+    with pytest.raises(ppq.PPQError, match="t holds"):
+        ppq.ph_residual(occ, vir, h, eri, np.zeros(ppq.amp_count(N)))
 
 
 def test_layout_map_round_trip():
