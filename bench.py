@@ -53,6 +53,10 @@ def parse():
                     help="also time a batched solve of this many H chains (H10-H50, 0.7-3.0 A)")
     ap.add_argument("--gradient", action="store_true",
                     help="also time the H50 (1.8 A) energy gradient through the Lambda equations")
+    ap.add_argument("--ph-rings", default="2,3,4,5",
+                    help="PH leg: acenes by ring count (2 naphthalene .. 7 heptacene); '' to skip")
+    ap.add_argument("--ph-fp64-max-rings", type=int, default=5,
+                    help="largest acene also solved FP64-only beside the mixed solve")
     return ap.parse_args()
 
 
@@ -140,6 +144,53 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_peak(name, pk):
+    """(bound, peak, unit, note) of a kernel class: the measured bf16 burst
+    scaled by the nominal ratio of the path's arithmetic (2.25 PF bf16 dense,
+    1.1 PF TF32, 1.25 TF FP64), the FP32 SIMT peak from unit counts and clock
+    (152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock), HBM the measured copy
+    bandwidth."""
+    bf16 = pk.get("bf16_tflops", 1900.0)
+    tf32 = bf16 * 1.1 / 2.25
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    if "k_t9_tc64" in name:
+        return "tensor", tf32 / 21.0, "TFLOP/s", "measured bf16 burst x 1.1/2.25 (TF32) / 21 slice products (of measured)"
+    if "k_t9_tc" in name:
+        return "tensor", tf32 / 3.0, "TFLOP/s", "measured bf16 burst x 1.1/2.25 (TF32) / 3 (of measured)"
+    if name.startswith("solver") or "gather" in name or "fill" in name:
+        return "hbm", pk.get("hbm_gbs", 6800.0), "GB/s", "measured HBM copy bandwidth"
+    if "FP64" in name:
+        return "alu", bf16 * 1.25 / 2250.0, "TFLOP/s", "FP64: measured bf16 burst x 1.25/2250 (nominal ratio)"
+    return "alu", 152 * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", "FP32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock (derived)"
+
+
+def kernel_table(prof, solve_ms, pk):
+    """Per-kernel table of a profiled solve (shares of the solve's stream time)
+    and the roofline entry of the largest kernel class."""
+    rows = []
+    for p in prof:
+        bound, peak, unit, note = kernel_peak(p["name"], pk)
+        rate = None
+        if p["ms"] > 0:
+            rate = (p["bytes"] / (p["ms"] * 1e-3) / 1e9) if unit == "GB/s" else (p["flops"] / (p["ms"] * 1e-3) / 1e12)
+        rows.append({"name": p["name"], "ms": p["ms"], "share": p["ms"] / solve_ms if solve_ms else None,
+                     "launches": p["launches"], "bound": bound, "achieved": rate, "peak": peak, "unit": unit,
+                     "frac": (rate / peak) if (rate and peak and (p["flops"] or p["bytes"])) else None,
+                     "per_launch_ms": p["ms"] / max(p["launches"], 1)})
+    kern = [r for r in rows if not r["name"].startswith("solver") and not r["name"].startswith("staging")]
+    top = max(kern, key=lambda r: r["ms"])
+    _, _, _, note = kernel_peak(top["name"], pk)
+    traffic = None
+    if "k_t9_tc64" in top["name"]:
+        traffic = TRAFFIC_FP64_QUARTIC
+    elif "k_t9_tc" in top["name"]:
+        traffic = TRAFFIC_TC_QUARTIC
+    roof = {"bound": top["bound"], "kernel": top["name"] + " (largest share of device time in the profiled solve)",
+            "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],
+            "traffic": traffic, "peak_note": note, "share_of_solve": top["share"]}
+    return rows, roof
+
+
 def workload(sites):
     from workloads import build_ppp
     H = build_ppp('polyene', sites, with_eri=False, orbitals="local")
@@ -151,10 +202,45 @@ def ppp_eri_device(H, torch):
     return build(H, torch)
 
 
-def cpu_baseline(sites, seconds, iters, seed=0):
+def host_info():
+    """Core count and CPU model of the host that times the oracle."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def _time_local_problem(job):
+    """Worker: one oracle local problem (O-det residual), wall time."""
+    cc, tl, h, v = job
+    t0 = time.perf_counter()
+    cc.residual(tl, h, v)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sites, seconds, iters, seed=0, all_cores=True):
     """Time the oracle (O-loc) on a bounded random sample of the local
     label-subset problems of one residual evaluation of this workload and scale
-    to a full solve: per-size mean time x number of subsets x iterations."""
+    to a full solve: per-size mean time x number of subsets x iterations.  The
+    same sample then runs on every host core (a spawn pool, so that no forked
+    child inherits a CUDA context) for the all-core figure."""
     from math import comb
     from workloads import build_ppp
     from oracle.loccc import LocalAssembly
@@ -165,6 +251,7 @@ def cpu_baseline(sites, seconds, iters, seed=0):
     t_start = time.perf_counter()
     budget = {1: 0.05, 2: 0.15, 3: 0.3, 4: 0.5}
     counts = {}
+    jobs, serial = [], 0.0
     for k in (1, 2, 3, 4):
         subs = [tuple(sorted(rng.choice(N, k, replace=False))) for _ in range(4096)]
         L = LocalAssembly(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, subsets=subs[:1])
@@ -173,26 +260,125 @@ def cpu_baseline(sites, seconds, iters, seed=0):
         for s in subs:
             loc = L._local(s)
             tl = loc['sgn'] * t[loc['glob']]
-            t0 = time.perf_counter()
-            loc['cc'].residual(tl, loc['h'], loc['v'])
-            spent += time.perf_counter() - t0
+            job = (loc['cc'], tl, loc['h'], loc['v'])
+            spent += _time_local_problem(job)
+            jobs.append(job)
             done += 1
             if spent > seconds * budget[k]:
                 break
         per_size[k] = spent / done
         counts[k] = done
+        serial += spent
     per_residual = sum(per_size[k] * comb(N, k) for k in per_size)
-    return {
+    info = host_info()
+    out = {
         "value": per_residual * iters, "unit": "s", "cores": 1, "kind": "oracle",
         "sample": (f"O-loc local problems of one residual of PPP C{sites}H{sites + 2}: "
                    + ", ".join(f"{counts[k]} of C({N},{k})={comb(N, k)} {k}-label" for k in counts)
                    + f"; mean time per problem x count x {iters} iterations (extrapolated)"),
         "per_residual_s": per_residual,
-        "sample_wall_s": time.perf_counter() - t_start,
+        "host": info,
     }
+    if all_cores and (info["nproc"] or 1) > 1:
+        import multiprocessing as mp
+        w0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(info["nproc"]) as pool:
+            pool.map(_time_local_problem, jobs[:info["nproc"]])      # start-up
+            w1 = time.perf_counter()
+            pool.map(_time_local_problem, jobs, chunksize=1)
+            wall = time.perf_counter() - w1
+        speedup = serial / wall
+        out["all_cores"] = {"value": per_residual * iters / speedup, "cores": info["nproc"],
+                            "speedup_on_sample": speedup, "pool_startup_s": w1 - w0,
+                            "sample_wall_s": wall}
+    out["sample_wall_s"] = time.perf_counter() - t_start
+    return out
+
+
+# residual evaluations of the GPU mixed solve of PPP C140H142 (the value the
+# GPU arm reports live as iters; the reference arm scales its oracle sample by
+# the same count)
+SOLVE_EVALS = 47
 
 
 METRIC = "PQ time to solution, PPP C140H142 (70 pairs), mixed FP32/FP64"
+
+ACENES = {2: "naphthalene", 3: "anthracene", 4: "tetracene", 5: "pentacene", 6: "hexacene", 7: "heptacene"}
+
+
+def ph_cpu_baseline(seconds_cap=60.0):
+    """The oracle (O-det, FP64, one core) timed on one PH residual of
+    naphthalene (N = 5: the whole system is one local problem)."""
+    from workloads import build_ppp
+    from oracle.detcc import Problem
+    H = build_ppp('acene', 2)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3)
+    t = np.random.default_rng(0).uniform(-0.01, 0.01, P.cc.n_amp)
+    t0 = time.perf_counter()
+    P.residual(t)
+    return time.perf_counter() - t0
+
+
+def ph_leg(args, stream, pk):
+    """PH (three-pair) solves of PPP acenes: mixed (FP32 bulk, FP64 finish) and
+    FP64-only, time to solution from device-resident integrals (CUDA events),
+    residual FLOP rate, |dE| mixed vs FP64, and the per-kernel profile of one
+    more mixed solve of the largest acene (the roofline of its dominant
+    kernel)."""
+    import torch
+    import paper_1609_00077_gb300 as ppq
+    from workloads import build_ppp
+    rings = [int(x) for x in args.ph_rings.split(",") if x.strip()]
+    out = {"model": "PH (K = 3, three-label integrals), exact", "orbitals": "canonical RHF, Fig. 1 pairing",
+           "convergence": "||R||_2 <= 1e-10 and |dE| <= 1e-10 Eh", "systems": []}
+    last = None
+    for nr in rings:
+        H = build_ppp('acene', nr)
+        h = torch.from_numpy(H.h).cuda(); eri = torch.from_numpy(H.eri).cuda()
+        kw = dict(r_tol=1e-10, e_tol=1e-10, max_iter=400, stream=stream.cuda_stream)
+        ppq.ph_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, precision=1, max_iter=2,
+                     stream=stream.cuda_stream)  # tables, warm-up
+        rows = {}
+        for prec in ((1, 0) if nr <= args.ph_fp64_max_rings else (1,)):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, e, _, info = ppq.ph_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, precision=prec, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            rows[prec] = {"seconds": sec, "status": rc, "e_total": e, "iters": info["iters"],
+                          "evals_fp32": info["evals_fp32"], "evals_fp64": info["evals_fp64"],
+                          "residual_s_mean": info["t_residual_ms"] / 1e3 / max(info["iters"], 1),
+                          "residual_tflops": info["residual_flops"] * info["iters"]
+                          / max(info["t_residual_ms"] * 1e-3, 1e-12) / 1e12}
+        entry = {"system": f"PPP {ACENES.get(nr, nr)} ({4 * nr + 2} e / {4 * nr + 2} o, {H.n_pairs} pairs)",
+                 "n_pairs": H.n_pairs, "mixed": rows[1], "fp64": rows.get(0)}
+        if 0 in rows:
+            entry["abs_dE_mixed_vs_fp64"] = abs(rows[1]["e_total"] - rows[0]["e_total"])
+        out["systems"].append(entry)
+        last = (H, h, eri)
+    if last is not None:
+        H, h, eri = last
+        ppq.ph_solve(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, precision=1, profile=1,
+                     r_tol=1e-10, e_tol=1e-10, max_iter=400, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        prof = ppq.profile_table()
+        total = sum(p["ms"] for p in prof)
+        top = prof[0]
+        hbm = pk.get("hbm_gbs", 6800.0)
+        ach = top["bytes"] / (top["ms"] * 1e-3) / 1e9 if top["ms"] > 0 else None
+        out["profile_system"] = f"PPP {ACENES.get(len(H.occ_of_pair) // 2, '')} mixed solve".strip()
+        out["kernels"] = [{"name": p["name"], "ms": p["ms"], "share": p["ms"] / total, "launches": p["launches"],
+                           "GB_per_s": p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None,
+                           "TFLOP_per_s": p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else None}
+                          for p in prof]
+        out["roofline"] = {"bound": "hbm", "kernel": top["name"], "achieved": ach, "peak": hbm, "unit": "GB/s",
+                           "frac": ach / hbm if ach else None, "traffic": None,
+                           "note": "algorithmic bytes (table entries, gathered amplitudes / integrals, psi rows) "
+                                   "over CUDA-event time; the psi rows of a chunk are largely L2-resident, so "
+                                   "this can exceed HBM (of measured HBM copy bandwidth)"}
+    return out
 
 
 def bench_config(args, world):
@@ -209,11 +395,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    iters = 40
+    iters = SOLVE_EVALS
     times = []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.sites, args.cpu_seconds / 3, iters, seed=k)
+        cb = cpu_baseline(args.sites, args.cpu_seconds / 3, iters, seed=k, all_cores=False)
         if k >= args.warmup:
             times.append(cb["value"])
     v = float(np.mean(times))
@@ -224,7 +410,7 @@ def run_reference(args):
            "config": bench_config(args, 1),
            "reference": "the oracle (O-loc, FP64, one core): a bounded sample of the local problems of one "
                         f"residual, scaled to a solve of {iters} residual evaluations",
-           "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+           "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample", "host")} | {"value": v, "unit": "s"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -287,19 +473,28 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            rc, e_mixed, _, info = solve(1, profile=1)
+            rc, e_mixed, _, info = solve(1)
             infos.append(info)
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist: dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist)
     info = infos[-1]
+    # one more mixed solve with every kernel timed (CUDA events on the solve
+    # stream, launched directly instead of as graphs), outside the timed region
+    pe0 = torch.cuda.Event(enable_timing=True); pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    _, _, _, pinfo = solve(1, profile=1)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof = ppq.profile_table()
+    prof_ms = pe0.elapsed_time(pe1)
     # FP64-only solve beside it
     fp64 = None
     if not args.no_fp64:
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rc64, e64, _, info64 = solve(0, profile=1)
+        rc64, e64, _, info64 = solve(0)
         e1.record(stream)
         torch.cuda.synchronize()
         fp64 = {"seconds": e0.elapsed_time(e1) / 1e3, "status": rc64, "iters": info64["iters"],
@@ -319,24 +514,8 @@ def main():
                          t_out=t_host.numpy(), precision=1, stream=stream.cuda_stream, **kw)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - w0) / args.steps
-    # roofline of the dominant kernel: the quartic GEMM, split by precision
     pk = peaks()
-    n32 = info["n_quartic32"]; n64 = info["n_quartic"] - n32
-    t32 = info["t_quartic32_ms"]; t64 = info["t_quartic_ms"] - t32
-    ach32 = info["quartic_flops"] / (t32 / max(n32, 1) * 1e-3) / 1e12 if n32 else None
-    ach64 = info["quartic_flops"] / (t64 / max(n64, 1) * 1e-3) / 1e12 if n64 else None
-    # peaks: the measured bf16 burst x the nominal ratio of the dtype (2.25 PF bf16 dense,
-    # 1.1 PF TF32, 1.25 TF FP64); the FP32 residual's quartic term runs as 3xTF32 MMAs,
-    # so its FP32-equivalent peak is a third of the TF32 figure
-    bf16 = pk.get("bf16_tflops", 1900.0)
-    tf32_peak = bf16 * 1.1 / 2.25
-    fp32_peak = tf32_peak / 3.0
-    fp64_alu_peak = bf16 * 1.25 / 2250.0
-    # the FP64 residual's quartic term runs as exact integer splitting on the
-    # tensor cores: 21 TF32 MMAs per FP64 product
-    fp64_peak = tf32_peak / 21.0
-    dominant64 = t64 > t32
-    achieved = ach64 if dominant64 else ach32
+    kernels, roof = kernel_table(prof, prof_ms, pk)
     n_launch = info["n_launches"]
     res_tflops = info["residual_flops"] * info["iters"] / (info["t_residual_ms"] * 1e-3) / 1e12
     out = {
@@ -350,25 +529,11 @@ def main():
         "residual_tflops": res_tflops,
         "fp64": fp64,
         "gpu_launches": n_launch * args.steps,
-        "roofline": {"bound": "tensor",
-                     "kernel": ("k_t9_tc64 (FP64 quartic term, exact splitting on tcgen05; largest share"
-                                " of device time)" if dominant64 else
-                                "k_t9_tc (FP32 quartic term, 3xTF32 on tcgen05; largest share of device time)"),
-                     "achieved": achieved, "peak": fp64_peak if dominant64 else fp32_peak,
-                     "unit": "TFLOP/s",
-                     "frac": achieved / (fp64_peak if dominant64 else fp32_peak),
-                     "traffic": TRAFFIC_FP64_QUARTIC if dominant64 else TRAFFIC_TC_QUARTIC,
-                     "peak_note": ("measured bf16 burst x 1.1/2.25 (TF32) / 21 slice products (of measured)"
-                                   if dominant64 else
-                                   "measured bf16 burst x 1.1/2.25 (TF32) / 3 (of measured)"),
-                     "fp32_launches": {"kernel": "k_t9_tc", "n": n32, "ms_total": t32, "tflops": ach32,
-                                       "peak_3xtf32": fp32_peak,
-                                       "frac": ach32 / fp32_peak if ach32 else None},
-                     "fp64_launches": {"kernel": "k_t9_tc64", "n": n64, "ms_total": t64,
-                                       "tflops": ach64, "peak_split_tf32": fp64_peak,
-                                       "frac": ach64 / fp64_peak if ach64 else None,
-                                       "fp64_alu_peak": fp64_alu_peak,
-                                       "of_fp64_alu_peak": ach64 / fp64_alu_peak if ach64 else None}},
+        "roofline": roof,
+        "kernels": {"solve_ms": prof_ms, "sum_ms": sum(k["ms"] for k in kernels),
+                    "note": "one extra mixed solve with every kernel timed by CUDA events on the solve stream "
+                            "(direct launches, not graphs); each kernel is charged the stream time since the "
+                            "previous event", "table": kernels},
         "evals": {"fp32": info["evals_fp32"], "fp64": info["evals_fp64"]},
         "e2e": {"value": e2e_s, "unit": "s",
                 "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),
@@ -412,9 +577,18 @@ def main():
                                "system": H50.name, "e_total": eg,
                                "evals": ig["iters"], "max_abs_dE_dkappa": float(dkg.abs().max()),
                                "note": "mixed solve + Lambda (FP64 adjoint) + dE/dh, dE/d(pq|rs), dE/dkappa"}
+    if args.ph_rings.strip():
+        out["ph"] = ph_leg(args, stream, pk)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args.sites, args.cpu_seconds, info["iters"])
-        out["cpu_baseline"]["cores"] = 1
+        if "ph" in out and out["ph"]["systems"]:
+            per = ph_cpu_baseline()
+            it = out["ph"]["systems"][0]["mixed"]["iters"]
+            out["ph"]["cpu_baseline"] = {
+                "value": per * it, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": f"O-det (oracle) one PH residual of naphthalene ({per:.2f} s) x {it} residual "
+                          "evaluations of the GPU mixed solve (extrapolated)",
+                "per_residual_s": per}
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -1,5 +1,6 @@
 /*
- * ppq.h -- C ABI of the GB300 PQ amplitude solver (perfect quadruples model).
+ * ppq.h -- C ABI of the GB300 PQ / PH amplitude solver (perfect quadruples and
+ * perfect hextuples models).
  *
  * The method (Theory section of the paper): coupled-cluster theory truncated
  * to amplitudes whose holes and particles carry at most K = 2 pairing labels
@@ -83,8 +84,9 @@ typedef struct {
   int diis_start;     /* 3                                                     */
   double level_shift; /* added to |denominator| (0)                             */
   int guess;          /* 0 = zero amplitudes, 1 = start from t_in               */
-  int profile;        /* 1 = time the quartic contraction kernel with CUDA      */
-                      /*     events on `stream` (fields t_quartic_ms, ... )     */
+  int profile;        /* 1 = time every kernel with CUDA events on `stream`     */
+                      /*     (ppq_profile_entry; pq_solve also fills            */
+                      /*     t_quartic_ms, ... )                                */
   int polish;         /* after the switch (precision = 1): 0 = plain FP64       */
                       /*     Jacobi/DIIS iterations; 1 = FP64 defect correction:*/
                       /*     each outer step evaluates R in FP64 (norm, energy, */
@@ -297,6 +299,19 @@ int ppq_release(void);
 /* Thread-local message of the last failing call on this thread ("" if none;
    library housekeeping, the paper has no counterpart). */
 const char* ppq_last_error(void);
+
+/* Per-kernel device time of the last call made with opts->profile = 1
+   (library instrumentation; the paper has no counterpart).  CUDA events are
+   recorded on the call's stream after every kernel, and each kernel class is
+   charged the stream time since the previous event, so the classes add up to
+   the stream time of the call.  ppq_profile_count returns the number of
+   classes (waiting for the recorded events); ppq_profile_entry(i, ...) fills
+   the class name (NUL-terminated, at most name_cap bytes), milliseconds,
+   launches, algorithmic bytes and FLOPs of class i (every output nullable).
+   Returns 0, or -2 for an index out of range. */
+int ppq_profile_count(void);
+int ppq_profile_entry(int i, char* name, int name_cap, double* ms, int* launches, double* bytes,
+                      double* flops);
 
 /* Work list of the tensor-core form of the quartic topology (Sec. II, the
    four-link term of the linked residual) for n_pairs <= 80; host only, no

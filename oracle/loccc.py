@@ -16,6 +16,8 @@ over L containing labels(mu) with |L| <= K + K_H gives
     c_k  = sum_{j=0}^{K+K_H-k} (-1)^j binom(N-k, j).
 
 The same holds for the energy with labels(mu) empty and K + K_H replaced by K_H.
+With untruncated integrals (K_H = -1) an element (pq|rs) carries at most four
+labels, so the bounds read K + 4 and 4.
 Each local problem is solved with ``detcc.DetCC`` in its own determinant space
 (orbital order preserved); amplitudes and residuals are mapped between the
 global and local excitation operators with the sign relating the two
@@ -45,6 +47,8 @@ class LocalAssembly:
         and eri are then not read)."""
         self.K = K
         self.K_H = K if K_H == 0 else K_H
+        # labels one Hamiltonian element can carry (four for untruncated integrals)
+        self.span_H = 4 if self.K_H < 0 else self.K_H
         self.occ = np.asarray(occ_of_pair); self.vir = np.asarray(vir_of_pair)
         self.N = len(self.occ)
         if truncated is None:
@@ -53,7 +57,7 @@ class LocalAssembly:
         self.manifold = enumerate_manifold(self.occ, self.vir, K)
         self.index = {d: k for k, d in enumerate(self.manifold)}
         self.global_ref = sum(1 << int(i) for i in self.occ)
-        kmax = K + self.K_H
+        kmax = K + self.span_H
         self.kmax = kmax
         self.locals = []
         if subsets is not None:
@@ -124,7 +128,7 @@ class LocalAssembly:
             tl = loc['sgn'] * t[loc['glob']]
             Rl, el = loc['cc'].residual(tl, loc['h'], loc['v'])
             R[loc['glob']] += _moebius_coeff(self.N, m, self.kmax) * loc['sgn'] * Rl
-            if m <= self.K_H:
-                e += _moebius_coeff(self.N, m, self.K_H) * (el - loc['e0'])
+            if m <= self.span_H:
+                e += _moebius_coeff(self.N, m, self.span_H) * (el - loc['e0'])
         # every amplitude's own label set must be counted from |labels(mu)| up
         return R, e

@@ -69,6 +69,8 @@ def lib():
         L.ph_residual.argtypes = [I, P, P, P, P, P, P, P, I, I, P]
         L.ph_tables_counts.argtypes = [I, I, I, P]
         L.ph_tables_copy.argtypes = [I, I, I, I, P]
+        L.ppq_profile_count.argtypes = []
+        L.ppq_profile_entry.argtypes = [I, ctypes.c_char_p, I, P, P, P, P]
         L.pq_solve_batched.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P, P, P, P]
         L.pq_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, P, P, P]
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
@@ -80,7 +82,7 @@ def lib():
                   L.pq_residual_static, L.pq_solve, L.ph_solve, L.pq_solve_batched,
                   L.pq_lagrangian_gradient,
                   L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan, L.ph_residual,
-                  L.ph_tables_counts, L.ph_tables_copy):
+                  L.ph_tables_counts, L.ph_tables_copy, L.ppq_profile_count, L.ppq_profile_entry):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -89,7 +91,8 @@ def lib():
 EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual",
             "pq_residual_static", "pq_solve", "ph_solve", "ph_residual", "pq_solve_batched",
             "pq_lagrangian_gradient", "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error",
-            "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy"]
+            "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy", "ppq_profile_count",
+            "ppq_profile_entry"]
 
 
 def _ptr(x):
@@ -169,6 +172,24 @@ def tc_plan(n_pairs):
     _check(lib().ppq_tc_plan(n_pairs, ch.ctypes.data, nc.value, ct.ctypes.data, nt.value,
                              ctypes.byref(nc), ctypes.byref(nt)), "ppq_tc_plan")
     return ch, ct
+
+
+def profile_table():
+    """Per-kernel classes of the last call made with profile=1: list of dicts
+    (name, ms, launches, bytes, flops), largest time first."""
+    L = lib()
+    out = []
+    for i in range(L.ppq_profile_count()):
+        name = ctypes.create_string_buffer(256)
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        _check(L.ppq_profile_entry(i, name, 256, ctypes.cast(ctypes.pointer(ms), ctypes.c_void_p),
+                                   ctypes.cast(ctypes.pointer(n), ctypes.c_void_p),
+                                   ctypes.cast(ctypes.pointer(by), ctypes.c_void_p),
+                                   ctypes.cast(ctypes.pointer(fl), ctypes.c_void_p)), "ppq_profile_entry")
+        out.append({"name": name.value.decode(), "ms": ms.value, "launches": n.value,
+                    "bytes": by.value, "flops": fl.value})
+    return sorted(out, key=lambda d: -d["ms"])
 
 
 def default_opts(**kw):

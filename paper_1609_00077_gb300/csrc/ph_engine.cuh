@@ -86,7 +86,8 @@ namespace ph {
 // ------------------------------------------------------------ device constants
 __constant__ int8_t c_A3[303 * 3];      // three-pair channel monomials
 __constant__ int16_t c_A3inv[4096];     // (a << 8 | b << 4 | c) -> channel, -1 if none
-__constant__ int8_t c_key[3][576 * 5];  // integral keys of 1, 2, 3 sites: (type, p, q, r, s)
+__constant__ int8_t c_key[4][576 * 5];  // integral keys of 1..4 sites: (type, p, q, r, s)
+__constant__ int c_binom[128 * 8];      // C(n, r), n < 128, r < 8
 
 constexpr int kNA3 = 303;
 constexpr int kNK3 = 576;
@@ -135,15 +136,19 @@ __device__ __forceinline__ double denom3(size_t i, int N, const double* fo, cons
 }
 
 // ------------------------------------------------------------ staging
-// G1[X][20], G2[X][W][232] (X < W), G3[X][Y][Z][576] (X < Y < Z) from the
-// bare one-body part hb and (pq|rs)
+// G1[X][20], G2[X][W][232] (X < W), G3[X][Y][Z][576] (X < Y < Z) and, with
+// four-label integrals, G4[rank of X < Y < Z < V][384] from the bare one-body
+// part hb and (pq|rs)
+constexpr int kNK4 = 384;
 __global__ void k_stage_g(int n, int N, int KH, const double* __restrict__ hb, const double* __restrict__ eri,
-                          const int* __restrict__ occ, const int* __restrict__ vir, double* __restrict__ G1,
-                          double* __restrict__ G2, double* __restrict__ G3) {
+                          const int* __restrict__ occ, const int* __restrict__ vir, const int8_t* __restrict__ subs4,
+                          int nsub4, double* __restrict__ G1, double* __restrict__ G2, double* __restrict__ G3,
+                          double* __restrict__ G4) {
   size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
   size_t t1 = (size_t)N * 20, t2 = (size_t)N * N * 232, t3 = KH >= 3 ? (size_t)N * N * N * kNK3 : 0;
-  int m, j, L[3];
+  size_t t4 = KH >= 4 ? (size_t)nsub4 * kNK4 : 0;
+  int m, j, L[4];
   double* dst;
   if (tid < t1) { m = 1; j = tid % 20; L[0] = tid / 20; dst = G1 + tid; }
   else if ((tid -= t1) < t2) {
@@ -153,8 +158,12 @@ __global__ void k_stage_g(int n, int N, int KH, const double* __restrict__ hb, c
     m = 3; j = tid % kNK3; size_t q = tid / kNK3; L[2] = q % N; L[1] = (q / N) % N; L[0] = q / ((size_t)N * N);
     dst = G3 + tid;
     if (!(L[0] < L[1] && L[1] < L[2])) { *dst = 0.0; return; }
+  } else if ((tid -= t3) < t4) {
+    m = 4; j = tid % kNK4; size_t q = tid / kNK4;
+    for (int x = 0; x < 4; ++x) L[x] = subs4[q * 4 + x];
+    dst = G4 + tid;
   } else return;
-  int o[6];
+  int o[8];
   for (int x = 0; x < m; ++x) { o[2 * x] = occ[L[x]]; o[2 * x + 1] = vir[L[x]]; }
   const int8_t* k = c_key[m - 1] + 5 * j;
   *dst = k[0] == 0 ? hb[o[k[1]] * n1 + o[k[2]]]
@@ -173,7 +182,7 @@ __global__ void k_gather_amp(int P, int p0, int nsub, int k, int nslot, const in
   R v = R(0);
   if (p0 + p < nsub) {
     int d = slot_desc[slot];
-    int m = d & 15, ch = d >> 16;
+    int m = d & 15, ch = d >> kDescIdx;
     const int8_t* L = subs + (size_t)(p0 + p) * k;
     size_t a = L[(d >> 4) & 15], idx;
     if (m == 1) idx = 3 * a + ch;
@@ -188,24 +197,30 @@ __global__ void k_gather_amp(int P, int p0, int nsub, int k, int nslot, const in
 }
 
 // vl[key slot][p]: integral of key slot for the p-th subset
+__device__ __forceinline__ int colex_d(const int* p, int m);
 template <typename R>
 __global__ void k_gather_int(int P, int p0, int nsub, int k, int nkey, const int* __restrict__ key_desc,
                              const int8_t* __restrict__ subs, int N, const double* __restrict__ G1,
-                             const double* __restrict__ G2, const double* __restrict__ G3, R* __restrict__ vl) {
+                             const double* __restrict__ G2, const double* __restrict__ G3,
+                             const double* __restrict__ G4, R* __restrict__ vl) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)nkey * P) return;
   int ks = i / P, p = i % P;
   R v = R(0);
   if (p0 + p < nsub) {
     int d = key_desc[ks];
-    int m = d & 15, j = d >> 16;
+    int m = d & 15, j = d >> kDescIdx;
     const int8_t* L = subs + (size_t)(p0 + p) * k;
     size_t a = L[(d >> 4) & 15];
     if (m == 1) v = R(G1[a * 20 + j]);
     else {
       size_t b = L[(d >> 8) & 15];
       if (m == 2) v = R(G2[(a * N + b) * 232 + j]);
-      else v = R(G3[((a * N + b) * N + (size_t)L[(d >> 12) & 15]) * kNK3 + j]);
+      else if (m == 3) v = R(G3[((a * N + b) * N + (size_t)L[(d >> 12) & 15]) * kNK3 + j]);
+      else {
+        int q[4] = {(int)a, (int)b, L[(d >> 12) & 15], L[(d >> 16) & 15]};
+        v = R(G4[(size_t)colex_d(q, 4) * kNK4 + j]);
+      }
     }
   }
   vl[i] = v;
@@ -217,76 +232,138 @@ __global__ void k_set_ref(int P, R* __restrict__ a, R* __restrict__ b) {
   if (p < P) { a[p] = R(1); b[p] = R(1); }
 }
 
-// One level of psi = exp(+-T)|ref>: warp per state, lane per subset.
-// Entries i of [s0, s1) (positions in level order); dst = order ? order[i] : i.
-template <typename R>
+// One level of psi = exp(+-T)|ref>: warp per state, lane per J subsets
+// (p, p + 32, ...).  Entries i of [s0, s1) (positions in level order);
+// dst = order ? order[i] : i.  An entry packs the sub-state (low 32 bits)
+// and 2 slot + (sign < 0) (high 32 bits).
+template <typename R, int J>
 __global__ void __launch_bounds__(256) k_psi(int P, int s0, int s1, const int* __restrict__ order,
-                                             const int* __restrict__ eptr, const int* __restrict__ esub,
-                                             const int16_t* __restrict__ eslot, const R* __restrict__ tl,
-                                             R tsign, R* __restrict__ psi) {
+                                             const int* __restrict__ eptr,
+                                             const unsigned long long* __restrict__ ent,
+                                             const R* __restrict__ tl, R tsign, R* __restrict__ psi) {
   int i = s0 + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= s1) return;
-  int p = blockIdx.y * 32 + (threadIdx.x & 31);
-  R acc = R(0);
+  int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
+  R acc[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) acc[j] = R(0);
   int e1 = eptr[i + 1];
   for (int e = eptr[i]; e < e1; ++e) {
-    int sl = eslot[e];
-    R a = tl[(size_t)(sl >> 1) * P + p] * psi[(size_t)esub[e] * P + p];
-    acc = (sl & 1) ? acc - a : acc + a;
+    unsigned long long w = ent[e];
+    unsigned sub = (unsigned)w, sl = (unsigned)(w >> 32);
+    const R* a = tl + (size_t)(sl >> 1) * P + p;
+    const R* b = psi + (size_t)sub * P + p;
+    if (sl & 1) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc[j] -= a[32 * j] * b[32 * j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc[j] += a[32 * j] * b[32 * j];
+    }
   }
-  int dst = order ? order[i] : i;
-  psi[(size_t)dst * P + p] = tsign * acc;
+  R* d = psi + (size_t)(order ? order[i] : i) * P + p;
+#pragma unroll
+  for (int j = 0; j < J; ++j) d[32 * j] = tsign * acc[j];
 }
 
 // phi[o][p] = <out o| H |psi> - E_0 psi[o], E_0 = <ref|H|ref>: the rows off
 // the diagonal in R, the diagonal and E_0 in FP64 from the same integrals (in
-// FP32 their large common part then cancels exactly)
-template <typename R>
+// FP32 their large common part then cancels exactly).  Off-diagonal entries
+// are grouped by state s within a row and packed: s (bits 0-19), key slot
+// (20-34), negative (35), coefficient 1/2 instead of 1 (36), first entry of
+// a state (37); a run sums c v[key] and multiplies psi[s] once.
+constexpr int kHsBits = 20, kHkBits = 15;
+constexpr int kHNeg = kHsBits + kHkBits, kHHalf = kHNeg + 1, kHNew = kHNeg + 2;
+template <typename R, int J>
 __global__ void __launch_bounds__(256) k_phi(int P, int nout, const int* __restrict__ hptr,
-                                             const int* __restrict__ hs, const int16_t* __restrict__ hkey,
-                                             const R* __restrict__ hc, const int* __restrict__ dptr,
-                                             const int16_t* __restrict__ dkey, const double* __restrict__ dc,
-                                             int ne0, const int16_t* __restrict__ e0key,
-                                             const double* __restrict__ e0c, const R* __restrict__ vl,
-                                             const R* __restrict__ psi, const int* __restrict__ out_state,
-                                             R* __restrict__ phi) {
+                                             const unsigned long long* __restrict__ hent,
+                                             const int* __restrict__ dptr, const int16_t* __restrict__ dkey,
+                                             const double* __restrict__ dc, int ne0,
+                                             const int16_t* __restrict__ e0key, const double* __restrict__ e0c,
+                                             const R* __restrict__ vl, const R* __restrict__ psi,
+                                             const int* __restrict__ out_state, R* __restrict__ phi) {
   int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (o >= nout) return;
-  int p = blockIdx.y * 32 + (threadIdx.x & 31);
-  double dg = 0.0;
-  for (int e = 0; e < ne0; ++e) dg -= e0c[e] * double(vl[(size_t)e0key[e] * P + p]);
+  int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
+  double dg[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) dg[j] = 0.0;
+  for (int e = 0; e < ne0; ++e) {
+    const R* v = vl + (size_t)e0key[e] * P + p;
+#pragma unroll
+    for (int j = 0; j < J; ++j) dg[j] -= e0c[e] * double(v[32 * j]);
+  }
   int d1 = dptr[o + 1];
-  for (int e = dptr[o]; e < d1; ++e) dg += dc[e] * double(vl[(size_t)dkey[e] * P + p]);
-  R acc = R(0);
+  for (int e = dptr[o]; e < d1; ++e) {
+    const R* v = vl + (size_t)dkey[e] * P + p;
+#pragma unroll
+    for (int j = 0; j < J; ++j) dg[j] += dc[e] * double(v[32 * j]);
+  }
+  R acc[J], run[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) { acc[j] = R(0); run[j] = R(0); }
+  const R* ps = psi + p;
   int e1 = hptr[o + 1];
-  for (int e = hptr[o]; e < e1; ++e) acc += hc[e] * vl[(size_t)hkey[e] * P + p] * psi[(size_t)hs[e] * P + p];
-  phi[(size_t)o * P + p] = acc + R(dg * double(psi[(size_t)out_state[o] * P + p]));
+  for (int e = hptr[o]; e < e1; ++e) {
+    unsigned long long w = hent[e];
+    if ((w >> kHNew) & 1) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) { acc[j] += run[j] * ps[32 * j]; run[j] = R(0); }
+      ps = psi + (size_t)(w & ((1u << kHsBits) - 1)) * P + p;
+    }
+    const R* v = vl + (size_t)((w >> kHsBits) & ((1u << kHkBits) - 1)) * P + p;
+    R c = ((w >> kHHalf) & 1) ? R(0.5) : R(1);
+    if ((w >> kHNeg) & 1) c = -c;
+#pragma unroll
+    for (int j = 0; j < J; ++j) run[j] += c * v[32 * j];
+  }
+  const R* pd = psi + (size_t)out_state[o] * P + p;
+  R* out = phi + (size_t)o * P + p;
+#pragma unroll
+  for (int j = 0; j < J; ++j) out[32 * j] = acc[j] + run[j] * ps[32 * j] + R(dg[j] * double(pd[32 * j]));
 }
 
-// R_loc[o][subset] = sum sign psi_minus(w) phi(kappa); E_loc[subset] = phi(ref)
-template <typename R>
+// R_loc[subset][o] = sum sign psi_minus(w) phi(kappa); E_loc[subset] = phi(ref)
+template <typename R, int J>
 __global__ void __launch_bounds__(256) k_backsub(int P, int p0, int nsub, int nout, const int* __restrict__ bptr,
                                                  const int* __restrict__ bk, const int* __restrict__ bw,
                                                  const R* __restrict__ psim, const R* __restrict__ phi,
                                                  double* __restrict__ Rloc, double* __restrict__ Eloc) {
   int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  int p = blockIdx.y * 32 + (threadIdx.x & 31);
-  if (o >= nout || p0 + p >= nsub) return;
-  if (o == 0) { Eloc[p0 + p] = double(phi[p]); return; }
-  R acc = R(0);
+  int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
+  if (o >= nout) return;
+  if (o == 0) {
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (p0 + p + 32 * j < nsub) Eloc[p0 + p + 32 * j] = double(phi[p + 32 * j]);
+    return;
+  }
+  R acc[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) acc[j] = R(0);
   int e1 = bptr[o + 1];
   for (int e = bptr[o]; e < e1; ++e) {
     int w = bw[e];
-    R a = psim[(size_t)(w >> 1) * P + p] * phi[(size_t)bk[e] * P + p];
-    acc = (w & 1) ? acc - a : acc + a;
+    const R* a = psim + (size_t)(w >> 1) * P + p;
+    const R* b = phi + (size_t)bk[e] * P + p;
+    if (w & 1) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc[j] -= a[32 * j] * b[32 * j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc[j] += a[32 * j] * b[32 * j];
+    }
   }
-  Rloc[(size_t)o * nsub + p0 + p] = double(acc);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+    if (p0 + p + 32 * j < nsub) Rloc[(size_t)(p0 + p + 32 * j) * nout + o] = double(acc[j]);
 }
 
 // ------------------------------------------------------------ assembly
 struct AsmArgs {
-  const double* Rloc[kMaxSites + 1];
+  const double* Rloc[kMaxSites + 1];  // [subset][output]
   int nsub[kMaxSites + 1];
+  int nout[kMaxSites + 1];
   double c[kMaxSites + 1];
   int kmax;
 };
@@ -294,7 +371,7 @@ struct AsmArgs {
 // colex rank of a sorted label set
 __device__ __forceinline__ int colex_d(const int* p, int m) {
   int r = 0;
-  for (int i = 0; i < m; ++i) r += binom_hd(p[i], i + 1);
+  for (int i = 0; i < m; ++i) r += c_binom[p[i] * 8 + i + 1];
   return r;
 }
 
@@ -314,7 +391,9 @@ __global__ void k_assemble(int N, int m, int nch, const int8_t* __restrict__ sub
     int j = k - m;
     int e[kMaxSites];
     for (int x = 0; x < j; ++x) e[x] = x;
-    int base = 1 + (m >= 2 ? 3 * k : 0) + (m >= 3 ? 29 * binom_hd(k, 2) : 0);
+    int base = 1 + (m >= 2 ? 3 * k : 0) + (m >= 3 ? 29 * c_binom[k * 8 + 2] : 0);
+    const double* Rk = A.Rloc[k];
+    const int nout = A.nout[k];
     double part = 0.0;
     for (;;) {
       // L = M + the e-th labels not in M (both sorted), merged
@@ -332,7 +411,7 @@ __global__ void k_assemble(int N, int m, int nch, const int8_t* __restrict__ sub
       }
       int rank = colex_d(Ls, k);
       int o = base + colex_d(pos, m) * nch + ch;
-      part += A.Rloc[k][(size_t)o * A.nsub[k] + rank];
+      part += Rk[(size_t)rank * nout + o];
       // next combination of j among nc (lexicographic)
       int x = j - 1;
       while (x >= 0 && e[x] == nc - j + x) --x;
@@ -512,13 +591,15 @@ namespace ph {
 // ------------------------------------------------------------ host side
 struct DevTables {
   int nstate = 0, nslot = 0, nout = 0, nkey = 0, ne0 = 0;
+  unsigned long long *ent = nullptr, *oent = nullptr, *hent = nullptr;  // packed entries
+  std::vector<double> lvl_ent, olvl_ent;  // recursion entries per level (algorithmic work)
+  double nh = 0, nruns = 0, nd = 0, nb = 0;
   std::vector<int> lvl_ptr, olvl_ptr;
-  int *ent_ptr = nullptr, *ent_sub = nullptr, *slot_desc = nullptr, *out_state = nullptr;
-  int *olvl_order = nullptr, *oent_ptr = nullptr, *oent_sub = nullptr, *key_desc = nullptr;
-  int *h_ptr = nullptr, *h_s = nullptr, *b_ptr = nullptr, *b_k = nullptr, *b_w = nullptr, *d_ptr = nullptr;
-  int16_t *ent_slot = nullptr, *oent_slot = nullptr, *h_key = nullptr, *e0_key = nullptr, *d_key = nullptr;
-  double *h_cd = nullptr, *e0_cd = nullptr, *d_c = nullptr;
-  float *h_cf = nullptr;
+  int *ent_ptr = nullptr, *slot_desc = nullptr, *out_state = nullptr;
+  int *olvl_order = nullptr, *oent_ptr = nullptr, *key_desc = nullptr;
+  int *h_ptr = nullptr, *b_ptr = nullptr, *b_k = nullptr, *b_w = nullptr, *d_ptr = nullptr;
+  int16_t *e0_key = nullptr, *d_key = nullptr;
+  double *e0_cd = nullptr, *d_c = nullptr;
 };
 
 struct Ctx {
@@ -531,7 +612,8 @@ struct Ctx {
   int nsub[kMaxSites + 1] = {};
   // gathered integrals
   int gN = 0;
-  double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr;
+  double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *G4 = nullptr;
+  int g4N = 0;
   // local-problem buffers
   size_t cap_psi = 0, cap_out = 0, cap_phi = 0, cap_tl = 0, cap_vl = 0;
   void *psi = nullptr, *psim = nullptr, *phi = nullptr, *tl = nullptr, *vl = nullptr;
@@ -562,14 +644,18 @@ int ph_consts(Ctx* c) {
     for (int x = 0; x < 3; ++x) a3[3 * ch + x] = (int8_t)A.A3[ch][x];
     inv[(A.A3[ch][0] << 8) | (A.A3[ch][1] << 4) | A.A3[ch][2]] = (int16_t)ch;
   }
-  int8_t keys[3][576 * 5];
+  int8_t keys[4][576 * 5];
   memset(keys, 0, sizeof keys);
-  for (int m = 1; m <= 3; ++m)
+  for (int m = 1; m <= 4; ++m)
     for (int j = 0; j < A.nkey(m); ++j)
       for (int x = 0; x < 5; ++x) keys[m - 1][5 * j + x] = (int8_t)A.key[m][j][x];
   CK(cudaMemcpyToSymbol(c_A3, a3, sizeof a3));
   CK(cudaMemcpyToSymbol(c_A3inv, inv, sizeof inv));
   CK(cudaMemcpyToSymbol(c_key, keys, sizeof keys));
+  int bn[128 * 8];
+  for (int n = 0; n < 128; ++n)
+    for (int r = 0; r < 8; ++r) bn[n * 8 + r] = binom(n, r);
+  CK(cudaMemcpyToSymbol(c_binom, bn, sizeof bn));
   c->consts = true;
   return 0;
 }
@@ -592,14 +678,47 @@ int dev_tables(Ctx* c, int k, int K, int KH, DevTables** out) {
   d->nstate = T->nstate; d->nslot = T->nslot; d->nout = T->nout; d->nkey = T->nkey;
   d->ne0 = (int)T->e0_c.size();
   d->lvl_ptr = T->lvl_ptr; d->olvl_ptr = T->olvl_ptr;
-  std::vector<float> hcf(T->h_c.begin(), T->h_c.end());
-  if ((rc = upload(&d->ent_ptr, T->ent_ptr)) || (rc = upload(&d->ent_sub, T->ent_sub)) ||
-      (rc = upload(&d->ent_slot, T->ent_slot)) || (rc = upload(&d->slot_desc, T->slot_desc)) ||
+  for (size_t lv = 0; lv + 1 < T->lvl_ptr.size(); ++lv)
+    d->lvl_ent.push_back((double)T->ent_ptr[T->lvl_ptr[lv + 1]] - T->ent_ptr[T->lvl_ptr[lv]]);
+  for (size_t lv = 0; lv + 1 < T->olvl_ptr.size(); ++lv)
+    d->olvl_ent.push_back((double)T->oent_ptr[T->olvl_ptr[lv + 1]] - T->oent_ptr[T->olvl_ptr[lv]]);
+  d->nh = (double)T->h_s.size(); d->nd = (double)T->d_key.size(); d->nb = (double)T->b_k.size();
+  // packed entries: recursion (sub | (2 slot + sign) << 32); Hamiltonian rows
+  // grouped by state, (s, key, sign, half, first-of-state) in one word
+  std::vector<unsigned long long> ent(T->ent_sub.size()), oent(T->oent_sub.size()), hent(T->h_s.size());
+  for (size_t e = 0; e < ent.size(); ++e)
+    ent[e] = (unsigned long long)(unsigned)T->ent_sub[e] | ((unsigned long long)(uint16_t)T->ent_slot[e] << 32);
+  for (size_t e = 0; e < oent.size(); ++e)
+    oent[e] = (unsigned long long)(unsigned)T->oent_sub[e] | ((unsigned long long)(uint16_t)T->oent_slot[e] << 32);
+  if (T->nstate >= (1 << kHsBits) || T->nkey >= (1 << kHkBits))
+    return fail(-5, "ph: table fields overflow for %d sites", k);
+  std::vector<int> hptr(T->h_ptr);
+  for (int o = 0; o < T->nout; ++o) {
+    std::vector<std::pair<long long, double>> row;
+    for (int e = T->h_ptr[o]; e < T->h_ptr[o + 1]; ++e)
+      row.push_back({(long long)T->h_s[e] * 65536 + T->h_key[e], T->h_c[e]});
+    std::sort(row.begin(), row.end());
+    int prev = -1;
+    for (size_t q = 0; q < row.size(); ++q) {
+      int st = (int)(row[q].first / 65536), ky = (int)(row[q].first % 65536);
+      double cv = row[q].second;
+      if (fabs(cv) != 1.0 && fabs(cv) != 0.5)
+        return fail(-5, "ph: unexpected Hamiltonian coefficient %g for %d sites", cv, k);
+      unsigned long long w = (unsigned long long)st | ((unsigned long long)ky << kHsBits) |
+                             ((unsigned long long)(cv < 0) << kHNeg) |
+                             ((unsigned long long)(fabs(cv) == 0.5) << kHHalf) |
+                             ((unsigned long long)(st != prev) << kHNew);
+      hent[T->h_ptr[o] + q] = w;
+      if (st != prev) d->nruns += 1;
+      prev = st;
+    }
+  }
+  if ((rc = upload(&d->ent_ptr, T->ent_ptr)) || (rc = upload(&d->ent, ent)) ||
+      (rc = upload(&d->slot_desc, T->slot_desc)) ||
       (rc = upload(&d->out_state, T->out_state)) || (rc = upload(&d->olvl_order, T->olvl_order)) ||
-      (rc = upload(&d->oent_ptr, T->oent_ptr)) || (rc = upload(&d->oent_sub, T->oent_sub)) ||
-      (rc = upload(&d->oent_slot, T->oent_slot)) || (rc = upload(&d->key_desc, T->key_desc)) ||
-      (rc = upload(&d->h_ptr, T->h_ptr)) || (rc = upload(&d->h_s, T->h_s)) || (rc = upload(&d->h_key, T->h_key)) ||
-      (rc = upload(&d->h_cd, T->h_c)) || (rc = upload(&d->h_cf, hcf)) || (rc = upload(&d->e0_key, T->e0_key)) ||
+      (rc = upload(&d->oent_ptr, T->oent_ptr)) || (rc = upload(&d->oent, oent)) ||
+      (rc = upload(&d->key_desc, T->key_desc)) ||
+      (rc = upload(&d->h_ptr, T->h_ptr)) || (rc = upload(&d->hent, hent)) || (rc = upload(&d->e0_key, T->e0_key)) ||
       (rc = upload(&d->e0_cd, T->e0_c)) || (rc = upload(&d->d_ptr, T->d_ptr)) || (rc = upload(&d->d_key, T->d_key)) ||
       (rc = upload(&d->d_c, T->d_c)) || (rc = upload(&d->b_ptr, T->b_ptr)) ||
       (rc = upload(&d->b_k, T->b_k)) || (rc = upload(&d->b_w, T->b_w))) {
@@ -656,11 +775,11 @@ int grow_buf(void** p, size_t* cap, size_t bytes) {
   return 0;
 }
 
-// subsets per chunk for k sites: a multiple of 32, psi within the budget
-int chunk_size(int nsub, int nstate, size_t elem) {
+// subsets per chunk for k sites: a multiple of mult, psi within the budget
+int chunk_size(int nsub, int nstate, size_t elem, int mult) {
   size_t cap = kPsiBudget / ((size_t)nstate * elem);
-  cap = std::max<size_t>(32, cap / 32 * 32);
-  size_t need = ((size_t)nsub + 31) / 32 * 32;
+  cap = std::max<size_t>(mult, cap / mult * mult);
+  size_t need = ((size_t)nsub + mult - 1) / mult * mult;
   return (int)std::min(cap, need);
 }
 
@@ -670,6 +789,49 @@ Ctx* ctx() {
   Ctx*& c = g_ph[dev];
   if (!c) { c = new Ctx(); c->dev = dev; }
   return c;
+}
+
+// psi and psi_minus level by level, phi, back-substitution for one chunk of
+// subsets (J subsets per lane)
+template <typename R, int J>
+int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStream_t s) {
+  const double nv = std::min(P, nsub - p0), es = sizeof(R);
+  R* psi = (R*)c->psi;
+  R* psim = (R*)c->psim;
+  R* phi = (R*)c->phi;
+  const R* tl = (const R*)c->tl;
+  const R* vl = (const R*)c->vl;
+  unsigned gy = (unsigned)(P / (32 * J));
+  for (size_t lv = 1; lv + 1 < T->lvl_ptr.size(); ++lv) {
+    int s0 = T->lvl_ptr[lv], s1 = T->lvl_ptr[lv + 1];
+    if (s1 <= s0) continue;
+    k_psi<R, J><<<dim3((unsigned)((s1 - s0 + 7) / 8), gy), 256, 0, s>>>(P, s0, s1, nullptr, T->ent_ptr, T->ent,
+                                                                         tl, R(1), psi);
+    c->n_launches++;
+    g_prof.done("ph::k_psi (exp(T)|ref> level)", s, T->lvl_ent[lv] * (8.0 + 2 * es * nv) + (s1 - s0) * es * nv,
+                2.0 * T->lvl_ent[lv] * nv);
+  }
+  for (size_t lv = 1; lv + 1 < T->olvl_ptr.size(); ++lv) {
+    int s0 = T->olvl_ptr[lv], s1 = T->olvl_ptr[lv + 1];
+    if (s1 <= s0) continue;
+    k_psi<R, J><<<dim3((unsigned)((s1 - s0 + 7) / 8), gy), 256, 0, s>>>(P, s0, s1, T->olvl_order, T->oent_ptr,
+                                                                         T->oent, tl, R(-1), psim);
+    c->n_launches++;
+    g_prof.done("ph::k_psi (exp(-T)|ref> on outputs)", s,
+                T->olvl_ent[lv] * (8.0 + 2 * es * nv) + (s1 - s0) * es * nv, 2.0 * T->olvl_ent[lv] * nv);
+  }
+  dim3 go((unsigned)((T->nout + 7) / 8), gy);
+  k_phi<R, J><<<go, 256, 0, s>>>(P, T->nout, T->h_ptr, T->hent, T->d_ptr, T->d_key, T->d_c, T->ne0, T->e0_key,
+                                 T->e0_cd, vl, psi, T->out_state, phi);
+  g_prof.done("ph::k_phi (<kappa|H|psi>)", s,
+              T->nh * 8.0 + (T->nh + T->nruns + T->nd) * es * nv + T->nout * 2 * es * nv,
+              2.0 * (T->nh + T->nruns + T->nd) * nv);
+  k_backsub<R, J><<<go, 256, 0, s>>>(P, p0, nsub, T->nout, T->b_ptr, T->b_k, T->b_w, psim, phi, c->Rloc[k],
+                                     c->Eloc[k]);
+  c->n_launches += 2;
+  g_prof.done("ph::k_backsub", s, T->nb * (8.0 + 2 * es * nv) + T->nout * 8.0 * nv, 2.0 * T->nb * nv);
+  CK(cudaGetLastError());
+  return 0;
 }
 
 // one residual evaluation: r (unique slots assembled, copies filled) and
@@ -688,7 +850,8 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
     DevTables* T;
     if ((rc = dev_tables(c, k, K, KH, &T))) return rc;
     int nsub = c->nsub[k];
-    int P = chunk_size(nsub, T->nstate, sizeof(R));
+    int J = nsub >= 384 ? 4 : nsub >= 96 ? 2 : 1;
+    int P = chunk_size(nsub, T->nstate, sizeof(R), 32 * J);
     if ((rc = grow_buf(&c->psi, &c->cap_psi, (size_t)T->nstate * P * sizeof(R)))) return rc;
     if ((rc = grow_buf(&c->psim, &c->cap_out, (size_t)T->nout * P * sizeof(R)))) return rc;
     if ((rc = grow_buf(&c->phi, &c->cap_phi, (size_t)T->nout * P * sizeof(R)))) return rc;
@@ -706,32 +869,16 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
       k_gather_amp<R><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc,
                                                                    c->subs[k], N, t, tl);
       k_gather_int<R><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
-                                                                   c->subs[k], N, c->G1, c->G2, c->G3, vl);
+                                                                   c->subs[k], N, c->G1, c->G2, c->G3, c->G4, vl);
       k_set_ref<R><<<(P + 127) / 128, 128, 0, s>>>(P, psi, psim);
       c->n_launches += 3;
-      for (size_t lv = 1; lv + 1 < T->lvl_ptr.size(); ++lv) {
-        int s0 = T->lvl_ptr[lv], s1 = T->lvl_ptr[lv + 1];
-        if (s1 <= s0) continue;
-        dim3 g((unsigned)((s1 - s0 + 7) / 8), (unsigned)(P / 32));
-        k_psi<R><<<g, 256, 0, s>>>(P, s0, s1, nullptr, T->ent_ptr, T->ent_sub, T->ent_slot, tl, R(1), psi);
-        c->n_launches++;
-      }
-      for (size_t lv = 1; lv + 1 < T->olvl_ptr.size(); ++lv) {
-        int s0 = T->olvl_ptr[lv], s1 = T->olvl_ptr[lv + 1];
-        if (s1 <= s0) continue;
-        dim3 g((unsigned)((s1 - s0 + 7) / 8), (unsigned)(P / 32));
-        k_psi<R><<<g, 256, 0, s>>>(P, s0, s1, T->olvl_order, T->oent_ptr, T->oent_sub, T->oent_slot, tl, R(-1),
-                                   psim);
-        c->n_launches++;
-      }
-      dim3 go((unsigned)((T->nout + 7) / 8), (unsigned)(P / 32));
-      k_phi<R><<<go, 256, 0, s>>>(P, T->nout, T->h_ptr, T->h_s, T->h_key,
-                                  f32 ? (const R*)T->h_cf : (const R*)T->h_cd, T->d_ptr, T->d_key, T->d_c,
-                                  T->ne0, T->e0_key, T->e0_cd, vl, psi, T->out_state, phi);
-      k_backsub<R><<<go, 256, 0, s>>>(P, p0, nsub, T->nout, T->b_ptr, T->b_k, T->b_w, psim, phi, c->Rloc[k],
-                                      c->Eloc[k]);
-      c->n_launches += 2;
+      g_prof.done("ph::gather (amplitudes, integrals)", s, (double)(T->nslot + T->nkey) * P * (sizeof(R) + 8.0));
+      if (J == 4) rc = local_problem<R, 4>(c, T, P, p0, nsub, k, s);
+      else if (J == 2) rc = local_problem<R, 2>(c, T, P, p0, nsub, k, s);
+      else rc = local_problem<R, 1>(c, T, P, p0, nsub, k, s);
+      if (rc) return rc;
     }
+    A.nout[k] = T->nout;
     A.Rloc[k] = c->Rloc[k]; A.nsub[k] = nsub; A.c[k] = ck;
     AE.Rloc[k] = c->Eloc[k]; AE.nsub[k] = nsub; AE.c[k] = ce;
   }
@@ -742,10 +889,15 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
     size_t nt = (size_t)c->nsub[m] * nch[m];
     k_assemble<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(N, m, nch[m], c->subs[m], c->nsub[m], A, r);
     c->n_launches++;
+    double terms = 0.0;
+    for (int k = m; k <= kmax; ++k)
+      if (A.c[k] != 0.0) terms += binom(N - m, k - m);
+    g_prof.done("ph::k_assemble", s, (double)nt * (terms + 1) * 8.0, 2.0 * nt * terms);
   }
   k_energy<<<1, 256, 0, s>>>(AE, e_dev);
   k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, K, r);
   c->n_launches += 2;
+  g_prof.done("ph::k_energy, k_fill_copies", s, 16.0 * L);
   CK(cudaGetLastError());
   return 0;
 }
@@ -765,12 +917,19 @@ int stage_ph(Ctx* c, Workspace* w, const Problem& P, int KH, cudaStream_t s) {
     CK(cudaMalloc((void**)&c->G3, sizeof(double) * N * N * N * kNK3));
     c->gN = N;
   }
-  // K_H = 3 keeps every (pq|ii), so the bare one-body part is h itself; for
+  // K_H >= 3 keeps every (pq|ii), so the bare one-body part is h itself; for
   // K_H = 2 it is h' = f - sum_i [2 v'(pq|ii) - v'(pi|iq)] (staged by the PQ path)
+  if (KH >= 4 && N >= 4 && c->g4N != N) {
+    if (c->G4) cudaFree(c->G4);
+    c->G4 = nullptr;
+    CK(cudaMalloc((void**)&c->G4, sizeof(double) * c->nsub[4] * kNK4));
+    c->g4N = N;
+  }
   const double* hb = KH >= 3 ? P.h : w->hp;
-  size_t tot = (size_t)N * 20 + (size_t)N * N * 232 + (KH >= 3 ? (size_t)N * N * N * kNK3 : 0);
-  k_stage_g<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, KH, hb, P.eri, w->occ, w->vir, c->G1, c->G2,
-                                                          c->G3);
+  size_t nq = KH >= 4 && N >= 4 ? (size_t)c->nsub[4] : 0;
+  size_t tot = (size_t)N * 20 + (size_t)N * N * 232 + (KH >= 3 ? (size_t)N * N * N * kNK3 : 0) + nq * kNK4;
+  k_stage_g<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, KH, hb, P.eri, w->occ, w->vir, c->subs[4], (int)nq,
+                                                          c->G1, c->G2, c->G3, c->G4);
   CK(cudaGetLastError());
   return 0;
 }
@@ -805,35 +964,46 @@ int residual_any(Ctx* c, int N, int K, int KH, int prec, const double* t, double
 
 }  // namespace ph
 
+namespace ph {
+
+// one residual evaluation through the C ABI: stage, copy t (sorted-label
+// entries; copies filled), evaluate, copy r and E_c out
+int residual_entry(int K, int KH, int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                   const double* eri, const double* t, double* r, double* e_corr, int precision, cudaStream_t s) {
+  if (precision != 0 && precision != 1) return fail(-4, "precision must be 0 or 1");
+  if (!t || !r) return fail(-2, "t and r must be non-null");
+  if (n_pairs > 127) return fail(-1, "n_pairs must be <= 127 for the label-subset residual");
+  Workspace* w = nullptr;
+  Problem P;
+  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
+  if (rc) return rc;
+  Ctx* c = ctx();
+  if ((rc = stage_ph(c, w, P, KH, s))) return rc;
+  int N = n_pairs;
+  size_t L = layout_len(N, K);
+  if ((rc = grow_solver(c, L, 1))) return rc;
+  CK(cudaMemcpyAsync(c->t, t, sizeof(double) * L, cudaMemcpyDefault, s));
+  k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, K, c->t);
+  if ((rc = residual_any(c, N, K, KH, precision, c->t, c->r, c->e, s))) return rc;
+  CK(cudaMemcpyAsync(r, c->r, sizeof(double) * L, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(c->host, c->e, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e_corr) *e_corr = c->host[0];
+  return 0;
+}
+
+}  // namespace ph
+
 extern "C" {
 
 int ph_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h, const double* eri,
                 const double* t, double* r, double* e_corr, int precision, int K_H, void* stream) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_err.clear();
-  cudaStream_t s = (cudaStream_t)stream;
   int KH = K_H == 0 ? 3 : K_H;
   if (KH != 2 && KH != 3) return fail(-4, "ph_residual: K_H must be 0, 2 or 3");
-  if (precision != 0 && precision != 1) return fail(-4, "precision must be 0 or 1");
-  if (!t || !r) return fail(-2, "t and r must be non-null");
-  if (n_pairs > 127) return fail(-1, "ph_residual: n_pairs must be <= 127");
-  Workspace* w = nullptr;
-  Problem P;
-  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
-  if (rc) return rc;
-  ph::Ctx* c = ph::ctx();
-  if ((rc = ph::stage_ph(c, w, P, KH, s))) return rc;
-  int N = n_pairs;
-  size_t L = ph::layout_len(N, 3);
-  if ((rc = ph::grow_solver(c, L, 1))) return rc;
-  CK(cudaMemcpyAsync(c->t, t, sizeof(double) * L, cudaMemcpyDefault, s));
-  ph::k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, 3, c->t);
-  if ((rc = ph::residual_any(c, N, 3, KH, precision, c->t, c->r, c->e, s))) return rc;
-  CK(cudaMemcpyAsync(r, c->r, sizeof(double) * L, cudaMemcpyDefault, s));
-  CK(cudaMemcpyAsync(c->host, c->e, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (e_corr) *e_corr = c->host[0];
-  return 0;
+  return ph::residual_entry(3, KH, n_pairs, occ_of_pair, vir_of_pair, h, eri, t, r, e_corr, precision,
+                            (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -851,7 +1021,7 @@ double residual_flops(int N, int K, int KH) {
     int rc;
     const Tables* T = host_tables(k, K, KH, &rc);
     if (!T) return 0.0;
-    double per = 2.0 * ((double)T->ent_sub.size() + (double)T->oent_sub.size() + 1.5 * (double)T->h_s.size() +
+    double per = 2.0 * ((double)T->ent_sub.size() + (double)T->oent_sub.size() + (double)T->h_s.size() +
                         (double)T->d_key.size() + (double)T->b_k.size());
     f += per * binom(N, k);
   }
@@ -860,7 +1030,7 @@ double residual_flops(int N, int K, int KH) {
 
 struct PhSolver {
   Ctx* c;
-  int N, KH;
+  int N, K, KH;
   size_t L;
   ppq_opts o;
   cudaStream_t s;
@@ -870,8 +1040,8 @@ struct PhSolver {
   double t_res_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<int> ring;  // slot ids, oldest first
-  PhSolver(Ctx* c_, Workspace* w_, int N_, int KH_, const ppq_opts& o_, cudaStream_t s_)
-      : c(c_), N(N_), KH(KH_), L(layout_len(N_, 3)), o(o_), s(s_), w(w_), lb((unsigned)((L + 255) / 256)) {}
+  PhSolver(Ctx* c_, Workspace* w_, int N_, int K_, int KH_, const ppq_opts& o_, cudaStream_t s_)
+      : c(c_), N(N_), K(K_), KH(KH_), L(layout_len(N_, K_)), o(o_), s(s_), w(w_), lb((unsigned)((L + 255) / 256)) {}
   ~PhSolver() {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -883,12 +1053,13 @@ struct PhSolver {
   }
   int eval(int prec, double* res, double* e) {
     CK(cudaEventRecord(ev0, s));
-    int rc = residual_any(c, N, 3, KH, prec, c->t, c->r, c->e, s);
+    int rc = residual_any(c, N, K, KH, prec, c->t, c->r, c->e, s);
     if (rc) return rc;
     CK(cudaEventRecord(ev1, s));
     k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, c->r, 0, c->slot_e, L, c->order, 0, c->part);
     k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1, c->part, c->e, c->rows);
     CK(cudaMemcpyAsync(c->host, c->rows, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
     CK(cudaStreamSynchronize(s));
     c->n_launches += 2;
     float ms = 0.f;
@@ -924,8 +1095,9 @@ struct PhSolver {
     int extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
     k_diis_solve<<<1, 32, 0, s>>>(m, c->order, slot, c->rows, c->B, kDiisMax, extrap, c->coef);
     k_extrap<<<lb, 256, 0, s>>>(L, m, c->coef, c->slot_t, L, c->order, c->t);
-    k_fill_copies<<<lb, 256, 0, s>>>(L, N, 3, c->t);
+    k_fill_copies<<<lb, 256, 0, s>>>(L, N, K, c->t);
     c->n_launches += 6;
+    g_prof.done("solver: Jacobi, DIIS (device solve), extrapolation", s, 8.0 * L * (4 + 2 * m));
     CK(cudaGetLastError());
     return 0;
   }
@@ -933,24 +1105,21 @@ struct PhSolver {
 
 }  // namespace ph
 
-extern "C" {
+namespace {
 
-int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
-             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
-             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  g_err.clear();
-  auto wall0 = std::chrono::steady_clock::now();
-  cudaStream_t s = (cudaStream_t)stream;
-  ppq_opts o;
-  if (opts) o = *opts; else ppq_default_opts(&o);
-  int KH = o.K_H == 0 ? 3 : o.K_H;
-  if (KH != 2 && KH != 3) return fail(-4, "ph_solve: K_H must be 0 (= 3), 2 or 3");
+// The K-pair model (K = 2 or 3) with integrals over at most KH labels (4 =
+// untruncated) solved through the label-subset residual: Jacobi steps with
+// orbital-energy denominators and device-side Pulay DIIS; the mixed form runs
+// FP32 residuals until switch_tol (or FP32 stagnation), then FP64.
+int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                 const double* eri, double e_const, const ppq_opts& o, const double* t_in, double* t_out,
+                 double* e_corr, double* e_total, ppq_info* info, cudaStream_t s,
+                 std::chrono::steady_clock::time_point wall0) {
   if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
   if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
-  if (n_pairs > 127) return fail(-1, "ph_solve: n_pairs must be <= 127");
+  if (n_pairs > 127) return fail(-1, "n_pairs must be <= 127 for the label-subset solver");
   Workspace* w = nullptr;
   Problem P;
   int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
@@ -960,20 +1129,23 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   }
   ph::Ctx* c = ph::ctx();
   c->n_launches = 0;
+  g_prof.reset(o.profile != 0);
+  g_prof.start(s);
   if ((rc = ph::stage_ph(c, w, P, KH, s))) return rc;
+  g_prof.done("staging (Fock, gathers)", s);
   int N = n_pairs, n = 2 * N;
-  size_t L = ph::layout_len(N, 3);
+  size_t L = ph::layout_len(N, K);
   int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
   if ((rc = ph::grow_solver(c, L, m_max))) return rc;
   if (o.guess == 1) {
     CK(cudaMemcpyAsync(c->t, t_in, sizeof(double) * L, cudaMemcpyDefault, s));
-    ph::k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, 3, c->t);
+    ph::k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, K, c->t);
   } else {
     CK(cudaMemsetAsync(c->t, 0, sizeof(double) * L, s));
   }
   k_eref<<<1, 1, 0, s>>>(N, n, P.h, w->f, w->occ, c->e + 1);
   CK(cudaMemcpyAsync(c->host + 40, c->e + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-  ph::PhSolver S(c, w, N, KH, o, s);
+  ph::PhSolver S(c, w, N, K, KH, o, s);
   if ((rc = S.init())) return rc;
   int prec = o.precision;
   int switched_at = prec ? -1 : 0;
@@ -987,13 +1159,15 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
     if (prec == 0 && have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
     if (prec == 1) {
+      // switch at switch_tol, or when FP32 stops gaining (< 10 % over three
+      // steps below 1e-4: the FP32 noise floor); the DIIS history is kept, its
+      // vectors are valid FP64 iterates
       size_t k = hist.size();
-      bool stagnant = k >= 4 && res < 1e-3 && hist[k - 1] > 0.9 * hist[k - 4];
+      bool stagnant = k >= 4 && res < 1e-4 && hist[k - 1] > 0.9 * hist[k - 4];
       if (res <= o.switch_tol || stagnant) {
         prec = 0;
         switched_at = it;
         have_old = false;
-        S.ring.clear();
         continue;  // re-evaluate at the same amplitudes in FP64
       }
     }
@@ -1018,12 +1192,44 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     info->e_total = e + e_ref + e_const;
     info->t_residual_ms = S.t_res_ms;
     info->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
-    info->residual_flops = ph::residual_flops(N, 3, KH);
+    info->residual_flops = ph::residual_flops(N, K, KH);
     info->n_launches = c->n_launches + 10;
     info->evals_fp32 = S.evals32;
     info->evals_fp64 = S.evals - S.evals32;
   }
   return status;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+             const double* eri, double e_const, const ppq_opts* opts, const double* t_in,
+             double* t_out, double* e_corr, double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int KH = o.K_H == 0 ? 3 : o.K_H;
+  if (KH != 2 && KH != 3) return fail(-4, "ph_solve: K_H must be 0 (= 3), 2 or 3");
+  return subset_solve(3, KH, n_pairs, occ_of_pair, vir_of_pair, h, eri, e_const, o, t_in, t_out, e_corr, e_total,
+                      info, (cudaStream_t)stream, wall0);
+}
+
+int ppq_subset_residual(int K, int K_H, int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                        const double* h, const double* eri, const double* t, double* r, double* e_corr,
+                        int precision, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  int KH = K_H == 0 ? K : (K_H < 0 ? 4 : K_H);
+  if (K != 2 && K != 3) return fail(-4, "ppq_subset_residual: K must be 2 or 3");
+  if (KH < 2 || KH > 4 || K + KH > ph::kMaxSites)
+    return fail(-4, "ppq_subset_residual: K_H must be 0, 2, 3 or -1 (untruncated, K = 2 only)");
+  return ph::residual_entry(K, KH, n_pairs, occ_of_pair, vir_of_pair, h, eri, t, r, e_corr, precision,
+                            (cudaStream_t)stream);
 }
 
 }  // extern "C"

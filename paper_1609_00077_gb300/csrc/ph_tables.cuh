@@ -14,8 +14,9 @@
 // Amplitude channels (Eq. decompose, Tables I-II): A1 (3 single-site
 // monomials), A2 (29 two-site pairs), A3 (303 three-site triples) of nonzero
 // monomials with zero total charge and S_z, in the order of the C-ABI layout.
-// Integral keys: 20 per site, 232 per two sites, 576 per three sites, the
-// (pq|rs) and one-body elements whose orbitals span exactly those sites.
+// Integral keys: 20 per site, 232 per two sites, 576 per three sites and 384
+// per four (untruncated integrals, K_H = 4 here), the (pq|rs) and one-body
+// elements whose orbitals span exactly those sites.
 //
 // For k sites the generator produces, once per (k, K, K_H):
 //   * the sector states, sorted by level (number of hole-particle pairs);
@@ -125,7 +126,7 @@ struct Algebra {
   std::vector<int> A1;
   std::vector<std::array<int, 2>> A2;
   std::vector<std::array<int, 3>> A3;
-  std::vector<std::array<int, 5>> key[4];  // (0 = one-body h', 1 = (pq|rs); local orbitals)
+  std::vector<std::array<int, 5>> key[5];  // (0 = one-body h', 1 = (pq|rs); local orbitals)
   Algebra() {
     for (int m = 0; m < 16; ++m) {
       qc[m] = popc(m & 12) - popc(m & 3);
@@ -164,6 +165,14 @@ struct Algebra {
             int sites = (1 << (p / 2)) | (1 << (q / 2)) | (1 << (r / 2)) | (1 << (s / 2));
             if (popc(sites) == 3) key[3].push_back({1, p, q, r, s});
           }
+    // four labels (untruncated integrals): every orbital on a different site
+    for (int p = 0; p < 8; ++p)
+      for (int q = 0; q < 8; ++q)
+        for (int r = 0; r < 8; ++r)
+          for (int s = 0; s < 8; ++s) {
+            int sites = (1 << (p / 2)) | (1 << (q / 2)) | (1 << (r / 2)) | (1 << (s / 2));
+            if (popc(sites) == 4) key[4].push_back({1, p, q, r, s});
+          }
   }
   int nch(int m) const { return m == 1 ? (int)A1.size() : m == 2 ? (int)A2.size() : (int)A3.size(); }
   int nkey(int m) const { return (int)key[m].size(); }
@@ -176,25 +185,27 @@ inline const Algebra& algebra() {
   return a;
 }
 
-// packed descriptor of (sorted positions, index): npos | p0 << 4 | p1 << 8 | p2 << 12 | idx << 16
+// packed descriptor of (sorted positions, index):
+// npos | p0 << 4 | p1 << 8 | p2 << 12 | p3 << 16 | idx << 20
+constexpr int kDescIdx = 20;
 inline int pack_desc(int m, const int* p, int idx) {
   int d = m;
   for (int i = 0; i < m; ++i) d |= p[i] << (4 + 4 * i);
-  return d | (idx << 16);
+  return d | (idx << kDescIdx);
 }
 
-// position sets of size m among k sites, in colex order
-inline std::vector<std::array<int, 3>> position_sets(int k, int m) {
-  std::vector<std::array<int, 3>> out(binom(k, m));
-  for (int a = 0; a < k; ++a) {
-    if (m == 1) { std::array<int, 3> p{a, 0, 0}; out[colex_rank(p.data(), 1)] = p; continue; }
-    for (int b = a + 1; b < k; ++b) {
-      if (m == 2) { std::array<int, 3> p{a, b, 0}; out[colex_rank(p.data(), 2)] = p; continue; }
-      for (int c = b + 1; c < k; ++c) {
-        std::array<int, 3> p{a, b, c};
-        out[colex_rank(p.data(), 3)] = p;
-      }
-    }
+// position sets of size m (1..4) among k sites, in colex order
+inline std::vector<std::array<int, 4>> position_sets(int k, int m) {
+  std::vector<std::array<int, 4>> out(binom(k, m));
+  std::array<int, 4> p{0, 0, 0, 0};
+  for (int i = 0; i < m; ++i) p[i] = i;
+  for (;;) {
+    out[colex_rank(p.data(), m)] = p;
+    int x = m - 1;
+    while (x >= 0 && p[x] == k - m + x) --x;
+    if (x < 0) break;
+    ++p[x];
+    for (int y = x + 1; y < m; ++y) p[y] = p[y - 1] + 1;
   }
   return out;
 }
@@ -231,7 +242,7 @@ struct Tables {
 
 inline int build_tables(int k, int K, int KH, Tables* T, int nthreads = 0) {
   const Algebra& A = algebra();
-  if (k < 1 || k > kMaxSites || K < 1 || K > 3 || KH < 1 || KH > 3) return -1;
+  if (k < 1 || k > kMaxSites || K < 1 || K > 3 || KH < 1 || KH > 4) return -1;
   T->k = k; T->K = K; T->KH = KH;
   // ---- sector states sorted by level then code
   const uint32_t ncode = 1u << (4 * k);
@@ -456,10 +467,10 @@ inline int build_tables(int k, int K, int KH, Tables* T, int nthreads = 0) {
 // cache of host tables per (k, K, K_H)
 inline const Tables* host_tables(int k, int K, int KH, int* rc) {
   static std::mutex mu;
-  static std::unique_ptr<Tables> cache[kMaxSites + 1][4][4];
+  static std::unique_ptr<Tables> cache[kMaxSites + 1][4][5];
   std::lock_guard<std::mutex> lk(mu);
   *rc = 0;
-  if (k < 1 || k > kMaxSites || K < 1 || K > 3 || KH < 1 || KH > 3) {
+  if (k < 1 || k > kMaxSites || K < 1 || K > 3 || KH < 1 || KH > 4) {
     *rc = -1;
     return nullptr;
   }

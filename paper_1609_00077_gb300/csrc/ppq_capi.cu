@@ -61,6 +61,75 @@ bool trace_on() {
 }
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
+// Per-kernel device time of one profiled call (opts.profile = 1): events are
+// recorded on the launching stream after every kernel, and each kernel is
+// charged the time since the previous event, so the classes add up to the
+// stream time of the call (gaps between launches included).  Algorithmic
+// bytes and FLOPs are summed per class beside the time.
+struct KProf {
+  bool on = false;
+  struct Cls {
+    std::string name;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+    int n = 0;
+  };
+  struct Mark {
+    cudaEvent_t ev;
+    int cls;
+    double bytes, flops;
+  };
+  std::vector<Cls> cls;
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+  }
+  int id(const char* name) {
+    for (size_t i = 0; i < cls.size(); ++i)
+      if (cls[i].name == name) return (int)i;
+    cls.push_back(Cls());
+    cls.back().name = name;
+    return (int)cls.size() - 1;
+  }
+  void reset(bool enable) {
+    flush();
+    on = enable;
+    cls.clear();
+  }
+  // start of a timed region on stream s
+  void start(cudaStream_t s) {
+    if (!on) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.push_back({e, -1, 0.0, 0.0});
+  }
+  // after a kernel of class `name` (charged the time since the previous mark)
+  void done(const char* name, cudaStream_t s, double bytes = 0.0, double flops = 0.0) {
+    if (!on) return;
+    if (marks.empty()) start(s);
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.push_back({e, id(name), bytes, flops});
+  }
+  // accumulate the recorded segments (waits for the stream's events)
+  void flush() {
+    for (size_t i = 1; i < marks.size(); ++i) {
+      if (marks[i].cls < 0) continue;
+      cudaEventSynchronize(marks[i].ev);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, marks[i - 1].ev, marks[i].ev);
+      Cls& c = cls[marks[i].cls];
+      c.ms += ms; c.n++; c.bytes += marks[i].bytes; c.flops += marks[i].flops;
+    }
+    for (auto& m : marks) pool.push_back(m.ev);
+    marks.clear();
+  }
+};
+KProf g_prof;
+
 // Per-device workspace, grown on demand and kept between calls.
 struct Workspace {
   int N = 0;       // capacity in pairs
@@ -646,9 +715,12 @@ int tuned_mt(Workspace* w, int N, cudaStream_t s, int* mt_out) {
   return 0;
 }
 
+double quartic_flops(int N);
+
 // one residual evaluation at w->t into w->r; energy pieces into esite/epair
 template <typename R>
 int residual(Workspace* w, int N, cudaStream_t s) {
+#define PN(x) (std::is_same<R, float>::value ? x " (FP32)" : x " (FP64)")
   int rc = 0;
   const R* g1 = std::is_same<R, double>::value ? (const R*)w->g1d : (const R*)w->g1f;
   const R* g2 = std::is_same<R, double>::value ? (const R*)w->g2d : (const R*)w->g2f;
@@ -661,52 +733,69 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   R* pc0 = (R*)w->pc0;
   int NN = N * N;
   ppq::k_links<R><<<(NN + 63) / 64, 64, 0, s>>>(N, t2, cl);
+  g_prof.done(PN("ppq::k_links"), s, 0.0, 2.0 * NN * PPQ_NSOP);
   ppq::k_site_closure<R><<<N, 64, 0, s>>>(N, g1, t1, hs, w->esite);
+  g_prof.done(PN("ppq::k_site_closure"), s);
   if ((rc = launch_pair_closure<R>(N, g2, t1, t2, pg, pt7, pc0, w->epair, (R*)w->pt7T, s))) return rc;
+  g_prof.done(PN("ppq::k_pair_closure_p"), s, 0.0, 2.0 * (NN - N) * (17792.0 + PPQ_PR_N + PPQ_PL_N));
   ppq::k_r1<R><<<dim3(N, kR1Split), 256, 0, s>>>(N, hs, pc0, cl, pg, w->r1part);
   ppq::k_r1_reduce<R><<<(3 * N + 127) / 128, 128, 0, s>>>(N, kR1Split, hs, w->r1part, w->r);
+  g_prof.done(PN("ppq::k_r1, k_r1_reduce"), s, 0.0, 2.0 * N * ((N - 1) * PPQ_NT3 + (double)(N - 1) * (N - 2) * PPQ_NT8));
   size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl_ld(N), cl, (R*)w->clT);
+  g_prof.done(PN("ppq::k_transpose_cl"), s);
   {
     // T7 as GEMMs over W
     int mt = std::max(1, (N + 15) / 16);
     if ((rc = launch_t7_gemm<R>(w, N, mt, s))) return rc;
   }
+  g_prof.done(PN("ppq::k_t7_gemm"), s, 0.0, 2.0 * PPQ_NK7 * (double)N * N * N);
   ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, (const R*)w->m7, pg, cl, t2, w->dir, w->abuf);
+  g_prof.done(PN("ppq::k_r2"), s, 0.0, 2.0 * ((NN - N) / 2.0 * (N - 2) * PPQ_NT4 + (NN - N) * (double)(PPQ_NT2 + PPQ_NT7 + PPQ_NSOP)));
   // quartic term
   if (std::is_same<R, float>::value && w->tc_N == N) {
     // tensor cores: split B operands, then the fused MMA + W-contraction kernel
     size_t nb = (size_t)PPQ_NS36 * w->tc_Kc * w->tc_Npad * 8;
     ppq::tc::k_t9_bprep<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(N, w->tc_Npad, w->tc_Kc, (const float*)pg,
                                                                        w->bpre);
+    g_prof.done(PN("tc::k_t9_bprep"), s);
     if (w->profile) CK(cudaEventRecord(w->evq0, s));
     if ((rc = launch_t9_tc(w, N, s))) return rc;
     if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    g_prof.done("tc::k_t9_tc (FP32 quartic, 3xTF32 tcgen05)", s, 0.0, quartic_flops(N));
     ppq::k_t9_reduce<float><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc_nslot, w->tc_part,
                                                                                    w->t9);
+    g_prof.done(PN("ppq::k_t9_reduce"), s);
   } else if (std::is_same<R, double>::value && w->tc64_N == N) {
     // tensor cores, exact splitting: split B operands, then the MMA + W-contraction kernel
     ppq::tc::k_t9_bprep64<<<PPQ_NS36, 128, 0, s>>>(
         N, w->tc64_Npad, w->tc64_Kc, (const double*)pg, w->bpre64, w->fexp64);
+    g_prof.done(PN("tc::k_t9_bprep64"), s);
     if (w->profile) CK(cudaEventRecord(w->evq0, s));
     if ((rc = launch_t9_tc64(w, N, s))) return rc;
     if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    g_prof.done("tc::k_t9_tc64 (FP64 quartic, exact splitting on tcgen05)", s, 0.0, quartic_flops(N));
     ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc64_nslot,
                                                                                     w->tc64_part, w->t9);
+    g_prof.done(PN("ppq::k_t9_reduce"), s);
   } else {
     // SIMT: transposed operands, GEMM, W-contraction
     ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
+    g_prof.done(PN("ppq::k_transpose_g"), s);
     if (w->profile) CK(cudaEventRecord(w->evq0, s));
     if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
     if (w->profile) CK(cudaEventRecord(w->evq1, s));
+    g_prof.done("ppq::k_t9_gemm (quartic, SIMT)", s, 0.0, quartic_flops(N));
     ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->n_work9, w->t9part,
                                                                                     w->t9);
   }
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
+  g_prof.done(PN("ppq::k_t9_reduce, k_assemble"), s);
   CK(cudaGetLastError());
   w->n_launches += 12;
   return 0;
+#undef PN
 }
 
 // One residual evaluation.  On a non-default stream the pipeline is captured
@@ -723,7 +812,7 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
   } else {
     if ((rc = tuned_mt<double>(w, N, s, &w->mt[0]))) return rc;
   }
-  if (s == 0) return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
+  if (s == 0 || g_prof.on) return precision ? residual<float>(w, N, s) : residual<double>(w, N, s);
   if (!w->graph[p] || w->graph_N[p] != N || w->graph_profile[p] != (int)w->profile) {
     if (w->graph[p]) { cudaGraphExecDestroy(w->graph[p]); w->graph[p] = nullptr; }
     cudaGraph_t g;
@@ -1045,6 +1134,7 @@ struct Solver {
     k_multidot<<<g, 256, 0, s>>>(L, N, w->r, 0, w->slot_e, L, w->order, 0, w->part);
     k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
     CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
     CK(cudaStreamSynchronize(s));
     w->n_launches += 2;
     account();
@@ -1111,6 +1201,7 @@ struct Solver {
     CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
     ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, x);
     w->n_launches += 4;
+    g_prof.done("solver: Jacobi, DIIS, extrapolation", s, 8.0 * L * (4 + 2 * m));
     CK(cudaGetLastError());
     return 0;
   }
@@ -1130,6 +1221,7 @@ struct Solver {
     if (rc) return rc;
     k_rowsum<<<1, 256, 0, s>>>(0, 0, w->part, N, w->esite, w->epair, w->scal);
     CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    g_prof.done("solver: energy of one more Jacobi step (closures, FP64)", s);
     CK(cudaStreamSynchronize(s));
     w->n_launches += 4;
     *e_next = w->host[0];
@@ -1197,6 +1289,7 @@ struct Solver {
       if ((rc = eval(1, &rn, &ed))) return rc;
       k_fd_rho<<<lb, 256, 0, s>>>(L, r64, w->r, rb, w->amax, eta, rho);
       w->n_launches += 3;
+      g_prof.done("solver: defect-correction vectors", s, 8.0 * L * 6);
       (*it_io)++;
       // weighted norm of rho
       dim3 g(kRedBlocks, 1);
@@ -1265,6 +1358,28 @@ int ppq_release(void) {
 
 const char* ppq_last_error(void) { return g_err.c_str(); }
 
+int ppq_profile_count(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof.flush();
+  return (int)g_prof.cls.size();
+}
+
+int ppq_profile_entry(int i, char* name, int name_cap, double* ms, int* launches, double* bytes, double* flops) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof.flush();
+  if (i < 0 || i >= (int)g_prof.cls.size()) return fail(-2, "ppq_profile_entry: index %d out of range", i);
+  const KProf::Cls& c = g_prof.cls[i];
+  if (name && name_cap > 0) {
+    strncpy(name, c.name.c_str(), name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (ms) *ms = c.ms;
+  if (launches) *launches = c.n;
+  if (bytes) *bytes = c.bytes;
+  if (flops) *flops = c.flops;
+  return 0;
+}
+
 int ppq_tc_plan(int n_pairs, int16_t* chunks, int max_chunks, int* ctas, int max_ctas, int* n_chunks,
                 int* n_ctas) {
   TcPlan pl;
@@ -1312,9 +1427,12 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
 
 namespace {
 
-int validate_opts(const ppq_opts& o) {
+int validate_opts(const ppq_opts& o, bool allow_full = false) {
   if (o.K != 2) return fail(-4, "pq_solve: K must be 2 (PQ)");
-  if (o.K_H != 0 && o.K_H != 2) return fail(-4, "pq_solve: only the two-label integral truncation (K_H = 2) is built");
+  if (o.K_H == -1 && !allow_full)
+    return fail(-4, "K_H = -1 (untruncated integrals) is solved by pq_solve only");
+  if (o.K_H != 0 && o.K_H != 2 && o.K_H != -1)
+    return fail(-4, "pq_solve: K_H must be 0 or 2 (two-label integrals) or -1 (untruncated)");
   if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
   if (o.polish != 0 && o.polish != 1) return fail(-4, "polish must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
@@ -1327,6 +1445,11 @@ int diis_slots(const ppq_opts& o) {
   return (o.precision == 1 && o.polish == 1) ? kDiisMax : m_max;
 }
 
+int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                 const double* eri, double e_const, const ppq_opts& o, const double* t_in, double* t_out,
+                 double* e_corr, double* e_total, ppq_info* info, cudaStream_t s,
+                 std::chrono::steady_clock::time_point wall0);
+
 // The solve of one system on a prepared workspace and stream.
 int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o,
                const double* t_in, double* t_out, double* e_corr, double* e_total, ppq_info* info,
@@ -1337,6 +1460,8 @@ int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o
   int N = n_pairs, n = 2 * N;
   size_t L = amp_len(N);
   w->profile = o.profile != 0;
+  g_prof.reset(w->profile);
+  g_prof.start(s);
   w->t_quartic_ms = 0.0;
   w->n_quartic = 0;
   w->t_quartic32_ms = 0.0;
@@ -1460,8 +1585,13 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   cudaStream_t s = (cudaStream_t)stream;
   ppq_opts o;
   if (opts) o = *opts; else ppq_default_opts(&o);
-  int rc = validate_opts(o);
+  int rc = validate_opts(o, true);
   if (rc) return rc;
+  // untruncated integrals: terms reach K + 4 = 6 labels, evaluated by the
+  // label-subset expansion
+  if (o.K_H == -1)
+    return subset_solve(2, 4, n_pairs, occ_of_pair, vir_of_pair, h, eri, e_const, o, t_in, t_out, e_corr, e_total,
+                        info, s, wall0);
   if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
   Workspace* w = nullptr;
   Problem P;

@@ -167,6 +167,18 @@ def triple_integral_keys():
     return keys
 
 
+def quad_integral_keys():
+    """Four-label integrals, kept only when the two-electron part is not
+    truncated (the paper's integral truncation controlled separately from the
+    amplitudes, Implementation section): (pq|rs) over the 8 spatial orbitals
+    2 X + x of four sites whose orbitals touch all four; 8 * 6 * 4 * 2 = 384
+    of them per ordered quadruple."""
+    keys = [("v", p, q, r, s) for p in range(8) for q in range(8) for r in range(8)
+            for s in range(8) if len({p // 2, q // 2, r // 2, s // 2}) == 4]
+    assert len(keys) == 384
+    return keys
+
+
 def _spin_orbital(site, x, sigma):
     return 4 * site + 2 * x + sigma
 

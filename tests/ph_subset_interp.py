@@ -61,7 +61,7 @@ def tables(k, K, K_H):
 def unpack(d):
     m = d & 15
     pos = [(d >> (4 + 4 * i)) & 15 for i in range(m)]
-    return m, pos, d >> 16
+    return m, pos, d >> 20
 
 
 def moebius(N, k, kmax):
@@ -70,7 +70,7 @@ def moebius(N, k, kmax):
 
 class SubsetInterp:
     """Residual of the K-pair model (K = 2 or 3) with integrals truncated to
-    K_H labels, from the generated tables."""
+    K_H labels (K_H = 4: untruncated), from the generated tables."""
 
     def __init__(self, h, eri, occ, vir, K, K_H):
         self.occ = [int(i) for i in occ]
@@ -78,7 +78,8 @@ class SubsetInterp:
         self.N = N = len(self.occ)
         self.K, self.K_H = K, K_H
         hp, v, _ = bare_truncated_hamiltonian(h, eri, np.array(self.occ), np.array(self.vir), K_H)
-        self.keys = {1: T.site_integral_keys(), 2: T.pair_integral_keys(), 3: T.triple_integral_keys()}
+        self.keys = {1: T.site_integral_keys(), 2: T.pair_integral_keys(), 3: T.triple_integral_keys(),
+                     4: T.quad_integral_keys()}
         self.nch = {1: 3, 2: 29, 3: 303}
         self.hp, self.v = hp, v
 

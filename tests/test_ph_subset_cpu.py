@@ -17,6 +17,7 @@ What this pins, without a GPU:
     normal-ordered Hamiltonian instead of the bare one;
   * a control: ignoring the signs of the recursion breaks the agreement.
 """
+import os
 from math import comb
 
 import numpy as np
@@ -24,7 +25,7 @@ import pytest
 
 import paper_1609_00077_gb300 as ppq
 from workloads import build_ppp, build_hchain
-from oracle.detcc import Problem
+from oracle.detcc import Problem, enumerate_manifold
 from oracle.loccc import LocalAssembly
 from tests.layout import LayoutMap
 from tests.ph_subset_interp import SubsetInterp, tables
@@ -89,6 +90,57 @@ def test_inclusion_exclusion_against_local_assembly(K, K_H, sites):
     R2, e2 = _interp(H, K, K_H, t, lm)
     assert np.abs(R2 - R).max() < 1e-12
     assert abs(e2 - e) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["C8H10", "H8"])
+def test_untruncated_integrals_two_pair(name):
+    # K_H = FULL: integrals over four labels enter (384 keys per quadruple),
+    # terms reach K + 4 = 6 labels; against O-det with the untruncated Hamiltonian
+    _lib()
+    H = {"C8H10": lambda: build_ppp('polyene', 8), "H8": lambda: build_hchain(8, 1.5)}[name]()
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, K_H=-1)
+    t = np.random.default_rng(9).uniform(-0.1, 0.1, P.cc.n_amp)
+    R, e = P.residual(t)
+    lm = LayoutMap(P.cc.manifold, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout(2))
+    R2, e2 = _interp(H, 2, 4, t, lm)
+    assert np.abs(R2 - R).max() < 1e-12
+    assert abs(e2 - e) < 1e-12
+    # the four-label integrals matter here
+    P2 = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=2, K_H=2)
+    assert np.abs(P2.residual(t)[0] - R).max() > 1e-4
+
+
+def _full_golden():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pq_full_c14h16.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    return np.load(path)
+
+
+def test_untruncated_integrals_inclusion_exclusion_n7():
+    # N = 7 > K + 4: every subset size enters; against the stored O-det values
+    _lib()
+    g = _full_golden()
+    occ, vir = g["occ"], g["vir"]
+    man = enumerate_manifold(occ, vir, 2)
+    lm = LayoutMap(man, occ, vir, g["h"].shape[0], ppq.amp_layout(2))
+    si = SubsetInterp(g["h"], g["eri"], occ, vir, 2, 4)
+    r, e2 = si.residual(lm.to_layout(g["t"]))
+    R2 = lm.from_layout(si.fill_copies(r, lm))
+    assert np.abs(g["R"]).max() > 0.05
+    assert np.abs(R2 - g["R"]).max() < 1e-12
+    assert abs(e2 - float(g["e_corr"])) < 1e-12
+
+
+@pytest.mark.skipif(not os.environ.get("PPQ_LONG_CHECKS"), reason="PPQ_LONG_CHECKS=1 (about 10 min)")
+def test_local_assembly_untruncated_against_stored_odet_n7():
+    # pins the oracle's local assembly with untruncated integrals (subset bound
+    # K + 4) against O-det at 7 pairs
+    g = _full_golden()
+    LA = LocalAssembly(g["h"], g["eri"], g["occ"], g["vir"], K=2, K_H=-1)
+    R, e = LA.residual(g["t"])
+    assert np.abs(R - g["R"]).max() < 1e-12
+    assert abs(e - float(g["e_corr"])) < 1e-12
 
 
 def test_recursion_sign_control():
