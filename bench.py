@@ -514,6 +514,27 @@ def main():
                          t_out=t_host.numpy(), precision=1, stream=stream.cuda_stream, **kw)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - w0) / args.steps
+    # end to end with the integrals as Cholesky factors (pq_solve_cd): 140
+    # vectors of 140 x 140 instead of the 140^4 array
+    e2e_cd = None
+    if not args.no_e2e:
+        from workloads import ppp_cholesky_vectors
+        B_host = torch.from_numpy(ppp_cholesky_vectors(H)).pin_memory()
+        ppq.pq_solve_cd(H.occ_of_pair, H.vir_of_pair, h_host.numpy(), B_host.numpy(), H.e_const,
+                        t_out=t_host.numpy(), precision=1, stream=stream.cuda_stream, **kw)   # warm-up
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            rccd, ecd, _, _ = ppq.pq_solve_cd(H.occ_of_pair, H.vir_of_pair, h_host.numpy(), B_host.numpy(),
+                                              H.e_const, t_out=t_host.numpy(), precision=1,
+                                              stream=stream.cuda_stream, **kw)
+        torch.cuda.synchronize()
+        e2e_cd = {"value": (time.perf_counter() - w0) / args.steps, "unit": "s",
+                  "h2d_bytes_per_step": int(B_host.numel() * 8 + h_host.numel() * 8),
+                  "d2h_bytes_per_step": int(L * 8 + 16), "status": rccd,
+                  "abs_dE_vs_dense_mixed": abs(ecd - e_mixed),
+                  "note": "pq_solve_cd from host buffers: (pq|rs) as 140 Cholesky vectors of the PPP site "
+                          "matrix (exact), contracted on the device"}
     pk = peaks()
     kernels, roof = kernel_table(prof, prof_ms, pk)
     n_launch = info["n_launches"]
@@ -538,6 +559,7 @@ def main():
         "e2e": {"value": e2e_s, "unit": "s",
                 "h2d_bytes_per_step": int(eri_host.numel() * 8 + h_host.numel() * 8),
                 "d2h_bytes_per_step": int(L * 8 + 16)},
+        "e2e_cd": e2e_cd,
         "clocks": clk.summary(),
     }
     if args.batch > 0:

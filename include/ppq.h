@@ -83,7 +83,11 @@ typedef struct {
   int diis_dim;       /* 8 (0 disables DIIS)                                    */
   int diis_start;     /* 3                                                     */
   double level_shift; /* added to |denominator| (0)                             */
-  int guess;          /* 0 = zero amplitudes, 1 = start from t_in               */
+  int guess;          /* 0 = zero amplitudes, 1 = start from t_in, 2 (pq_solve, */
+                      /*     pq_solve_cd) = start from the solution of the     */
+                      /*     single-pair truncation (K = 1: amplitudes inside  */
+                      /*     one pairing label, the perfect-pairing-type       */
+                      /*     model), solved first by the label-subset solver   */
   int profile;        /* 1 = time every kernel with CUDA events on `stream`     */
                       /*     (ppq_profile_entry; pq_solve also fills            */
                       /*     t_quartic_ms, ... )                                */
@@ -155,7 +159,9 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
 
 /* Solve the PQ amplitude equations (Theory section) by Jacobi steps with
    orbital-energy denominators and DIIS (Implementation section); the energy
-   is Eq. Ec.  t_in (nullable unless guess == 1) and
+   is Eq. Ec.  opts->K_H = 0 or 2 runs the two-label PQ kernels; -1 keeps every
+   two-electron integral and runs the label-subset solver of ph_solve with
+   K = 2 (n_pairs <= 127).  t_in (nullable unless guess == 1) and
    t_out use the layout above; e_corr / e_total / info are host pointers
    (nullable).  e_total = e_corr + E_ref + e_const with
    E_ref = sum_i (h_ii + f_ii) over the occupied orbitals. */
@@ -188,8 +194,12 @@ int ph_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
    with the arguments and conventions of pq_solve; t_in / t_out use the K = 3
    layout.  opts->K is ignored (the entry point sets K = 3); opts->K_H = 0 or
    3 keeps three-label integrals, 2 keeps two.  precision 1 runs FP32
-   residuals until ||R|| <= switch_tol or stagnation, then FP64 iterations to
-   the final tolerances (opts->polish is ignored).  The DIIS least-squares
+   residuals until ||R|| <= switch_tol or stagnation, then FP64 to the final
+   tolerances: with opts->polish = 1 (default) by defect correction (each
+   outer step evaluates R in FP64 and solves J d = -R with forward-difference
+   Jacobian products of FP32 residuals), with 0 by plain FP64 Jacobi/DIIS,
+   which it also falls back to when an outer step gains less than 10x or
+   ||R|| <= r_tol.  The DIIS least-squares
    problem is solved on the device; the host reads ||R|| and E_c once per
    iteration.  info->residual_flops counts 2 FLOPs per table entry and label
    subset of one residual evaluation.  n_pairs <= 127.
@@ -200,6 +210,18 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
              const double* h, const double* eri, double e_const,
              const ppq_opts* opts, const double* t_in, double* t_out,
              double* e_corr, double* e_total, ppq_info* info, void* stream);
+
+/* One residual evaluation by the label-subset expansion (the evaluation of
+   ph_residual) for amplitudes over at most K = 2 or 3 pairing labels (Theory
+   section, Eq. decompose) and two-electron integrals over at most K_H labels:
+   K_H = 0 (= K), 2, 3, or -1 = untruncated (K = 2 only: then a linked term
+   carries up to K + 4 = 6 labels; the paper's integral truncation controlled
+   separately from the amplitudes, Implementation section).  Layout, pointers
+   and errors as ph_residual, with the layout of K (3N + 29N^2 for K = 2).
+   pq_solve runs this evaluation for opts->K_H = -1. */
+int ppq_subset_residual(int K, int K_H, int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                        const double* h, const double* eri, const double* t, double* r,
+                        double* e_corr, int precision, void* stream);
 
 /* Host-only export of the structure tables that ph_residual generates for
    local problems of k sites (amplitudes over at most K labels, integrals over
@@ -214,6 +236,24 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
    call.  Returns 0, or < 0 for k outside 1..6 or K, K_H outside 1..3. */
 int ph_tables_counts(int k, int K, int K_H, int64_t* counts);
 int ph_tables_copy(int k, int K, int K_H, int which, void* dst);
+
+/* pq_solve and ph_solve with the two-electron integrals given as three-index
+   factors, (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s] (Cholesky or RI vectors; the
+   paper builds its integral blocks from such B matrices, Implementation
+   section, with a Cholesky threshold in the Results section).  B is FP64,
+   naux x n_orb x n_orb row-major, host or device (detected), read only; the
+   dense n_orb^4 array is never formed: the Fock matrix and every gathered
+   integral block are contracted from B on the device (B is transposed once
+   into a [pq][Q] working copy of the same size).  Other arguments, statuses
+   and outputs as pq_solve / ph_solve; pq_solve_cd accepts opts->K_H = -1. */
+int pq_solve_cd(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                const double* h, const double* B, int naux, double e_const,
+                const ppq_opts* opts, const double* t_in, double* t_out,
+                double* e_corr, double* e_total, ppq_info* info, void* stream);
+int ph_solve_cd(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                const double* h, const double* B, int naux, double e_const,
+                const ppq_opts* opts, const double* t_in, double* t_out,
+                double* e_corr, double* e_total, ppq_info* info, void* stream);
 
 /* Solve n_sys independent PQ problems of (possibly different) sizes in one
    call: the batched form of the paper's calculations, e.g. a bond-length scan
@@ -277,20 +317,35 @@ int pq_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
    are code running inside another framework's memory pool or under a fixed
    device-memory budget, or code on a path where cudaMalloc's implicit device
    synchronisation is not acceptable.  Every intermediate lives in one
-   file-scope device array of 16 MiB.  Each GPU that loads the library holds
-   that array until the process exits, so the call is limited to
-   n_pairs <= 12; larger sizes return -6 with a message.
+   file-scope device array of 8 MiB, sized for at most 12 pairs (the
+   intermediates grow as n_pairs^2 and take 4.4 MiB at 12 pairs).  Each GPU
+   that loads the library holds that array until the process exits; larger
+   sizes return -6 with a message.
    h, eri, t and r must be device pointers (else -7); occ_of_pair / vir_of_pair
-   are host arrays; e_corr is a host pointer (nullable).  Like pq_residual, the
-   call returns after `stream` has finished the work.
-   The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) while that device is current; make that first call
-   before any stream capture.  All calls share the one array, and each call
-   clears the part it uses before use.  Calls that overlap on the GPU (from
-   several host threads or streams) race on the array, so serialise them. */
+   are host arrays; e_corr is a host pointer (nullable).  The quartic term uses
+   the SIMT kernel with a fixed tile (no autotuning).  The call is synchronous:
+   it returns after `stream` has finished its work, also on an error after
+   work was queued.  The first call on a device looks up the array's device
+   address (cudaGetSymbolAddress) while that device is current; make that
+   first call before any stream capture.  Each call clears the part of the
+   array it uses before use.  Calls from this library are serialised by its
+   mutex and by that final synchronisation; kernels of two calls could only
+   overlap on the GPU if a caller bypassed both (for example by queuing the
+   array's users from another library copy), and such overlapping calls race
+   on the array. */
 int pq_residual_static(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
                        const double* h, const double* eri, const double* t,
                        double* r, double* e_corr, int precision, void* stream);
+
+/* Natural occupation numbers (Results section: the occupations that measure
+   static correlation, e.g. of the acenes): the eigenvalues, in descending
+   order, of a symmetric one-particle density matrix gamma (n_orb x n_orb, FP64,
+   host or device; the relaxed density dE_total/dh returned by pq_gradient is
+   one), by cyclic Jacobi rotations in one thread block on the device.
+   occ_out receives n_orb values; vecs_out (nullable) the natural orbitals as
+   columns (n_orb x n_orb, row-major).  n_orb <= 160 (<= 120 with vecs_out).
+   Synchronous on `stream`.  Returns 0 or < 0 on invalid arguments. */
+int ppq_natural_occupations(int n_orb, const double* gamma, double* occ_out, double* vecs_out, void* stream);
 
 /* Free the cached workspace of the current device (library housekeeping;
    the paper has no counterpart).  Returns 0. */

@@ -67,6 +67,10 @@ def lib():
                                ctypes.POINTER(Info), P]
         L.ph_solve.argtypes = L.pq_solve.argtypes
         L.ph_residual.argtypes = [I, P, P, P, P, P, P, P, I, I, P]
+        L.ppq_subset_residual.argtypes = [I, I, I, P, P, P, P, P, P, P, I, P]
+        L.pq_solve_cd.argtypes = [I, P, P, P, P, I, D, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(Info), P]
+        L.ph_solve_cd.argtypes = L.pq_solve_cd.argtypes
+        L.ppq_natural_occupations.argtypes = [I, P, P, P, P]
         L.ph_tables_counts.argtypes = [I, I, I, P]
         L.ph_tables_copy.argtypes = [I, I, I, I, P]
         L.ppq_profile_count.argtypes = []
@@ -82,7 +86,8 @@ def lib():
                   L.pq_residual_static, L.pq_solve, L.ph_solve, L.pq_solve_batched,
                   L.pq_lagrangian_gradient,
                   L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan, L.ph_residual,
-                  L.ph_tables_counts, L.ph_tables_copy, L.ppq_profile_count, L.ppq_profile_entry):
+                  L.ph_tables_counts, L.ph_tables_copy, L.ppq_profile_count, L.ppq_profile_entry,
+                  L.ppq_subset_residual, L.pq_solve_cd, L.ph_solve_cd, L.ppq_natural_occupations):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -92,7 +97,8 @@ EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual"
             "pq_residual_static", "pq_solve", "ph_solve", "ph_residual", "pq_solve_batched",
             "pq_lagrangian_gradient", "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error",
             "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy", "ppq_profile_count",
-            "ppq_profile_entry"]
+            "ppq_profile_entry", "ppq_subset_residual", "pq_solve_cd", "ph_solve_cd",
+            "ppq_natural_occupations"]
 
 
 def _ptr(x):
@@ -225,7 +231,7 @@ def pq_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, stream
 
 
 def pq_residual_static(occ_of_pair, vir_of_pair, h, eri, t, r, precision=0, stream=None):
-    """pq_residual without device allocation (scratch in a fixed 16 MiB device
+    """pq_residual without device allocation (scratch in a fixed 8 MiB device
     array, n_pairs <= 12).  For callers that cannot call cudaMalloc: h, eri, t
     and r must already be device tensors (torch CUDA).  Returns e_corr."""
     occ, vir = _pairs(occ_of_pair, vir_of_pair)
@@ -233,7 +239,7 @@ def pq_residual_static(occ_of_pair, vir_of_pair, h, eri, t, r, precision=0, stre
     n = 2 * N
     dev = _device_of(t)
     if dev is None:
-        raise PPQError("pq_residual_static: t must be a CUDA tensor (device memory)")
+        raise PPQError("pq_residual_static needs device pointers: t must be a CUDA tensor")
     for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, amp_count(N), "t"), (r, amp_count(N), "r")):
         _check_buf(x, cnt, name, device=dev)
     e = ctypes.c_double()
@@ -285,6 +291,26 @@ def ph_residual(occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, K_H=3,
     return r, e.value
 
 
+def subset_residual(K, K_H, occ_of_pair, vir_of_pair, h, eri, t, r=None, precision=0, stream=None):
+    """R(T) and E_c by the label-subset expansion for amplitudes over K = 2 or
+    3 labels and integrals over K_H labels (0 = K, -1 = untruncated with
+    K = 2), in the layout of include/ppq.h for K.  Returns (r, e_corr)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    L = amp_count(N, K)
+    if r is None:
+        r = np.zeros(L) if isinstance(t, np.ndarray) else t.new_zeros(L)
+    n = 2 * N
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, L, "t"), (r, L, "r")):
+        _check_buf(x, cnt, name)
+    e = ctypes.c_double()
+    rc = lib().ppq_subset_residual(K, K_H, N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t),
+                                   _ptr(r), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p), precision,
+                                   _stream(stream))
+    _check(rc, "ppq_subset_residual")
+    return r, e.value
+
+
 def ph_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=None, stream=None, **opts):
     """Solve the three-pair (PH) equations.  Returns (status, e_total, t_out,
     info dict); t_out uses the K = 3 layout."""
@@ -310,6 +336,55 @@ def ph_solve(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, t_in=None, t_out=Non
                         ctypes.byref(info), _stream(stream))
     _check(rc, "ph_solve")
     return rc, et.value, t_out, info.as_dict()
+
+
+def _solve_cd(fn, K, occ_of_pair, vir_of_pair, h, B, e_const, t_in, t_out, stream, opts):
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    L = amp_count(N, K)
+    o = default_opts(**opts)
+    if t_in is not None and 'guess' not in opts:
+        o.guess = 1
+    if t_out is None:
+        t_out = np.zeros(L)
+    n = 2 * N
+    naux = (B.shape[0] if hasattr(B, "shape") else 0)
+    for x, cnt, name in ((h, n * n, "h"), (B, naux * n * n, "B"), (t_out, L, "t_out")):
+        _check_buf(x, cnt, name)
+    if t_in is not None:
+        _check_buf(t_in, L, "t_in")
+    ec, et = ctypes.c_double(), ctypes.c_double()
+    info = Info()
+    rc = fn(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(B), int(naux), float(e_const), ctypes.byref(o),
+            _ptr(t_in), _ptr(t_out), ctypes.cast(ctypes.pointer(ec), ctypes.c_void_p),
+            ctypes.cast(ctypes.pointer(et), ctypes.c_void_p), ctypes.byref(info), _stream(stream))
+    _check(rc, fn.__name__)
+    return rc, et.value, t_out, info.as_dict()
+
+
+def pq_solve_cd(occ_of_pair, vir_of_pair, h, B, e_const=0.0, t_in=None, t_out=None, stream=None, **opts):
+    """pq_solve with the integrals as factors B[Q][p][q] ((pq|rs) = sum_Q
+    B[Q,p,q] B[Q,r,s]; shape (naux, n, n)).  Returns (status, e_total, t_out,
+    info dict)."""
+    return _solve_cd(lib().pq_solve_cd, 2, occ_of_pair, vir_of_pair, h, B, e_const, t_in, t_out, stream, opts)
+
+
+def ph_solve_cd(occ_of_pair, vir_of_pair, h, B, e_const=0.0, t_in=None, t_out=None, stream=None, **opts):
+    """ph_solve with the integrals as factors B[Q][p][q]."""
+    return _solve_cd(lib().ph_solve_cd, 3, occ_of_pair, vir_of_pair, h, B, e_const, t_in, t_out, stream, opts)
+
+
+def natural_occupations(gamma, vectors=False, stream=None):
+    """Eigenvalues (descending) of a symmetric density matrix gamma (torch CUDA
+    tensor or numpy array, n x n FP64), and the natural orbitals as columns
+    when vectors=True.  Returns numpy arrays."""
+    n = gamma.shape[0]
+    _check_buf(gamma, n * n, "gamma")
+    occ = np.zeros(n)
+    vec = np.zeros((n, n)) if vectors else None
+    _check(lib().ppq_natural_occupations(n, _ptr(gamma), occ.ctypes.data, None if vec is None else vec.ctypes.data,
+                                         _stream(stream)), "ppq_natural_occupations")
+    return (occ, vec) if vectors else occ
 
 
 def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):

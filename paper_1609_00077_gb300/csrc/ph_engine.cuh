@@ -140,12 +140,12 @@ __device__ __forceinline__ double denom3(size_t i, int N, const double* fo, cons
 // four-label integrals, G4[rank of X < Y < Z < V][384] from the bare one-body
 // part hb and (pq|rs)
 constexpr int kNK4 = 384;
-__global__ void k_stage_g(int n, int N, int KH, const double* __restrict__ hb, const double* __restrict__ eri,
+__global__ void k_stage_g(int n, int N, int KH, const double* __restrict__ hb, ppq::EriSrc E,
                           const int* __restrict__ occ, const int* __restrict__ vir, const int8_t* __restrict__ subs4,
                           int nsub4, double* __restrict__ G1, double* __restrict__ G2, double* __restrict__ G3,
                           double* __restrict__ G4) {
   size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  size_t n1 = n;
   size_t t1 = (size_t)N * 20, t2 = (size_t)N * N * 232, t3 = KH >= 3 ? (size_t)N * N * N * kNK3 : 0;
   size_t t4 = KH >= 4 ? (size_t)nsub4 * kNK4 : 0;
   int m, j, L[4];
@@ -166,8 +166,7 @@ __global__ void k_stage_g(int n, int N, int KH, const double* __restrict__ hb, c
   int o[8];
   for (int x = 0; x < m; ++x) { o[2 * x] = occ[L[x]]; o[2 * x + 1] = vir[L[x]]; }
   const int8_t* k = c_key[m - 1] + 5 * j;
-  *dst = k[0] == 0 ? hb[o[k[1]] * n1 + o[k[2]]]
-                   : eri[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]];
+  *dst = k[0] == 0 ? hb[o[k[1]] * n1 + o[k[2]]] : E(o[k[1]], o[k[2]], o[k[3]], o[k[4]]);
 }
 
 // ------------------------------------------------------------ local problems
@@ -522,68 +521,6 @@ __global__ void k_jacobi3(size_t L, int N, const double* __restrict__ t, const d
   en[i] = e;
 }
 
-// Pulay DIIS on the device: B (kDiis x kDiis, by slot id) gains the new row
-// from dots[1..m]; the bordered system [B -1; -1 0][c; l] = [0; -1] over the
-// active slots (order[0..m), newest last) is solved in FP64 by one thread
-// (error block scaled by its largest diagonal, which leaves c unchanged);
-// coef = c, or the newest iterate alone if the system is singular or
-// extrapolation is off.
-__global__ void k_diis_solve(int m, const int* __restrict__ order, int inew, const double* __restrict__ dots,
-                             double* __restrict__ B, int ldb, int extrap, double* __restrict__ coef) {
-  if (threadIdx.x || blockIdx.x) return;
-  for (int j = 0; j < m; ++j) {
-    double d = dots[1 + j];
-    B[order[j] * ldb + inew] = d;
-    B[inew * ldb + order[j]] = d;
-  }
-  for (int j = 0; j < m; ++j) coef[j] = j == m - 1 ? 1.0 : 0.0;
-  if (!extrap || m < 2) return;
-  const int nn = m + 1;
-  double A[17][18];
-  double sc = 0.0;
-  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(B[order[i] * ldb + order[i]]));
-  if (!(sc > 0.0)) sc = 1.0;
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i][j] = B[order[i] * ldb + order[j]] / sc;
-    A[i][m] = -1.0;
-    A[i][nn] = 0.0;
-  }
-  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
-  A[m][m] = 0.0;
-  A[m][nn] = -1.0;
-  for (int col = 0; col < nn; ++col) {
-    int piv = col;
-    for (int r2 = col + 1; r2 < nn; ++r2)
-      if (fabs(A[r2][col]) > fabs(A[piv][col])) piv = r2;
-    if (fabs(A[piv][col]) < 1e-300) return;
-    if (piv != col)
-      for (int q = 0; q <= nn; ++q) { double x = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = x; }
-    for (int r2 = col + 1; r2 < nn; ++r2) {
-      double f = A[r2][col] / A[col][col];
-      for (int q = col; q <= nn; ++q) A[r2][q] -= f * A[col][q];
-    }
-  }
-  double x[17];
-  for (int r2 = nn - 1; r2 >= 0; --r2) {
-    double s = A[r2][nn];
-    for (int q = r2 + 1; q < nn; ++q) s -= A[r2][q] * x[q];
-    x[r2] = s / A[r2][r2];
-  }
-  bool finite = true;
-  for (int j = 0; j < m; ++j) finite = finite && isfinite(x[j]);
-  if (finite)
-    for (int j = 0; j < m; ++j) coef[j] = x[j];
-}
-
-__global__ void k_extrap(size_t L, int m, const double* __restrict__ coef, const double* __restrict__ slots,
-                         size_t ld, const int* __restrict__ order, double* __restrict__ t) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L) return;
-  double s = 0.0;
-  for (int q = 0; q < m; ++q) s += coef[q] * slots[(size_t)order[q] * ld + i];
-  t[i] = s;
-}
-
 }  // namespace ph
 
 namespace ph {
@@ -624,6 +561,8 @@ struct Ctx {
   size_t cap_L = 0;
   int cap_diis = 0;
   double *t = nullptr, *r = nullptr, *slot_t = nullptr, *slot_e = nullptr;
+  double *tb = nullptr, *r64 = nullptr, *rb = nullptr, *del = nullptr, *rho = nullptr;  // defect correction
+  unsigned long long* amax = nullptr;
   double *B = nullptr, *coef = nullptr, *part = nullptr, *rows = nullptr, *e = nullptr;
   int* order = nullptr;
   double* host = nullptr;  // pinned scalars / order staging
@@ -928,7 +867,7 @@ int stage_ph(Ctx* c, Workspace* w, const Problem& P, int KH, cudaStream_t s) {
   const double* hb = KH >= 3 ? P.h : w->hp;
   size_t nq = KH >= 4 && N >= 4 ? (size_t)c->nsub[4] : 0;
   size_t tot = (size_t)N * 20 + (size_t)N * N * 232 + (KH >= 3 ? (size_t)N * N * N * kNK3 : 0) + nq * kNK4;
-  k_stage_g<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, KH, hb, P.eri, w->occ, w->vir, c->subs[4], (int)nq,
+  k_stage_g<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, KH, hb, P.src(), w->occ, w->vir, c->subs[4], (int)nq,
                                                           c->G1, c->G2, c->G3, c->G4);
   CK(cudaGetLastError());
   return 0;
@@ -938,12 +877,15 @@ int grow_solver(Ctx* c, size_t L, int diis) {
   if (L <= c->cap_L && diis <= c->cap_diis && c->host) return 0;
   size_t Lc = std::max(L, c->cap_L);
   int dc = std::max(diis, c->cap_diis);
-  void* ps[] = {c->t, c->r, c->slot_t, c->slot_e, c->B, c->coef, c->part, c->rows, c->e, c->order};
+  void* ps[] = {c->t, c->r, c->slot_t, c->slot_e, c->B, c->coef, c->part, c->rows, c->e, c->order,
+                c->tb, c->r64, c->rb, c->del, c->rho, c->amax};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->host) cudaFreeHost(c->host);
   CK(cudaMalloc((void**)&c->t, sizeof(double) * Lc));
   CK(cudaMalloc((void**)&c->r, sizeof(double) * Lc));
+  for (double** b : {&c->tb, &c->r64, &c->rb, &c->del, &c->rho}) CK(cudaMalloc((void**)b, sizeof(double) * Lc));
+  CK(cudaMalloc((void**)&c->amax, sizeof(unsigned long long)));
   CK(cudaMalloc((void**)&c->slot_t, sizeof(double) * Lc * std::max(dc, 1)));
   CK(cudaMalloc((void**)&c->slot_e, sizeof(double) * Lc * std::max(dc, 1)));
   CK(cudaMalloc((void**)&c->B, sizeof(double) * kDiisMax * kDiisMax));
@@ -1073,20 +1015,20 @@ struct PhSolver {
       fprintf(stderr, "ph eval %4d %s |R| %.3e E_c %.12f (%.2f ms)\n", evals, prec ? "fp32" : "fp64", *res, *e, ms);
     return 0;
   }
-  // Jacobi step t + R/D on the unique slots, Pulay DIIS over the ring (device)
-  int step(int it) {
+  // Jacobi step x + res/D on the unique slots, Pulay DIIS over `ring` (device)
+  int step_on(double* x, const double* res, int it, std::vector<int>& rg) {
     int m_max = o.diis_dim > 0 ? o.diis_dim : 1;
-    int slot = (int)ring.size() < m_max ? (int)ring.size() : ring.front();
+    int slot = (int)rg.size() < m_max ? (int)rg.size() : rg.front();
     std::vector<int> act;
-    for (int id : ring)
+    for (int id : rg)
       if (id != slot) act.push_back(id);
     if ((int)act.size() >= m_max) act.erase(act.begin());
     act.push_back(slot);
-    ring = act;
+    rg = act;
     int m = (int)act.size();
     double* st = c->slot_t + (size_t)slot * L;
     double* se = c->slot_e + (size_t)slot * L;
-    k_jacobi3<<<lb, 256, 0, s>>>(L, N, c->t, c->r, w->fo, w->fv, o.level_shift, st, se);
+    k_jacobi3<<<lb, 256, 0, s>>>(L, N, x, res, w->fo, w->fv, o.level_shift, st, se);
     int* ho = (int*)(c->host + 32);
     for (int i = 0; i < m; ++i) ho[i] = act[i];
     CK(cudaMemcpyAsync(c->order, ho, sizeof(int) * m, cudaMemcpyHostToDevice, s));
@@ -1094,10 +1036,70 @@ struct PhSolver {
     k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, c->part, nullptr, c->rows);
     int extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
     k_diis_solve<<<1, 32, 0, s>>>(m, c->order, slot, c->rows, c->B, kDiisMax, extrap, c->coef);
-    k_extrap<<<lb, 256, 0, s>>>(L, m, c->coef, c->slot_t, L, c->order, c->t);
-    k_fill_copies<<<lb, 256, 0, s>>>(L, N, K, c->t);
-    c->n_launches += 6;
+    k_extrap<<<lb, 256, 0, s>>>(L, m, c->coef, c->slot_t, L, c->order, x);
+    c->n_launches += 5;
     g_prof.done("solver: Jacobi, DIIS (device solve), extrapolation", s, 8.0 * L * (4 + 2 * m));
+    CK(cudaGetLastError());
+    return 0;
+  }
+  int step(int it) {
+    int rc = step_on(c->t, c->r, it, ring);
+    if (rc) return rc;
+    k_fill_copies<<<lb, 256, 0, s>>>(L, N, K, c->t);
+    c->n_launches++;
+    return 0;
+  }
+  // weighted norm of x over the unique slots (host value)
+  int norm(const double* x, double* out) {
+    k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, x, 0, c->slot_e, L, c->order, 0, c->part);
+    k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1, c->part, nullptr, c->rows);
+    CK(cudaMemcpyAsync(c->host, c->rows, sizeof(double), cudaMemcpyDeviceToHost, s));
+    g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
+    CK(cudaStreamSynchronize(s));
+    c->n_launches += 2;
+    *out = sqrt(c->host[0]);
+    return 0;
+  }
+  // FP64 defect correction (the polish of the mixed form): c->r holds R_64(t)
+  // on entry.  Solves r + J d = 0 to a relative 1e-3 with DIIS-accelerated
+  // Jacobi, Jacobian products by forward differences of FP32 residuals, then
+  // t <- t + d.  The step is eta = 1e-2 in max norm: the FP32 residual of the
+  // label-subset expansion carries a noise floor of ~1e-5 (inclusion-exclusion
+  // coefficients of hundreds), which a smaller step would not rise above.
+  int defect_correction(double r0, int* it_io) {
+    const double eta = 1e-2, tol = 1e-3;
+    int rc;
+    CK(cudaMemcpyAsync(c->tb, c->t, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->r64, c->r, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    double rn, ed;
+    if ((rc = eval(1, &rn, &ed))) return rc;
+    CK(cudaMemcpyAsync(c->rb, c->r, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(c->del, 0, sizeof(double) * L, s));
+    CK(cudaMemcpyAsync(c->rho, c->r64, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    std::vector<int> inner_ring;
+    std::vector<double> hist;
+    for (int inner = 0; inner < 30 && *it_io < o.max_iter; ++inner) {
+      if ((rc = step_on(c->del, c->rho, inner + 1, inner_ring))) return rc;
+      CK(cudaMemsetAsync(c->amax, 0, sizeof(unsigned long long), s));
+      k_absmax<<<kRedBlocks, 256, 0, s>>>(L, c->del, c->amax);
+      k_fd_point<<<lb, 256, 0, s>>>(L, c->tb, c->del, c->amax, eta, c->t);
+      if ((rc = eval(1, &rn, &ed))) return rc;
+      k_fd_rho<<<lb, 256, 0, s>>>(L, c->r64, c->r, c->rb, c->amax, eta, c->rho);
+      c->n_launches += 3;
+      g_prof.done("solver: defect-correction vectors", s, 8.0 * L * 6);
+      (*it_io)++;
+      double rr;
+      if ((rc = norm(c->rho, &rr))) return rc;
+      if (trace_on()) fprintf(stderr, "ph   inner %2d |r + J d| %.3e (target %.3e)\n", inner, rr, tol * r0);
+      if (!isfinite(rr)) break;
+      if (rr <= tol * r0) break;
+      hist.push_back(rr);
+      size_t k = hist.size();
+      if (k >= 4 && hist[k - 1] > 0.9 * hist[k - 4]) break;
+    }
+    k_axpy_to<<<lb, 256, 0, s>>>(L, c->tb, c->del, c->t);
+    k_fill_copies<<<lb, 256, 0, s>>>(L, N, K, c->t);
+    c->n_launches += 2;
     CK(cudaGetLastError());
     return 0;
   }
@@ -1112,9 +1114,9 @@ namespace {
 // orbital-energy denominators and device-side Pulay DIIS; the mixed form runs
 // FP32 residuals until switch_tol (or FP32 stagnation), then FP64.
 int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
-                 const double* eri, double e_const, const ppq_opts& o, const double* t_in, double* t_out,
-                 double* e_corr, double* e_total, ppq_info* info, cudaStream_t s,
-                 std::chrono::steady_clock::time_point wall0) {
+                 const double* eri, const double* B, int naux, double e_const, const ppq_opts& o,
+                 const double* t_in, double* t_out, double* e_corr, double* e_total, ppq_info* info,
+                 cudaStream_t s, std::chrono::steady_clock::time_point wall0) {
   if (o.precision != 0 && o.precision != 1) return fail(-4, "precision must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
@@ -1122,7 +1124,8 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
   if (n_pairs > 127) return fail(-1, "n_pairs must be <= 127 for the label-subset solver");
   Workspace* w = nullptr;
   Problem P;
-  int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
+  int rc = B ? prepare_cd(n_pairs, occ_of_pair, vir_of_pair, h, B, naux, 1, s, &w, &P)
+             : prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
   if (rc) {
     if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
     return rc;
@@ -1130,6 +1133,7 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
   ph::Ctx* c = ph::ctx();
   c->n_launches = 0;
   g_prof.reset(o.profile != 0);
+  struct ProfOff { ~ProfOff() { g_prof.on = false; } } prof_off;
   g_prof.start(s);
   if ((rc = ph::stage_ph(c, w, P, KH, s))) return rc;
   g_prof.done("staging (Fock, gathers)", s);
@@ -1153,21 +1157,46 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
   bool have_old = false;
   int status = 1, it;
   std::vector<double> hist;
+  bool defect = false;  // FP64 defect-correction polish active
+  double last_outer = 0.0;
   for (it = 1; it <= o.max_iter; ++it) {
+    if (defect) {
+      // one outer step: FP64 residual and test, then r + J d = 0 with FP32
+      // finite-difference Jacobian products
+      if ((rc = S.eval(0, &res, &e))) return rc;
+      hist.push_back(res);
+      if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
+      if (have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
+      bool stalled = last_outer > 0.0 && res > 0.1 * last_outer;
+      e_old = e;
+      have_old = true;
+      if (stalled || res <= o.r_tol) {
+        // the correction stopped paying, or only the energy test is left:
+        // plain FP64 Jacobi/DIIS from here
+        defect = false;
+        S.ring.clear();
+        if ((rc = S.step(it))) return rc;
+        continue;
+      }
+      last_outer = res;
+      if ((rc = S.defect_correction(res, &it))) return rc;
+      continue;
+    }
     if ((rc = S.eval(prec, &res, &e))) return rc;
     hist.push_back(res);
     if (!isfinite(res) || !isfinite(e) || res > 1e6) { status = 2; break; }
     if (prec == 0 && have_old && res <= o.r_tol && fabs(e - e_old) <= o.e_tol) { status = 0; break; }
     if (prec == 1) {
       // switch at switch_tol, or when FP32 stops gaining (< 10 % over three
-      // steps below 1e-4: the FP32 noise floor); the DIIS history is kept, its
-      // vectors are valid FP64 iterates
+      // steps below 1e-4: the FP32 noise floor)
       size_t k = hist.size();
       bool stagnant = k >= 4 && res < 1e-4 && hist[k - 1] > 0.9 * hist[k - 4];
       if (res <= o.switch_tol || stagnant) {
         prec = 0;
         switched_at = it;
         have_old = false;
+        S.ring.clear();
+        if (o.polish == 1) defect = true;
         continue;  // re-evaluate at the same amplitudes in FP64
       }
     }
@@ -1215,8 +1244,23 @@ int ph_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   if (opts) o = *opts; else ppq_default_opts(&o);
   int KH = o.K_H == 0 ? 3 : o.K_H;
   if (KH != 2 && KH != 3) return fail(-4, "ph_solve: K_H must be 0 (= 3), 2 or 3");
-  return subset_solve(3, KH, n_pairs, occ_of_pair, vir_of_pair, h, eri, e_const, o, t_in, t_out, e_corr, e_total,
-                      info, (cudaStream_t)stream, wall0);
+  return subset_solve(3, KH, n_pairs, occ_of_pair, vir_of_pair, h, eri, nullptr, 0, e_const, o, t_in, t_out, e_corr,
+                      e_total, info, (cudaStream_t)stream, wall0);
+}
+
+int ph_solve_cd(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h, const double* B,
+                int naux, double e_const, const ppq_opts* opts, const double* t_in, double* t_out, double* e_corr,
+                double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int KH = o.K_H == 0 ? 3 : o.K_H;
+  if (KH != 2 && KH != 3) return fail(-4, "ph_solve_cd: K_H must be 0 (= 3), 2 or 3");
+  if (!B) return fail(-2, "B must be non-null");
+  return subset_solve(3, KH, n_pairs, occ_of_pair, vir_of_pair, h, nullptr, B, naux, e_const, o, t_in, t_out,
+                      e_corr, e_total, info, (cudaStream_t)stream, wall0);
 }
 
 int ppq_subset_residual(int K, int K_H, int n_pairs, const int* occ_of_pair, const int* vir_of_pair,

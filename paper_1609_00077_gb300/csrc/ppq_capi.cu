@@ -137,6 +137,8 @@ struct Workspace {
   int diis_cap = 0;
   // staged inputs
   double *h = nullptr, *eri = nullptr;  // only when the caller passes host pointers
+  double *Bcd = nullptr, *Bt = nullptr;  // three-index factors (raw host copy, transposed)
+  size_t cd_cap = 0;
   int *occ = nullptr, *vir = nullptr, *lab = nullptr;
   double *f = nullptr, *hp = nullptr, *fo = nullptr, *fv = nullptr;
   double *g1d = nullptr, *g2d = nullptr;
@@ -174,7 +176,7 @@ struct Workspace {
   int n_work9 = 0;
   double *esite = nullptr, *epair = nullptr;
   // reductions
-  double *part = nullptr, *scal = nullptr, *coef = nullptr;
+  double *part = nullptr, *scal = nullptr, *coef = nullptr, *Bdiis = nullptr;
   int* ok = nullptr;
   int* order = nullptr;
   double* host = nullptr;  // pinned host scalars
@@ -218,9 +220,9 @@ constexpr int kTcMaxCtas = 1024;
 constexpr int kTcPartRows = 152 * 128;  // slots x unordered pairs of the partial buffer
 
 void free_ws(Workspace* w) {
-  void* ps[] = {w->h, w->eri, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
+  void* ps[] = {w->h, w->eri, w->Bcd, w->Bt, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
-                w->esite, w->epair, w->part, w->scal, w->coef, w->ok, w->order, w->slot_t, w->slot_e,
+                w->esite, w->epair, w->part, w->scal, w->coef, w->Bdiis, w->ok, w->order, w->slot_t, w->slot_e,
                 w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
                 w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part,
                 w->bpre64, w->fexp64, w->tc64_chunk, w->tc64_cta, w->tc64_part, w->r1part};
@@ -301,6 +303,7 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->esite, sizeof(double) * Nc); AL(w->epair, sizeof(double) * NN);
   AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
   AL(w->scal, sizeof(double) * (kDiisMax + 4)); AL(w->coef, sizeof(double) * kDiisMax);
+  AL(w->Bdiis, sizeof(double) * kDiisMax * kDiisMax);
   AL(w->ok, sizeof(int)); AL(w->order, sizeof(int) * kDiisMax);
   if (dc > 0) {
     AL(w->slot_t, sizeof(double) * L * dc);
@@ -404,18 +407,21 @@ __global__ void k_rowsum(int nb, int rows, const double* __restrict__ part, int 
 struct Problem {
   int N, n;
   const double* h;    // device
-  const double* eri;  // device
+  const double* eri;  // device (nullptr when the integrals come as factors)
+  const double* Bt = nullptr;  // device [n * n][naux] factors, (pq|rs) = B[pq] . B[rs]
+  int naux = 0;
+  ppq::EriSrc src() const { return ppq::EriSrc{eri, Bt, naux, n}; }
 };
 
 // stage integrals: Fock, h', gathers, denominators
 int stage(Workspace* w, const Problem& P, cudaStream_t s) {
   int N = P.N, n = P.n;
-  ppq::k_fock<<<(n * n + 127) / 128, 128, 0, s>>>(n, N, P.h, P.eri, w->occ, w->lab, w->f, w->hp);
+  ppq::k_fock<<<(n * n + 127) / 128, 128, 0, s>>>(n, N, P.h, P.src(), w->occ, w->lab, w->f, w->hp);
   k_fdiag<<<1, 256, 0, s>>>(N, n, w->f, w->occ, w->vir, w->fo, w->fv);
   size_t tot = (size_t)N * N * PPQ_NG2 + (size_t)N * PPQ_NG1;
   unsigned nb = (unsigned)((tot + 255) / 256);
-  ppq::k_gather<double><<<nb, 256, 0, s>>>(n, N, w->hp, P.eri, w->occ, w->vir, w->g1d, w->g2d);
-  ppq::k_gather<float><<<nb, 256, 0, s>>>(n, N, w->hp, P.eri, w->occ, w->vir, w->g1f, w->g2f);
+  ppq::k_gather<double><<<nb, 256, 0, s>>>(n, N, w->hp, P.src(), w->occ, w->vir, w->g1d, w->g2d);
+  ppq::k_gather<float><<<nb, 256, 0, s>>>(n, N, w->hp, P.src(), w->occ, w->vir, w->g1f, w->g2f);
   CK(cudaGetLastError());
   return 0;
 }
@@ -910,6 +916,71 @@ int prepare(int N, const int* occ, const int* vir, const double* h, const double
   return prepare_ws(w, N, occ, vir, h, eri, diis, s, P);
 }
 
+// B[Q][pq] -> Bt[pq][Q] (the factor of one integral index pair contiguous)
+__global__ void k_transpose_B(int naux, size_t n2, const double* __restrict__ B, double* __restrict__ Bt) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2 * naux) return;
+  size_t pq = i / naux, Q = i % naux;
+  Bt[i] = B[Q * n2 + pq];
+}
+
+// entry preparation from three-index factors B[Q][p][q], (pq|rs) = sum_Q
+// B[Q][p][q] B[Q][r][s]: pairing, h and B on the device (B transposed to
+// [pq][Q]), non-finite screen, staging from the factors
+int prepare_cd(int N, const int* occ, const int* vir, const double* h, const double* B, int naux, int diis,
+               cudaStream_t s, Workspace** pw, Problem* P) {
+  std::vector<int> lab;
+  int rc = check_pairing(N, occ, vir, lab);
+  if (rc) return rc;
+  if (!h || !B) return fail(-2, "h and B must be non-null");
+  if (naux < 1) return fail(-2, "naux must be >= 1");
+  int dev;
+  CK(cudaGetDevice(&dev));
+  Workspace*& w = g_ws[dev];
+  if (!w) w = new Workspace();
+  *pw = w;
+  if ((rc = grow(w, N, diis))) return rc;
+  int n = 2 * N;
+  size_t n2 = (size_t)n * n, nb = n2 * naux;
+  CK(cudaMemcpyAsync(w->occ, occ, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->vir, vir, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->lab, lab.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  P->N = N;
+  P->n = n;
+  P->eri = nullptr;
+  if (is_device_ptr(h)) P->h = h;
+  else {
+    CK(cudaMemcpyAsync(w->h, h, sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+    P->h = w->h;
+  }
+  // factors: raw copy (when on the host) and the transposed working copy
+  if (w->cd_cap < nb) {
+    if (w->Bcd) cudaFree(w->Bcd);
+    if (w->Bt) cudaFree(w->Bt);
+    w->Bcd = w->Bt = nullptr;
+    w->cd_cap = 0;
+    CK(cudaMalloc((void**)&w->Bcd, sizeof(double) * nb));
+    CK(cudaMalloc((void**)&w->Bt, sizeof(double) * nb));
+    w->cd_cap = nb;
+  }
+  const double* Bd = B;
+  if (!is_device_ptr(B)) {
+    CK(cudaMemcpyAsync(w->Bcd, B, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    Bd = w->Bcd;
+  }
+  k_transpose_B<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(naux, n2, Bd, w->Bt);
+  P->Bt = w->Bt;
+  P->naux = naux;
+  CK(cudaMemsetAsync(w->ok, 0, sizeof(int), s));
+  k_count_nonfinite<<<kRedBlocks, 256, 0, s>>>(n2, P->h, w->ok);
+  k_count_nonfinite<<<kRedBlocks, 256, 0, s>>>(nb, w->Bt, w->ok);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, w->ok, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return 3;
+  return stage(w, *P, s);
+}
+
 int copy_amps(double* dst, const double* src, size_t L, cudaStream_t s) {
   CK(cudaMemcpyAsync(dst, src, sizeof(double) * L, cudaMemcpyDefault, s));
   return 0;
@@ -1062,50 +1133,77 @@ __global__ void k_axpy_to(size_t L, const double* __restrict__ a, const double* 
   if (i < L) out[i] = a[i] + b[i];
 }
 
-// Pulay DIIS state: slot ids (oldest first) and the error-dot matrix by slot id
-struct Diis {
-  int m_max;
-  std::vector<int> ring;
-  std::vector<double> B;
-  explicit Diis(int m) : m_max(m), B(kDiisMax * kDiisMax, 0.0) {}
-  void reset() { ring.clear(); }
-};
-
-// Solve the bordered DIIS system [B -1; -1 0][c; l] = [0; -1] (FP64, host);
-// the error block is scaled by its largest diagonal (c is unchanged).
-bool diis_coefficients(const Diis& d, const std::vector<int>& act, std::vector<double>& c) {
-  int m = (int)act.size(), nn = m + 1;
-  std::vector<double> A((size_t)nn * (nn + 1), 0.0);
-  double sc = 0.0;
-  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(d.B[act[i] * kDiisMax + act[i]]));
-  if (sc <= 0.0) sc = 1.0;
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i * (nn + 1) + j] = d.B[act[i] * kDiisMax + act[j]] / sc;
-    A[i * (nn + 1) + m] = -1.0;
+// Pulay DIIS on the device: B (kDiis x kDiis, by slot id) gains the new row
+// from dots[1..m]; the bordered system [B -1; -1 0][c; l] = [0; -1] over the
+// active slots (order[0..m), newest last) is solved in FP64 by one thread
+// (error block scaled by its largest diagonal, which leaves c unchanged);
+// coef = c, or the newest iterate alone if the system is singular or
+// extrapolation is off.
+__global__ void k_diis_solve(int m, const int* __restrict__ order, int inew, const double* __restrict__ dots,
+                             double* __restrict__ B, int ldb, int extrap, double* __restrict__ coef) {
+  if (threadIdx.x || blockIdx.x) return;
+  for (int j = 0; j < m; ++j) {
+    double d = dots[1 + j];
+    B[order[j] * ldb + inew] = d;
+    B[inew * ldb + order[j]] = d;
   }
-  for (int j = 0; j < m; ++j) A[m * (nn + 1) + j] = -1.0;
-  A[m * (nn + 1) + nn] = -1.0;
+  for (int j = 0; j < m; ++j) coef[j] = j == m - 1 ? 1.0 : 0.0;
+  if (!extrap || m < 2) return;
+  const int nn = m + 1;
+  double A[17][18];
+  double sc = 0.0;
+  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(B[order[i] * ldb + order[i]]));
+  if (!(sc > 0.0)) sc = 1.0;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i][j] = B[order[i] * ldb + order[j]] / sc;
+    A[i][m] = -1.0;
+    A[i][nn] = 0.0;
+  }
+  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
+  A[m][m] = 0.0;
+  A[m][nn] = -1.0;
   for (int col = 0; col < nn; ++col) {
     int piv = col;
     for (int r2 = col + 1; r2 < nn; ++r2)
-      if (fabs(A[r2 * (nn + 1) + col]) > fabs(A[piv * (nn + 1) + col])) piv = r2;
-    if (fabs(A[piv * (nn + 1) + col]) < 1e-300) return false;
+      if (fabs(A[r2][col]) > fabs(A[piv][col])) piv = r2;
+    if (fabs(A[piv][col]) < 1e-300) return;
     if (piv != col)
-      for (int k = 0; k <= nn; ++k) std::swap(A[col * (nn + 1) + k], A[piv * (nn + 1) + k]);
+      for (int q = 0; q <= nn; ++q) { double x = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = x; }
     for (int r2 = col + 1; r2 < nn; ++r2) {
-      double f = A[r2 * (nn + 1) + col] / A[col * (nn + 1) + col];
-      for (int k = col; k <= nn; ++k) A[r2 * (nn + 1) + k] -= f * A[col * (nn + 1) + k];
+      double f = A[r2][col] / A[col][col];
+      for (int q = col; q <= nn; ++q) A[r2][q] -= f * A[col][q];
     }
   }
-  std::vector<double> x(nn, 0.0);
+  double x[17];
   for (int r2 = nn - 1; r2 >= 0; --r2) {
-    double sum = A[r2 * (nn + 1) + nn];
-    for (int k = r2 + 1; k < nn; ++k) sum -= A[r2 * (nn + 1) + k] * x[k];
-    x[r2] = sum / A[r2 * (nn + 1) + r2];
+    double s = A[r2][nn];
+    for (int q = r2 + 1; q < nn; ++q) s -= A[r2][q] * x[q];
+    x[r2] = s / A[r2][r2];
   }
-  c.assign(x.begin(), x.begin() + m);
-  return true;
+  bool finite = true;
+  for (int j = 0; j < m; ++j) finite = finite && isfinite(x[j]);
+  if (finite)
+    for (int j = 0; j < m; ++j) coef[j] = x[j];
 }
+
+__global__ void k_extrap(size_t L, int m, const double* __restrict__ coef, const double* __restrict__ slots,
+                         size_t ld, const int* __restrict__ order, double* __restrict__ t) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double s = 0.0;
+  for (int q = 0; q < m; ++q) s += coef[q] * slots[(size_t)order[q] * ld + i];
+  t[i] = s;
+}
+
+
+// Pulay DIIS ring: slot ids, oldest first (the error-dot matrix lives on the
+// device, indexed by slot id)
+struct Diis {
+  int m_max;
+  std::vector<int> ring;
+  explicit Diis(int m) : m_max(m) {}
+  void reset() { ring.clear(); }
+};
 
 // The iteration machinery of pq_solve around the residual pipeline.
 struct Solver {
@@ -1180,27 +1278,12 @@ struct Solver {
     dim3 g(kRedBlocks, 1 + m);
     k_multidot<<<g, 256, 0, s>>>(L, N, res, m, w->slot_e, L, w->order, slot, w->part);
     k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
-    CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
     d.ring = act;
-    for (int i = 0; i < m; ++i) {
-      double dd = w->host[1 + i];
-      d.B[act[i] * kDiisMax + slot] = dd;
-      d.B[slot * kDiisMax + act[i]] = dd;
-    }
-    std::vector<double> c;
-    bool extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
-    if (!extrap || !diis_coefficients(d, act, c)) {
-      c.assign(m, 0.0);
-      c[m - 1] = 1.0;
-    }
-    for (int i = 0; i < m; ++i) w->host[8 + i] = c[i];
-    int one = 1;
-    memcpy(w->host + 32, &one, sizeof(int));
-    CK(cudaMemcpyAsync(w->coef, w->host + 8, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(w->ok, w->host + 32, sizeof(int), cudaMemcpyHostToDevice, s));
-    ppq::k_extrapolate<<<lb, 256, 0, s>>>(L, m, w->coef, w->ok, w->slot_t, L, w->order, x);
-    w->n_launches += 4;
+    // bordered least squares and extrapolation on the device (no host round trip)
+    int extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
+    k_diis_solve<<<1, 32, 0, s>>>(m, w->order, slot, w->scal, w->Bdiis, kDiisMax, extrap, w->coef);
+    k_extrap<<<lb, 256, 0, s>>>(L, m, w->coef, w->slot_t, L, w->order, x);
+    w->n_launches += 5;
     g_prof.done("solver: Jacobi, DIIS, extrapolation", s, 8.0 * L * (4 + 2 * m));
     CK(cudaGetLastError());
     return 0;
@@ -1429,6 +1512,8 @@ namespace {
 
 int validate_opts(const ppq_opts& o, bool allow_full = false) {
   if (o.K != 2) return fail(-4, "pq_solve: K must be 2 (PQ)");
+  if (o.guess < 0 || o.guess > 2 || (o.guess == 2 && !allow_full))
+    return fail(-4, "guess must be 0 (zero), 1 (t_in) or 2 (single-pair start, pq_solve only)");
   if (o.K_H == -1 && !allow_full)
     return fail(-4, "K_H = -1 (untruncated integrals) is solved by pq_solve only");
   if (o.K_H != 0 && o.K_H != 2 && o.K_H != -1)
@@ -1446,9 +1531,9 @@ int diis_slots(const ppq_opts& o) {
 }
 
 int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
-                 const double* eri, double e_const, const ppq_opts& o, const double* t_in, double* t_out,
-                 double* e_corr, double* e_total, ppq_info* info, cudaStream_t s,
-                 std::chrono::steady_clock::time_point wall0);
+                 const double* eri, const double* B, int naux, double e_const, const ppq_opts& o,
+                 const double* t_in, double* t_out, double* e_corr, double* e_total, ppq_info* info,
+                 cudaStream_t s, std::chrono::steady_clock::time_point wall0);
 
 // The solve of one system on a prepared workspace and stream.
 int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o,
@@ -1461,6 +1546,7 @@ int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o
   size_t L = amp_len(N);
   w->profile = o.profile != 0;
   g_prof.reset(w->profile);
+  struct ProfOff { ~ProfOff() { g_prof.on = false; } } prof_off;
   g_prof.start(s);
   w->t_quartic_ms = 0.0;
   w->n_quartic = 0;
@@ -1587,11 +1673,28 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
   if (opts) o = *opts; else ppq_default_opts(&o);
   int rc = validate_opts(o, true);
   if (rc) return rc;
+  std::vector<double> pp;
+  if (o.guess == 2) {
+    // perfect-pairing-type start: solve the single-pair truncation (K = 1,
+    // amplitudes inside one pairing label, two-label integrals) first and
+    // start from its amplitudes (the two-pair block zero)
+    ppq_opts o1 = o;
+    o1.guess = 0;
+    o1.profile = 0;
+    size_t L = amp_len(n_pairs);
+    pp.assign(L, 0.0);
+    int rc1 = subset_solve(1, 2, n_pairs, occ_of_pair, vir_of_pair, h, eri, nullptr, 0, 0.0, o1, nullptr, pp.data(),
+                           nullptr, nullptr, nullptr, s, wall0);
+    if (rc1 < 0) return rc1;
+    if (rc1 == 2 || rc1 == 3) pp.assign(L, 0.0);  // no usable start: zero amplitudes
+    o.guess = 1;
+    t_in = pp.data();
+  }
   // untruncated integrals: terms reach K + 4 = 6 labels, evaluated by the
   // label-subset expansion
   if (o.K_H == -1)
-    return subset_solve(2, 4, n_pairs, occ_of_pair, vir_of_pair, h, eri, e_const, o, t_in, t_out, e_corr, e_total,
-                        info, s, wall0);
+    return subset_solve(2, 4, n_pairs, occ_of_pair, vir_of_pair, h, eri, nullptr, 0, e_const, o, t_in, t_out, e_corr,
+                        e_total, info, s, wall0);
   if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
   Workspace* w = nullptr;
   Problem P;
@@ -1601,6 +1704,146 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     return rc;
   }
   return solve_core(w, P, e_const, o, t_in, t_out, e_corr, e_total, info, s, wall0);
+}
+
+int pq_solve_cd(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h, const double* B,
+                int naux, double e_const, const ppq_opts* opts, const double* t_in, double* t_out, double* e_corr,
+                double* e_total, ppq_info* info, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  auto wall0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  ppq_opts o;
+  if (opts) o = *opts; else ppq_default_opts(&o);
+  int rc = validate_opts(o, true);
+  if (rc) return rc;
+  if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
+  if (!B) return fail(-2, "B must be non-null");
+  if (o.K_H == -1)
+    return subset_solve(2, 4, n_pairs, occ_of_pair, vir_of_pair, h, nullptr, B, naux, e_const, o, t_in, t_out, e_corr,
+                        e_total, info, s, wall0);
+  Workspace* w = nullptr;
+  Problem P;
+  rc = prepare_cd(n_pairs, occ_of_pair, vir_of_pair, h, B, naux, diis_slots(o), s, &w, &P);
+  if (rc) {
+    if (rc == 3 && info) { memset(info, 0, sizeof *info); info->status = 3; }
+    return rc;
+  }
+  return solve_core(w, P, e_const, o, t_in, t_out, e_corr, e_total, info, s, wall0);
+}
+
+// Eigenvalues (and optionally eigenvectors, columns) of a symmetric n x n
+// matrix by cyclic Jacobi rotations in one block's shared memory; the values
+// sorted in descending order.  n <= kNatMax.
+constexpr int kNatMax = 160;
+__global__ void k_sym_eig(int n, const double* __restrict__ a_in, double* __restrict__ w_out,
+                          double* __restrict__ v_out, int* __restrict__ sweeps_out) {
+  extern __shared__ double sm[];
+  double* A = sm;              // n x n
+  double* V = sm + n * n;      // n x n (eigenvectors, only when v_out)
+  __shared__ double cs[2];
+  __shared__ double off;
+  const bool vec = v_out != nullptr;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    A[i] = 0.5 * (a_in[i] + a_in[(i % n) * n + i / n]);
+    if (vec) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 64; ++sweep) {
+    if (threadIdx.x == 0) off = 0.0;
+    __syncthreads();
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      if (i / n != i % n) part += A[i] * A[i];
+    atomicAdd(&off, part);
+    __syncthreads();
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale += A[i * n + i] * A[i * n + i];
+    if (off <= 1e-30 * (scale + 1e-300)) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (threadIdx.x == 0) {
+          double apq = A[p * n + q];
+          double c = 1.0, sn = 0.0;
+          if (fabs(apq) > 1e-300) {
+            double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+            double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
+          cs[0] = c; cs[1] = sn;
+        }
+        __syncthreads();
+        double c = cs[0], sn = cs[1];
+        if (sn != 0.0) {
+          // columns p, q
+          for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double akp = A[k * n + p], akq = A[k * n + q];
+            A[k * n + p] = c * akp - sn * akq;
+            A[k * n + q] = sn * akp + c * akq;
+            if (vec) {
+              double vkp = V[k * n + p], vkq = V[k * n + q];
+              V[k * n + p] = c * vkp - sn * vkq;
+              V[k * n + q] = sn * vkp + c * vkq;
+            }
+          }
+          __syncthreads();
+          // rows p, q
+          for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double apk = A[p * n + k], aqk = A[q * n + k];
+            A[p * n + k] = c * apk - sn * aqk;
+            A[q * n + k] = sn * apk + c * aqk;
+          }
+        }
+        __syncthreads();
+      }
+  }
+  if (threadIdx.x == 0) {
+    // selection sort of the diagonal, descending (vectors follow)
+    for (int i = 0; i < n; ++i) w_out[i] = A[i * n + i];
+    int order[kNatMax];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j)
+        if (w_out[order[j]] > w_out[order[i]]) { int x = order[i]; order[i] = order[j]; order[j] = x; }
+    double tmp[kNatMax];
+    for (int i = 0; i < n; ++i) tmp[i] = w_out[order[i]];
+    for (int i = 0; i < n; ++i) w_out[i] = tmp[i];
+    if (vec)
+      for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) v_out[k * n + i] = V[k * n + order[i]];
+    if (sweeps_out) *sweeps_out = sweep;
+  }
+}
+
+int ppq_natural_occupations(int n_orb, const double* gamma, double* occ_out, double* vecs_out, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_orb < 1 || n_orb > kNatMax) return fail(-1, "ppq_natural_occupations: n_orb must be 1..%d", kNatMax);
+  if (!gamma || !occ_out) return fail(-2, "gamma and occ_out must be non-null");
+  if (vecs_out && n_orb > 120) return fail(-1, "ppq_natural_occupations: eigenvectors need n_orb <= 120");
+  size_t nn = (size_t)n_orb * n_orb;
+  double *dg = nullptr, *dw = nullptr, *dv = nullptr;
+  CK(cudaMalloc((void**)&dg, sizeof(double) * nn));
+  CK(cudaMalloc((void**)&dw, sizeof(double) * n_orb));
+  if (vecs_out) CK(cudaMalloc((void**)&dv, sizeof(double) * nn));
+  CK(cudaMemcpyAsync(dg, gamma, sizeof(double) * nn, cudaMemcpyDefault, s));
+  size_t smem = sizeof(double) * nn * (vecs_out ? 2 : 1);
+  if (smem > 227 * 1024) {
+    cudaFree(dg); cudaFree(dw); if (dv) cudaFree(dv);
+    return fail(-1, "ppq_natural_occupations: eigenvectors need n_orb <= 120");
+  }
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sym_eig<<<1, 256, smem, s>>>(n_orb, dg, dw, dv, nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(occ_out, dw, sizeof(double) * n_orb, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && vecs_out) e = cudaMemcpyAsync(vecs_out, dv, sizeof(double) * nn, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dg); cudaFree(dw); if (dv) cudaFree(dv);
+  if (e != cudaSuccess) return fail(-100, "CUDA error %s in ppq_natural_occupations", cudaGetErrorString(e));
+  return 0;
 }
 
 int pq_solve_batched(int n_sys, const int* n_pairs, const int* const* occ_of_pair,
@@ -1800,8 +2043,10 @@ int pq_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
 // workspace, for callers that must not allocate device memory.
 namespace {
 
+// The array is sized for the stated maximum of 12 pairs: the intermediates
+// grow as n_pairs^2 and take 4.4 MiB at 12 pairs; 8 MiB keeps headroom.
 constexpr int kStaticMaxPairs = 12;
-constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB on every device that loads the library
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB on every device that loads the library
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 std::map<int, unsigned char*> g_static_addr;  // device address of g_static_scratch, per device
 
@@ -1884,26 +2129,33 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
   if (cv.off > kStaticScratchBytes)
     return fail(-6, "pq_residual_static: %zu bytes of scratch needed, %zu available", cv.off,
                 kStaticScratchBytes);
-  // the array keeps the previous call's contents: clear the part this call uses
-  CK(cudaMemsetAsync(base, 0, cv.off, s));
-  CK(cudaMemcpyAsync(w.occ, occ_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(w.vir, vir_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(w.lab, lab.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(w.work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice, s));
-  Problem P{N, n, h, eri};
-  if ((rc = stage(&w, P, s))) return rc;
-  w.t = const_cast<double*>(t);  // read only by the residual kernels
-  w.r = r;
-  // launched directly on any stream: capturing a graph here would instantiate
-  // (allocate) one per call
-  if (precision) {
-    if ((rc = tuned_mt<float>(&w, N, s, &w.mt[1]))) return rc;
-    rc = residual<float>(&w, N, s);
-  } else {
-    if ((rc = tuned_mt<double>(&w, N, s, &w.mt[0]))) return rc;
-    rc = residual<double>(&w, N, s);
+  // From the first enqueue on, every failure waits for the work already queued
+  // on the stream before returning, so that no kernel of this call still uses
+  // the array when the next call clears it.
+  auto enqueue = [&]() -> int {
+    // the array keeps the previous call's contents: clear the part this call uses
+    CK(cudaMemsetAsync(base, 0, cv.off, s));
+    CK(cudaMemcpyAsync(w.occ, occ_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.vir, vir_of_pair, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.lab, lab.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.work9, wk.data(), sizeof(int) * wk.size(), cudaMemcpyHostToDevice, s));
+    Problem P{N, n, h, eri};
+    int rc2 = stage(&w, P, s);
+    if (rc2) return rc2;
+    w.t = const_cast<double*>(t);  // read only by the residual kernels
+    w.r = r;
+    // launched directly on any stream (capturing a graph here would
+    // instantiate, i.e. allocate, one per call) with the fixed micro-tile
+    // ceil(N / 16) of the SIMT quartic kernel: no autotuning, no events
+    int mt = std::max(1, (N + 15) / 16);
+    w.mt[0] = w.mt[1] = mt;
+    return precision ? residual<float>(&w, N, s) : residual<double>(&w, N, s);
+  };
+  rc = enqueue();
+  if (rc) {
+    cudaStreamSynchronize(s);
+    return rc;
   }
-  if (rc) return rc;
   k_rowsum<<<1, 256, 0, s>>>(1, 0, w.part, N, w.esite, w.epair, w.scal);
   double e = 0.0;
   CK(cudaMemcpyAsync(&e, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -30,18 +30,38 @@ __device__ __forceinline__ R unpack_sign(int32_t e) { return (e & 1) ? R(-1) : R
 // f_pq = h_pq + sum_i [2 (pq|ii) - (pi|iq)];  h'_pq keeps the mean field of the
 // occupied orbitals whose label lies outside {L(p), L(q)} (those integrals are
 // three-label ones, dropped by the two-label truncation).
-__global__ void k_fock(int n, int N, const double* __restrict__ h, const double* __restrict__ eri,
+// two-electron integrals (pq|rs): the dense n^4 array, or a three-index
+// factorisation (pq|rs) = sum_Q B[pq][Q] B[rs][Q] (Cholesky vectors; the
+// paper builds its integral blocks from such B matrices, Implementation section)
+struct EriSrc {
+  const double* eri;  // dense, row-major (pq|rs); nullptr for the factorised form
+  const double* Bt;   // [n * n][naux]
+  int naux;
+  int n;
+  __device__ __forceinline__ double operator()(int p, int q, int r, int s) const {
+    if (eri) {
+      size_t n1 = n;
+      return eri[((p * n1 + q) * n1 + r) * n1 + s];
+    }
+    const double* a = Bt + ((size_t)p * n + q) * naux;
+    const double* b = Bt + ((size_t)r * n + s) * naux;
+    double v = 0.0;
+    for (int Q = 0; Q < naux; ++Q) v += a[Q] * b[Q];
+    return v;
+  }
+};
+
+__global__ void k_fock(int n, int N, const double* __restrict__ h, EriSrc E,
                        const int* __restrict__ occ, const int* __restrict__ lab,
                        double* __restrict__ f, double* __restrict__ hp) {
   int pq = blockIdx.x * blockDim.x + threadIdx.x;
   if (pq >= n * n) return;
   int p = pq / n, q = pq % n;
-  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
   double mf = 0.0, mfl = 0.0;
   int lp = lab[p], lq = lab[q];
   for (int k = 0; k < N; ++k) {
-    size_t i = occ[k];
-    double v = 2.0 * eri[p * n3 + q * n2 + i * n1 + i] - eri[p * n3 + i * n2 + i * n1 + q];
+    int i = occ[k];
+    double v = 2.0 * E(p, q, i, i) - E(p, i, i, q);
     mf += v;
     if (k == lp || k == lq) mfl += v;
   }
@@ -51,11 +71,11 @@ __global__ void k_fock(int n, int N, const double* __restrict__ h, const double*
 
 // gather the per-site (20) and per-ordered-pair (232) integrals
 template <typename R>
-__global__ void k_gather(int n, int N, const double* __restrict__ hp, const double* __restrict__ eri,
+__global__ void k_gather(int n, int N, const double* __restrict__ hp, EriSrc E,
                          const int* __restrict__ occ, const int* __restrict__ vir,
                          R* __restrict__ g1, R* __restrict__ g2) {
   size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t n1 = n, n2 = n1 * n, n3 = n2 * n;
+  size_t n1 = n;
   size_t tot2 = (size_t)N * N * PPQ_NG2;
   if (tid < tot2) {
     int j = tid % PPQ_NG2;
@@ -66,7 +86,7 @@ __global__ void k_gather(int n, int N, const double* __restrict__ hp, const doub
     int o[4] = {occ[X], vir[X], occ[W], vir[W]};
     double v;
     if (k[0] == 0) v = hp[o[k[1]] * n1 + o[k[2]]];
-    else v = eri[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]];
+    else v = E(o[k[1]], o[k[2]], o[k[3]], o[k[4]]);
     g2[tid] = R(v);
     return;
   }
@@ -77,7 +97,7 @@ __global__ void k_gather(int n, int N, const double* __restrict__ hp, const doub
     int o[2] = {occ[X], vir[X]};
     double v;
     if (k[0] == 0) v = hp[o[k[1]] * n1 + o[k[2]]];
-    else v = eri[o[k[1]] * n3 + o[k[2]] * n2 + o[k[3]] * n1 + o[k[4]]];
+    else v = E(o[k[1]], o[k[2]], o[k[3]], o[k[4]]);
     g1[tid] = R(v);
   }
 }

@@ -88,7 +88,7 @@ def test_binding_checks_buffers_before_any_launch():
         ppq.pq_residual(occ, vir, h, eri, np.zeros((L, 2))[:, 0])
     with pytest.raises(ppq.PPQError, match="r holds"):
         ppq.pq_residual(occ, vir, h, eri, np.zeros(L), np.zeros(3))
-    with pytest.raises(ppq.PPQError, match="CUDA tensor"):
+    with pytest.raises(ppq.PPQError, match="device pointers"):
         ppq.pq_residual_static(occ, vir, h, eri, np.zeros(L), np.zeros(L))
     with pytest.raises(ppq.PPQError, match="t_out holds"):
         ppq.ph_solve(occ, vir, h, eri, t_out=np.zeros(ppq.amp_count(N, 3) - 1))

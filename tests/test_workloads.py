@@ -55,3 +55,17 @@ def test_acene_geometry_hueckel_spectra():
         if n == 2:
             want = want + [-w for w in want]
         assert np.allclose(ev, np.sort(want), atol=1e-12)
+
+
+def test_cholesky_factors_reproduce_integrals():
+    # the three-index inputs of pq_solve_cd: exact for PPP (one vector per
+    # site), within the pivot threshold for the Gaussian H-chain integrals
+    from workloads import ppp_cholesky_vectors, cholesky_vectors
+    H = build_ppp('polyene', 8)
+    B = ppp_cholesky_vectors(H)
+    assert B.shape == (8, 8, 8)
+    assert np.abs(np.einsum('qab,qcd->abcd', B, B) - H.eri).max() < 1e-14
+    Hh = build_hchain(8, 1.5)
+    B2 = cholesky_vectors(Hh.eri, 1e-12)
+    assert B2.shape[0] < Hh.n_orb ** 2
+    assert np.abs(np.einsum('qab,qcd->abcd', B2, B2) - Hh.eri).max() < 1e-10

@@ -2,7 +2,7 @@
 
 Some callers cannot allocate device memory, for example code inside another
 framework's memory pool or under a fixed memory budget. pq_residual_static
-serves them: it uses a fixed 16 MiB device array instead of the cached
+serves them: it uses a fixed 8 MiB device array instead of the cached
 workspace. This test calls it through the C ABI twice in a row, with
 different amplitudes, and checks each result against pq_residual within the
 FP64 parity tolerance used elsewhere. The second call catches state left in
@@ -23,13 +23,13 @@ from workloads import build_ppp, build_hchain
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_static_residual_matches_allocating_entry_point_twice(precision):
-    for H in (build_ppp('polyene', 8), build_hchain(12, 1.7)):
+    # 4, 6 and 12 pairs (the stated maximum)
+    for H in (build_ppp('polyene', 8), build_hchain(12, 1.7), build_ppp('polyene', 24)):
         h = torch.from_numpy(H.h).cuda()
         eri = torch.from_numpy(H.eri).cuda()
         L = ppq.amp_count(H.n_pairs)
         for seed in (1, 2):
             t = torch.from_numpy(np.random.default_rng(seed).uniform(-0.1, 0.1, L)).cuda()
-            # keep the two stored copies of each pair amplitude consistent
             r_ref, e_ref = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, h, eri, t,
                                            precision=precision)
             r = torch.zeros_like(t)

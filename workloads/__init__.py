@@ -8,11 +8,13 @@ it without sharing any of the method's code.
 """
 from .ppp import polyene_geometry, acene_geometry, ppp_site_hamiltonian
 from .hchain import hchain_ao_integrals
-from .scf import rhf, mo_integrals, pair_orbitals, Hamiltonian, build_ppp, build_hchain, ppp_eri_device
+from .scf import (rhf, mo_integrals, pair_orbitals, Hamiltonian, build_ppp, build_hchain, ppp_eri_device,
+                  ppp_cholesky_vectors, cholesky_vectors)
 from .rng import random_pair_amplitude_seed
 
 __all__ = [
     "polyene_geometry", "acene_geometry", "ppp_site_hamiltonian",
     "hchain_ao_integrals", "rhf", "mo_integrals", "pair_orbitals",
-    "Hamiltonian", "build_ppp", "build_hchain", "random_pair_amplitude_seed",
+    "Hamiltonian", "build_ppp", "build_hchain", "random_pair_amplitude_seed", "ppp_cholesky_vectors",
+    "cholesky_vectors",
 ]

@@ -156,6 +156,37 @@ def build_ppp(kind, size, beta_ev=-2.4, u_ev=11.26, with_eri=True, orbitals="can
     return H
 
 
+def ppp_cholesky_vectors(H):
+    """Three-index factors B[Q, p, q] of a PPP workload with (pq|rs) =
+    sum_Q B[Q,p,q] B[Q,r,s]: the site matrix gamma (zero differential overlap,
+    positive definite for the Ohno form at these geometries) factored as
+    gamma = L L^T, B[Q] = C^T diag(L[:, Q]) C -- one vector per site, exact."""
+    L = np.linalg.cholesky(H.gamma_site)
+    return np.ascontiguousarray(np.einsum('aq,ap,ar->qpr', L, H.C, H.C))
+
+
+def cholesky_vectors(eri, tol=1e-12):
+    """Pivoted (incomplete) Cholesky factors of the (pq),(rs) supermatrix of a
+    real 8-fold symmetric (pq|rs): B[Q, p, q] with |(pq|rs) - sum_Q B B| <= tol
+    on the diagonal, stopping once the largest remaining diagonal is below tol."""
+    n = eri.shape[0]
+    M = eri.reshape(n * n, n * n)
+    d = np.diag(M).copy()
+    vecs = []
+    while True:
+        k = int(np.argmax(d))
+        if d[k] <= tol:
+            break
+        v = M[:, k].copy()
+        for u in vecs:
+            v -= u * u[k]
+        v /= np.sqrt(d[k])
+        vecs.append(v)
+        d -= v * v
+        d[k] = 0.0
+    return np.ascontiguousarray(np.array(vecs).reshape(len(vecs), n, n))
+
+
 def build_hchain(n_atoms, spacing_angstrom, orbitals="canonical", bond_bohr=None):
     """orbitals: 'canonical' (Fig. 1 energy pairing) or 'local' (Boys-localised
     occupied and virtual orbitals paired by nearest centroid, the stand-in
