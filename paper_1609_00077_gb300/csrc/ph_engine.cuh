@@ -225,10 +225,18 @@ __global__ void k_gather_int(int P, int p0, int nsub, int k, int nkey, const int
   vl[i] = v;
 }
 
+// psi(ref) = psi_minus(ref) = 1, and E_0 = <ref|H|ref> of every subset of the
+// chunk (FP64, from the gathered integrals)
 template <typename R>
-__global__ void k_set_ref(int P, R* __restrict__ a, R* __restrict__ b) {
+__global__ void k_set_ref(int P, R* __restrict__ a, R* __restrict__ b, int ne0, const int16_t* __restrict__ e0key,
+                          const double* __restrict__ e0c, const R* __restrict__ vl, double* __restrict__ e0) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < P) { a[p] = R(1); b[p] = R(1); }
+  if (p >= P) return;
+  a[p] = R(1);
+  b[p] = R(1);
+  double s = 0.0;
+  for (int e = 0; e < ne0; ++e) s += e0c[e] * double(vl[(size_t)e0key[e] * P + p]);
+  e0[p] = s;
 }
 
 // One level of psi = exp(+-T)|ref>: warp per state, lane per J subsets
@@ -277,8 +285,7 @@ template <typename R, int J>
 __global__ void __launch_bounds__(256) k_phi(int P, int nout, const int* __restrict__ hptr,
                                              const unsigned long long* __restrict__ hent,
                                              const int* __restrict__ dptr, const int16_t* __restrict__ dkey,
-                                             const double* __restrict__ dc, int ne0,
-                                             const int16_t* __restrict__ e0key, const double* __restrict__ e0c,
+                                             const double* __restrict__ dc, const double* __restrict__ e0,
                                              const R* __restrict__ vl, const R* __restrict__ psi,
                                              const int* __restrict__ out_state, R* __restrict__ phi) {
   int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -286,12 +293,7 @@ __global__ void __launch_bounds__(256) k_phi(int P, int nout, const int* __restr
   int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
   double dg[J];
 #pragma unroll
-  for (int j = 0; j < J; ++j) dg[j] = 0.0;
-  for (int e = 0; e < ne0; ++e) {
-    const R* v = vl + (size_t)e0key[e] * P + p;
-#pragma unroll
-    for (int j = 0; j < J; ++j) dg[j] -= e0c[e] * double(v[32 * j]);
-  }
+  for (int j = 0; j < J; ++j) dg[j] = -e0[p + 32 * j];
   int d1 = dptr[o + 1];
   for (int e = dptr[o]; e < d1; ++e) {
     const R* v = vl + (size_t)dkey[e] * P + p;
@@ -554,6 +556,8 @@ struct Ctx {
   // local-problem buffers
   size_t cap_psi = 0, cap_out = 0, cap_phi = 0, cap_tl = 0, cap_vl = 0;
   void *psi = nullptr, *psim = nullptr, *phi = nullptr, *tl = nullptr, *vl = nullptr;
+  double* e0loc = nullptr;  // E_0 of every subset of the chunk
+  size_t cap_e0 = 0;
   double* Rloc[kMaxSites + 1] = {};
   double* Eloc[kMaxSites + 1] = {};
   size_t cap_R[kMaxSites + 1] = {}, cap_E[kMaxSites + 1] = {};
@@ -760,8 +764,8 @@ int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStre
                 T->olvl_ent[lv] * (8.0 + 2 * es * nv) + (s1 - s0) * es * nv, 2.0 * T->olvl_ent[lv] * nv);
   }
   dim3 go((unsigned)((T->nout + 7) / 8), gy);
-  k_phi<R, J><<<go, 256, 0, s>>>(P, T->nout, T->h_ptr, T->hent, T->d_ptr, T->d_key, T->d_c, T->ne0, T->e0_key,
-                                 T->e0_cd, vl, psi, T->out_state, phi);
+  k_phi<R, J><<<go, 256, 0, s>>>(P, T->nout, T->h_ptr, T->hent, T->d_ptr, T->d_key, T->d_c, c->e0loc, vl, psi,
+                                 T->out_state, phi);
   g_prof.done("ph::k_phi (<kappa|H|psi>)", s,
               T->nh * 8.0 + (T->nh + T->nruns + T->nd) * es * nv + T->nout * 2 * es * nv,
               2.0 * (T->nh + T->nruns + T->nd) * nv);
@@ -796,6 +800,7 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
     if ((rc = grow_buf(&c->phi, &c->cap_phi, (size_t)T->nout * P * sizeof(R)))) return rc;
     if ((rc = grow_buf(&c->tl, &c->cap_tl, (size_t)T->nslot * P * sizeof(R)))) return rc;
     if ((rc = grow_buf(&c->vl, &c->cap_vl, (size_t)T->nkey * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf((void**)&c->e0loc, &c->cap_e0, (size_t)P * sizeof(double)))) return rc;
     if ((rc = grow_buf((void**)&c->Rloc[k], &c->cap_R[k], (size_t)T->nout * nsub * sizeof(double)))) return rc;
     if ((rc = grow_buf((void**)&c->Eloc[k], &c->cap_E[k], (size_t)nsub * sizeof(double)))) return rc;
     R* psi = (R*)c->psi;
@@ -809,7 +814,7 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
                                                                    c->subs[k], N, t, tl);
       k_gather_int<R><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
                                                                    c->subs[k], N, c->G1, c->G2, c->G3, c->G4, vl);
-      k_set_ref<R><<<(P + 127) / 128, 128, 0, s>>>(P, psi, psim);
+      k_set_ref<R><<<(P + 127) / 128, 128, 0, s>>>(P, psi, psim, T->ne0, T->e0_key, T->e0_cd, vl, c->e0loc);
       c->n_launches += 3;
       g_prof.done("ph::gather (amplitudes, integrals)", s, (double)(T->nslot + T->nkey) * P * (sizeof(R) + 8.0));
       if (J == 4) rc = local_problem<R, 4>(c, T, P, p0, nsub, k, s);

@@ -1135,55 +1135,73 @@ __global__ void k_axpy_to(size_t L, const double* __restrict__ a, const double* 
 
 // Pulay DIIS on the device: B (kDiis x kDiis, by slot id) gains the new row
 // from dots[1..m]; the bordered system [B -1; -1 0][c; l] = [0; -1] over the
-// active slots (order[0..m), newest last) is solved in FP64 by one thread
-// (error block scaled by its largest diagonal, which leaves c unchanged);
+// active slots (order[0..m), newest last) is solved in FP64 by one warp (a
+// lane per row, partial pivoting; back-substitution by lane 0), the error
+// block scaled by its largest diagonal, which leaves c unchanged;
 // coef = c, or the newest iterate alone if the system is singular or
 // extrapolation is off.
-__global__ void k_diis_solve(int m, const int* __restrict__ order, int inew, const double* __restrict__ dots,
-                             double* __restrict__ B, int ldb, int extrap, double* __restrict__ coef) {
-  if (threadIdx.x || blockIdx.x) return;
-  for (int j = 0; j < m; ++j) {
-    double d = dots[1 + j];
-    B[order[j] * ldb + inew] = d;
-    B[inew * ldb + order[j]] = d;
+__global__ void __launch_bounds__(32) k_diis_solve(int m, const int* __restrict__ order, int inew,
+                                                   const double* __restrict__ dots, double* __restrict__ B, int ldb,
+                                                   int extrap, double* __restrict__ coef) {
+  // one warp: lane r owns row r of the bordered system (at most 17 rows)
+  __shared__ double A[17][19];
+  __shared__ int ord[16];
+  const int lane = threadIdx.x;
+  if (lane < m) ord[lane] = order[lane];
+  __syncwarp();
+  if (lane < m) {
+    double d = dots[1 + lane];
+    B[ord[lane] * ldb + inew] = d;
+    B[inew * ldb + ord[lane]] = d;
   }
-  for (int j = 0; j < m; ++j) coef[j] = j == m - 1 ? 1.0 : 0.0;
+  __threadfence_block();
+  __syncwarp();
+  if (lane < m) coef[lane] = lane == m - 1 ? 1.0 : 0.0;
   if (!extrap || m < 2) return;
   const int nn = m + 1;
-  double A[17][18];
-  double sc = 0.0;
-  for (int i = 0; i < m; ++i) sc = fmax(sc, fabs(B[order[i] * ldb + order[i]]));
-  if (!(sc > 0.0)) sc = 1.0;
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i][j] = B[order[i] * ldb + order[j]] / sc;
-    A[i][m] = -1.0;
-    A[i][nn] = 0.0;
+  double dd = lane < m ? fabs(B[ord[lane] * ldb + ord[lane]]) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) dd = fmax(dd, __shfl_xor_sync(0xffffffffu, dd, o));
+  const double sc = dd > 0.0 ? dd : 1.0;
+  if (lane < nn) {
+    for (int j = 0; j < m; ++j) A[lane][j] = lane < m ? B[ord[lane] * ldb + ord[j]] / sc : -1.0;
+    A[lane][m] = lane < m ? -1.0 : 0.0;
+    A[lane][nn] = lane < m ? 0.0 : -1.0;
   }
-  for (int j = 0; j < m; ++j) A[m][j] = -1.0;
-  A[m][m] = 0.0;
-  A[m][nn] = -1.0;
+  __syncwarp();
   for (int col = 0; col < nn; ++col) {
-    int piv = col;
-    for (int r2 = col + 1; r2 < nn; ++r2)
-      if (fabs(A[r2][col]) > fabs(A[piv][col])) piv = r2;
-    if (fabs(A[piv][col]) < 1e-300) return;
-    if (piv != col)
-      for (int q = 0; q <= nn; ++q) { double x = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = x; }
-    for (int r2 = col + 1; r2 < nn; ++r2) {
-      double f = A[r2][col] / A[col][col];
-      for (int q = col; q <= nn; ++q) A[r2][q] -= f * A[col][q];
+    // partial pivot: the first row of largest |A[r][col]|, r >= col
+    double v = (lane >= col && lane < nn) ? fabs(A[lane][col]) : -1.0;
+    int idx = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+      double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
     }
+    if (fabs(A[idx][col]) < 1e-300) return;  // singular: keep the newest iterate
+    if (idx != col && lane <= nn) {
+      double x = A[col][lane];
+      A[col][lane] = A[idx][lane];
+      A[idx][lane] = x;
+    }
+    __syncwarp();
+    if (lane > col && lane < nn) {
+      double f = A[lane][col] / A[col][col];
+      for (int q = col; q <= nn; ++q) A[lane][q] -= f * A[col][q];
+    }
+    __syncwarp();
   }
-  double x[17];
-  for (int r2 = nn - 1; r2 >= 0; --r2) {
-    double s = A[r2][nn];
-    for (int q = r2 + 1; q < nn; ++q) s -= A[r2][q] * x[q];
-    x[r2] = s / A[r2][r2];
+  if (lane == 0) {
+    double x[17];
+    for (int r2 = nn - 1; r2 >= 0; --r2) {
+      double s = A[r2][nn];
+      for (int q = r2 + 1; q < nn; ++q) s -= A[r2][q] * x[q];
+      x[r2] = s / A[r2][r2];
+    }
+    bool finite = true;
+    for (int j = 0; j < m; ++j) finite = finite && isfinite(x[j]);
+    if (finite)
+      for (int j = 0; j < m; ++j) coef[j] = x[j];
   }
-  bool finite = true;
-  for (int j = 0; j < m; ++j) finite = finite && isfinite(x[j]);
-  if (finite)
-    for (int j = 0; j < m; ++j) coef[j] = x[j];
 }
 
 __global__ void k_extrap(size_t L, int m, const double* __restrict__ coef, const double* __restrict__ slots,
