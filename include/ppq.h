@@ -32,7 +32,8 @@
  * Conventions of every entry point
  *   - return 0 on success; < 0 on invalid arguments (nothing written, message
  *     in ppq_last_error); > 0 numerical status (1 not converged within
- *     max_iter, 2 diverged, 3 non-finite input) with outputs written;
+ *     max_iter, 2 diverged, 3 non-finite input) with outputs written; -9 when
+ *     a tensor-core kernel's bounded wait timed out (see ppq_wait_selftest);
  *   - n_pairs >= 2; occ_of_pair / vir_of_pair are HOST int32 arrays of length
  *     n_pairs that together list every one of the 2 n_pairs active orbitals
  *     exactly once;
@@ -346,6 +347,16 @@ int pq_residual_static(int n_pairs, const int* occ_of_pair, const int* vir_of_pa
    columns (n_orb x n_orb, row-major).  n_orb <= 160 (<= 120 with vecs_out).
    Synchronous on `stream`.  Returns 0 or < 0 on invalid arguments. */
 int ppq_natural_occupations(int n_orb, const double* gamma, double* occ_out, double* vecs_out, void* stream);
+
+/* Self-test of the bounded waits (library housekeeping; the paper has no
+   counterpart).  The tensor-core kernels bound every mbarrier wait (about 1 s);
+   on a timeout they stop issuing work, drain what they issued, flag the error
+   and poison their output, and the solvers then return -9 with a message
+   instead of a number.  This call runs the same bounded wait on a barrier
+   that nothing arrives on, with a limit of `cycles` clock cycles (1 .. 4e9),
+   and sets *timed_out = 1 when the wait ran out (the expected outcome); no
+   copy, MMA or tensor memory is involved.  Returns 0, or < 0 on errors. */
+int ppq_wait_selftest(long long cycles, int* timed_out, void* stream);
 
 /* Free the cached workspace of the current device (library housekeeping;
    the paper has no counterpart).  Returns 0. */

@@ -71,6 +71,7 @@ def lib():
         L.pq_solve_cd.argtypes = [I, P, P, P, P, I, D, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(Info), P]
         L.ph_solve_cd.argtypes = L.pq_solve_cd.argtypes
         L.ppq_natural_occupations.argtypes = [I, P, P, P, P]
+        L.ppq_wait_selftest.argtypes = [ctypes.c_longlong, P, P]
         L.ph_tables_counts.argtypes = [I, I, I, P]
         L.ph_tables_copy.argtypes = [I, I, I, I, P]
         L.ppq_profile_count.argtypes = []
@@ -87,7 +88,8 @@ def lib():
                   L.pq_lagrangian_gradient,
                   L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan, L.ph_residual,
                   L.ph_tables_counts, L.ph_tables_copy, L.ppq_profile_count, L.ppq_profile_entry,
-                  L.ppq_subset_residual, L.pq_solve_cd, L.ph_solve_cd, L.ppq_natural_occupations):
+                  L.ppq_subset_residual, L.pq_solve_cd, L.ph_solve_cd, L.ppq_natural_occupations,
+                  L.ppq_wait_selftest):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -98,7 +100,7 @@ EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual"
             "pq_lagrangian_gradient", "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error",
             "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy", "ppq_profile_count",
             "ppq_profile_entry", "ppq_subset_residual", "pq_solve_cd", "ph_solve_cd",
-            "ppq_natural_occupations"]
+            "ppq_natural_occupations", "ppq_wait_selftest"]
 
 
 def _ptr(x):
@@ -385,6 +387,15 @@ def natural_occupations(gamma, vectors=False, stream=None):
     _check(lib().ppq_natural_occupations(n, _ptr(gamma), occ.ctypes.data, None if vec is None else vec.ctypes.data,
                                          _stream(stream)), "ppq_natural_occupations")
     return (occ, vec) if vectors else occ
+
+
+def wait_selftest(cycles=100000, stream=None):
+    """Run the bounded-wait self-test (a barrier nothing arrives on); True when
+    the wait ran out after `cycles` clock cycles, as it must."""
+    flag = ctypes.c_int(0)
+    _check(lib().ppq_wait_selftest(int(cycles), ctypes.cast(ctypes.pointer(flag), ctypes.c_void_p),
+                                   _stream(stream)), "ppq_wait_selftest")
+    return bool(flag.value)
 
 
 def pq_solve_batched(systems, stream=None, with_amplitudes=False, **opts):

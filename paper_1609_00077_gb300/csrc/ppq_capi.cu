@@ -304,7 +304,7 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->part, sizeof(double) * kRedBlocks * (kDiisMax + 2));
   AL(w->scal, sizeof(double) * (kDiisMax + 4)); AL(w->coef, sizeof(double) * kDiisMax);
   AL(w->Bdiis, sizeof(double) * kDiisMax * kDiisMax);
-  AL(w->ok, sizeof(int)); AL(w->order, sizeof(int) * kDiisMax);
+  AL(w->ok, sizeof(int) * 4); AL(w->order, sizeof(int) * kDiisMax);
   if (dc > 0) {
     AL(w->slot_t, sizeof(double) * L * dc);
     AL(w->slot_e, sizeof(double) * L * dc);
@@ -402,6 +402,19 @@ __global__ void k_rowsum(int nb, int rows, const double* __restrict__ part, int 
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) e += 0.5 * epair[i];
   e = ppq::block_sum(e, red);
   if (threadIdx.x == 0) out[rows] = e;
+}
+
+// The tensor-core quartic kernels bound every wait; on a timeout they stop,
+// drain their copies and MMAs, flag tc_err and poison the residual with a NaN.
+// After the stream has synchronised, the host reads the flag (copied beside
+// the norm) and turns it into an error with its cause; the flag is cleared so
+// the next call starts clean.
+int check_tc_flag(Workspace* w, int flag, cudaStream_t s) {
+  if (!flag) return 0;
+  cudaMemsetAsync(w->tc_err, 0, sizeof(int), s);
+  cudaStreamSynchronize(s);
+  return fail(-9, "a tensor-core kernel's bounded wait timed out (about 1 s); the residual was poisoned and "
+                  "the solve stopped; the device context is intact");
 }
 
 struct Problem {
@@ -1250,8 +1263,10 @@ struct Solver {
     k_multidot<<<g, 256, 0, s>>>(L, N, w->r, 0, w->slot_e, L, w->order, 0, w->part);
     k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
     CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(w->host + 60, w->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
     CK(cudaStreamSynchronize(s));
+    if (int rc2 = check_tc_flag(w, *(int*)(w->host + 60), s)) return rc2;
     w->n_launches += 2;
     account();
     evals++;
@@ -1519,7 +1534,9 @@ int pq_residual(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
   k_rowsum<<<1, 256, 0, s>>>(1, 0, w->part, N, w->esite, w->epair, w->scal);
   if ((rc = copy_amps(r, w->r, L, s))) return rc;
   CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(w->host + 60, w->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if ((rc = check_tc_flag(w, *(int*)(w->host + 60), s))) return rc;
   if (e_corr) *e_corr = w->host[0];
   return 0;
 }
@@ -1861,6 +1878,53 @@ int ppq_natural_occupations(int n_orb, const double* gamma, double* occ_out, dou
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(dg); cudaFree(dw); if (dv) cudaFree(dv);
   if (e != cudaSuccess) return fail(-100, "CUDA error %s in ppq_natural_occupations", cudaGetErrorString(e));
+  return 0;
+}
+
+// Self-test of the bounded mbarrier wait used by the tensor-core kernels: one
+// CTA initialises a barrier that expects one arrival, nobody arrives, and the
+// wait gives up after `cycles` clock cycles and reports it.  No copy, MMA or
+// tensor memory is involved, so the timeout leaves nothing in flight.
+__global__ void k_wait_selftest(long long cycles, int* __restrict__ out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    ppq::tc::mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  bool done = false;
+  if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    while (!(done = ppq::tc::mbar_try(&bar, 0)))
+      if (clock64() - t0 > cycles) { abort_flag = 1; break; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = abort_flag;    // 1: the wait ran out
+    out[1] = done ? 1 : 0;  // 1: the phase completed (it must not)
+  }
+}
+
+int ppq_wait_selftest(long long cycles, int* timed_out, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cycles < 1 || cycles > 4000000000LL) return fail(-2, "cycles must be in 1 .. 4e9");
+  int dev;
+  CK(cudaGetDevice(&dev));
+  Workspace*& w = g_ws[dev];
+  if (!w) w = new Workspace();
+  int rc = grow(w, 2, 1);
+  if (rc) return rc;
+  k_wait_selftest<<<1, 32, 0, s>>>(cycles, w->ok);
+  CK(cudaGetLastError());
+  int host[2] = {0, 0};
+  CK(cudaMemcpyAsync(host, w->ok, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (host[1]) return fail(-100, "wait self-test: a barrier phase completed without an arrival");
+  if (timed_out) *timed_out = host[0];
   return 0;
 }
 

@@ -145,3 +145,18 @@ def test_warm_start_from_converged_amplitudes():
     rc2, e2, t2, info2 = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri),
                                       H.e_const, t_in=t)
     assert rc2 == 0 and info2['iters'] <= 10 and abs(e2 - e) < 1e-10
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    # the bounded mbarrier wait of the tensor-core kernels, on a barrier that
+    # nothing arrives on: it must give up (a short limit, then a 0.1 s one),
+    # report it, and leave the context usable: a residual afterwards is
+    # bit-identical to one before
+    H, res, lm, n_amp = system("C8H10")
+    t = np.random.default_rng(5).uniform(-0.1, 0.1, n_amp)
+    tl = dev(lm.to_layout(t))
+    r1, e1 = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), tl)
+    assert ppq.wait_selftest(1000) is True
+    assert ppq.wait_selftest(200000000) is True
+    r2, e2 = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), tl)
+    assert torch.equal(r1, r2) and e1 == e2
