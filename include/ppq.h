@@ -230,11 +230,12 @@ int ppq_subset_residual(int K, int K_H, int n_pairs, const int* occ_of_pair, con
    Hamiltonian rows and the back-substitution.  The paper has no counterpart:
    this is how the library lays out the exact evaluation, exported so that a
    CPU check can interpret the tables against the oracle.  ph_tables_counts
-   fills counts[0..25] (counts must hold 32) with the element count of each
-   table; ph_tables_copy copies table `which` (0..25) into dst (host memory of
+   fills counts[0..46] (counts must hold 48) with the element count of each
+   table; ph_tables_copy copies table `which` (0..46) into dst (host memory of
    counts[which] elements: uint32 codes; int32 pointers, indices and
-   descriptors; int16 slot / key fields; double coefficients).  No device
-   call.  Returns 0, or < 0 for k outside 1..6 or K, K_H outside 1..3. */
+   descriptors; int16 slot / key fields; double coefficients; 26..46 are the
+   transposed (adjoint) tables of the Lambda / gradient pass, with uint64 or
+   uint32 packed entries).  No device call.  Returns 0, or < 0 for k outside 1..6 or K, K_H outside 1..3. */
 int ph_tables_counts(int k, int K, int K_H, int64_t* counts);
 int ph_tables_copy(int k, int K, int K_H, int which, void* dst);
 

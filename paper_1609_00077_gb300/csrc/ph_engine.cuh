@@ -27,7 +27,9 @@ int ph_tables_counts(int k, int K, int K_H, int64_t* counts) {
   int rc;
   const ph::Tables* T = ph::host_tables(k, K, K_H, &rc);
   if (!T) return fail(-1, "ph_tables: cannot build tables for k=%d K=%d K_H=%d (%d)", k, K, K_H, rc);
-  int64_t c[32] = {(int64_t)T->code.size(), (int64_t)T->lvl_ptr.size(), (int64_t)T->ent_ptr.size(),
+  const ph::AdjTables* A = ph::host_adjoint(k, K, K_H, &rc);
+  if (!A) return fail(-1, "ph_tables: cannot build adjoint tables for k=%d (%d)", k, rc);
+  int64_t c[48] = {(int64_t)T->code.size(), (int64_t)T->lvl_ptr.size(), (int64_t)T->ent_ptr.size(),
                    (int64_t)T->ent_sub.size(), (int64_t)T->ent_slot.size(), (int64_t)T->slot_desc.size(),
                    (int64_t)T->out_state.size(), (int64_t)T->out_desc.size(), (int64_t)T->olvl_ptr.size(),
                    (int64_t)T->olvl_order.size(), (int64_t)T->oent_ptr.size(), (int64_t)T->oent_sub.size(),
@@ -35,7 +37,14 @@ int ph_tables_counts(int k, int K, int K_H, int64_t* counts) {
                    (int64_t)T->h_s.size(), (int64_t)T->h_key.size(), (int64_t)T->h_c.size(),
                    (int64_t)T->e0_key.size(), (int64_t)T->e0_c.size(), (int64_t)T->b_ptr.size(),
                    (int64_t)T->b_k.size(), (int64_t)T->b_w.size(), (int64_t)T->d_ptr.size(),
-                   (int64_t)T->d_key.size(), (int64_t)T->d_c.size(), 0, 0, 0, 0, 0};
+                   (int64_t)T->d_key.size(), (int64_t)T->d_c.size(),
+                   (int64_t)A->bs_ptr.size(), (int64_t)A->bs_ent.size(), (int64_t)A->bl_ptr.size(),
+                   (int64_t)A->bl_ent.size(), (int64_t)A->obs_ptr.size(), (int64_t)A->obs_ent.size(),
+                   (int64_t)A->obl_ptr.size(), (int64_t)A->obl_ent.size(), (int64_t)A->hs_ptr.size(),
+                   (int64_t)A->hs_ent.size(), (int64_t)A->hk_ptr.size(), (int64_t)A->hk_ent.size(),
+                   (int64_t)A->dk_ptr.size(), (int64_t)A->dk_out.size(), (int64_t)A->dk_c.size(),
+                   (int64_t)A->e0_by_key.size(), (int64_t)A->bk_ptr.size(), (int64_t)A->bk_ent.size(),
+                   (int64_t)A->bw_ptr.size(), (int64_t)A->bw_ent.size(), (int64_t)A->out_of_state.size(), 0};
   memcpy(counts, c, sizeof c);
   return 0;
 }
@@ -44,6 +53,8 @@ int ph_tables_copy(int k, int K, int K_H, int which, void* dst) {
   int rc;
   const ph::Tables* T = ph::host_tables(k, K, K_H, &rc);
   if (!T) return fail(-1, "ph_tables: cannot build tables for k=%d K=%d K_H=%d (%d)", k, K, K_H, rc);
+  const ph::AdjTables* A = ph::host_adjoint(k, K, K_H, &rc);
+  if (!A) return fail(-1, "ph_tables: cannot build adjoint tables for k=%d (%d)", k, rc);
   auto cp = [&](const auto& v) {
     memcpy(dst, v.data(), v.size() * sizeof(v[0]));
     return 0;
@@ -75,6 +86,27 @@ int ph_tables_copy(int k, int K, int K_H, int which, void* dst) {
     case 23: return cp(T->d_ptr);
     case 24: return cp(T->d_key);
     case 25: return cp(T->d_c);
+    case 26: return cp(A->bs_ptr);
+    case 27: return cp(A->bs_ent);
+    case 28: return cp(A->bl_ptr);
+    case 29: return cp(A->bl_ent);
+    case 30: return cp(A->obs_ptr);
+    case 31: return cp(A->obs_ent);
+    case 32: return cp(A->obl_ptr);
+    case 33: return cp(A->obl_ent);
+    case 34: return cp(A->hs_ptr);
+    case 35: return cp(A->hs_ent);
+    case 36: return cp(A->hk_ptr);
+    case 37: return cp(A->hk_ent);
+    case 38: return cp(A->dk_ptr);
+    case 39: return cp(A->dk_out);
+    case 40: return cp(A->dk_c);
+    case 41: return cp(A->e0_by_key);
+    case 42: return cp(A->bk_ptr);
+    case 43: return cp(A->bk_ent);
+    case 44: return cp(A->bw_ptr);
+    case 45: return cp(A->bw_ent);
+    case 46: return cp(A->out_of_state);
     default: return fail(-2, "ph_tables_copy: unknown table %d", which);
   }
 }

@@ -485,3 +485,164 @@ inline const Tables* host_tables(int k, int K, int KH, int* rc) {
 }
 
 }  // namespace ph
+
+namespace ph {
+
+// ------------------------------------------------------------ adjoint tables
+// The transposed forms of the tables, for the reverse pass of a local problem
+// (the Lambda equations and the energy gradient): every entry of the forward
+// tables appears once, grouped by the operand it is differentiated against.
+struct AdjTables {
+  // sector recursion psi(s) = sum sign t_c psi(sub): by sub -> (s, 2 slot + sign);
+  // by slot -> (s, sub, sign) packed s | sub << 20 | sign << 40
+  std::vector<int> bs_ptr;
+  std::vector<unsigned long long> bs_ent;
+  std::vector<int> bl_ptr;
+  std::vector<unsigned long long> bl_ent;
+  // the same for the output recursion (indices are output indices; bs grouped
+  // by output, in the level order of the outputs)
+  std::vector<int> obs_ptr;
+  std::vector<unsigned long long> obs_ent;
+  std::vector<int> obl_ptr;
+  std::vector<unsigned long long> obl_ent;
+  // Hamiltonian rows off the diagonal, by state s -> (kappa, key, coef) and by
+  // key -> (kappa, s, coef); coef in {+-1/2, +-1}: kappa | key << 13 |
+  // neg << 28 | half << 29 (by state), kappa | s << 13 | neg << 33 | half << 34 (by key)
+  std::vector<int> hs_ptr;
+  std::vector<unsigned> hs_ent;
+  std::vector<int> hk_ptr;
+  std::vector<unsigned long long> hk_ent;
+  // diagonal entries by key -> (kappa, d_c); E_0 coefficient by key
+  std::vector<int> dk_ptr, dk_out;
+  std::vector<double> dk_c, e0_by_key;
+  // back-substitution by kappa -> (o, w, sign) and by w -> (o, kappa, sign):
+  // o | x << 13 | sign << 26
+  std::vector<int> bk_ptr, bw_ptr;
+  std::vector<unsigned> bk_ent, bw_ent;
+  std::vector<int> out_of_state;  // sector state -> output index, -1 if none
+};
+
+template <typename E, typename F>
+inline void group_csr(int ngroups, size_t n, F key_of, std::vector<int>& ptr, std::vector<E>& ent,
+                      const std::vector<E>& val) {
+  ptr.assign(ngroups + 1, 0);
+  for (size_t e = 0; e < n; ++e) ptr[key_of(e) + 1]++;
+  for (int g = 0; g < ngroups; ++g) ptr[g + 1] += ptr[g];
+  ent.resize(n);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t e = 0; e < n; ++e) ent[fill[key_of(e)]++] = val[e];
+}
+
+inline int build_adjoint(const Tables& T, AdjTables* A) {
+  const int ns = T.nstate, no = T.nout;
+  if (no >= (1 << 13) || ns >= (1 << 20) || T.nkey >= (1 << 15)) return -1;
+  A->out_of_state.assign(ns, -1);
+  for (int o = 0; o < no; ++o) A->out_of_state[T.out_state[o]] = o;
+  // sector recursion
+  {
+    size_t ne = T.ent_sub.size();
+    std::vector<int> owner(ne);
+    for (int s = 0; s < ns; ++s)
+      for (int e = T.ent_ptr[s]; e < T.ent_ptr[s + 1]; ++e) owner[e] = s;
+    std::vector<unsigned long long> v1(ne), v2(ne);
+    for (size_t e = 0; e < ne; ++e) {
+      unsigned sl = (uint16_t)T.ent_slot[e];
+      v1[e] = (unsigned long long)owner[e] | ((unsigned long long)sl << 32);
+      v2[e] = (unsigned long long)owner[e] | ((unsigned long long)T.ent_sub[e] << 20) |
+              ((unsigned long long)(sl & 1) << 40);
+    }
+    group_csr(ns, ne, [&](size_t e) { return T.ent_sub[e]; }, A->bs_ptr, A->bs_ent, v1);
+    group_csr(T.nslot, ne, [&](size_t e) { return (int)((uint16_t)T.ent_slot[e] >> 1); }, A->bl_ptr, A->bl_ent, v2);
+  }
+  // output recursion: forward entries are indexed by level-order position
+  {
+    size_t ne = T.oent_sub.size();
+    std::vector<int> owner(ne);
+    for (size_t i = 0; i < T.olvl_order.size(); ++i)
+      for (int e = T.oent_ptr[i]; e < T.oent_ptr[i + 1]; ++e) owner[e] = T.olvl_order[i];
+    std::vector<int> pos_of_out(no);
+    for (size_t i = 0; i < T.olvl_order.size(); ++i) pos_of_out[T.olvl_order[i]] = (int)i;
+    std::vector<unsigned long long> v1(ne), v2(ne);
+    for (size_t e = 0; e < ne; ++e) {
+      unsigned sl = (uint16_t)T.oent_slot[e];
+      v1[e] = (unsigned long long)owner[e] | ((unsigned long long)sl << 32);
+      v2[e] = (unsigned long long)owner[e] | ((unsigned long long)T.oent_sub[e] << 20) |
+              ((unsigned long long)(sl & 1) << 40);
+    }
+    // grouped by the level-order position of the sub output (kernels walk positions)
+    group_csr(no, ne, [&](size_t e) { return pos_of_out[T.oent_sub[e]]; }, A->obs_ptr, A->obs_ent, v1);
+    group_csr(T.nslot, ne, [&](size_t e) { return (int)((uint16_t)T.oent_slot[e] >> 1); }, A->obl_ptr, A->obl_ent,
+              v2);
+  }
+  // Hamiltonian rows
+  {
+    size_t ne = T.h_s.size();
+    std::vector<int> owner(ne);
+    for (int o = 0; o < no; ++o)
+      for (int e = T.h_ptr[o]; e < T.h_ptr[o + 1]; ++e) owner[e] = o;
+    std::vector<unsigned> v1(ne);
+    std::vector<unsigned long long> v2(ne);
+    for (size_t e = 0; e < ne; ++e) {
+      double cv = T.h_c[e];
+      if (fabs(cv) != 1.0 && fabs(cv) != 0.5) return -2;
+      unsigned neg = cv < 0, half = fabs(cv) == 0.5;
+      v1[e] = (unsigned)owner[e] | ((unsigned)T.h_key[e] << 13) | (neg << 28) | (half << 29);
+      v2[e] = (unsigned long long)owner[e] | ((unsigned long long)T.h_s[e] << 13) |
+              ((unsigned long long)neg << 33) | ((unsigned long long)half << 34);
+    }
+    group_csr(ns, ne, [&](size_t e) { return T.h_s[e]; }, A->hs_ptr, A->hs_ent, v1);
+    group_csr(T.nkey, ne, [&](size_t e) { return (int)T.h_key[e]; }, A->hk_ptr, A->hk_ent, v2);
+  }
+  // diagonal by key, E_0 by key
+  {
+    size_t ne = T.d_key.size();
+    std::vector<int> owner(ne);
+    for (int o = 0; o < no; ++o)
+      for (int e = T.d_ptr[o]; e < T.d_ptr[o + 1]; ++e) owner[e] = o;
+    std::vector<int> idx(ne);
+    for (size_t e = 0; e < ne; ++e) idx[e] = (int)e;
+    std::vector<int> grouped;
+    group_csr(T.nkey, ne, [&](size_t e) { return (int)T.d_key[e]; }, A->dk_ptr, grouped, idx);
+    A->dk_out.resize(ne);
+    A->dk_c.resize(ne);
+    for (size_t q = 0; q < ne; ++q) { A->dk_out[q] = owner[grouped[q]]; A->dk_c[q] = T.d_c[grouped[q]]; }
+    A->e0_by_key.assign(T.nkey, 0.0);
+    for (size_t e = 0; e < T.e0_key.size(); ++e) A->e0_by_key[T.e0_key[e]] += T.e0_c[e];
+  }
+  // back-substitution
+  {
+    // the row of output 0 is left out: the reference enters the Lagrangian as
+    // phi'(ref) itself (the energy), never through a back-substituted R_0
+    std::vector<unsigned> v1, v2;
+    std::vector<int> kk_of, w_of;
+    for (int o = 1; o < no; ++o)
+      for (int e = T.b_ptr[o]; e < T.b_ptr[o + 1]; ++e) {
+        unsigned sg = T.b_w[e] & 1, w = T.b_w[e] >> 1, kk = T.b_k[e];
+        v1.push_back((unsigned)o | (w << 13) | (sg << 26));
+        v2.push_back((unsigned)o | (kk << 13) | (sg << 26));
+        kk_of.push_back((int)kk);
+        w_of.push_back((int)w);
+      }
+    group_csr(no, v1.size(), [&](size_t e) { return kk_of[e]; }, A->bk_ptr, A->bk_ent, v1);
+    group_csr(no, v2.size(), [&](size_t e) { return w_of[e]; }, A->bw_ptr, A->bw_ent, v2);
+  }
+  return 0;
+}
+
+inline const AdjTables* host_adjoint(int k, int K, int KH, int* rc) {
+  static std::mutex mu;
+  static std::unique_ptr<AdjTables> cache[kMaxSites + 1][4][5];
+  const Tables* T = host_tables(k, K, KH, rc);
+  if (!T) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto& slot = cache[k][K][KH];
+  if (!slot) {
+    std::unique_ptr<AdjTables> A(new AdjTables());
+    *rc = build_adjoint(*T, A.get());
+    if (*rc) return nullptr;
+    slot = std::move(A);
+  }
+  return slot.get();
+}
+
+}  // namespace ph

@@ -15,7 +15,10 @@ What this pins, without a GPU:
     three-pair amplitudes with two-label integrals at N = 6 (K + K_H = 5 < N),
     against the oracle's own local assembly (O-loc), which restricts the
     normal-ordered Hamiltonian instead of the bare one;
-  * a control: ignoring the signs of the recursion breaks the agreement.
+  * a control: ignoring the signs of the recursion breaks the agreement;
+  * the transposed (adjoint) tables: grad_t L of the Lagrangian E_c +
+    lambda . R equals the oracle's complex-step Jacobian product at N = 2, 3,
+    and the integral adjoints equal central differences of the Lagrangian.
 """
 import os
 from math import comb
@@ -149,3 +152,64 @@ def test_recursion_sign_control():
     t, R, e, lm = _oracle_case(H, 3, 3)
     R2, _ = _interp(H, 3, 3, t, lm, sign_flip_control=True)
     assert np.abs(R2 - R).max() > 1e-3
+
+
+@pytest.mark.parametrize("name,K_H", [("C4H6", 3), ("C4H6", 2), ("C6H8", 3)])
+def test_adjoint_tables_match_oracle_lagrangian_gradient(name, K_H):
+    # the transposed tables (reverse pass of the local problems, weighted by
+    # c_k lambda and c^E_k) give grad_t L = dE_c/dt + J^T lambda of the oracle,
+    # whose Jacobian is taken by the complex step through O-det
+    _lib()
+    from oracle.gradient import grad_t_lagrangian
+    from tests.ph_subset_interp import SubsetAdjoint
+    H = {"C4H6": lambda: build_ppp('polyene', 4), "C6H8": lambda: build_ppp('polyene', 6)}[name]()
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=K_H)
+    rng = np.random.default_rng(21)
+    t = rng.uniform(-0.1, 0.1, P.cc.n_amp)
+    lam = rng.uniform(-0.1, 0.1, P.cc.n_amp)
+    g_ref = grad_t_lagrangian(P, t, lam)
+    lm = LayoutMap(P.cc.manifold, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout(3))
+    sa = SubsetAdjoint(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, 3, K_H)
+    g, _ = sa.lagrangian_gradient(lm.to_layout(t), lm.to_layout(lam))
+    g2 = lm.from_layout(sa.fill_copies(g, lm))
+    assert np.abs(g_ref).max() > 0.05
+    assert np.abs(g2 - g_ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("K,K_H,sites", [(3, 3, 8), (3, 2, 10)])
+def test_adjoint_tables_integral_keys_by_central_differences(K, K_H, sites):
+    # dL/d(integral key) of the reverse pass against central differences of
+    # the Lagrangian in the bare truncated integrals, for the ten keys of
+    # largest gradient (one dense element may feed several keys: the keys of
+    # an element are summed)
+    _lib()
+    from tests.ph_subset_interp import SubsetAdjoint
+    H = build_ppp('polyene', sites)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=K, K_H=K_H)
+    rng = np.random.default_rng(22)
+    lm = LayoutMap(P.cc.manifold, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout(K))
+    t = lm.to_layout(rng.uniform(-0.1, 0.1, P.cc.n_amp))
+    lam = lm.to_layout(rng.uniform(-0.1, 0.1, P.cc.n_amp))
+    sa = SubsetAdjoint(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K, K_H)
+    uniq = lm.to_layout(np.arange(1, P.cc.n_amp + 1)) != 0
+    _, gv = sa.lagrangian_gradient(t, lam)
+    dense = {}
+    for (labels, j), val in gv.items():
+        kind = sa.keys[len(labels)][j]
+        orbs = [o for X in labels for o in (sa.occ[X], sa.vir[X])]
+        el = (kind[0],) + tuple(orbs[i] for i in kind[1:(3 if kind[0] == 'h' else 5)])
+        dense[el] = dense.get(el, 0.0) + val
+    top = sorted(dense.items(), key=lambda kv: -abs(kv[1]))[:10]
+    assert abs(top[0][1]) > 0.05
+
+    def lag(el, delta):
+        arr = sa.hp if el[0] == 'h' else sa.v
+        arr[el[1:]] += delta
+        r, e = sa.residual(t)
+        arr[el[1:]] -= delta
+        return e + np.sum(lam[uniq] * r[uniq])
+
+    eps = 1e-5
+    for el, val in top:
+        fd = (lag(el, eps) - lag(el, -eps)) / (2 * eps)
+        assert abs(fd - val) < 1e-8, (el, fd, val)
