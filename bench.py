@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer C-ABI leg")
-    ap.add_argument("--mode", default="solve", choices=["solve", "residual"],
-                    help="'residual': only --steps residual evaluations (for ncu captures)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "residual", "ph-residual"],
+                    help="'residual': only --steps PQ residual evaluations; 'ph-residual': --steps PH "
+                         "residual evaluations of the first acene of --ph-rings (both for ncu captures)")
     ap.add_argument("--precision", type=int, default=1, help="residual mode: 0 FP64, 1 FP32")
     ap.add_argument("--batch", type=int, default=0,
                     help="also time a batched solve of this many H chains (H10-H50, 0.7-3.0 A)")
@@ -434,12 +435,33 @@ def residual_mode(args):
                       "norm": float(r.norm())}))
 
 
+def ph_residual_mode(args):
+    """--steps PH residual evaluations of one acene at seeded amplitudes
+    (uniform +-0.01, seed 1): the small case of the PH kernel captures."""
+    import torch
+    import paper_1609_00077_gb300 as ppq
+    from workloads import build_ppp
+    rings = int(args.ph_rings.split(",")[0])
+    H = build_ppp('acene', rings)
+    N = H.n_pairs
+    h = torch.from_numpy(H.h).cuda()
+    eri = torch.from_numpy(H.eri).cuda()
+    t = torch.from_numpy(np.random.default_rng(1).uniform(-0.01, 0.01, ppq.amp_count(N, 3))).cuda()
+    for _ in range(args.steps):
+        r, e = ppq.ph_residual(H.occ_of_pair, H.vir_of_pair, h, eri, t, precision=args.precision)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "ph-residual", "rings": rings, "n_pairs": N, "steps": args.steps,
+                      "e_corr": e, "norm": float(r.norm())}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "residual":
         return residual_mode(args)
+    if args.mode == "ph-residual":
+        return ph_residual_mode(args)
     import torch
     import paper_1609_00077_gb300 as ppq
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -314,6 +314,35 @@ int pq_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
                 double* lam_out, double* dE_dh, double* dE_deri, double* dE_dkappa,
                 double* e_total, ppq_info* info, void* stream);
 
+/* grad_t L(t, lambda) of the PH model (K = 3; K_H = 0 or 3: three-label
+   integrals, 2: two-label), the Lagrangian L = E_c + sum over unique mu of
+   lambda_mu R_mu (Theory section: lambda on the truncated manifold of t).
+   t and lam use the K = 3 layout (ppq_amp_count(N, 3) doubles, host or
+   device; only the sorted-label entries are read).  The reverse pass runs
+   through every local problem of the label-subset expansion (transposed
+   structure tables, FP64) and sums each adjoint over the subsets containing
+   its labels in a fixed order: the result is reproducible.  grad is written
+   in the same layout, copies filled by the copy rule.  e_corr (host,
+   nullable) receives E_c(t).  Returns 0 or < 0 (-4 bad K_H, -2 null buffer,
+   -1 bad pairing or n_pairs > 127). */
+int ph_lagrangian_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair,
+                           const double* h, const double* eri, const double* t,
+                           const double* lam, int K_H, double* grad, double* e_corr, void* stream);
+
+/* Energy gradients of the PH model: solve the amplitudes (opts as ph_solve,
+   from zero amplitudes), then the Lambda equations grad_t L = 0 (FP64 Jacobi steps
+   with device DIIS, from zero, to opts->r_tol), then the relaxed integral
+   gradients from the adjoints of every gathered integral, transposed to
+   dense dE_total/dh (n_orb^2) and dE_total/d(pq|rs) (n_orb^4) through the
+   chain rule of the bare one-body part and of E_ref, and the
+   orbital-rotation gradient dE/dkappa (n_orb^2) as pq_gradient.  eri must be
+   dense.  Outputs nullable, host or device; t_out and lam_out in the K = 3
+   layout.  Returns the larger of the amplitude and Lambda statuses, or < 0. */
+int ph_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const double* h,
+                const double* eri, double e_const, const ppq_opts* opts, double* t_out,
+                double* lam_out, double* dE_dh, double* dE_deri, double* dE_dkappa,
+                double* e_total, ppq_info* info, void* stream);
+
 /* pq_residual without any device allocation.  The paper has no counterpart:
    this entry point exists for callers that cannot call cudaMalloc.  Examples
    are code running inside another framework's memory pool or under a fixed

@@ -81,6 +81,8 @@ def lib():
         L.pq_lambda.argtypes = [I, P, P, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
         L.pq_gradient.argtypes = [I, P, P, P, P, D, ctypes.POINTER(Opts), P, P, P, P, P, P,
                                   ctypes.POINTER(Info), P]
+        L.ph_gradient.argtypes = L.pq_gradient.argtypes
+        L.ph_lagrangian_gradient.argtypes = [I, P, P, P, P, P, P, I, P, P, P]
         L.ppq_tc_plan.argtypes = [I, P, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.ppq_last_error.restype = ctypes.c_char_p
         for f in (L.ppq_default_opts, L.ppq_amp_count, L.ppq_amp_layout, L.pq_residual,
@@ -89,7 +91,7 @@ def lib():
                   L.pq_lambda, L.pq_gradient, L.ppq_release, L.ppq_tc_plan, L.ph_residual,
                   L.ph_tables_counts, L.ph_tables_copy, L.ppq_profile_count, L.ppq_profile_entry,
                   L.ppq_subset_residual, L.pq_solve_cd, L.ph_solve_cd, L.ppq_natural_occupations,
-                  L.ppq_wait_selftest):
+                  L.ppq_wait_selftest, L.ph_gradient, L.ph_lagrangian_gradient):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -100,7 +102,7 @@ EXPORTED = ["ppq_default_opts", "ppq_amp_count", "ppq_amp_layout", "pq_residual"
             "pq_lagrangian_gradient", "pq_lambda", "pq_gradient", "ppq_release", "ppq_last_error",
             "ppq_tc_plan", "ph_tables_counts", "ph_tables_copy", "ppq_profile_count",
             "ppq_profile_entry", "ppq_subset_residual", "pq_solve_cd", "ph_solve_cd",
-            "ppq_natural_occupations", "ppq_wait_selftest"]
+            "ppq_natural_occupations", "ppq_wait_selftest", "ph_gradient", "ph_lagrangian_gradient"]
 
 
 def _ptr(x):
@@ -475,6 +477,56 @@ def pq_gradient(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, want
                            ctypes.cast(ctypes.pointer(et), ctypes.c_void_p), ctypes.byref(info),
                            _stream(stream))
     _check(rc, "pq_gradient")
+    return rc, et.value, dh, dv, dk, info.as_dict()
+
+
+def ph_lagrangian_gradient(occ_of_pair, vir_of_pair, h, eri, t, lam, K_H=3, grad=None, stream=None):
+    """grad_t L(t, lambda) of the PH model (K = 3 layout; FP64 reverse pass of
+    the label-subset expansion).  Returns (grad, e_corr)."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    L = amp_count(N, 3)
+    if grad is None:
+        grad = np.zeros(L) if isinstance(t, np.ndarray) else t.new_zeros(L)
+    n = 2 * N
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri"), (t, L, "t"), (lam, L, "lam"), (grad, L, "grad")):
+        _check_buf(x, cnt, name)
+    e = ctypes.c_double()
+    rc = lib().ph_lagrangian_gradient(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), _ptr(t), _ptr(lam),
+                                      K_H, _ptr(grad), ctypes.cast(ctypes.pointer(e), ctypes.c_void_p),
+                                      _stream(stream))
+    _check(rc, "ph_lagrangian_gradient")
+    return grad, e.value
+
+
+def ph_gradient(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, want_eri=True, t_out=None,
+                lam_out=None, **opts):
+    """Solve PH, then Lambda, then return (status, e_total, dE/dh, dE/d(pq|rs)
+    or None, dE/dkappa, info).  Outputs are torch CUDA tensors when h is one,
+    else numpy; t_out / lam_out (K = 3 layout) are filled when given."""
+    occ, vir = _pairs(occ_of_pair, vir_of_pair)
+    N = len(occ)
+    n = 2 * N
+    L = amp_count(N, 3)
+    if isinstance(h, np.ndarray):
+        dh = np.zeros((n, n)); dk = np.zeros((n, n))
+        dv = np.zeros((n, n, n, n)) if want_eri else None
+    else:
+        dh = h.new_zeros((n, n)); dk = h.new_zeros((n, n))
+        dv = h.new_zeros((n, n, n, n)) if want_eri else None
+    for x, cnt, name in ((h, n * n, "h"), (eri, n ** 4, "eri")):
+        _check_buf(x, cnt, name)
+    for x, name in ((t_out, "t_out"), (lam_out, "lam_out")):
+        if x is not None:
+            _check_buf(x, L, name)
+    et = ctypes.c_double()
+    info = Info()
+    o = default_opts(**opts)
+    rc = lib().ph_gradient(N, occ.ctypes.data, vir.ctypes.data, _ptr(h), _ptr(eri), float(e_const),
+                           ctypes.byref(o), _ptr(t_out), _ptr(lam_out), _ptr(dh),
+                           _ptr(dv) if dv is not None else None, _ptr(dk),
+                           ctypes.cast(ctypes.pointer(et), ctypes.c_void_p), ctypes.byref(info), _stream(stream))
+    _check(rc, "ph_gradient")
     return rc, et.value, dh, dv, dk, info.as_dict()
 
 

@@ -408,6 +408,40 @@ __device__ __forceinline__ int colex_d(const int* p, int m) {
   return r;
 }
 
+// sum over the k-subsets L containing the sorted labels M (m <= 4 of them)
+// of X[rank(L) * ld + base + colex(positions of M in L) * nper + j]; the
+// subsets in a fixed order (the added labels in lexicographic order)
+__device__ double superset_sum(int N, const int* M, int m, int k, const double* __restrict__ X, int ld, int base,
+                               int nper, int j) {
+  int nc = N - m, na = k - m;
+  int e[kMaxSites];
+  for (int x = 0; x < na; ++x) e[x] = x;
+  double part = 0.0;
+  for (;;) {
+    // L = M + the e-th labels not in M (both sorted), merged
+    int Ls[kMaxSites], pos[4], El[kMaxSites];
+    for (int x = 0; x < na; ++x) {
+      int lab = e[x];
+      for (int y = 0; y < m; ++y)
+        if (M[y] <= lab) ++lab;
+      El[x] = lab;
+    }
+    int nl = 0, im = 0, ie = 0;
+    while (nl < k) {
+      if (im < m && (ie >= na || M[im] < El[ie])) { pos[im] = nl; Ls[nl++] = M[im++]; }
+      else Ls[nl++] = El[ie++];
+    }
+    part += X[(size_t)colex_d(Ls, k) * ld + base + colex_d(pos, m) * nper + j];
+    // next combination of na among nc (lexicographic)
+    int x = na - 1;
+    while (x >= 0 && e[x] == nc - na + x) --x;
+    if (x < 0) break;
+    ++e[x];
+    for (int y = x + 1; y < na; ++y) e[y] = e[y - 1] + 1;
+  }
+  return part;
+}
+
 // r at the unique slots of m-label outputs: sum over subsets L containing the
 // labels, |L| = k <= kmax, of c_k R_loc^(L); subsets in a fixed order
 __global__ void k_assemble(int N, int m, int nch, const int8_t* __restrict__ subs_m, int nsets, AsmArgs A,
@@ -418,41 +452,10 @@ __global__ void k_assemble(int N, int m, int nch, const int8_t* __restrict__ sub
   int M[3];
   for (int x = 0; x < m; ++x) M[x] = subs_m[(size_t)set * m + x];
   double acc = 0.0;
-  int nc = N - m;
   for (int k = m; k <= A.kmax; ++k) {
     if (A.c[k] == 0.0 || A.nsub[k] == 0) continue;
-    int j = k - m;
-    int e[kMaxSites];
-    for (int x = 0; x < j; ++x) e[x] = x;
     int base = 1 + (m >= 2 ? 3 * k : 0) + (m >= 3 ? 29 * c_binom[k * 8 + 2] : 0);
-    const double* Rk = A.Rloc[k];
-    const int nout = A.nout[k];
-    double part = 0.0;
-    for (;;) {
-      // L = M + the e-th labels not in M (both sorted), merged
-      int Ls[kMaxSites], pos[3], El[kMaxSites];
-      for (int x = 0; x < j; ++x) {
-        int lab = e[x];
-        for (int y = 0; y < m; ++y)
-          if (M[y] <= lab) ++lab;
-        El[x] = lab;
-      }
-      int nl = 0, im = 0, ie = 0;
-      while (nl < k) {
-        if (im < m && (ie >= j || M[im] < El[ie])) { pos[im] = nl; Ls[nl++] = M[im++]; }
-        else Ls[nl++] = El[ie++];
-      }
-      int rank = colex_d(Ls, k);
-      int o = base + colex_d(pos, m) * nch + ch;
-      part += Rk[(size_t)rank * nout + o];
-      // next combination of j among nc (lexicographic)
-      int x = j - 1;
-      while (x >= 0 && e[x] == nc - j + x) --x;
-      if (x < 0) break;
-      ++e[x];
-      for (int y = x + 1; y < j; ++y) e[y] = e[y - 1] + 1;
-    }
-    acc += A.c[k] * part;
+    acc += A.c[k] * superset_sum(N, M, m, k, A.Rloc[k], A.nout[k], base, nch, ch);
   }
   size_t idx;
   if (m == 1) idx = 3 * (size_t)M[0] + ch;
@@ -769,7 +772,7 @@ Ctx* ctx() {
 // psi and psi_minus level by level, phi, back-substitution for one chunk of
 // subsets (J subsets per lane)
 template <typename R, int J>
-int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStream_t s) {
+int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStream_t s, bool backsub = true) {
   const double nv = std::min(P, nsub - p0), es = sizeof(R);
   R* psi = (R*)c->psi;
   R* psim = (R*)c->psim;
@@ -801,9 +804,14 @@ int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStre
   g_prof.done("ph::k_phi (<kappa|H|psi>)", s,
               T->nh * 8.0 + (T->nh + T->nruns + T->nd) * es * nv + T->nout * 2 * es * nv,
               2.0 * (T->nh + T->nruns + T->nd) * nv);
+  c->n_launches++;
+  if (!backsub) {
+    CK(cudaGetLastError());
+    return 0;
+  }
   k_backsub<R, J><<<go, 256, 0, s>>>(P, p0, nsub, T->nout, T->b_ptr, T->b_k, T->b_w, psim, phi, c->Rloc[k],
                                      c->Eloc[k]);
-  c->n_launches += 2;
+  c->n_launches++;
   g_prof.done("ph::k_backsub", s, T->nb * (8.0 + 2 * es * nv) + T->nout * 8.0 * nv, 2.0 * T->nb * nv);
   CK(cudaGetLastError());
   return 0;

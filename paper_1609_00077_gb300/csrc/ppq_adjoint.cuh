@@ -536,8 +536,10 @@ __global__ void k_scatter_gather(int n, int N, const double* __restrict__ gb1,
 // chain rule through h'_pq = h_pq + sum_{k not in {L(p),L(q)}} [2 (pq|ii) - (pi|iq)]
 // (for L(p) != L(q)) and through E_ref = sum_i (h_ii + f_ii):
 // dv[p,q,i,i] += 2 dh'[p,q], dv[p,i,i,q] -= dh'[p,q]; E_ref terms on occupied i, j
+// (trunc = 0: h' = h, only the E_ref terms)
 __global__ void k_grad_chain(int n, int N, const double* __restrict__ dhp, const int* __restrict__ occ,
-                             const int* __restrict__ lab, double* __restrict__ dh, double* __restrict__ dv) {
+                             const int* __restrict__ lab, double* __restrict__ dh, double* __restrict__ dv,
+                             int trunc) {
   int pq = blockIdx.x * blockDim.x + threadIdx.x;
   if (pq >= n * n) return;
   int p = pq / n, q = pq % n;
@@ -545,7 +547,7 @@ __global__ void k_grad_chain(int n, int N, const double* __restrict__ dhp, const
   double d = dhp[pq];
   dh[pq] = d;
   int lp = lab[p], lq = lab[q];
-  if (lp != lq && d != 0.0) {
+  if (trunc && lp != lq && d != 0.0) {
     for (int k = 0; k < N; ++k) {
       if (k == lp || k == lq) continue;
       size_t i = occ[k];

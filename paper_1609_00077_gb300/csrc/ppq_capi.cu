@@ -1102,7 +1102,7 @@ int integral_gradients(Workspace* w, const Problem& P, cudaStream_t s) {
   ppq::adj::k_scatter_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, N, w->gb1, w->gb2, w->occ,
                                                                             w->vir, w->gh, w->gv_raw);
   ppq::adj::k_grad_chain<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, N, w->gh, w->occ, w->lab,
-                                                                      w->gh_raw, w->gv_raw);
+                                                                      w->gh_raw, w->gv_raw, 1);
   ppq::adj::k_sym_h<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, w->gh_raw, w->gh);
   ppq::adj::k_sym_v<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n, w->gv_raw, w->gv);
   ppq::adj::k_orbital_grad<<<(unsigned)((n2 + 127) / 128), 128, 0, s>>>(n, P.h, P.eri, w->gh, w->gv, w->ab);
@@ -2247,3 +2247,4 @@ extern "C" int pq_residual_static(int n_pairs, const int* occ_of_pair, const int
 }
 
 #include "ph_engine.cuh"
+#include "ph_adjoint.cuh"
