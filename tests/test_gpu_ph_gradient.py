@@ -8,7 +8,7 @@
 * at N = 7 (every subset size enters with a nonzero coefficient) the
   directional derivative along a random direction equals the central
   difference of L = E_c + lambda . R from FP64 GPU residuals (themselves held
-  to the oracle element by element in test_gpu_ph.py), tolerance 1e-7
+  to the oracle element by element in test_gpu_ph.py), tolerance 1e-6
   relative; and two calls give identical bits;
 * hexatriene 6e/6o: PH is FCI there, so by Hellmann-Feynman dE/dh is the FCI
   one-particle density matrix, dE/d(pq|rs) half the FCI two-particle one
@@ -108,7 +108,7 @@ def test_lagrangian_gradient_directional_n7_and_reproducible():
     fd = (lag(t0 + eps * d) - lag(t0 - eps * d)) / (2 * eps)
     an = float(np.sum(g[uniq] * d[uniq]))
     assert abs(an) > 1e-2
-    assert abs(fd - an) < 1e-7 * max(1.0, abs(an)), (fd, an)
+    assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (fd, an)
 
 
 def test_ph_gradient_is_fci_density_at_6e6o():
