@@ -170,16 +170,17 @@ __global__ void k_site_closure(int N, const R* __restrict__ g1, const double* __
 // two-site closure Ht_XW = exp(-I) H_XW exp(I), I = T_X + T_W + T_XW, on the
 // charge/S_z block layout (4900 entries); writes the entries the topologies
 // use (G row, T7 entries and their transpose, column 0) and the pair energy.
-// Persistent: each CTA stages the compact tables (per-sector sweep lists,
-// output element lists) in shared memory once, reads the Hamiltonian CSR
-// through L1, and then loops over pairs XW.  Right multiplication by
-// (1 + t_o O_o) only mixes entries of one row and left multiplication only
-// entries of one column, so a thread takes one row through all 35 operators,
-// then one column, with no barrier between operators.  Threads are ordered by
-// sector, so the lanes of a warp walk the same list; the lists come in groups
-// of 4 entries of one operator (independent targets), loaded together.  The
-// shared copy of M pads every sector row to dim + 1 entries (no bank
-// conflicts between rows dim apart).  The gather multiplies by the five
+// Persistent: each CTA stages the output element lists in shared memory once,
+// reads the Hamiltonian CSR through L1, and then loops over pairs XW.  Right
+// multiplication by (1 + t_o O_o) only mixes entries of one row and left
+// multiplication only entries of one column, and every row (column) of a
+// sector goes through the same sequence: a thread loads its row into
+// registers, runs the sector's generated straight-line sequence of
+// multiply-adds over all 35 operators (ppq_sweep_right), stores the row, and
+// then does the same for its column (ppq_sweep_left).  Threads are ordered by
+// sector, so the lanes of a warp run the same sequence.  The shared copy of M
+// pads every sector row to dim + 1 entries (no bank conflicts when the threads
+// of a sector load their rows or columns).  The gather multiplies by the five
 // coefficient values -1, -1/2, 1/2, 1, 2 through a pre-scaled copy of the
 // integrals (the products are exact).  Element for element the arithmetic of
 // the flat operator-by-operator sweeps (ppq_p_right / ppq_p_left, used by the
@@ -188,9 +189,7 @@ struct ClosureSmem {
   static constexpr int kM = PPQ_BLKP + 8;
   static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2;   // pre-scaled integrals
   template <typename R>
-  static __host__ __device__ constexpr size_t off_sl() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
-  template <typename R>
-  static __host__ __device__ constexpr size_t off_oel() { return off_sl<R>() + (size_t)(PPQ_PSR_N + PPQ_PSL_N) * 4; }
+  static __host__ __device__ constexpr size_t off_oel() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
   template <typename R>
   static __host__ __device__ constexpr size_t total() {
     return off_oel<R>() + ((PPQ_NS36 + PPQ_NT7E + PPQ_NCOL0) * 2 + 15) / 16 * 16;
@@ -205,12 +204,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(
   R* M = reinterpret_cast<R*>(smem_raw);
   R* gsv = M + ClosureSmem::kM;                          // [code][j]
   R* fac = gsv + ClosureSmem::kG;                        // [2 o + sign], slots 70, 71 = 0
-  int32_t* srl = reinterpret_cast<int32_t*>(smem_raw + ClosureSmem::off_sl<R>());
-  int32_t* sll = srl + PPQ_PSR_N;
   int16_t* oel = reinterpret_cast<int16_t*>(smem_raw + ClosureSmem::off_oel<R>());
   const int tid = threadIdx.x;
-  for (int i = tid; i < PPQ_PSR_N; i += blockDim.x) srl[i] = ppq_ps_right[i];
-  for (int i = tid; i < PPQ_PSL_N; i += blockDim.x) sll[i] = ppq_ps_left[i];
   for (int i = tid; i < PPQ_NS36; i += blockDim.x) oel[i] = ppq_g_elp[i];
   for (int i = tid; i < PPQ_NT7E; i += blockDim.x) oel[PPQ_NS36 + i] = ppq_t7_elp[i];
   for (int i = tid; i < PPQ_NCOL0; i += blockDim.x) oel[PPQ_NS36 + PPQ_NT7E + i] = ppq_col0_elp[i];
@@ -219,7 +214,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(
   const int q = ppq_st_sec[st], dp = ppq_sec_dim[q] + 1;
   const int rowbase = ppq_sec_pbase[q] + ppq_st_pos[st] * dp;
   const int colbase = ppq_sec_pbase[q] + ppq_st_pos[st];
-  const int r0 = ppq_ps_rptr[q], r1 = ppq_ps_rptr[q + 1], l0 = ppq_ps_lptr[q], l1 = ppq_ps_lptr[q + 1];
   const int NN = N * N;
   for (int XW = blockIdx.x; XW < NN; XW += gridDim.x) {
     const int X = XW / N, W = XW % N;
@@ -256,39 +250,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(
     }
     __syncthreads();
     const R h00 = M[PPQ_EL00P];
-    // right: M <- M exp(I), along this thread's row
-    for (int e = r0; e < r1; e += 4) {
-      int ti[4], si[4];
-      R f[4], mt[4], ms[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int32_t w = srl[e + k];
-        ti[k] = rowbase + (w & 0xFFF);
-        si[k] = rowbase + ((w >> 12) & 0xFFF);
-        f[k] = fac[w >> 24];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { ms[k] = M[si[k]]; mt[k] = M[ti[k]]; }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) M[ti[k]] = mt[k] + f[k] * ms[k];
-    }
+    // right: M <- M exp(I), this thread's row in registers (generated per sector)
+    ppq_sweep_right<R>(q, M, rowbase, fac);
     __syncthreads();
-    // left: M <- exp(-I) M, along this thread's column
-    for (int e = l0; e < l1; e += 4) {
-      int ti[4], si[4];
-      R f[4], mt[4], ms[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int32_t w = sll[e + k];
-        ti[k] = colbase + (w & 0xFFF);
-        si[k] = colbase + ((w >> 12) & 0xFFF);
-        f[k] = fac[w >> 24];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { ms[k] = M[si[k]]; mt[k] = M[ti[k]]; }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) M[ti[k]] = mt[k] - f[k] * ms[k];
-    }
+    // left: M <- exp(-I) M, this thread's column in registers
+    ppq_sweep_left<R>(q, M, colbase, fac);
     __syncthreads();
     for (int i = tid; i < PPQ_NS36; i += blockDim.x) pg[(size_t)XW * PPQ_NS36 + i] = M[oel[i]];
     for (int i = tid; i < PPQ_NT7E; i += blockDim.x) {

@@ -573,6 +573,59 @@ def site_transform_lists(T):
             np.array(left, dtype=np.int64), np.array(lptr, dtype=np.int64))
 
 
+def pair_sweep_code(T, L):
+    """C++ source of the pair closure's per-sector sweeps with one thread's row
+    (right, exp(I)) or column (left, exp(-I)) held in registers: for every
+    sector q a straight-line sequence over the sector's positions, operator
+    by operator in the order of pair_sector_lists (without its padding),
+    each entry one multiply-add.  Factors fac[2 o + (sign < 0)] are read into
+    locals once per sector.  Right entry: v[a] += fac[f] v[b]; left entry:
+    v[b] -= fac[f] v[a] (positions inside the sector)."""
+    ops = []
+    for k in range(3):
+        ops.append(T.site_ops2a[T.site_ops2a[:, 0] == k])
+    for k in range(3):
+        ops.append(T.site_ops2b[T.site_ops2b[:, 0] == k])
+    for k in range(29):
+        ops.append(T.pair_ops[T.pair_ops[:, 0] == k])
+    nq = len(L.sectors)
+    ent = [[] for _ in range(nq)]
+    for o, tab in enumerate(ops):
+        for _, src, dst, sg in tab:
+            q = int(L.sec_of[src])
+            ent[q].append((int(L.pos[src]), int(L.pos[dst]), 2 * o + (1 if sg < 0 else 0)))
+    out = []
+    for side in ("right", "left"):
+        out.append("template <typename R>")
+        out.append(f"__device__ __forceinline__ void ppq_sweep_{side}(int q, R* __restrict__ M, int base, "
+                   "const R* __restrict__ fac) {")
+        out.append("  switch (q) {")
+        for q in range(nq):
+            if not ent[q]:
+                continue
+            d = L.dim[q]
+            step = 1 if side == "right" else d + 1
+            fs = sorted({f for _, _, f in ent[q]})
+            out.append(f"    case {q}: {{")
+            out.append(f"      R v[{d}];")
+            out.append(f"#pragma unroll")
+            out.append(f"      for (int i = 0; i < {d}; ++i) v[i] = M[base + i * {step}];")
+            out.append("      " + " ".join(f"const R f{f} = fac[{f}];" for f in fs))
+            for a, b, f in ent[q]:
+                if side == "right":
+                    out.append(f"      v[{a}] += f{f} * v[{b}];")
+                else:
+                    out.append(f"      v[{b}] -= f{f} * v[{a}];")
+            out.append(f"#pragma unroll")
+            out.append(f"      for (int i = 0; i < {d}; ++i) M[base + i * {step}] = v[i];")
+            out.append("    } break;")
+        out.append("    default: break;")
+        out.append("  }")
+        out.append("}")
+        out.append("")
+    return "\n".join(out), ent
+
+
 def csr_from_structure(struct, elem_of):
     r, c, j, coef, _ = struct
     ent = {}
@@ -653,6 +706,7 @@ def emit_header(path):
             _c_array("ppq_ps_left", "int32_t", sl), _c_array("ppq_ps_lptr", "int16_t", slp),
             _c_array("ppq_st_sec", "int8_t", L.sec_of), _c_array("ppq_st_pos", "int8_t", L.pos),
             _c_array("ppq_sec_dim", "int8_t", np.array(L.dim))]
+    out.append(pair_sweep_code(T, L)[0])
     # thread -> two-site state, grouped by sector (largest first) so that the
     # lanes of a warp walk the same list
     order = sorted(range(256), key=lambda st: (-L.dim[L.sec_of[st]], L.sec_of[st], L.pos[st]))

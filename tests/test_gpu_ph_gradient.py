@@ -15,8 +15,11 @@
   (both symmetrised), and dE/dkappa vanishes (FCI is invariant to orbital
   rotations); tolerance 1e-8;
 * octatetraene (N = 4): central differences (step 1e-4) of converged oracle PH
-  energies along a random symmetric direction in (h, (pq|rs)) and along a
-  random orbital rotation, tolerance 1e-6;
+  energies along a random symmetric direction in (h, (pq|rs)) (scaled by 0.1
+  and 0.01 as in the PQ tests: the energy's third derivative along an
+  unscaled random (pq|rs) direction makes the difference quotient miss by
+  3e-2 at this step, by 3e-4 at 1e-5) and along a random orbital rotation,
+  tolerance 1e-6;
 * naphthalene (N = 5): central differences of converged GPU energies along
   random directions and for single symmetric elements of h and (pq|rs).
 """
@@ -132,6 +135,7 @@ def test_ph_gradient_octatetraene_against_oracle_energy_differences():
     dh, dv, dk = dh.cpu().numpy(), dv.cpu().numpy(), dk.cpu().numpy()
     rng = np.random.default_rng(11)
     Dh, Dv = sym_dirs(n, rng)
+    Dh *= 0.1; Dv *= 0.01          # keeps the O(step^2) truncation of the differences below 1e-7
     step = 1e-4
 
     def E(h, eri):
@@ -163,6 +167,7 @@ def test_ph_gradient_naphthalene_against_gpu_energy_differences():
 
     rng = np.random.default_rng(12)
     Dh, Dv = sym_dirs(n, rng)
+    Dh *= 0.1; Dv *= 0.01
     fd = (E(H.h + step * Dh, H.eri + step * Dv) - E(H.h - step * Dh, H.eri - step * Dv)) / (2 * step)
     assert abs(fd - (np.sum(dh * Dh) + np.sum(dv * Dv))) < 1e-6
     # single symmetric elements: h_oo, h_ov, and (pq|rs) classes over one to four labels

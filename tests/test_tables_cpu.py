@@ -6,6 +6,9 @@ kernels rely on (no GPU needed).
   reproduce the flat operator-by-operator sweeps exactly, stay inside their
   sector block, and give every thread of a sector a row start in its own
   shared-memory bank.
+* The generated straight-line sweeps (ppq_sweep_right / ppq_sweep_left, the
+  C++ source the kernel compiles, parsed back here) give the same entries as
+  the flat sweeps on every sector, row by row and column by column.
 * The exact integer splitting of the FP64 quartic kernel (six 7-bit slices,
   K <= 80): every grouped slice-product sum is an exact FP32 integer below
   2^23, and the recombined product is within 3e-12 of row-max x column-max x K.
@@ -73,6 +76,63 @@ def test_sector_lists_reproduce_flat_sweeps(layout):
     for q, ss in enumerate(L.sectors):
         banks = [(pbase[q] + L.pos[r] * (L.dim[q] + 1)) % 32 for r in ss[:32]]
         assert len(set(banks)) == len(banks)
+
+
+def test_generated_sweep_code_reproduces_flat_sweeps(layout):
+    import re
+    Tb, L = layout
+    code, _ = T.pair_sweep_code(Tb, L)
+    pr, prp, pl, plp = T.pair_transform_lists(Tb, L)
+    rng = np.random.default_rng(4)
+    M0 = rng.standard_normal(L.size)
+    t = rng.standard_normal(35) * 0.3
+    M = M0.copy()
+    for o in range(35):
+        for w in pr[prp[o]:prp[o + 1]]:
+            M[w >> 17] += t[o] * (-1 if w & 1 else 1) * M[(w >> 1) & 0xFFFF]
+    for o in range(35):
+        for w in pl[plp[o]:plp[o + 1]]:
+            M[w >> 17] -= t[o] * (-1 if w & 1 else 1) * M[(w >> 1) & 0xFFFF]
+    fac = np.zeros(72)
+    fac[0:70:2], fac[1:70:2] = t, -t
+    # parse: side -> sector -> list of (target, source, factor slot, sign)
+    prog = {}
+    side = q = None
+    for line in code.splitlines():
+        m = re.match(r".*void ppq_sweep_(right|left)\(", line)
+        if m:
+            side = m.group(1); prog[side] = {}
+            continue
+        m = re.match(r"\s*case (\d+): \{", line)
+        if m:
+            q = int(m.group(1)); prog[side][q] = []
+            continue
+        m = re.match(r"\s*v\[(\d+)\] ([+-])= f(\d+) \* v\[(\d+)\];", line)
+        if m:
+            prog[side][q].append((int(m.group(1)), int(m.group(4)), int(m.group(3)),
+                                  1.0 if m.group(2) == "+" else -1.0))
+    assert set(prog) == {"right", "left"}
+    A = np.zeros((256, 256))
+    for r in range(256):
+        for c in range(256):
+            e = L.elem(r, c)
+            if e >= 0:
+                A[r, c] = M0[e]
+    for sname, rows in (("right", True), ("left", False)):
+        for qq, ss in enumerate(L.sectors):
+            for st in ss:
+                v = np.array([A[st, c] if rows else A[c, st] for c in ss])
+                for a, b, f, sg in prog[sname].get(qq, []):
+                    v[a] = v[a] + sg * fac[f] * v[b]
+                for i, c in enumerate(ss):
+                    if rows:
+                        A[st, c] = v[i]
+                    else:
+                        A[c, st] = v[i]
+    for qq, ss in enumerate(L.sectors):
+        for r in ss:
+            for c in ss:
+                assert A[r, c] == M[L.elem(r, c)]
 
 
 def _split(M, bits=7, nsl=6):
