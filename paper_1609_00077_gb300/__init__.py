@@ -530,18 +530,26 @@ def ph_gradient(occ_of_pair, vir_of_pair, h, eri, e_const=0.0, stream=None, want
     return rc, et.value, dh, dv, dk, info.as_dict()
 
 
-def _autograd_function():
+_FUNCTIONS = {}
+
+
+def _autograd_function(model="pq"):
+    """torch.autograd.Function of the PQ or PH total energy of (h, (pq|rs)):
+    forward solves the amplitudes and the Lambda equations (pq_gradient /
+    ph_gradient), backward returns the relaxed densities dE/dh and
+    dE/d(pq|rs) scaled by the incoming gradient."""
+    if model in _FUNCTIONS:
+        return _FUNCTIONS[model]
     import torch
+    grad_fn = pq_gradient if model == "pq" else ph_gradient
 
-    class PQEnergy(torch.autograd.Function):
-        """E_PQ(h, (pq|rs)) with the adjoint gradient in backward (FP64 CUDA tensors)."""
-
+    class Energy(torch.autograd.Function):
         @staticmethod
         def forward(ctx, h, eri, occ_of_pair, vir_of_pair, e_const, opts):
-            rc, e, dh, dv, dk, info = pq_gradient(occ_of_pair, vir_of_pair, h.contiguous(),
-                                                  eri.contiguous(), e_const, **(opts or {}))
+            rc, e, dh, dv, dk, info = grad_fn(occ_of_pair, vir_of_pair, h.contiguous(), eri.contiguous(), e_const,
+                                              **(opts or {}))
             if rc != 0:
-                raise PPQError(f"pq_gradient status {rc}")
+                raise PPQError(f"{model}_gradient status {rc}")
             ctx.save_for_backward(dh, dv)
             return h.new_tensor(e)
 
@@ -550,13 +558,40 @@ def _autograd_function():
             dh, dv = ctx.saved_tensors
             return g * dh, g * dv, None, None, None, None
 
-    return PQEnergy
+    Energy.__name__ = "PQEnergy" if model == "pq" else "PHEnergy"
+    _FUNCTIONS[model] = Energy
+    return Energy
 
 
-def pq_energy(h, eri, occ_of_pair, vir_of_pair, e_const=0.0, **opts):
+def _rotated(h, eri, kappa):
+    """(U^T h U, (pq|rs) in the rotated orbitals), U = exp(kappa - kappa^T):
+    the orbital rotation C -> C U as torch operations, so that autograd
+    carries dE/dh and dE/d(pq|rs) on to kappa."""
+    import torch
+    U = torch.linalg.matrix_exp(kappa - kappa.transpose(0, 1))
+    h2 = U.transpose(0, 1) @ h @ U
+    v2 = torch.einsum('pqrs,pi,qj,rk,sl->ijkl', eri, U, U, U, U)
+    return h2, v2
+
+
+def pq_energy(h, eri, occ_of_pair, vir_of_pair, e_const=0.0, kappa=None, **opts):
     """Differentiable PQ total energy (torch.autograd): gradients w.r.t. h and
-    (pq|rs) come from the Lambda equations (pq_gradient)."""
-    return _autograd_function().apply(h, eri, occ_of_pair, vir_of_pair, e_const, opts)
+    (pq|rs) come from the Lambda equations (pq_gradient).  With kappa (an
+    n_orb x n_orb tensor; only its antisymmetric part acts) the integrals are
+    first rotated by U = exp(kappa - kappa^T), so that the energy is also
+    differentiable in the orbitals: at kappa = 0 the gradient with respect to
+    kappa is the orbital-rotation gradient dE/dkappa of pq_gradient."""
+    if kappa is not None:
+        h, eri = _rotated(h, eri, kappa)
+    return _autograd_function("pq").apply(h, eri, occ_of_pair, vir_of_pair, e_const, opts)
+
+
+def ph_energy(h, eri, occ_of_pair, vir_of_pair, e_const=0.0, kappa=None, **opts):
+    """Differentiable PH total energy (torch.autograd) through ph_gradient;
+    kappa as in pq_energy."""
+    if kappa is not None:
+        h, eri = _rotated(h, eri, kappa)
+    return _autograd_function("ph").apply(h, eri, occ_of_pair, vir_of_pair, e_const, opts)
 
 
 def release():

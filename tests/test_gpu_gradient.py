@@ -9,7 +9,8 @@ facts the paper and mathematics fix:
   random symmetric directions in h and (pq|rs), and along a random orbital
   rotation, for 6 and 8 orbitals; tolerance 1e-6;
 * the same against GPU energies for 16 orbitals;
-* the torch.autograd function returns the same gradients.
+* the torch.autograd function returns the same gradients, and with an
+  orbital rotation kappa the same dE/dkappa.
 """
 import numpy as np
 import pytest
@@ -111,6 +112,13 @@ def test_gradient_vs_gpu_fd_h16_and_autograd():
     assert abs(float(E2.detach()) - e) < 1e-10
     assert float((h2.grad - dh).abs().max()) < 1e-10
     assert float((v2.grad - dv).abs().max()) < 1e-10
+    # the orbital-rotation gradient through autograd: E(U^T h U, U^4 eri),
+    # U = exp(kappa - kappa^T), at kappa = 0
+    kap = torch.zeros_like(h, requires_grad=True)
+    E3 = ppq.pq_energy(h, eri, H.occ_of_pair, H.vir_of_pair, H.e_const, kappa=kap, **TIGHT)
+    E3.backward()
+    assert abs(float(E3.detach()) - e) < 1e-10
+    assert float((kap.grad - dk).abs().max()) < 1e-9
 
 
 def test_h50_asymmetric_gradient_vs_central_differences():

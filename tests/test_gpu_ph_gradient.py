@@ -21,7 +21,9 @@
   3e-2 at this step, by 3e-4 at 1e-5) and along a random orbital rotation,
   tolerance 1e-6;
 * naphthalene (N = 5): central differences of converged GPU energies along
-  random directions and for single symmetric elements of h and (pq|rs).
+  random directions and for single symmetric elements of h and (pq|rs); the
+  torch.autograd function (ph_energy) returns the same dE/dh, dE/d(pq|rs)
+  and, through an orbital rotation, dE/dkappa.
 """
 import numpy as np
 import pytest
@@ -184,3 +186,20 @@ def test_ph_gradient_naphthalene_against_gpu_energy_differences():
             D[a, b, c, d] = 1.0
         fd = (E(H.h, H.eri + step * D) - E(H.h, H.eri - step * D)) / (2 * step)
         assert abs(fd - np.sum(dv * D)) < 1e-6, ((p, q, r, s), fd, np.sum(dv * D))
+
+
+def test_ph_energy_autograd_naphthalene():
+    H = build_ppp('acene', 2)
+    h, eri = dev(H.h), dev(H.eri)
+    rc, e, dh, dv, dk, info = ppq.ph_gradient(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, precision=0,
+                                              **TIGHT)
+    assert rc == 0
+    h2 = h.clone().requires_grad_(True); v2 = eri.clone().requires_grad_(True)
+    kap = torch.zeros_like(h, requires_grad=True)
+    E = ppq.ph_energy(h2, v2, H.occ_of_pair, H.vir_of_pair, H.e_const, kappa=kap, precision=0, **TIGHT)
+    E.backward()
+    assert abs(float(E.detach()) - e) < 1e-10
+    # at kappa = 0 the rotation is the identity: h and (pq|rs) receive dE/dh, dE/d(pq|rs)
+    assert float((h2.grad - dh).abs().max()) < 1e-9
+    assert float((v2.grad - dv).abs().max()) < 1e-9
+    assert float((kap.grad - dk).abs().max()) < 1e-9

@@ -327,3 +327,28 @@ def test_local_assembly_truncated_integrals_h10():
     R1, e1 = P.residual(t)
     R2, e2 = L.residual(t)
     assert np.abs(R1 - R2).max() < 1e-12 and abs(e1 - e2) < 1e-12
+
+
+def test_fci_lanczos_branch():
+    # The Lanczos branch of fci_energy (spaces above 800 determinants) against
+    # the dense eigensolver on the same sigma products (the lowest 7 orbitals of
+    # octatetraene, 3 + 3 electrons: 1225 determinants), and against the
+    # additivity of FCI over
+    # two non-interacting fragments: butadiene + H4 has 4900 determinants
+    # (Lanczos) while each fragment has 36 (dense).
+    from oracle.fci import Strings, sigma
+    H = build_ppp('polyene', 8)
+    h7, eri7 = H.h[:7, :7].copy(), H.eri[:7, :7, :7, :7].copy()
+    S = Strings(7, 3)
+    dim = S.n * S.n
+    assert dim == 1225
+    Hm = np.empty((dim, dim))
+    for j in range(dim):
+        c = np.zeros(dim); c[j] = 1.0
+        Hm[:, j] = sigma(S, h7, eri7, c.reshape(S.n, S.n)).ravel()
+    e_dense = float(np.linalg.eigvalsh(0.5 * (Hm + Hm.T))[0])
+    assert abs(fci_energy(h7, eri7, 3) - e_dense) < 1e-10
+    A, B = build_ppp('polyene', 4), build_hchain(4, 1.6)
+    AB = _direct_sum(A, B)
+    e_ab = fci_energy(AB.h, AB.eri, 4, AB.e_const)
+    assert abs(e_ab - (fci_energy(A.h, A.eri, 2, A.e_const) + fci_energy(B.h, B.eri, 2, B.e_const))) < 1e-9
