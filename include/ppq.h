@@ -97,6 +97,13 @@ typedef struct {
                       /*     each outer step evaluates R in FP64 (norm, energy, */
                       /*     convergence test) and solves J d = -R with FP32    */
                       /*     finite-difference Jacobian products (default 1)    */
+  int max_rank;       /* excitation-rank mask (Conclusions: higher excitations  */
+                      /*     disabled, e.g. PH with singles and doubles only,   */
+                      /*     a local CCSD): 0 = every rank; r = 1..6 keeps the  */
+                      /*     amplitudes of excitation rank <= r and drops the   */
+                      /*     residual equations of the others (the label-subset */
+                      /*     solver: ph_solve, ph_solve_cd, ph_gradient, and    */
+                      /*     pq_solve with K_H = -1); default 0                 */
 } ppq_opts;
 
 typedef struct {

@@ -60,9 +60,12 @@ def truncated_hamiltonian(h, eri, occ_of_pair, vir_of_pair, K_H):
     return hp, vt, f, e_ref
 
 
-def enumerate_manifold(occ_of_pair, vir_of_pair, K):
+def enumerate_manifold(occ_of_pair, vir_of_pair, K, max_rank=0):
     """All M_s-conserving excitations whose orbitals span 1..K pair labels.
-    Each is (a_holes, a_parts, b_holes, b_parts) as sorted spatial indices."""
+    Each is (a_holes, a_parts, b_holes, b_parts) as sorted spatial indices.
+    max_rank > 0 keeps only excitations of at most that many electrons (the
+    Conclusions section: higher excitations disabled, e.g. PH with singles and
+    doubles only)."""
     N = len(occ_of_pair)
     out = []
     for m in range(1, min(K, N) + 1):
@@ -79,6 +82,8 @@ def enumerate_manifold(occ_of_pair, vir_of_pair, K):
             for ah, ap in sides:
                 for bh, bp in sides:
                     if not (ah or bh):
+                        continue
+                    if max_rank and len(ah) + len(bh) > max_rank:
                         continue
                     labs = {lab[x] for x in ah + ap + bh + bp}
                     if len(labs) == m:
@@ -178,13 +183,14 @@ class Problem:
     """A PQ/PH problem: Hamiltonian + pairing + truncation, with residual,
     energy and the Jacobi/DIIS solver of the amplitude equations."""
 
-    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0, e_const=0.0):
+    def __init__(self, h, eri, occ_of_pair, vir_of_pair, K, K_H=0, e_const=0.0, max_rank=0):
         self.K = K
         self.K_H = K if K_H == 0 else K_H
         self.hp, self.vt, self.f, e_ref = truncated_hamiltonian(
             h, eri, occ_of_pair, vir_of_pair, self.K_H)
         self.e_ref = e_ref + e_const
-        self.cc = DetCC(h.shape[0], occ_of_pair, vir_of_pair, K)
+        man = enumerate_manifold(occ_of_pair, vir_of_pair, K, max_rank) if max_rank else None
+        self.cc = DetCC(h.shape[0], occ_of_pair, vir_of_pair, K, manifold=man)
         self.e_ref_bare = self.cc.reference_energy(self.hp, self.vt)
 
     def residual(self, t):

@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
                 ("e_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_dim", ctypes.c_int), ("diis_start", ctypes.c_int),
                 ("level_shift", ctypes.c_double), ("guess", ctypes.c_int),
-                ("profile", ctypes.c_int), ("polish", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("polish", ctypes.c_int), ("max_rank", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -147,6 +147,23 @@ __device__ __forceinline__ int is_unique(size_t i, int N) {
   return P < Q && Q < R;
 }
 
+// excitation rank (number of holes) of the amplitude at layout index i
+__device__ __forceinline__ int slot_rank(size_t i, int N) {
+  if (i < (size_t)3 * N) return ppq_nhole[ppq_A1[i % 3]];
+  if (i < off3(N)) {
+    int ch = (i - 3 * N) % 29;
+    return ppq_nhole[ppq_A2[2 * ch]] + ppq_nhole[ppq_A2[2 * ch + 1]];
+  }
+  int ch = (i - off3(N)) % kNA3;
+  return ppq_nhole[c_A3[3 * ch]] + ppq_nhole[c_A3[3 * ch + 1]] + ppq_nhole[c_A3[3 * ch + 2]];
+}
+
+// a unique slot that the excitation-rank mask keeps (mr = 0: every rank;
+// Conclusions: higher excitations disabled)
+__device__ __forceinline__ int is_active(size_t i, int N, int mr) {
+  return is_unique(i, N) && (mr == 0 || slot_rank(i, N) <= mr);
+}
+
 // orbital-energy denominator of a unique slot (Implementation section)
 __device__ __forceinline__ double denom3(size_t i, int N, const double* fo, const double* fv, double shift) {
   int lab[3], mon[3], m;
@@ -515,9 +532,10 @@ __global__ void k_fill_copies(size_t L, int N, int K, double* __restrict__ v) {
 }
 
 // ------------------------------------------------------------ solver kernels
-// rows: 0 -> sum over unique slots of x0^2; j >= 1 -> <e_slot[order[j-1]], e_slot[inew]>
-__global__ void k_udots(size_t L, int N, const double* __restrict__ x0, int m, const double* __restrict__ slots,
-                        size_t ld, const int* __restrict__ order, int inew, double* __restrict__ part) {
+// rows: 0 -> sum over active unique slots of x0^2; j >= 1 -> <e_slot[order[j-1]], e_slot[inew]>
+__global__ void k_udots(size_t L, int N, int mr, const double* __restrict__ x0, int m,
+                        const double* __restrict__ slots, size_t ld, const int* __restrict__ order, int inew,
+                        double* __restrict__ part) {
   __shared__ double red[32];
   int row = blockIdx.y;
   const double* a;
@@ -526,7 +544,7 @@ __global__ void k_udots(size_t L, int N, const double* __restrict__ x0, int m, c
   else { a = slots + (size_t)order[row - 1] * ld; b = slots + (size_t)inew * ld; }
   double s = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (size_t)gridDim.x * blockDim.x)
-    if (is_unique(i, N)) s += a[i] * b[i];
+    if (is_active(i, N, mr)) s += a[i] * b[i];
   s = ppq::block_sum(s, red);
   if (threadIdx.x == 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
 }
@@ -545,13 +563,20 @@ __global__ void k_rows(int nb, int rows, const double* __restrict__ part, const 
   if (threadIdx.x == 0 && e) out[rows] = *e;
 }
 
-// Jacobi step on the unique slots: tn = t + r / D, en = r / D; zero elsewhere
-__global__ void k_jacobi3(size_t L, int N, const double* __restrict__ t, const double* __restrict__ r,
+// zero the unique slots the excitation-rank mask drops
+__global__ void k_mask_rank(size_t L, int N, int mr, double* __restrict__ t) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L && is_unique(i, N) && !is_active(i, N, mr)) t[i] = 0.0;
+}
+
+// Jacobi step on the active unique slots: tn = t + r / D, en = r / D; zero
+// elsewhere (copies, and slots the excitation-rank mask drops)
+__global__ void k_jacobi3(size_t L, int N, int mr, const double* __restrict__ t, const double* __restrict__ r,
                           const double* __restrict__ fo, const double* __restrict__ fv, double shift,
                           double* __restrict__ tn, double* __restrict__ en) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
-  if (!is_unique(i, N)) { tn[i] = 0.0; en[i] = 0.0; return; }
+  if (!is_active(i, N, mr)) { tn[i] = 0.0; en[i] = 0.0; return; }
   double d = denom3(i, N, fo, fv, shift);
   double e = d != 0.0 ? r[i] / d : 0.0;
   tn[i] = t[i] + e;
@@ -1043,7 +1068,7 @@ struct PhSolver {
     int rc = residual_any(c, N, K, KH, prec, c->t, c->r, c->e, s);
     if (rc) return rc;
     CK(cudaEventRecord(ev1, s));
-    k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, c->r, 0, c->slot_e, L, c->order, 0, c->part);
+    k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, o.max_rank, c->r, 0, c->slot_e, L, c->order, 0, c->part);
     k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1, c->part, c->e, c->rows);
     CK(cudaMemcpyAsync(c->host, c->rows, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
     g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
@@ -1073,11 +1098,12 @@ struct PhSolver {
     int m = (int)act.size();
     double* st = c->slot_t + (size_t)slot * L;
     double* se = c->slot_e + (size_t)slot * L;
-    k_jacobi3<<<lb, 256, 0, s>>>(L, N, x, res, w->fo, w->fv, o.level_shift, st, se);
+    k_jacobi3<<<lb, 256, 0, s>>>(L, N, o.max_rank, x, res, w->fo, w->fv, o.level_shift, st, se);
     int* ho = (int*)(c->host + 32);
     for (int i = 0; i < m; ++i) ho[i] = act[i];
     CK(cudaMemcpyAsync(c->order, ho, sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    k_udots<<<dim3(kRedBlocks, 1 + m), 256, 0, s>>>(L, N, se, m, c->slot_e, L, c->order, slot, c->part);
+    k_udots<<<dim3(kRedBlocks, 1 + m), 256, 0, s>>>(L, N, o.max_rank, se, m, c->slot_e, L, c->order, slot,
+                                                   c->part);
     k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, c->part, nullptr, c->rows);
     int extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
     k_diis_solve<<<1, 32, 0, s>>>(m, c->order, slot, c->rows, c->B, kDiisMax, extrap, c->coef);
@@ -1096,7 +1122,7 @@ struct PhSolver {
   }
   // weighted norm of x over the unique slots (host value)
   int norm(const double* x, double* out) {
-    k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, x, 0, c->slot_e, L, c->order, 0, c->part);
+    k_udots<<<dim3(kRedBlocks, 1), 256, 0, s>>>(L, N, o.max_rank, x, 0, c->slot_e, L, c->order, 0, c->part);
     k_rows<<<1, 256, 0, s>>>(kRedBlocks, 1, c->part, nullptr, c->rows);
     CK(cudaMemcpyAsync(c->host, c->rows, sizeof(double), cudaMemcpyDeviceToHost, s));
     g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
@@ -1166,6 +1192,7 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
   if (o.guess == 1 && !t_in) return fail(-2, "guess = 1 needs t_in");
+  if (o.max_rank < 0 || o.max_rank > 2 * K) return fail(-4, "max_rank must be 0 (every rank) or 1..%d", 2 * K);
   if (n_pairs > 127) return fail(-1, "n_pairs must be <= 127 for the label-subset solver");
   Workspace* w = nullptr;
   Problem P;
@@ -1188,6 +1215,7 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
   if ((rc = ph::grow_solver(c, L, m_max))) return rc;
   if (o.guess == 1) {
     CK(cudaMemcpyAsync(c->t, t_in, sizeof(double) * L, cudaMemcpyDefault, s));
+    if (o.max_rank) ph::k_mask_rank<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, o.max_rank, c->t);
     ph::k_fill_copies<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, N, K, c->t);
   } else {
     CK(cudaMemsetAsync(c->t, 0, sizeof(double) * L, s));

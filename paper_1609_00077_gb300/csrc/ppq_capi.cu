@@ -1438,7 +1438,7 @@ int ppq_default_opts(ppq_opts* o) {
   o->K = 2; o->K_H = 0; o->precision = 0;
   o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-10;
   o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
-  o->level_shift = 0.0; o->guess = 0; o->profile = 0; o->polish = 1;
+  o->level_shift = 0.0; o->guess = 0; o->profile = 0; o->polish = 1; o->max_rank = 0;
   return 0;
 }
 
@@ -1557,6 +1557,9 @@ int validate_opts(const ppq_opts& o, bool allow_full = false) {
   if (o.polish != 0 && o.polish != 1) return fail(-4, "polish must be 0 or 1");
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
+  if (o.max_rank < 0 || o.max_rank > 6) return fail(-4, "max_rank must be 0 (every rank) or 1..6");
+  if (o.max_rank != 0 && o.K_H != -1)
+    return fail(-4, "max_rank needs the label-subset solver (ph_solve, or pq_solve with K_H = -1)");
   return 0;
 }
 
@@ -1716,6 +1719,7 @@ int pq_solve(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, const 
     ppq_opts o1 = o;
     o1.guess = 0;
     o1.profile = 0;
+    o1.max_rank = o.max_rank == 1 ? 1 : 0;  // single-pair amplitudes have ranks 1 and 2
     size_t L = amp_len(n_pairs);
     pp.assign(L, 0.0);
     int rc1 = subset_solve(1, 2, n_pairs, occ_of_pair, vir_of_pair, h, eri, nullptr, 0, 0.0, o1, nullptr, pp.data(),

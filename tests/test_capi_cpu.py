@@ -61,6 +61,10 @@ def test_ph_entry_points_reject_bad_arguments_without_gpu():
         ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri, K_H=4)
     with pytest.raises(ppq.PPQError, match="twice"):
         ppq.ph_solve([2, 2, 0], [3, 4, 5], h, eri)
+    with pytest.raises(ppq.PPQError, match=r"pq_solve failed \(-4\).*max_rank"):
+        ppq.pq_solve([2, 1, 0], [3, 4, 5], h, eri, max_rank=2)
+    with pytest.raises(ppq.PPQError, match=r"ph_solve failed \(-4\).*max_rank"):
+        ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri, max_rank=7)
     t = np.zeros(ppq.amp_count(3, 3))
     with pytest.raises(ppq.PPQError, match=r"ph_residual failed \(-4\).*K_H"):
         ppq.ph_residual([2, 1, 0], [3, 4, 5], h, eri, t, K_H=1)

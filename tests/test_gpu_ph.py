@@ -21,7 +21,9 @@ Cases:
     random amplitudes inside the fragments: each fragment's elements equal its
     own oracle residual, the mixed elements vanish, the energies add;
   * ph_solve: FCI at 6e/6o (PH is exact there), the oracle's PH energy for
-    octatetraene, additivity over the direct sum, mixed against FP64.
+    octatetraene, additivity over the direct sum, mixed against FP64, and the
+    excitation-rank mask (ranks <= 2 and <= 4) against the oracle on the
+    reduced manifold.
 """
 import os
 
@@ -209,3 +211,27 @@ def test_ph_solve_direct_sum_is_additive_n7():
     rc, e, _, info = ppq.ph_solve(AB.occ_of_pair, AB.vir_of_pair, dev(AB.h), dev(AB.eri), AB.e_const,
                                   precision=0, max_iter=300)
     assert rc == 0 and abs(e - (ea + eb)) < 1e-9, (e, ea + eb)
+
+
+@pytest.mark.parametrize("max_rank", [2, 4])
+def test_ph_solve_excitation_rank_mask_matches_oracle(max_rank):
+    # PH with the excitations above max_rank disabled (Conclusions: PH with
+    # singles and doubles is a local CCSD) against the oracle on the same
+    # reduced manifold; the dropped amplitudes stay zero
+    H = build_ppp('polyene', 8)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, K_H=3, e_const=H.e_const, max_rank=max_rank)
+    res = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    assert res['converged']
+    eo = res['e_corr'] + P.e_ref
+    rc, e, t, info = ppq.ph_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const, precision=0,
+                                  max_rank=max_rank)
+    assert rc == 0 and abs(e - eo) < 1e-9, (e, eo)
+    lm = LayoutMap(P.cc.manifold, H.occ_of_pair, H.vir_of_pair, H.n_orb, _layout3())
+    assert np.abs(lm.from_layout(t) - res['t']).max() < 1e-7
+    full = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 3)
+    dropped = [k for k, (ah, ap, bh, bp) in enumerate(full) if len(ah) + len(bh) > max_rank]
+    lf = LayoutMap(full, H.occ_of_pair, H.vir_of_pair, H.n_orb, _layout3())
+    assert len(dropped) > 0 and np.abs(lf.from_layout(t)[dropped]).max() == 0.0
+    rc, em, _, _ = ppq.ph_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const, precision=1,
+                                max_rank=max_rank)
+    assert rc == 0 and abs(em - eo) < 1e-8

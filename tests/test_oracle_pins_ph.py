@@ -11,6 +11,12 @@
 * Size consistency of PH (Theory section): a direct sum of a three-pair and a
   one-pair fragment, pairs interleaved, has the sum of the fragment FCI
   energies (PH is exact for each fragment).
+* The excitation-rank mask (Conclusions: higher excitations disabled; PH
+  with singles and doubles is a local CCSD): with ranks <= 2 kept, three
+  non-interacting H2 molecules (one pair each) still get the sum of their FCI
+  energies (CCSD is exact for two electrons, and the connected higher
+  excitations of a product of two-electron fragments vanish), while
+  hexatriene does not get its FCI energy; with every rank kept (6) it does.
 """
 import numpy as np
 import pytest
@@ -127,3 +133,24 @@ def test_ph_size_consistency_three_plus_one_pairs():
     fa = fci_energy(A.h, A.eri, 3, A.e_const)
     fb = fci_energy(B.h, B.eri, 1, B.e_const)
     assert abs(r['e_corr'] + P.e_ref - (fa + fb)) < 1e-9
+
+
+def test_excitation_rank_mask():
+    A, B, C = build_hchain(2, 1.4), build_hchain(2, 1.5), build_hchain(2, 1.3)
+    ABC = _direct_sum(_direct_sum(A, B), C)
+    P = Problem(ABC.h, ABC.eri, ABC.occ_of_pair, ABC.vir_of_pair, K=3, e_const=ABC.e_const, max_rank=2)
+    assert P.cc.n_amp < Problem(ABC.h, ABC.eri, ABC.occ_of_pair, ABC.vir_of_pair, K=3).cc.n_amp
+    r = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+    assert r['converged']
+    fsum = sum(fci_energy(X.h, X.eri, 1, X.e_const) for X in (A, B, C))
+    assert abs(r['e_corr'] + P.e_ref - fsum) < 1e-9
+    H = build_ppp('polyene', 6)
+    fci = fci_energy(H.h, H.eri, 3, H.e_const)
+    es = {}
+    for mr in (2, 4, 6):
+        P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=3, e_const=H.e_const, max_rank=mr)
+        r = P.solve(r_tol=1e-11, e_tol=1e-13, max_iter=400)
+        assert r['converged']
+        es[mr] = r['e_corr'] + P.e_ref
+    assert abs(es[6] - fci) < 1e-9
+    assert abs(es[2] - fci) > 1e-4 and abs(es[4] - fci) < abs(es[2] - fci)
