@@ -58,6 +58,8 @@ def parse():
                     help="PH leg: acenes by ring count (2 naphthalene .. 7 heptacene); '' to skip")
     ap.add_argument("--ph-fp64-max-rings", type=int, default=5,
                     help="largest acene also solved FP64-only beside the mixed solve")
+    ap.add_argument("--ph-grad-max-rings", type=int, default=4,
+                    help="largest acene whose PH energy gradient (Lambda equations) is timed")
     return ap.parse_args()
 
 
@@ -357,6 +359,20 @@ def ph_leg(args, stream, pk):
                  "n_pairs": H.n_pairs, "mixed": rows[1], "fp64": rows.get(0)}
         if 0 in rows:
             entry["abs_dE_mixed_vs_fp64"] = abs(rows[1]["e_total"] - rows[0]["e_total"])
+        if nr <= args.ph_grad_max_rings:
+            # energy gradient: mixed amplitude solve, FP64 Lambda equations, dE/dh,
+            # dE/d(pq|rs), dE/dkappa (device outputs)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rcg, eg, dh, dv, dk, ginfo = ppq.ph_gradient(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const,
+                                                         precision=1, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry["gradient"] = {"seconds": e0.elapsed_time(e1) / 1e3, "status": rcg,
+                                 "abs_dE_vs_mixed_solve": abs(eg - rows[1]["e_total"]),
+                                 "trace_dE_dh": float(torch.trace(dh)), "electrons": 2 * H.n_pairs,
+                                 "max_abs_dE_dkappa": float(dk.abs().max())}
         out["systems"].append(entry)
         last = (H, h, eri)
     if last is not None:
