@@ -187,7 +187,7 @@ __global__ void k_site_closure(int N, const R* __restrict__ g1, const double* __
 // adjoint's forward recomputation).
 struct ClosureSmem {
   static constexpr int kM = PPQ_BLKP + 8;
-  static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2;   // pre-scaled integrals
+  static constexpr int kG = PPQ_H2_NCODE * PPQ_NG2 + 8;   // pre-scaled integrals, then zeros
   template <typename R>
   static __host__ __device__ constexpr size_t off_oel() { return ((kM + kG + 72) * sizeof(R) + 15) / 16 * 16; }
   template <typename R>
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(
   for (int i = tid; i < PPQ_NS36; i += blockDim.x) oel[i] = ppq_g_elp[i];
   for (int i = tid; i < PPQ_NT7E; i += blockDim.x) oel[PPQ_NS36 + i] = ppq_t7_elp[i];
   for (int i = tid; i < PPQ_NCOL0; i += blockDim.x) oel[PPQ_NS36 + PPQ_NT7E + i] = ppq_col0_elp[i];
+  if (tid < 8) gsv[PPQ_H2_NCODE * PPQ_NG2 + tid] = R(0);  // the zero term of the padded streams
   // this thread's row / column (blockDim.x == 256 two-site states, by sector)
   const int st = ppq_th_state[tid];
   const int q = ppq_st_sec[st], dp = ppq_sec_dim[q] + 1;
@@ -241,12 +242,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_pair_closure_p(
     }
     for (int i = tid; i < ClosureSmem::kM; i += blockDim.x) M[i] = R(0);
     __syncthreads();
-    for (int el = tid; el < PPQ_H2_NEL; el += blockDim.x) {
-      // the Hamiltonian CSR is read through L1 (the same 52 KB for every pair)
+    {
+      // the Hamiltonian gather as this thread's term stream (coalesced words
+      // read through L1, the same 70 KB for every pair): sum the pre-scaled
+      // integrals of an element, store it at its last term
       R acc = R(0);
-      const int p1 = __ldg(ppq_h2_ptr + el + 1);
-      for (int p = __ldg(ppq_h2_ptr + el); p < p1; ++p) acc += gsv[__ldg(ppq_h2_cj + p)];
-      M[__ldg(ppq_h2_elp + el)] = acc;
+      const uint32_t* sw = ppq_h2_stream + tid;
+#pragma unroll 8
+      for (int j = 0; j < PPQ_H2_SLEN; ++j) {
+        const uint32_t w = __ldg(sw + (size_t)j * 256);
+        acc += gsv[w & 0x7FFu];
+        if (w >> 31) {
+          M[(w >> 11) & 0x1FFFu] = acc;
+          acc = R(0);
+        }
+      }
     }
     __syncthreads();
     const R h00 = M[PPQ_EL00P];

@@ -729,6 +729,34 @@ def emit_header(path):
         return pbase[q] + r * (L.dim[q] + 1) + c
     out += [f"#define PPQ_BLKP {off}", _c_array("ppq_sec_pbase", "int16_t", np.array(pbase)),
             _c_array("ppq_h2_elp", "int16_t", np.array([padded(e) for e in e2]))]
+    # the gather as one term stream per thread (256 threads): elements dealt
+    # out longest first to the least-loaded thread, a thread's terms stored at
+    # [j][thread] (coalesced), padded with zero terms to the longest stream.
+    # Word: gsv index (11 bits) | padded element offset << 11 (13 bits) |
+    # last term of its element << 31; the zero term reads gsv index 1160.
+    cnt = np.diff(p2)
+    load = [0] * 256
+    own = [[] for _ in range(256)]
+    for el in sorted(range(len(e2)), key=lambda x: (-int(cnt[x]), x)):
+        t = int(np.argmin(load))
+        own[t].append(el)
+        load[t] += int(cnt[el])
+    slen = max(load)
+    zero_term = len(codes) * PPQ_NG2_VALUE
+    assert zero_term < 2048 and off < 8192
+    stream = np.full((slen, 256), zero_term, dtype=np.int64)
+    cj_all = cidx * PPQ_NG2_VALUE + np.asarray(j2).astype(np.int64)
+    for t in range(256):
+        j = 0
+        for el in sorted(own[t]):
+            for k in range(p2[el], p2[el + 1]):
+                w = int(cj_all[k]) | (padded(e2[el]) << 11)
+                if k == p2[el + 1] - 1:
+                    w |= 1 << 31
+                stream[j, t] = w
+                j += 1
+    out += [f"#define PPQ_H2_SLEN {slen}",
+            _c_array("ppq_h2_stream", "uint32_t", stream.ravel())]
     padded_of = padded
     # outputs of the pair closure: G row, T7 entries, column-0 entries, element (0,0)
     g_el = [L.elem(0, 16 * a + b) for a, b in st]
