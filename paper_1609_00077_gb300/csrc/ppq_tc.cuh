@@ -139,17 +139,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-// 8 consecutive TMEM columns of this thread's lane, waited on before return
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+// 8 consecutive TMEM columns of this thread's lane, issued without waiting:
+// the registers are valid after tmem_wait8 on the same array
+__device__ __forceinline__ void tmem_issue8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+// wait for the issued TMEM loads; the registers pass through the wait so that
+// no use of them is scheduled before it
+__device__ __forceinline__ void tmem_wait8(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
 }
 // 4 consecutive TMEM columns of this thread's lane, waited on before return
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
@@ -403,27 +406,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float* py = clT + (size_t)c[0] * NNp + Y;     // Cl[W,Y][c3] at W * N
           const float* pz = clT + (size_t)c[1] * NNp + Z;     // Cl[W,Z][c4] at W * N
           float v0 = 0.f, v1 = 0.f;
+          // software pipeline: the Cl factors of block W0 + 8 are loaded while
+          // the TMEM columns of block W0 are in flight
+          float a[8], bz[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            a[i] = i < N ? __ldg(py + i * N) : 0.f;
+            bz[i] = i < N ? __ldg(pz + i * N) : 0.f;
+          }
 #pragma unroll
           for (int W0 = 0; W0 < NW; W0 += 8) {
-            float a[8], bz[8], D[8];
-            if (W0 + 8 <= N) {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) { a[i] = __ldg(py + i * N); bz[i] = __ldg(pz + i * N); }
-            } else {
+            uint32_t D[8];
+            tmem_issue8(col + (uint32_t)W0, D);
+            float an[8], bn[8];
+            if (W0 + 8 < NW) {
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                a[i] = W0 + i < N ? __ldg(py + i * N) : 0.f;
-                bz[i] = W0 + i < N ? __ldg(pz + i * N) : 0.f;
+                const bool in = W0 + 8 + i < N;
+                an[i] = in ? __ldg(py + (W0 + 8 + i) * N) : 0.f;
+                bn[i] = in ? __ldg(pz + (W0 + 8 + i) * N) : 0.f;
               }
             }
-            tmem_ld8(col + (uint32_t)W0, D);
+            tmem_wait8(D);
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
-              v0 = fmaf(D[i] * a[i], bz[i], v0);
-              v1 = fmaf(D[i + 1] * a[i + 1], bz[i + 1], v1);
+              v0 = fmaf(__uint_as_float(D[i]) * a[i], bz[i], v0);
+              v1 = fmaf(__uint_as_float(D[i + 1]) * a[i + 1], bz[i + 1], v1);
             }
-            py += 8 * N;
-            pz += 8 * N;
+            if (W0 + 8 < NW) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) { a[i] = an[i]; bz[i] = bn[i]; }
+            }
           }
           if (valid) acc[c[2]] += 0.5f * float(c[3]) * (v0 + v1);
         }
