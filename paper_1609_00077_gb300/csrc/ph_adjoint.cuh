@@ -347,7 +347,19 @@ struct AdjCtx {
   size_t cap_n = 0;
   double *dhp = nullptr, *gh_raw = nullptr, *gh = nullptr, *gv_raw = nullptr, *gv = nullptr, *dk = nullptr,
          *ab = nullptr;
+  // forward quantities of every chunk (psi, psi_minus, phi, t, v, E_0 per
+  // subset) kept in HBM while t is fixed (the Lambda iterations, then the
+  // integral gradients): a reverse pass then runs only the reverse kernels
+  bool fwd_valid = false;
+  int fwd_key = -1;
+  void* fwd[kMaxSites + 1] = {};
+  size_t fwd_cap[kMaxSites + 1] = {};
 };
+
+// bytes of the cached forward quantities of one chunk of P subsets of k sites
+inline size_t fwd_chunk_bytes(const DevTables* T, int P) {
+  return (size_t)(T->nstate + 2 * (size_t)T->nout + T->nslot + T->nkey + 1) * P * sizeof(double);
+}
 
 std::map<int, AdjCtx*> g_ph_adj;
 
@@ -445,10 +457,35 @@ int adjoint_local(Ctx* c, AdjCtx* a, DevTables* T, DevAdj* D, int P, int p0, int
 // grad_t L at amplitudes c->t and multipliers lam (layout, copies consistent)
 // into grad (unique slots assembled, copies filled); with keys also the
 // adjoints of the gathered integrals into a->Gb[m] (label sets in colex order)
+//
+// cache: keep (or reuse) the forward quantities of every chunk in HBM; the
+// caller guarantees that t is unchanged while a->fwd_valid is set
 int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, double* grad, bool keys,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool cache = false) {
   int rc;
   int kfull = K + KH, kmax = std::min(kfull, N);
+  const int key = (N * 8 + K) * 8 + KH;
+  bool reuse = cache && a->fwd_valid && a->fwd_key == key;
+  bool fill = cache && !reuse;
+  if (fill) {
+    // the cache grows only while it stays within half of the free device memory
+    size_t extra = 0;
+    for (int k = 1; k <= kmax; ++k) {
+      DevTables* T;
+      if ((rc = dev_tables(c, k, K, KH, &T))) return rc;
+      int nsub = c->nsub[k];
+      int J = nsub >= 384 ? 4 : nsub >= 96 ? 2 : 1;
+      int P = chunk_size(nsub, T->nstate, 2 * sizeof(double), 32 * J);
+      size_t need = fwd_chunk_bytes(T, P) * (size_t)((nsub + P - 1) / P);
+      if (need > a->fwd_cap[k]) extra += need;
+    }
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if (extra > fr / 2) fill = false;
+    a->fwd_valid = false;
+  }
+  struct Saved { void *psi, *psim, *phi, *tl, *vl; double* e0; } saved{c->psi, c->psim, c->phi, c->tl, c->vl,
+                                                                        c->e0loc};
   AsmArgs A{};
   A.kmax = kmax;
   KeyAsm KA{};
@@ -476,29 +513,49 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
       return rc;
     if (keys && (rc = grow_buf((void**)&a->Vloc[k], &a->cap_V[k], (size_t)T->nkey * nsub * sizeof(double))))
       return rc;
-    double* tl = (double*)c->tl;
-    double* vl = (double*)c->vl;
+    const size_t cb = fwd_chunk_bytes(T, P);
+    if (fill && (rc = grow_buf(&a->fwd[k], &a->fwd_cap[k], cb * (size_t)((nsub + P - 1) / P)))) return rc;
     for (int p0 = 0; p0 < nsub; p0 += P) {
+      if (fill || reuse) {
+        // this chunk's forward quantities live in the cache
+        double* base = (double*)((char*)a->fwd[k] + cb * (size_t)(p0 / P));
+        c->psi = base;
+        c->psim = base + (size_t)T->nstate * P;
+        c->phi = base + (size_t)(T->nstate + T->nout) * P;
+        c->tl = base + (size_t)(T->nstate + 2 * (size_t)T->nout) * P;
+        c->vl = base + (size_t)(T->nstate + 2 * (size_t)T->nout + T->nslot) * P;
+        c->e0loc = base + (size_t)(T->nstate + 2 * (size_t)T->nout + T->nslot + T->nkey) * P;
+      }
+      double* tl = (double*)c->tl;
+      double* vl = (double*)c->vl;
       size_t nt = (size_t)T->nslot * P, nk = (size_t)T->nkey * P, nw = (size_t)(T->nslot + 1) * P;
-      k_gather_amp<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc,
-                                                                        c->subs[k], N, t, tl);
-      k_gather_int<double><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
-                                                                        c->subs[k], N, c->G1, c->G2, c->G3, c->G4,
-                                                                        vl);
-      k_set_ref<double><<<(P + 127) / 128, 128, 0, s>>>(P, (double*)c->psi, (double*)c->psim, T->ne0, T->e0_key,
-                                                        T->e0_cd, vl, c->e0loc);
+      if (!reuse) {
+        k_gather_amp<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc,
+                                                                          c->subs[k], N, t, tl);
+        k_gather_int<double><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
+                                                                          c->subs[k], N, c->G1, c->G2, c->G3, c->G4,
+                                                                          vl);
+        k_set_ref<double><<<(P + 127) / 128, 128, 0, s>>>(P, (double*)c->psi, (double*)c->psim, T->ne0, T->e0_key,
+                                                          T->e0_cd, vl, c->e0loc);
+        c->n_launches += 3;
+      }
       k_gather_w<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc, c->subs[k], N,
                                                               lam, ck, ce, a->wl);
-      c->n_launches += 4;
+      c->n_launches++;
       g_prof.done("ph::gather (amplitudes, integrals, multipliers)", s,
-                  (double)(2 * T->nslot + T->nkey) * P * 16.0);
-      if (J == 4) rc = local_problem<double, 4>(c, T, P, p0, nsub, k, s, false);
-      else if (J == 2) rc = local_problem<double, 2>(c, T, P, p0, nsub, k, s, false);
-      else rc = local_problem<double, 1>(c, T, P, p0, nsub, k, s, false);
-      if (rc) return rc;
-      if (J == 4) rc = adjoint_local<4>(c, a, T, D, P, p0, nsub, k, keys, s);
-      else if (J == 2) rc = adjoint_local<2>(c, a, T, D, P, p0, nsub, k, keys, s);
-      else rc = adjoint_local<1>(c, a, T, D, P, p0, nsub, k, keys, s);
+                  (double)((reuse ? 1 : 2) * T->nslot + (reuse ? 0 : T->nkey)) * P * 16.0);
+      if (!reuse) {
+        if (J == 4) rc = local_problem<double, 4>(c, T, P, p0, nsub, k, s, false);
+        else if (J == 2) rc = local_problem<double, 2>(c, T, P, p0, nsub, k, s, false);
+        else rc = local_problem<double, 1>(c, T, P, p0, nsub, k, s, false);
+      }
+      if (!rc) {
+        if (J == 4) rc = adjoint_local<4>(c, a, T, D, P, p0, nsub, k, keys, s);
+        else if (J == 2) rc = adjoint_local<2>(c, a, T, D, P, p0, nsub, k, keys, s);
+        else rc = adjoint_local<1>(c, a, T, D, P, p0, nsub, k, keys, s);
+      }
+      c->psi = saved.psi; c->psim = saved.psim; c->phi = saved.phi; c->tl = saved.tl; c->vl = saved.vl;
+      c->e0loc = saved.e0;
       if (rc) return rc;
     }
     A.Rloc[k] = a->Tloc[k]; A.nout[k] = T->nslot + 1; A.nsub[k] = nsub; A.c[k] = 1.0;
@@ -525,6 +582,10 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
   }
   g_prof.done("ph::assembly of the adjoints", s);
   CK(cudaGetLastError());
+  if (fill) {
+    a->fwd_valid = true;
+    a->fwd_key = key;
+  }
   return 0;
 }
 
@@ -548,13 +609,14 @@ int solve_lambda(Ctx* c, AdjCtx* a, Workspace* w, int N, int K, int KH, const pp
   size_t L = layout_len(N, K);
   if ((rc = grow_adjoint_state(a, L))) return rc;
   CK(cudaMemsetAsync(a->lam, 0, sizeof(double) * L, s));
+  a->fwd_valid = false;  // new amplitudes: the first reverse pass refills the cache
   PhSolver S(c, w, N, K, KH, o, s);
   if ((rc = S.init())) return rc;
   std::vector<int> ring;
   double res = 0.0;
   int it = 1, status = 1;
   for (; it <= o.max_iter; ++it) {
-    if ((rc = adjoint_pass(c, a, N, K, KH, a->lam, a->grad, false, s))) return rc;
+    if ((rc = adjoint_pass(c, a, N, K, KH, a->lam, a->grad, false, s, true))) return rc;
     if ((rc = S.norm(a->grad, &res))) return rc;
     if (trace_on()) fprintf(stderr, "ph lambda %3d |grad_t L| %.3e\n", it, res);
     if (!isfinite(res) || res > 1e6) { status = 2; break; }
@@ -588,7 +650,8 @@ int integral_gradients(Ctx* c, AdjCtx* a, Workspace* w, const Problem& P, int K,
     CK(cudaMalloc((void**)&a->ab, sizeof(double) * 2 * n2));
     a->cap_n = n;
   }
-  if ((rc = adjoint_pass(c, a, N, K, KH, a->lam, a->grad, true, s))) return rc;
+  if ((rc = adjoint_pass(c, a, N, K, KH, a->lam, a->grad, true, s, true))) return rc;
+  a->fwd_valid = false;
   CK(cudaMemsetAsync(a->dhp, 0, sizeof(double) * n2, s));
   CK(cudaMemsetAsync(a->gv_raw, 0, sizeof(double) * n4, s));
   const int nk[5] = {0, 20, 232, 576, 384};
