@@ -735,6 +735,12 @@ int ph_gradient(int n_pairs, const int* occ_of_pair, const int* vir_of_pair, con
   Problem P;
   int rc = prepare(n_pairs, occ_of_pair, vir_of_pair, h, eri, 1, s, &w, &P);
   if (rc) return rc;
+  // the kernel profile of the amplitude solve continues through the reverse passes
+  if (o.profile) {
+    g_prof.on = true;
+    g_prof.start(s);
+  }
+  struct ProfOff { ~ProfOff() { g_prof.on = false; } } prof_off;
   ph::Ctx* c = ph::ctx();
   ph::AdjCtx* a = ph::adj_ctx();
   int N = n_pairs, n = 2 * N, K = 3;
