@@ -484,8 +484,7 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
     if (extra > fr / 2) fill = false;
     a->fwd_valid = false;
   }
-  struct Saved { void *psi, *psim, *phi, *tl, *vl; double* e0; } saved{c->psi, c->psim, c->phi, c->tl, c->vl,
-                                                                        c->e0loc};
+
   AsmArgs A{};
   A.kmax = kmax;
   KeyAsm KA{};
@@ -516,6 +515,9 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
     const size_t cb = fwd_chunk_bytes(T, P);
     if (fill && (rc = grow_buf(&a->fwd[k], &a->fwd_cap[k], cb * (size_t)((nsub + P - 1) / P)))) return rc;
     for (int p0 = 0; p0 < nsub; p0 += P) {
+      // the working buffers as grown above, put back after the chunk
+      struct Saved { void *psi, *psim, *phi, *tl, *vl; double* e0; } saved{c->psi, c->psim, c->phi, c->tl, c->vl,
+                                                                          c->e0loc};
       if (fill || reuse) {
         // this chunk's forward quantities live in the cache
         double* base = (double*)((char*)a->fwd[k] + cb * (size_t)(p0 / P));
