@@ -842,50 +842,8 @@ int local_problem(Ctx* c, DevTables* T, int P, int p0, int nsub, int k, cudaStre
   return 0;
 }
 
-// every local problem of the k-label subsets in precision R: R_loc[k] and
-// E_loc[k] (FP64) at layout amplitudes t
-template <typename R>
-int subset_size(Ctx* c, DevTables* T, int N, int k, const double* t, cudaStream_t s) {
-  int rc;
-  int nsub = c->nsub[k];
-  int J = nsub >= 384 ? 4 : nsub >= 96 ? 2 : 1;
-  int P = chunk_size(nsub, T->nstate, sizeof(R), 32 * J);
-  if ((rc = grow_buf(&c->psi, &c->cap_psi, (size_t)T->nstate * P * sizeof(R)))) return rc;
-  if ((rc = grow_buf(&c->psim, &c->cap_out, (size_t)T->nout * P * sizeof(R)))) return rc;
-  if ((rc = grow_buf(&c->phi, &c->cap_phi, (size_t)T->nout * P * sizeof(R)))) return rc;
-  if ((rc = grow_buf(&c->tl, &c->cap_tl, (size_t)T->nslot * P * sizeof(R)))) return rc;
-  if ((rc = grow_buf(&c->vl, &c->cap_vl, (size_t)T->nkey * P * sizeof(R)))) return rc;
-  if ((rc = grow_buf((void**)&c->e0loc, &c->cap_e0, (size_t)P * sizeof(double)))) return rc;
-  if ((rc = grow_buf((void**)&c->Rloc[k], &c->cap_R[k], (size_t)T->nout * nsub * sizeof(double)))) return rc;
-  if ((rc = grow_buf((void**)&c->Eloc[k], &c->cap_E[k], (size_t)nsub * sizeof(double)))) return rc;
-  R* psi = (R*)c->psi;
-  R* psim = (R*)c->psim;
-  R* tl = (R*)c->tl;
-  R* vl = (R*)c->vl;
-  for (int p0 = 0; p0 < nsub; p0 += P) {
-    size_t nt = (size_t)T->nslot * P, nk = (size_t)T->nkey * P;
-    k_gather_amp<R><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc,
-                                                                 c->subs[k], N, t, tl);
-    k_gather_int<R><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
-                                                                 c->subs[k], N, c->G1, c->G2, c->G3, c->G4, vl);
-    k_set_ref<R><<<(P + 127) / 128, 128, 0, s>>>(P, psi, psim, T->ne0, T->e0_key, T->e0_cd, vl, c->e0loc);
-    c->n_launches += 3;
-    g_prof.done("ph::gather (amplitudes, integrals)", s, (double)(T->nslot + T->nkey) * P * (sizeof(R) + 8.0));
-    if (J == 4) rc = local_problem<R, 4>(c, T, P, p0, nsub, k, s);
-    else if (J == 2) rc = local_problem<R, 2>(c, T, P, p0, nsub, k, s);
-    else rc = local_problem<R, 1>(c, T, P, p0, nsub, k, s);
-    if (rc) return rc;
-  }
-  return 0;
-}
-
 // one residual evaluation: r (unique slots assembled, copies filled) and
-// e_dev (device scalar E_c) at layout amplitudes t (device, copies consistent).
-// R = float is the mixed form: only the largest subsets (k = min(K + K_H, N),
-// most of the work) run in FP32.  The smaller subsets run in FP64: they carry
-// the large inclusion-exclusion coefficients (|c_1| = 126 at N = 11, 1287 at
-// N = 15) that would amplify FP32 rounding into the residual's noise floor,
-// and cost a few per cent of the largest ones.
+// e_dev (device scalar E_c) at layout amplitudes t (device, copies consistent)
 template <typename R>
 int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e_dev, cudaStream_t s) {
   int rc;
@@ -893,15 +851,42 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
   AsmArgs A{}, AE{};
   A.kmax = kmax;
   AE.kmax = std::min(KH, N);
+  const bool f32 = std::is_same<R, float>::value;
   for (int k = 1; k <= kmax; ++k) {
     double ck = moebius(N, k, kfull), ce = k <= KH ? moebius(N, k, KH) : 0.0;
     if (ck == 0.0 && ce == 0.0) continue;
     DevTables* T;
     if ((rc = dev_tables(c, k, K, KH, &T))) return rc;
     int nsub = c->nsub[k];
-    rc = std::is_same<R, float>::value && k < kmax ? subset_size<double>(c, T, N, k, t, s)
-                                                   : subset_size<R>(c, T, N, k, t, s);
-    if (rc) return rc;
+    int J = nsub >= 384 ? 4 : nsub >= 96 ? 2 : 1;
+    int P = chunk_size(nsub, T->nstate, sizeof(R), 32 * J);
+    if ((rc = grow_buf(&c->psi, &c->cap_psi, (size_t)T->nstate * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf(&c->psim, &c->cap_out, (size_t)T->nout * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf(&c->phi, &c->cap_phi, (size_t)T->nout * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf(&c->tl, &c->cap_tl, (size_t)T->nslot * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf(&c->vl, &c->cap_vl, (size_t)T->nkey * P * sizeof(R)))) return rc;
+    if ((rc = grow_buf((void**)&c->e0loc, &c->cap_e0, (size_t)P * sizeof(double)))) return rc;
+    if ((rc = grow_buf((void**)&c->Rloc[k], &c->cap_R[k], (size_t)T->nout * nsub * sizeof(double)))) return rc;
+    if ((rc = grow_buf((void**)&c->Eloc[k], &c->cap_E[k], (size_t)nsub * sizeof(double)))) return rc;
+    R* psi = (R*)c->psi;
+    R* psim = (R*)c->psim;
+    R* phi = (R*)c->phi;
+    R* tl = (R*)c->tl;
+    R* vl = (R*)c->vl;
+    for (int p0 = 0; p0 < nsub; p0 += P) {
+      size_t nt = (size_t)T->nslot * P, nk = (size_t)T->nkey * P;
+      k_gather_amp<R><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nslot, T->slot_desc,
+                                                                   c->subs[k], N, t, tl);
+      k_gather_int<R><<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(P, p0, nsub, k, T->nkey, T->key_desc,
+                                                                   c->subs[k], N, c->G1, c->G2, c->G3, c->G4, vl);
+      k_set_ref<R><<<(P + 127) / 128, 128, 0, s>>>(P, psi, psim, T->ne0, T->e0_key, T->e0_cd, vl, c->e0loc);
+      c->n_launches += 3;
+      g_prof.done("ph::gather (amplitudes, integrals)", s, (double)(T->nslot + T->nkey) * P * (sizeof(R) + 8.0));
+      if (J == 4) rc = local_problem<R, 4>(c, T, P, p0, nsub, k, s);
+      else if (J == 2) rc = local_problem<R, 2>(c, T, P, p0, nsub, k, s);
+      else rc = local_problem<R, 1>(c, T, P, p0, nsub, k, s);
+      if (rc) return rc;
+    }
     A.nout[k] = T->nout;
     A.Rloc[k] = c->Rloc[k]; A.nsub[k] = nsub; A.c[k] = ck;
     AE.Rloc[k] = c->Eloc[k]; AE.nsub[k] = nsub; AE.c[k] = ce;
