@@ -169,42 +169,56 @@ __global__ void __launch_bounds__(256) k_adj_rows(int P, int nstate, const int* 
   for (int j = 0; j < J; ++j) psib[(size_t)st * P + p + 32 * j] = acc[j];
 }
 
-// tbar[slot] of every subset of the chunk, warp per slot, stored transposed
-// as Tloc[subset][1 + slot] for the assembly: the exp(-T) entries
-// (s | sub << 20 | sign << 40, psi_minus = exp(-T)) and the exp(T) entries
+// tbar[slot] from the entries that read the slot's amplitude: the exp(-T)
+// entries (s | sub << 20 | sign << 40, psi_minus = exp(-T)) and the exp(T)
+// entries.  A slot's entry list is cut into segments of at most kSegLen
+// entries (single-site amplitudes occur in up to 2.3e5 entries of a six-site
+// sector, the mean is 7e3); warp per segment, the segment's partial sum to
+// part[seg][p].  seg_slot packs the slot and (bit 31) exp(T) entries;
+// seg_rng[2 seg], seg_rng[2 seg + 1] are the segment's first and end entry.
+constexpr int kSegLen = 1024;
 template <int J>
-__global__ void __launch_bounds__(256) k_adj_tbar(int P, int p0, int nsub, int nslot, const int* __restrict__ obl_ptr,
-                                                  const unsigned long long* __restrict__ obl_ent,
-                                                  const int* __restrict__ bl_ptr,
-                                                  const unsigned long long* __restrict__ bl_ent,
-                                                  const double* __restrict__ pm, const double* __restrict__ pmb,
-                                                  const double* __restrict__ psi, const double* __restrict__ psib,
-                                                  double* __restrict__ Tloc) {
-  int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (sl >= nslot) return;
+__global__ void __launch_bounds__(256) k_adj_tbar_part(int P, int nseg, const int* __restrict__ seg_slot,
+                                                       const int* __restrict__ seg_rng,
+                                                       const unsigned long long* __restrict__ obl_ent,
+                                                       const unsigned long long* __restrict__ bl_ent,
+                                                       const double* __restrict__ pm, const double* __restrict__ pmb,
+                                                       const double* __restrict__ psi,
+                                                       const double* __restrict__ psib, double* __restrict__ part) {
+  int sg = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sg >= nseg) return;
   int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
+  const bool fwd = seg_slot[sg] < 0;   // bit 31: exp(T) entries
+  const int e0 = seg_rng[2 * sg], e1 = seg_rng[2 * sg + 1];
+  const unsigned long long* ent = fwd ? bl_ent : obl_ent;
+  const double* X = fwd ? psi : pm;
+  const double* Xb = fwd ? psib : pmb;
+  const double pos = fwd ? 1.0 : -1.0;   // psi_minus carries -T
   double acc[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) acc[j] = 0.0;
-  for (int e = obl_ptr[sl]; e < obl_ptr[sl + 1]; ++e) {
-    unsigned long long w = obl_ent[e];
-    const double* a = pm + (size_t)((w >> 20) & 0xFFFFFu) * P + p;
-    const double* b = pmb + (size_t)(w & 0xFFFFFu) * P + p;
-    double sg = ((w >> 40) & 1u) ? 1.0 : -1.0;  // psi_minus carries -T
+  for (int e = e0; e < e1; ++e) {
+    unsigned long long w = ent[e];
+    const double* a = X + (size_t)((w >> 20) & 0xFFFFFu) * P + p;
+    const double* b = Xb + (size_t)(w & 0xFFFFFu) * P + p;
+    double sgn = ((w >> 40) & 1u) ? -pos : pos;
 #pragma unroll
-    for (int j = 0; j < J; ++j) acc[j] += sg * a[32 * j] * b[32 * j];
-  }
-  for (int e = bl_ptr[sl]; e < bl_ptr[sl + 1]; ++e) {
-    unsigned long long w = bl_ent[e];
-    const double* a = psi + (size_t)((w >> 20) & 0xFFFFFu) * P + p;
-    const double* b = psib + (size_t)(w & 0xFFFFFu) * P + p;
-    double sg = ((w >> 40) & 1u) ? -1.0 : 1.0;
-#pragma unroll
-    for (int j = 0; j < J; ++j) acc[j] += sg * a[32 * j] * b[32 * j];
+    for (int j = 0; j < J; ++j) acc[j] += sgn * a[32 * j] * b[32 * j];
   }
 #pragma unroll
-  for (int j = 0; j < J; ++j)
-    if (p0 + p + 32 * j < nsub) Tloc[(size_t)(p0 + p + 32 * j) * (nslot + 1) + 1 + sl] = acc[j];
+  for (int j = 0; j < J; ++j) part[(size_t)sg * P + p + 32 * j] = acc[j];
+}
+
+// Tloc[subset][1 + slot] = the slot's segment sums in a fixed order
+__global__ void k_adj_tbar_sum(int P, int p0, int nsub, int nslot, const int* __restrict__ seg_ptr,
+                               const double* __restrict__ part, double* __restrict__ Tloc) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nslot * P) return;
+  int sl = i / P, p = i % P;
+  if (p0 + p >= nsub) return;
+  double acc = 0.0;
+  for (int sg = seg_ptr[sl]; sg < seg_ptr[sl + 1]; ++sg) acc += part[(size_t)sg * P + p];
+  Tloc[(size_t)(p0 + p) * (nslot + 1) + 1 + sl] = acc;
 }
 
 // S[p] = sum_o psi(state(o)) phibar(o): block per 32 subsets, 8 warps over
@@ -331,12 +345,18 @@ struct DevAdj {
   double *dk_c = nullptr, *e0_by_key = nullptr;
   std::vector<int> bs_lvl, obs_lvl;  // reverse-recursion entries per level
   double nent = 0.0;                 // all entries (algorithmic work per subset)
+  // segments of the by-slot entry lists (k_adj_tbar_part): slot (bit 31: exp(T)
+  // entries), [first, end) entry, and the segments of each slot (CSR)
+  int nseg = 0;
+  int *seg_slot = nullptr, *seg_rng = nullptr, *seg_ptr = nullptr;
 };
 
 struct AdjCtx {
   std::map<int, DevAdj*> tabs;
   size_t cap_w = 0, cap_phib = 0, cap_pmb = 0, cap_psib = 0, cap_S = 0;
   double *wl = nullptr, *phib = nullptr, *pmb = nullptr, *psib = nullptr, *S = nullptr;
+  double* part = nullptr;  // segment partial sums of tbar
+  size_t cap_part = 0;
   double* Tloc[kMaxSites + 1] = {};
   double* Vloc[kMaxSites + 1] = {};
   size_t cap_T[kMaxSites + 1] = {}, cap_V[kMaxSites + 1] = {};
@@ -386,6 +406,26 @@ int dev_adjoint(AdjCtx* a, int k, int K, int KH, DevAdj** out) {
     d->obs_lvl.push_back(A->obs_ptr[T->olvl_ptr[lv + 1]] - A->obs_ptr[T->olvl_ptr[lv]]);
   d->nent = (double)A->bs_ent.size() + A->bl_ent.size() + A->obs_ent.size() + A->obl_ent.size() +
             A->hs_ent.size() + A->bk_ent.size() + A->bw_ent.size();
+  {
+    // per slot: segments of the exp(-T) entries, then of the exp(T) entries
+    std::vector<int> ss, rng, sp(1, 0);
+    for (int sl = 0; sl < T->nslot; ++sl) {
+      for (int kind = 0; kind < 2; ++kind) {
+        const std::vector<int>& ptr = kind ? A->bl_ptr : A->obl_ptr;
+        for (int e = ptr[sl]; e < ptr[sl + 1]; e += kSegLen) {
+          ss.push_back(kind ? (int)(sl | 0x80000000u) : sl);
+          rng.push_back(e);
+          rng.push_back(std::min(e + kSegLen, ptr[sl + 1]));
+        }
+      }
+      sp.push_back((int)ss.size());
+    }
+    d->nseg = (int)ss.size();
+    if ((rc = upload(&d->seg_slot, ss)) || (rc = upload(&d->seg_rng, rng)) || (rc = upload(&d->seg_ptr, sp))) {
+      delete d;
+      return rc;
+    }
+  }
   if ((rc = upload(&d->bs_ptr, A->bs_ptr)) || (rc = upload(&d->bs_ent, A->bs_ent)) ||
       (rc = upload(&d->bl_ptr, A->bl_ptr)) || (rc = upload(&d->bl_ent, A->bl_ent)) ||
       (rc = upload(&d->obs_ptr, A->obs_ptr)) || (rc = upload(&d->obs_ent, A->obs_ent)) ||
@@ -427,9 +467,13 @@ int adjoint_local(Ctx* c, AdjCtx* a, DevTables* T, DevAdj* D, int P, int p0, int
                                                                           D->obs_ent, tl, -1.0, a->pmb);
     c->n_launches++;
   }
+  c->n_launches++;
+  g_prof.done("ph::adjoint: back-substitution, exp(-T) reverse levels", s);
   dim3 gs((unsigned)((T->nstate + 7) / 8), gy);
   k_adj_rows<J><<<gs, 256, 0, s>>>(P, T->nstate, D->hs_ptr, D->hs_ent, D->out_of_state, T->d_ptr, T->d_key, T->d_c,
                                    c->e0loc, vl, a->phib, a->psib);
+  c->n_launches++;
+  g_prof.done("ph::adjoint: Hamiltonian rows by state (k_adj_rows)", s);
   for (int lv = (int)T->lvl_ptr.size() - 2; lv >= 1; --lv) {
     int s0 = T->lvl_ptr[lv], s1 = T->lvl_ptr[lv + 1];
     if (s1 <= s0 || D->bs_lvl[lv] == 0) continue;
@@ -437,19 +481,24 @@ int adjoint_local(Ctx* c, AdjCtx* a, DevTables* T, DevAdj* D, int P, int p0, int
                                                                           tl, 1.0, a->psib);
     c->n_launches++;
   }
-  dim3 gt((unsigned)((T->nslot + 7) / 8), gy);
-  k_adj_tbar<J><<<gt, 256, 0, s>>>(P, p0, nsub, T->nslot, D->obl_ptr, D->obl_ent, D->bl_ptr, D->bl_ent, pm, a->pmb,
-                                   psi, a->psib, a->Tloc[k]);
-  c->n_launches += 3;
+  g_prof.done("ph::adjoint: exp(T) reverse levels (k_rev_level)", s);
+  dim3 gt((unsigned)((D->nseg + 7) / 8), gy);
+  k_adj_tbar_part<J><<<gt, 256, 0, s>>>(P, D->nseg, D->seg_slot, D->seg_rng, D->obl_ent, D->bl_ent, pm, a->pmb,
+                                        psi, a->psib, a->part);
+  size_t ns = (size_t)T->nslot * P;
+  k_adj_tbar_sum<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(P, p0, nsub, T->nslot, D->seg_ptr, a->part,
+                                                                a->Tloc[k]);
+  c->n_launches += 2;
+  g_prof.done("ph::adjoint: amplitude adjoints by slot (k_adj_tbar_part, k_adj_tbar_sum)", s,
+              D->nent * 8.0 + 3.0 * D->nent * 8.0 * nv, 2.0 * D->nent * nv);
   if (keys) {
     k_adj_S<<<(unsigned)(P / 32), 256, 0, s>>>(P, T->nout, T->out_state, psi, a->phib, a->S);
     dim3 gk((unsigned)((T->nkey + 7) / 8), gy);
     k_adj_vbar<J><<<gk, 256, 0, s>>>(P, p0, nsub, T->nkey, D->hk_ptr, D->hk_ent, D->dk_ptr, D->dk_out, D->dk_c,
                                      D->e0_by_key, T->out_state, psi, a->phib, a->S, a->Vloc[k]);
     c->n_launches += 2;
+    g_prof.done("ph::adjoint: integral-key adjoints (k_adj_S, k_adj_vbar)", s);
   }
-  g_prof.done("ph::adjoint of the local problems (reverse recursions, rows, back-substitution)", s,
-              D->nent * 8.0 + 3.0 * D->nent * 8.0 * nv, 2.0 * D->nent * nv);
   CK(cudaGetLastError());
   return 0;
 }
@@ -508,6 +557,7 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
         (rc = grow_buf((void**)&a->pmb, &a->cap_pmb, T->nout * pd)) ||
         (rc = grow_buf((void**)&a->psib, &a->cap_psib, T->nstate * pd)) ||
         (rc = grow_buf((void**)&a->S, &a->cap_S, pd)) ||
+        (rc = grow_buf((void**)&a->part, &a->cap_part, (size_t)D->nseg * pd)) ||
         (rc = grow_buf((void**)&a->Tloc[k], &a->cap_T[k], (size_t)(T->nslot + 1) * nsub * sizeof(double))))
       return rc;
     if (keys && (rc = grow_buf((void**)&a->Vloc[k], &a->cap_V[k], (size_t)T->nkey * nsub * sizeof(double))))
