@@ -26,6 +26,14 @@
 namespace ph {
 
 // ------------------------------------------------------------ kernels
+// Entry lists longer than kSegLen are cut into segments: a warp sums one
+// segment into part[segment][lane], a second kernel adds a row's segments in
+// a fixed order.  The lists of the reverse pass are very uneven (a
+// single-site amplitude occurs in up to 2.3e5 entries of a six-site sector,
+// the reference state and output in 6.5e3), and a warp per whole row would
+// wait on its longest row.
+constexpr int kSegLen = 1024;
+
 __device__ __forceinline__ size_t slot_index(int d, const int8_t* L, int N) {
   int m = d & 15, ch = d >> kDescIdx;
   size_t a = L[(d >> 4) & 15];
@@ -49,81 +57,90 @@ __global__ void k_gather_w(int P, int p0, int nsub, int k, int nslot, const int*
   wl[i] = v;
 }
 
-// reverse back-substitution, warp per output row: phibar[kappa] from the
-// entries that read phi(kappa), pmbar[u] from those that read psi_minus(u);
-// the reference row adds w_ref (E_c takes phi'(ref) itself).  Entries pack
-// o | x << 13 | sign << 26.
+// one level of a reverse recursion (the rows of a level read only rows of
+// higher levels, final before these launches), in segments: part[sg - sg0][p]
+// = sum sign t[slot] x[s] over segment sg's entries (s | (2 slot + sign) << 32),
+// the segments of the level's rows being [sg0, sg1)
 template <int J>
-__global__ void __launch_bounds__(256) k_adj_backsub(int P, int nout, const int* __restrict__ bk_ptr,
-                                                     const unsigned* __restrict__ bk_ent,
-                                                     const int* __restrict__ bw_ptr,
-                                                     const unsigned* __restrict__ bw_ent,
-                                                     const double* __restrict__ wl, const double* __restrict__ pm,
-                                                     const double* __restrict__ phi, double* __restrict__ phib,
-                                                     double* __restrict__ pmb) {
-  int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (o >= nout) return;
-  int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
-  double a[J], b[J];
-#pragma unroll
-  for (int j = 0; j < J; ++j) { a[j] = 0.0; b[j] = 0.0; }
-  for (int e = bk_ptr[o]; e < bk_ptr[o + 1]; ++e) {
-    unsigned x = bk_ent[e];
-    const double* W = wl + (size_t)(x & 8191u) * P + p;
-    const double* M = pm + (size_t)((x >> 13) & 8191u) * P + p;
-    double sg = (x >> 26) & 1u ? -1.0 : 1.0;
-#pragma unroll
-    for (int j = 0; j < J; ++j) a[j] += sg * W[32 * j] * M[32 * j];
-  }
-  for (int e = bw_ptr[o]; e < bw_ptr[o + 1]; ++e) {
-    unsigned x = bw_ent[e];
-    const double* W = wl + (size_t)(x & 8191u) * P + p;
-    const double* F = phi + (size_t)((x >> 13) & 8191u) * P + p;
-    double sg = (x >> 26) & 1u ? -1.0 : 1.0;
-#pragma unroll
-    for (int j = 0; j < J; ++j) b[j] += sg * W[32 * j] * F[32 * j];
-  }
-  if (o == 0) {
-#pragma unroll
-    for (int j = 0; j < J; ++j) a[j] += wl[p + 32 * j];
-  }
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    phib[(size_t)o * P + p + 32 * j] = a[j];
-    pmb[(size_t)o * P + p + 32 * j] = b[j];
-  }
-}
-
-// one level of a reverse recursion, warp per row i of [s0, s1):
-// x[dst] += tsign sum sign t[slot] x[s] over the entries (s | (2 slot + sign) << 32)
-// of the row, dst = order ? order[i] : i.  The rows of a level read only rows
-// of higher levels, final before this launch.
-template <int J>
-__global__ void __launch_bounds__(256) k_rev_level(int P, int s0, int s1, const int* __restrict__ order,
-                                                   const int* __restrict__ eptr,
-                                                   const unsigned long long* __restrict__ ent,
-                                                   const double* __restrict__ tl, double tsign,
-                                                   double* __restrict__ x) {
-  int i = s0 + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (i >= s1) return;
-  int e0 = eptr[i], e1 = eptr[i + 1];
-  if (e0 == e1) return;
+__global__ void __launch_bounds__(256) k_rev_part(int P, int sg0, int sg1, const int* __restrict__ rng,
+                                                  const unsigned long long* __restrict__ ent,
+                                                  const double* __restrict__ tl, const double* __restrict__ x,
+                                                  double* __restrict__ part) {
+  int sg = sg0 + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sg >= sg1) return;
   int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
   double acc[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) acc[j] = 0.0;
-  for (int e = e0; e < e1; ++e) {
+  for (int e = rng[2 * sg]; e < rng[2 * sg + 1]; ++e) {
     unsigned long long w = ent[e];
     unsigned sl = (unsigned)(w >> 32);
     const double* a = tl + (size_t)(sl >> 1) * P + p;
     const double* b = x + (size_t)(unsigned)w * P + p;
-    double sg = (sl & 1) ? -1.0 : 1.0;
+    double sgn = (sl & 1) ? -1.0 : 1.0;
 #pragma unroll
-    for (int j = 0; j < J; ++j) acc[j] += sg * a[32 * j] * b[32 * j];
+    for (int j = 0; j < J; ++j) acc[j] += sgn * a[32 * j] * b[32 * j];
   }
-  double* d = x + (size_t)(order ? order[i] : i) * P + p;
 #pragma unroll
-  for (int j = 0; j < J; ++j) d[32 * j] += tsign * acc[j];
+  for (int j = 0; j < J; ++j) part[(size_t)(sg - sg0) * P + p + 32 * j] = acc[j];
+}
+
+// x[dst(i)] += tsign * (row i's segment sums, in order) for the rows [r0, r1)
+__global__ void k_rev_sum(int P, int r0, int r1, const int* __restrict__ order, const int* __restrict__ segptr,
+                          int sg0, const double* __restrict__ part, double tsign, double* __restrict__ x) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)(r1 - r0) * P) return;
+  int i = r0 + (int)(t / P), p = t % P;
+  int g0 = segptr[i], g1 = segptr[i + 1];
+  if (g0 == g1) return;
+  double acc = 0.0;
+  for (int sg = g0; sg < g1; ++sg) acc += part[(size_t)(sg - sg0) * P + p];
+  x[(size_t)(order ? order[i] : i) * P + p] += tsign * acc;
+}
+
+// the back-substitution in reverse, in segments: kind 0 (bit 31 clear) sums
+// sign w[o] psi_minus(x) over entries of bk (-> phibar), kind 1 sums
+// sign w[o] phi(x) over entries of bw (-> pmbar); entries o | x << 13 | sign << 26
+template <int J>
+__global__ void __launch_bounds__(256) k_adj_bsub_part(int P, int nseg, const int* __restrict__ seg_kind,
+                                                       const int* __restrict__ rng, const unsigned* __restrict__ bk_ent,
+                                                       const unsigned* __restrict__ bw_ent,
+                                                       const double* __restrict__ wl, const double* __restrict__ pm,
+                                                       const double* __restrict__ phi, double* __restrict__ part) {
+  int sg = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sg >= nseg) return;
+  int p = blockIdx.y * 32 * J + (threadIdx.x & 31);
+  const bool kw = seg_kind[sg] < 0;
+  const unsigned* ent = kw ? bw_ent : bk_ent;
+  const double* X = kw ? phi : pm;
+  double acc[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) acc[j] = 0.0;
+  for (int e = rng[2 * sg]; e < rng[2 * sg + 1]; ++e) {
+    unsigned x = ent[e];
+    const double* W = wl + (size_t)(x & 8191u) * P + p;
+    const double* M = X + (size_t)((x >> 13) & 8191u) * P + p;
+    double sgn = (x >> 26) & 1u ? -1.0 : 1.0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] += sgn * W[32 * j] * M[32 * j];
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) part[(size_t)sg * P + p + 32 * j] = acc[j];
+}
+
+// phibar[o] and pmbar[o] from their segment sums in order; the reference row
+// of phibar adds w_ref (E_c takes phi'(ref) itself)
+__global__ void k_adj_bsub_sum(int P, int nout, const int* __restrict__ kptr, const int* __restrict__ wptr,
+                               const double* __restrict__ part, const double* __restrict__ wl,
+                               double* __restrict__ phib, double* __restrict__ pmb) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)nout * P) return;
+  int o = t / P, p = t % P;
+  double a = o == 0 ? wl[p] : 0.0, b = 0.0;
+  for (int sg = kptr[o]; sg < kptr[o + 1]; ++sg) a += part[(size_t)sg * P + p];
+  for (int sg = wptr[o]; sg < wptr[o + 1]; ++sg) b += part[(size_t)sg * P + p];
+  phib[(size_t)o * P + p] = a;
+  pmb[(size_t)o * P + p] = b;
 }
 
 // psibar[s] before the reverse recursion, warp per sector state: the
@@ -176,7 +193,6 @@ __global__ void __launch_bounds__(256) k_adj_rows(int P, int nstate, const int* 
 // sector, the mean is 7e3); warp per segment, the segment's partial sum to
 // part[seg][p].  seg_slot packs the slot and (bit 31) exp(T) entries;
 // seg_rng[2 seg], seg_rng[2 seg + 1] are the segment's first and end entry.
-constexpr int kSegLen = 1024;
 template <int J>
 __global__ void __launch_bounds__(256) k_adj_tbar_part(int P, int nseg, const int* __restrict__ seg_slot,
                                                        const int* __restrict__ seg_rng,
@@ -343,13 +359,32 @@ struct DevAdj {
   unsigned long long *bs_ent = nullptr, *bl_ent = nullptr, *obs_ent = nullptr, *obl_ent = nullptr, *hk_ent = nullptr;
   unsigned *hs_ent = nullptr, *bk_ent = nullptr, *bw_ent = nullptr;
   double *dk_c = nullptr, *e0_by_key = nullptr;
-  std::vector<int> bs_lvl, obs_lvl;  // reverse-recursion entries per level
   double nent = 0.0;                 // all entries (algorithmic work per subset)
   // segments of the by-slot entry lists (k_adj_tbar_part): slot (bit 31: exp(T)
   // entries), [first, end) entry, and the segments of each slot (CSR)
   int nseg = 0;
   int *seg_slot = nullptr, *seg_rng = nullptr, *seg_ptr = nullptr;
+  // segments of the reverse recursions (rows in level order) and of the
+  // back-substitution lists; the level ranges on the host
+  int *rs_rng = nullptr, *rs_ptr = nullptr, *ro_rng = nullptr, *ro_ptr = nullptr;
+  std::vector<int> rs_lvl, ro_lvl;
+  int nbseg = 0;
+  int *bseg_kind = nullptr, *bseg_rng = nullptr, *bk_segptr = nullptr, *bw_segptr = nullptr;
+  size_t part_rows = 0;  // segments one launch writes at most (size of the partial buffer / P)
 };
+
+// segments of at most kSegLen entries of the rows [0, nrows) of a CSR list:
+// entry ranges (rng, two ints each) and the rows' segments (ptr)
+inline void segment_rows(const std::vector<int>& eptr, std::vector<int>& rng, std::vector<int>& ptr) {
+  ptr.assign(1, 0);
+  for (size_t i = 0; i + 1 < eptr.size(); ++i) {
+    for (int e = eptr[i]; e < eptr[i + 1]; e += kSegLen) {
+      rng.push_back(e);
+      rng.push_back(std::min(e + kSegLen, eptr[i + 1]));
+    }
+    ptr.push_back((int)(rng.size() / 2));
+  }
+}
 
 struct AdjCtx {
   std::map<int, DevAdj*> tabs;
@@ -400,10 +435,6 @@ int dev_adjoint(AdjCtx* a, int k, int K, int KH, DevAdj** out) {
   const AdjTables* A = T ? host_adjoint(k, K, KH, &rc) : nullptr;
   if (!A) return fail(-5, "ph: adjoint table generation failed for %d sites (%d)", k, rc);
   DevAdj* d = new DevAdj();
-  for (size_t lv = 0; lv + 1 < T->lvl_ptr.size(); ++lv)
-    d->bs_lvl.push_back(A->bs_ptr[T->lvl_ptr[lv + 1]] - A->bs_ptr[T->lvl_ptr[lv]]);
-  for (size_t lv = 0; lv + 1 < T->olvl_ptr.size(); ++lv)
-    d->obs_lvl.push_back(A->obs_ptr[T->olvl_ptr[lv + 1]] - A->obs_ptr[T->olvl_ptr[lv]]);
   d->nent = (double)A->bs_ent.size() + A->bl_ent.size() + A->obs_ent.size() + A->obl_ent.size() +
             A->hs_ent.size() + A->bk_ent.size() + A->bw_ent.size();
   {
@@ -422,6 +453,39 @@ int dev_adjoint(AdjCtx* a, int k, int K, int KH, DevAdj** out) {
     }
     d->nseg = (int)ss.size();
     if ((rc = upload(&d->seg_slot, ss)) || (rc = upload(&d->seg_rng, rng)) || (rc = upload(&d->seg_ptr, sp))) {
+      delete d;
+      return rc;
+    }
+    d->part_rows = ss.size();
+  }
+  {
+    // reverse recursions: segments of every row, the first segment of each level
+    std::vector<int> rng, ptr;
+    segment_rows(A->bs_ptr, rng, ptr);
+    for (size_t lv = 0; lv < T->lvl_ptr.size(); ++lv) d->rs_lvl.push_back(ptr[T->lvl_ptr[lv]]);
+    for (size_t lv = 0; lv + 1 < d->rs_lvl.size(); ++lv)
+      d->part_rows = std::max(d->part_rows, (size_t)(d->rs_lvl[lv + 1] - d->rs_lvl[lv]));
+    if ((rc = upload(&d->rs_rng, rng)) || (rc = upload(&d->rs_ptr, ptr))) { delete d; return rc; }
+    std::vector<int> rng2, ptr2;
+    segment_rows(A->obs_ptr, rng2, ptr2);
+    for (size_t lv = 0; lv < T->olvl_ptr.size(); ++lv) d->ro_lvl.push_back(ptr2[T->olvl_ptr[lv]]);
+    for (size_t lv = 0; lv + 1 < d->ro_lvl.size(); ++lv)
+      d->part_rows = std::max(d->part_rows, (size_t)(d->ro_lvl[lv + 1] - d->ro_lvl[lv]));
+    if ((rc = upload(&d->ro_rng, rng2)) || (rc = upload(&d->ro_ptr, ptr2))) { delete d; return rc; }
+    // back-substitution: the bk rows' segments, then the bw rows'
+    std::vector<int> brng, kptr, wptr;
+    segment_rows(A->bk_ptr, brng, kptr);
+    int nk = (int)(brng.size() / 2);
+    std::vector<int> wrng;
+    segment_rows(A->bw_ptr, wrng, wptr);
+    for (int& v : wptr) v += nk;
+    brng.insert(brng.end(), wrng.begin(), wrng.end());
+    std::vector<int> kind(brng.size() / 2, 0);
+    for (size_t g = nk; g < kind.size(); ++g) kind[g] = (int)0x80000000u;
+    d->nbseg = (int)kind.size();
+    d->part_rows = std::max(d->part_rows, kind.size());
+    if ((rc = upload(&d->bseg_kind, kind)) || (rc = upload(&d->bseg_rng, brng)) || (rc = upload(&d->bk_segptr, kptr)) ||
+        (rc = upload(&d->bw_segptr, wptr))) {
       delete d;
       return rc;
     }
@@ -457,17 +521,23 @@ int adjoint_local(Ctx* c, AdjCtx* a, DevTables* T, DevAdj* D, int P, int p0, int
   const double* vl = (const double*)c->vl;
   const double nv = std::min(P, nsub - p0);
   unsigned gy = (unsigned)(P / (32 * J));
-  dim3 go((unsigned)((T->nout + 7) / 8), gy);
-  k_adj_backsub<J><<<go, 256, 0, s>>>(P, T->nout, D->bk_ptr, D->bk_ent, D->bw_ptr, D->bw_ent, a->wl, pm, phi,
-                                      a->phib, a->pmb);
+  k_adj_bsub_part<J><<<dim3((unsigned)((D->nbseg + 7) / 8), gy), 256, 0, s>>>(
+      P, D->nbseg, D->bseg_kind, D->bseg_rng, D->bk_ent, D->bw_ent, a->wl, pm, phi, a->part);
+  size_t no = (size_t)T->nout * P;
+  k_adj_bsub_sum<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(P, T->nout, D->bk_segptr, D->bw_segptr, a->part, a->wl,
+                                                                a->phib, a->pmb);
+  c->n_launches += 2;
   for (int lv = (int)T->olvl_ptr.size() - 2; lv >= 1; --lv) {
     int s0 = T->olvl_ptr[lv], s1 = T->olvl_ptr[lv + 1];
-    if (s1 <= s0 || D->obs_lvl[lv] == 0) continue;
-    k_rev_level<J><<<dim3((unsigned)((s1 - s0 + 7) / 8), gy), 256, 0, s>>>(P, s0, s1, T->olvl_order, D->obs_ptr,
-                                                                          D->obs_ent, tl, -1.0, a->pmb);
-    c->n_launches++;
+    int g0 = D->ro_lvl[lv], g1 = D->ro_lvl[lv + 1];
+    if (s1 <= s0 || g1 <= g0) continue;
+    k_rev_part<J><<<dim3((unsigned)((g1 - g0 + 7) / 8), gy), 256, 0, s>>>(P, g0, g1, D->ro_rng, D->obs_ent, tl,
+                                                                         a->pmb, a->part);
+    size_t nr = (size_t)(s1 - s0) * P;
+    k_rev_sum<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(P, s0, s1, T->olvl_order, D->ro_ptr, g0, a->part, -1.0,
+                                                           a->pmb);
+    c->n_launches += 2;
   }
-  c->n_launches++;
   g_prof.done("ph::adjoint: back-substitution, exp(-T) reverse levels", s);
   dim3 gs((unsigned)((T->nstate + 7) / 8), gy);
   k_adj_rows<J><<<gs, 256, 0, s>>>(P, T->nstate, D->hs_ptr, D->hs_ent, D->out_of_state, T->d_ptr, T->d_key, T->d_c,
@@ -476,12 +546,15 @@ int adjoint_local(Ctx* c, AdjCtx* a, DevTables* T, DevAdj* D, int P, int p0, int
   g_prof.done("ph::adjoint: Hamiltonian rows by state (k_adj_rows)", s);
   for (int lv = (int)T->lvl_ptr.size() - 2; lv >= 1; --lv) {
     int s0 = T->lvl_ptr[lv], s1 = T->lvl_ptr[lv + 1];
-    if (s1 <= s0 || D->bs_lvl[lv] == 0) continue;
-    k_rev_level<J><<<dim3((unsigned)((s1 - s0 + 7) / 8), gy), 256, 0, s>>>(P, s0, s1, nullptr, D->bs_ptr, D->bs_ent,
-                                                                          tl, 1.0, a->psib);
-    c->n_launches++;
+    int g0 = D->rs_lvl[lv], g1 = D->rs_lvl[lv + 1];
+    if (s1 <= s0 || g1 <= g0) continue;
+    k_rev_part<J><<<dim3((unsigned)((g1 - g0 + 7) / 8), gy), 256, 0, s>>>(P, g0, g1, D->rs_rng, D->bs_ent, tl,
+                                                                         a->psib, a->part);
+    size_t nr = (size_t)(s1 - s0) * P;
+    k_rev_sum<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(P, s0, s1, nullptr, D->rs_ptr, g0, a->part, 1.0, a->psib);
+    c->n_launches += 2;
   }
-  g_prof.done("ph::adjoint: exp(T) reverse levels (k_rev_level)", s);
+  g_prof.done("ph::adjoint: exp(T) reverse levels (k_rev_part, k_rev_sum)", s);
   dim3 gt((unsigned)((D->nseg + 7) / 8), gy);
   k_adj_tbar_part<J><<<gt, 256, 0, s>>>(P, D->nseg, D->seg_slot, D->seg_rng, D->obl_ent, D->bl_ent, pm, a->pmb,
                                         psi, a->psib, a->part);
@@ -557,7 +630,7 @@ int adjoint_pass(Ctx* c, AdjCtx* a, int N, int K, int KH, const double* lam, dou
         (rc = grow_buf((void**)&a->pmb, &a->cap_pmb, T->nout * pd)) ||
         (rc = grow_buf((void**)&a->psib, &a->cap_psib, T->nstate * pd)) ||
         (rc = grow_buf((void**)&a->S, &a->cap_S, pd)) ||
-        (rc = grow_buf((void**)&a->part, &a->cap_part, (size_t)D->nseg * pd)) ||
+        (rc = grow_buf((void**)&a->part, &a->cap_part, D->part_rows * pd)) ||
         (rc = grow_buf((void**)&a->Tloc[k], &a->cap_T[k], (size_t)(T->nslot + 1) * nsub * sizeof(double))))
       return rc;
     if (keys && (rc = grow_buf((void**)&a->Vloc[k], &a->cap_V[k], (size_t)T->nkey * nsub * sizeof(double))))
