@@ -19,12 +19,13 @@
 // 16-byte core matrices, K-adjacent cores 128 B apart (leading byte offset),
 // 8-row groups 256 B apart (stride byte offset); one K stage is 8 TF32 values.
 //
-// Roles (672 threads): warps 0-15 epilogue (TMEM lane quarter = warp % 4; the
+// Roles (800 threads): warps 0-15 epilogue (TMEM lane quarter = warp % 4; the
 // four warps of a quarter take the channels of output o = warp / 4 mod 4, so
 // every (row, o) sum has one owner and a fixed order; D is read from TMEM
-// eight columns at a time next to the loads of the Cl factors), warps 16-19
-// producers (A generation; thread 512 also issues the bulk copies of B and of
-// the Cl slices), warp 20 TMEM allocation and MMA issue (lane 0).
+// eight columns at a time next to the loads of the Cl factors), warps 16-23
+// producers (A generation, two threads per row, each one 4-wide K core of a
+// stage; thread 512 also issues the bulk copies of B and of the Cl slices),
+// warp 24 TMEM allocation and MMA issue (lane 0).
 // Each CTA writes the sums of its rows (all 29 outputs) to its own slot of
 // a partial buffer, part[slot][p][o]; k_t9_reduce adds the slots in a fixed
 // order, so the result does not depend on scheduling.
@@ -41,12 +42,14 @@ constexpr int kStages = 4;
 constexpr int kRows = 128;                 // MMA M, rows per tile
 constexpr int kMaxCols = 256;              // TMEM columns per accumulator buffer
 constexpr int kEpiThreads = 512;           // warps 0-15
-constexpr int kProdBase = kEpiThreads;     // warps 16-19
+constexpr int kProdThreads = 256;          // warps 16-23: two per row, one K core (4 of the 8 K) each
+constexpr int kProdBase = kEpiThreads;
 constexpr int kProdWarp0 = kProdBase / 32;
-constexpr int kMmaWarp = kProdWarp0 + kRows / 32;
+constexpr int kMmaWarp = kProdWarp0 + kProdThreads / 32;
 constexpr int kThreads = (kMmaWarp + 1) * 32;
 static_assert(kEpiThreads % kRows == 0 && kEpiThreads / kRows == 4, "four epilogue groups of 128 rows");
-static_assert(kThreads == 672, "20 role warps + the MMA warp");
+static_assert(kProdThreads == 2 * kRows, "two producer threads per row");
+static_assert(kThreads == 800, "24 role warps + the MMA warp");
 constexpr long long kWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
 constexpr int kChunkFields = 12;           // c1, c2, n_g, n_cols, g[4], q[4]
 
@@ -220,12 +223,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* st9 = reinterpret_cast<float*>(sm + Smem::t9(NNp));             // [128][29]
   int* rowYZ = reinterpret_cast<int*>(sm + Smem::rows(NNp));             // [128][2]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem::bars(NNp));
-  uint64_t* fullA = bars;                     // [S] producers wrote A (count 128)
+  uint64_t* fullA = bars;                     // [S] producers wrote A (count 256)
   uint64_t* fullB = bars + kStages;           // [S] B copies landed (count 1 + tx)
   uint64_t* empty = bars + 2 * kStages;       // [S] MMAs of the stage done (commit)
   uint64_t* done = bars + 3 * kStages;        // all MMAs of the CTA done (commit)
   uint64_t* slf = bars + 4 * kStages;         // [2] Cl slices landed (count 1 + tx)
-  uint64_t* sle = slf + 2;                    // [2] producers done with the slices (count 128)
+  uint64_t* sle = slf + 2;                    // [2] producers done with the slices (count 256)
   uint64_t* tmf = sle + 2;                    // [2] accumulator buffer ready (commit)
   uint64_t* tme = tmf + 2;                    // [2] epilogue done with the buffer (count 512)
   uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + Smem::kNBars);
@@ -238,14 +241,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&fullA[s], 128);
+      mbar_init(&fullA[s], kProdThreads);
       mbar_init(&fullB[s], 1);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&slf[b], 1);
-      mbar_init(&sle[b], 128);
+      mbar_init(&sle[b], kProdThreads);
       mbar_init(&tmf[b], 1);
       mbar_init(&tme[b], kEpiThreads);
     }
@@ -278,9 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp >= kProdWarp0 && warp < kMmaWarp) {
     // ------------------------------------------------------------ producers
-    const int r = tid - kProdBase;
+    const int pr = tid - kProdBase, r = pr & (kRows - 1), hh = pr / kRows;  // row, K core
     const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
-    const bool lead = (r == 0);
+    const bool lead = (pr == 0);
     int issued_b = 0, issued_s = 0;  // stage / slice fills issued by the lead thread
     if (lead && nloc > 0) {
       const int16_t* h = chunks + (size_t)cb * kChunkFields;
@@ -320,23 +323,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                        bpre + ((size_t)(h[4 + j] * 2 + sp) * Kc + kc) * blk, (uint32_t)(blk * 4), &fullB[s]);
           ++issued_b;
         }
-        float hi[8], lo[8];
+        float hi[4], lo[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          int X = kc * 8 + k;
+        for (int k = 0; k < 4; ++k) {
+          int X = kc * 8 + 4 * hh + k;
           float a = (Y >= 0 && X < N) ? c1s[X * N + Y] * c2s[X * N + Z] : 0.f;
           hi[k] = tf32_rna(a);
           lo[k] = tf32_rna(a - hi[k]);
         }
         float* adst = sA + (size_t)s * 2 * (Smem::kA / 4);
-        const int base = (r >> 3) * 64 + (r & 7) * 4;   // floats: row group 256 B, row 16 B
-#pragma unroll
-        for (int kcore = 0; kcore < 2; ++kcore) {
-          *reinterpret_cast<float4*>(adst + base + kcore * 32) =
-              make_float4(hi[4 * kcore], hi[4 * kcore + 1], hi[4 * kcore + 2], hi[4 * kcore + 3]);
-          *reinterpret_cast<float4*>(adst + (Smem::kA / 4) + base + kcore * 32) =
-              make_float4(lo[4 * kcore], lo[4 * kcore + 1], lo[4 * kcore + 2], lo[4 * kcore + 3]);
-        }
+        const int base = (r >> 3) * 64 + (r & 7) * 4 + hh * 32;   // floats: row group 256 B, row 16 B, K core
+        *reinterpret_cast<float4*>(adst + base) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(adst + (Smem::kA / 4) + base) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         fence_async_smem();
         mbar_arrive(&fullA[s]);
       }

@@ -108,12 +108,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* rowYZ = reinterpret_cast<int*>(sm + Smem64::rows(NNp));                  // [128][2]
   int* rowE = rowYZ + 2 * kRows;                                                // [4][128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Smem64::bars(NNp));
-  uint64_t* fullA = bars;                       // [S] count 128
+  uint64_t* fullA = bars;                       // [S] count 256
   uint64_t* fullB = bars + kStages64;           // [S] count 1 + tx
   uint64_t* empty = bars + 2 * kStages64;       // [S] commit
   uint64_t* done = bars + 3 * kStages64;        // commit
   uint64_t* slf = done + 1;                     // Cl slices landed (count 1 + tx)
-  uint64_t* sle = slf + 1;                      // producers done with the slices (count 128)
+  uint64_t* sle = slf + 1;                      // producers done with the slices (count 256)
   uint64_t* tmf = sle + 1;                      // accumulators ready (commit)
   uint64_t* tme = tmf + 1;                      // epilogue done with TMEM (count 512)
   uint64_t* ref = tme + 1;                      // [4] row exponents written (count 128)
@@ -127,13 +127,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < kStages64; ++s) {
-      mbar_init(&fullA[s], 128);
+      mbar_init(&fullA[s], kProdThreads);
       mbar_init(&fullB[s], 1);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
     mbar_init(slf, 1);
-    mbar_init(sle, 128);
+    mbar_init(sle, kProdThreads);
     mbar_init(tmf, 1);
     mbar_init(tme, kEpiThreads);
     for (int b = 0; b < 4; ++b) mbar_init(&ref[b], 128);
@@ -165,9 +165,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp >= kProdWarp0 && warp < kMmaWarp) {
     // ------------------------------------------------------------ producers
-    const int r = tid - kProdBase;
+    const int pr = tid - kProdBase, r = pr & (kRows - 1), hh = pr / kRows;  // row, K core
     const int Y = rowYZ[2 * r], Z = rowYZ[2 * r + 1];
-    const bool lead = (r == 0);
+    const bool lead = (pr == 0);
     int issued_b = 0, fills = 0;   // stage fills / slice fills by the lead thread
     int it = 0, e = 0;
     double scale = 0.0;
@@ -197,8 +197,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (mx > 0.0) frexp(mx, &e);
         scale = ldexp(1.0, kSl * kSlBits - e);
       }
-      rowE[(l & 3) * kRows + r] = e;
-      mbar_arrive(&ref[l & 3]);
+      if (hh == 0) {   // both threads of a row found the same exponent
+        rowE[(l & 3) * kRows + r] = e;
+        mbar_arrive(&ref[l & 3]);
+      }
       const int g = h[4];
       for (int kc = 0; kc < Kc; ++kc, ++it) {
         const int s = it % kStages64;
@@ -212,21 +214,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                      (uint32_t)(blk * 4), &fullB[s]);
           ++issued_b;
         }
-        float sl[8][kSl];
+        float sl[4][kSl];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int X = kc * 8 + k;
+        for (int k = 0; k < 4; ++k) {
+          const int X = kc * 8 + 4 * hh + k;
           const double a = (Y >= 0 && X < N) ? sCl[X * N + Y] * sCl[NNp + X * N + Z] : 0.0;
           split6(a, scale, sl[k]);
         }
         float* adst = sA + (size_t)s * kSl * (Smem64::kA / 4);
-        const int base = (r >> 3) * 64 + (r & 7) * 4;
+        const int base = (r >> 3) * 64 + (r & 7) * 4 + hh * 32;   // this thread's K core
 #pragma unroll
         for (int i = 0; i < kSl; ++i)
-#pragma unroll
-          for (int kcore = 0; kcore < 2; ++kcore)
-            *reinterpret_cast<float4*>(adst + i * (Smem64::kA / 4) + base + kcore * 32) =
-                make_float4(sl[4 * kcore][i], sl[4 * kcore + 1][i], sl[4 * kcore + 2][i], sl[4 * kcore + 3][i]);
+          *reinterpret_cast<float4*>(adst + i * (Smem64::kA / 4) + base) =
+              make_float4(sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
         fence_async_smem();
         mbar_arrive(&fullA[s]);
       }
