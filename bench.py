@@ -92,8 +92,8 @@ def batch_systems(count, seed=1609):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # quartic kernels on this workload, from single ncu captures of the current
 # kernels (profiles/quartic_kernels_c140h142.md); None until captured
-TRAFFIC_TC_QUARTIC = None          # k_t9_tc<80>: recaptured after the producer change
-TRAFFIC_FP64_QUARTIC = None        # k_t9_tc64<80>: recaptured after the producer change
+TRAFFIC_TC_QUARTIC = 2268928      # k_t9_tc<80>: 2.27 MB read, 0 B written
+TRAFFIC_FP64_QUARTIC = 6098688    # k_t9_tc64<80>: 6.10 MB read, 0 B written
 
 
 def peaks():
