@@ -851,7 +851,6 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
   AsmArgs A{}, AE{};
   A.kmax = kmax;
   AE.kmax = std::min(KH, N);
-  const bool f32 = std::is_same<R, float>::value;
   for (int k = 1; k <= kmax; ++k) {
     double ck = moebius(N, k, kfull), ce = k <= KH ? moebius(N, k, KH) : 0.0;
     if (ck == 0.0 && ce == 0.0) continue;
@@ -870,7 +869,6 @@ int residual(Ctx* c, int N, int K, int KH, const double* t, double* r, double* e
     if ((rc = grow_buf((void**)&c->Eloc[k], &c->cap_E[k], (size_t)nsub * sizeof(double)))) return rc;
     R* psi = (R*)c->psi;
     R* psim = (R*)c->psim;
-    R* phi = (R*)c->phi;
     R* tl = (R*)c->tl;
     R* vl = (R*)c->vl;
     for (int p0 = 0; p0 < nsub; p0 += P) {
