@@ -148,6 +148,7 @@ struct Workspace {
   // residual scratch (sized for double, reused as float)
   void *cl = nullptr, *hs = nullptr, *pg = nullptr, *pt7 = nullptr, *pc0 = nullptr;
   void *clT = nullptr, *gT = nullptr, *B9 = nullptr;  // quartic GEMM operands / output
+  float2* clT2 = nullptr;                              // FP64 quartic epilogue: clT as float pairs
   void *pt7T = nullptr, *m7 = nullptr;                 // T7 GEMM operand / output
   // tensor-core quartic kernel (FP32 residual): split B operands, work list
   bool tc_allowed = false;  // set for workspaces that own their buffers
@@ -223,7 +224,7 @@ void free_ws(Workspace* w) {
   void* ps[] = {w->h, w->eri, w->Bcd, w->Bt, w->occ, w->vir, w->lab, w->f, w->hp, w->fo, w->fv, w->g1d, w->g2d,
                 w->g1f, w->g2f, w->t, w->r, w->dir, w->abuf, w->cl, w->hs, w->pg, w->pt7, w->pc0,
                 w->esite, w->epair, w->part, w->scal, w->coef, w->Bdiis, w->ok, w->order, w->slot_t, w->slot_e,
-                w->clT, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
+                w->clT, w->clT2, w->gT, w->B9, w->t9, w->work9, w->tb, w->r64, w->rb, w->del, w->rho,
                 w->amax, w->pt7T, w->m7, w->bpre, w->tc_chunk, w->tc_cta, w->tc_err, w->tc_part, w->t9part,
                 w->bpre64, w->fexp64, w->tc64_chunk, w->tc64_cta, w->tc64_part, w->r1part};
   for (void* p : ps)
@@ -264,6 +265,7 @@ int grow(Workspace* w, int N, int diis) {
   AL(w->pg, sizeof(double) * NN * PPQ_NS36); AL(w->pt7, sizeof(double) * NN * PPQ_NT7E);
   AL(w->pc0, sizeof(double) * NN * PPQ_NCOL0);
   AL(w->clT, sizeof(double) * cl_ld(Nc) * PPQ_NS36); AL(w->gT, sizeof(double) * NN * PPQ_NS36);
+  AL(w->clT2, sizeof(float2) * cl_ld(Nc) * PPQ_NS36);
   AL(w->tb, sizeof(double) * L); AL(w->r64, sizeof(double) * L); AL(w->rb, sizeof(double) * L);
   AL(w->del, sizeof(double) * L); AL(w->rho, sizeof(double) * L);
   AL(w->amax, sizeof(unsigned long long));
@@ -674,8 +676,8 @@ int launch_t9_tc64_nw(Workspace* w, int N, cudaStream_t s) {
   if (e != cudaSuccess) return fail(-100, "k_t9_tc64 attribute: %s", cudaGetErrorString(e));
   const int P = N * (N - 1) / 2;
   ppq::tc::k_t9_tc64<NW><<<w->tc64_nctas, ppq::tc::kThreads, w->tc64_smem, s>>>(
-      N, P, w->tc64_Kc, cl_ld(N), (const double*)w->clT, w->bpre64, w->fexp64, w->tc64_cta, w->tc64_chunk,
-      w->tc64_nslot, w->tc64_part, w->tc_err);
+      N, P, w->tc64_Kc, cl_ld(N), (const double*)w->clT, w->clT2, w->bpre64, w->fexp64, w->tc64_cta,
+      w->tc64_chunk, w->tc64_nslot, w->tc64_part, w->tc_err);
   return 0;
 }
 
@@ -789,6 +791,8 @@ int residual(Workspace* w, int N, cudaStream_t s) {
     // tensor cores, exact splitting: split B operands, then the MMA + W-contraction kernel
     ppq::tc::k_t9_bprep64<<<PPQ_NS36, 128, 0, s>>>(
         N, w->tc64_Npad, w->tc64_Kc, (const double*)pg, w->bpre64, w->fexp64);
+    size_t ncl = (size_t)cl_ld(N) * PPQ_NS36;
+    ppq::tc::k_split_cl<<<(unsigned)((ncl + 255) / 256), 256, 0, s>>>(ncl, (const double*)w->clT, w->clT2);
     g_prof.done(PN("tc::k_t9_bprep64"), s);
     if (w->profile) CK(cudaEventRecord(w->evq0, s));
     if ((rc = launch_t9_tc64(w, N, s))) return rc;

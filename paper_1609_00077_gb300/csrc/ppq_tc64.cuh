@@ -49,6 +49,32 @@ __device__ __forceinline__ void split6(double v, double scale, float* s) {
   }
 }
 
+// an exact integer |d| < 2^58 as a float pair d = dh + dl (to 2^-48 |d|):
+// limbs d = d2 2^46 + d1 2^23 + d0 (each exact in FP32 through the 2^23
+// magic-number conversion), then two fast two-sums, valid because each
+// partial sum is zero or at least the next limb in magnitude
+__device__ __forceinline__ void dpair(long long d, float& dh, float& dl) {
+  const int d2 = (int)(d >> 46);
+  const int d1 = (int)((d >> 23) & 0x7FFFFF), d0 = (int)(d & 0x7FFFFF);
+  const float f2 = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + d2), 12582912.f), 70368744177664.f);
+  const float f1 = __fmul_rn(__fsub_rn(__int_as_float(0x4B000000 | d1), 8388608.f), 8388608.f);
+  const float f0 = __fsub_rn(__int_as_float(0x4B000000 | d0), 8388608.f);
+  const float x = __fadd_rn(f2, f1), e1 = __fsub_rn(f1, __fsub_rn(x, f2));
+  dh = __fadd_rn(x, f0);
+  const float e2 = __fsub_rn(f0, __fsub_rn(dh, x));
+  dl = __fadd_rn(e1, e2);
+}
+
+// the link coefficients of the epilogue as float pairs: clT2[i] = (hi, lo),
+// hi = x rounded to FP32, lo = (x - hi) rounded (hi + lo = x to 2^-48)
+__global__ void k_split_cl(size_t n, const double* __restrict__ clT, float2* __restrict__ clT2) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = clT[i];
+  const float hi = __double2float_rn(x);
+  clT2[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
 // B slices per K stage: bpre64[g][j][kc][W / 8][kcore][W % 8][k % 4] (value
 // slice j of G[X,W][g] 2^-f_g), X = 8 kc + 4 kcore + k % 4; one block per g,
 // the exponent f_g (0 for an all-zero g) in fexp[g]
@@ -96,9 +122,9 @@ struct Smem64 {
 // chunk records as for k_t9_tc, one g per chunk (n_cols = Npad)
 template <int NW>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_t9_tc64(int N, int P, int Kc, int NNp, const double* __restrict__ clT, const float* __restrict__ bpre,
-              const int* __restrict__ fexp, const int* __restrict__ cta, const int16_t* __restrict__ chunks,
-              int nslot, double* __restrict__ part, int* __restrict__ err) {
+    k_t9_tc64(int N, int P, int Kc, int NNp, const double* __restrict__ clT, const float2* __restrict__ clT2,
+              const float* __restrict__ bpre, const int* __restrict__ fexp, const int* __restrict__ cta,
+              const int16_t* __restrict__ chunks, int nslot, double* __restrict__ part, int* __restrict__ err) {
   constexpr int Npad = NW;
   extern __shared__ __align__(1024) unsigned char sm[];
   float* sA = reinterpret_cast<float*>(sm);                                     // [S][6][128 x 8]
@@ -286,16 +312,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int ch = ppq_c9qp[q]; ch < ppq_c9qp[q + 1]; ++ch) {
         const int16_t* c = ppq_c9q + 4 * ch;
         if ((c[2] & 3) != grp) continue;                      // warp-uniform
-        const double* py = clT + (size_t)c[0] * NNp + Y;
-        const double* pz = clT + (size_t)c[1] * NNp + Z;
-        double v = 0.0;
+        // the W contraction on the FP32 pipe in double-float arithmetic: the
+        // link coefficients come as float pairs (hi, lo), so a b = p + pe to
+        // 2^-48 (a two-product); the exact integer combination D of the slice
+        // accumulators becomes a float pair (dh, dl) through three exact
+        // 23-bit limbs and two fast two-sums; the terms D a b accumulate in
+        // (vh, vl) with a two-sum
+        const float2* py = clT2 + (size_t)c[0] * NNp + Y;
+        const float2* pz = clT2 + (size_t)c[1] * NNp + Z;
+        float vh = 0.f, vl = 0.f;
 #pragma unroll 2
         for (int W0 = 0; W0 < NW; W0 += 4) {
-          double ab[4];
+          float2 a[4], b[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const bool in = W0 + i < N;
-            ab[i] = in ? __ldg(py + (size_t)(W0 + i) * N) * __ldg(pz + (size_t)(W0 + i) * N) : 0.0;
+            a[i] = in ? __ldg(py + (size_t)(W0 + i) * N) : make_float2(0.f, 0.f);
+            b[i] = in ? __ldg(pz + (size_t)(W0 + i) * N) : make_float2(0.f, 0.f);
           }
           long long dint[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -306,8 +339,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < 4; ++i) dint[i] += (long long)__float2int_rn(sv[i]) << (kSlBits * (kSl - 1 - gg));
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) v = fma((double)dint[i], ab[i], v);
+          for (int i = 0; i < 4; ++i) {
+            float dh, dl;
+            dpair(dint[i], dh, dl);
+            const float p = __fmul_rn(a[i].x, b[i].x);
+            float pe = fmaf(a[i].x, b[i].x, -p);
+            pe = fmaf(a[i].x, b[i].y, pe);
+            pe = fmaf(a[i].y, b[i].x, pe);
+            const float hp = __fmul_rn(dh, p);
+            float he = fmaf(dh, p, -hp);
+            he = fmaf(dh, pe, he);
+            he = fmaf(dl, p, he);
+            const float sm2 = __fadd_rn(vh, hp), bb = __fsub_rn(sm2, vh);
+            vl += __fadd_rn(__fsub_rn(vh, __fsub_rn(sm2, bb)), __fsub_rn(hp, bb)) + he;
+            vh = sm2;
+          }
         }
+        double v = (double)vh + (double)vl;
         v *= rscale;
         if (valid) acc[c[2]] += 0.5 * double(c[3]) * v;
       }
