@@ -12,10 +12,12 @@
 // pairs (i, j) with i + j = g below 2^23: every TMEM accumulator S_g is an
 // exact integer in FP32.  With the 21 pairs i + j <= 5,
 //   D = 2^(e_p + f_g - 49) sum_g S_g 2^(7 (5 - g)),
-// combined in int64 (exact) and converted once; the dropped pairs i + j >= 6
-// bound the error by about 2e-12 of max|A row| max|B_g| per X term.
-// The W contraction with Cl[W,Y][c3] Cl[W,Z][c4] is FP64, on the integer
-// combination, with the power of two applied once per row and channel.
+// combined in int64 (exact); the dropped pairs i + j >= 6 bound the error by
+// about 2e-12 of max|A row| max|B_g| per X term.  The slicing works on the
+// bit patterns with integer operations (no FP64 arithmetic in the producers
+// but the product A[p][X]).  The W contraction with Cl[W,Y][c3] Cl[W,Z][c4]
+// runs in double-float arithmetic on the FP32 pipe (about 2^-46 relative per
+// term), with the power of two applied once per row and channel in FP64.
 //
 // Same pipeline as k_t9_tc (producers, one MMA thread, 16 epilogue warps,
 // bounded waits): chunks hold one g each (six accumulator groups of Npad
@@ -33,20 +35,35 @@ namespace tc {
 constexpr int kSl = 6;            // slices per operand
 constexpr int kSlBits = 7;        // bits per slice
 constexpr int kStages64 = 2;
+static_assert(kSl == 6 && kSlBits == 7, "split6 cuts 42 bits into six 7-bit slices");
 
-__device__ __forceinline__ void split6(double v, double scale, float* s) {
-  // v times scale = 2^(42 - e), rounded to an integer, cut into 7-bit slices
-  long long xi = __double2ll_rn(v * scale);
-  long long a0 = xi >> 35;
-  long long r = xi - (a0 << 35);
-  s[0] = (float)a0;
-#pragma unroll
-  for (int i = 1; i < kSl; ++i) {
-    const int sh = kSlBits * (kSl - 1 - i);
-    long long a = r >> sh;
-    r -= a << sh;
-    s[i] = (float)a;
-  }
+// v 2^(42 - e) (|v| < 2^e) rounded to the nearest integer x (ties away from
+// zero), by integer operations on the bit pattern of v, then cut into 7-bit
+// slices x = sum_i a_i 2^(7 (5 - i)): a_0 signed (|a_0| <= 128), a_1..a_5 in
+// [0, 128).  The slices are small integers, converted to FP32 exactly by the
+// 1.5 2^23 magic number; no FP64 arithmetic or 64-bit conversion is involved.
+__device__ __forceinline__ float small_int_to_float(int a) {   // |a| < 2^22
+  return __fsub_rn(__int_as_float(0x4B400000 + a), 12582912.f);
+}
+
+__device__ __forceinline__ void split6(double v, int e, float* s) {
+  const long long b = __double_as_longlong(v);
+  const int ev = (int)((b >> 52) & 0x7FF);
+  const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+  // v = m 2^(ev - 1075), so x = round(m 2^-sh) with sh >= 11 for |v| < 2^e
+  const int sh = 1075 - kSl * kSlBits + e - ev;
+  long long x = 0;
+  if (ev != 0 && sh > 0 && sh < 64) x = (m + (1LL << (sh - 1))) >> sh;
+  if (b < 0) x = -x;
+  const int a0 = (int)(x >> 35);
+  const long long r = x - ((long long)a0 << 35);       // [0, 2^35)
+  const int rh = (int)(r >> 14), rl = (int)(r & 0x3FFF);
+  s[0] = small_int_to_float(a0);
+  s[1] = small_int_to_float(rh >> 14);
+  s[2] = small_int_to_float((rh >> 7) & 127);
+  s[3] = small_int_to_float(rh & 127);
+  s[4] = small_int_to_float(rl >> 7);
+  s[5] = small_int_to_float(rl & 127);
 }
 
 // an exact integer |d| < 2^58 as a float pair d = dh + dl (to 2^-48 |d|):
@@ -93,13 +110,12 @@ __global__ void __launch_bounds__(128) k_t9_bprep64(int N, int Npad, int Kc, con
   int f = 0;
   if (red[0] > 0.0) frexp(red[0], &f);
   if (tid == 0) fexp[g] = f;
-  const double scale = ldexp(1.0, kSl * kSlBits - f);
   const size_t per = (size_t)Npad * 8;
   for (int i = tid; i < Kc * 8 * Npad; i += blockDim.x) {
     const int X = i / Npad, W = i % Npad;
     const double v = (W < N && X < N) ? pg[((size_t)X * N + W) * PPQ_NS36 + g] : 0.0;
     float sl[kSl];
-    split6(v, scale, sl);
+    split6(v, f, sl);
     const int kc = X >> 3, k = X & 7, kcore = k >> 2, e = k & 3;
     const size_t off = ((size_t)((W >> 3) * 2 + kcore) * 8 + (W & 7)) * 4 + e;
 #pragma unroll
@@ -196,7 +212,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool lead = (pr == 0);
     int issued_b = 0, fills = 0;   // stage fills / slice fills by the lead thread
     int it = 0, e = 0;
-    double scale = 0.0;
     int16_t c1 = -1, c2 = -1;
     for (int l = 0; l < nloc && !*abort; ++l) {
       const int16_t* h = chunks + (size_t)(cb + l) * kChunkFields;
@@ -221,7 +236,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int X = 0; X < N; ++X) mx = fmax(mx, fabs(sCl[X * N + Y] * sCl[NNp + X * N + Z]));
         e = 0;
         if (mx > 0.0) frexp(mx, &e);
-        scale = ldexp(1.0, kSl * kSlBits - e);
       }
       if (hh == 0) {   // both threads of a row found the same exponent
         rowE[(l & 3) * kRows + r] = e;
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < 4; ++k) {
           const int X = kc * 8 + 4 * hh + k;
           const double a = (Y >= 0 && X < N) ? sCl[X * N + Y] * sCl[NNp + X * N + Z] : 0.0;
-          split6(a, scale, sl[k]);
+          split6(a, e, sl[k]);
         }
         float* adst = sA + (size_t)s * kSl * (Smem64::kA / 4);
         const int base = (r >> 3) * 64 + (r & 7) * 4 + hh * 32;   // this thread's K core
@@ -311,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double rscale = ldexp(1.0, rowE[(l & 3) * kRows + r] + fexp[g] - kSlBits * (kSl + 1));
       for (int ch = ppq_c9qp[q]; ch < ppq_c9qp[q + 1]; ++ch) {
         const int16_t* c = ppq_c9q + 4 * ch;
-        if ((c[2] & 3) != grp) continue;                      // warp-uniform
+        if (ppq_c9grp[ch] != grp) continue;                   // warp-uniform; one group per output
         // the W contraction on the FP32 pipe in double-float arithmetic: the
         // link coefficients come as float pairs (hi, lo), so a b = p + pe to
         // 2^-48 (a two-product); the exact integer combination D of the slice

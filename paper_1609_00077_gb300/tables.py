@@ -833,6 +833,20 @@ def emit_header(path):
     c9g = gstart + [len(c9q)]
     gq = c9q[gstart, 0]
     c9gp = [int(np.sum(gq < q)) for q in range(len(q9) + 1)]
+    # epilogue group of each channel for the one-q-per-chunk FP64 kernel: the
+    # outputs of a q go whole to one of four thread groups (so that no two
+    # groups add into the same output), largest output first onto the least
+    # loaded group (ties to the lower group)
+    c9grp = np.zeros(len(c9q), dtype=np.int64)
+    for q in range(len(q9)):
+        lo, hi = c9qp[q], c9qp[q + 1]
+        outs, cnt = np.unique(c9q[lo:hi, 3], return_counts=True)
+        load = [0, 0, 0, 0]
+        for k in sorted(range(len(outs)), key=lambda k: (-cnt[k], outs[k])):
+            gsel = min(range(4), key=lambda j: (load[j], j))
+            load[gsel] += int(cnt[k])
+            c9grp[lo:hi][c9q[lo:hi, 3] == outs[k]] = gsel
+    out.append(_c_array("ppq_c9grp", "int8_t", c9grp))
     out += [_c_array("ppq_c9q", "int16_t", c9q[:, 1:]), _c_array("ppq_c9qp", "int16_t", c9qp),
             _c_array("ppq_c9g", "int16_t", np.array(c9g)), _c_array("ppq_c9gp", "int16_t", np.array(c9gp))]
     ch9, c9p = by_out(ch9arr, 3, 29)
