@@ -204,6 +204,7 @@ struct Workspace {
   int mt[2] = {1, 1};  // tuned GEMM micro-tile per precision for the current N
   int graph_N[2] = {0, 0};
   int graph_profile[2] = {0, 0};
+  int graph_launches[2] = {0, 0};   // kernels in each captured pipeline
 };
 
 std::mutex g_mu;
@@ -389,15 +390,19 @@ __global__ void k_multidot(size_t L, int N, const double* __restrict__ x0, int m
   if (threadIdx.x == 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
 }
 
+// out[r] = sum of part row r (r < rows), one block per row; block `rows`
+// writes out[rows] = the energy, sum of the site and (halved) pair elements
 __global__ void k_rowsum(int nb, int rows, const double* __restrict__ part, int N,
                          const double* __restrict__ esite, const double* __restrict__ epair,
                          double* __restrict__ out) {
   __shared__ double red[32];
-  for (int r = 0; r < rows; ++r) {
+  const int r = blockIdx.x;
+  if (r < rows) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[(size_t)r * nb + i];
     s = ppq::block_sum(s, red);
     if (threadIdx.x == 0) out[r] = s;
+    return;
   }
   double e = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) e += esite[i];
@@ -759,10 +764,13 @@ int residual(Workspace* w, int N, cudaStream_t s) {
   g_prof.done(PN("ppq::k_site_closure"), s);
   if ((rc = launch_pair_closure<R>(N, g2, t1, t2, pg, pt7, pc0, w->epair, (R*)w->pt7T, s))) return rc;
   g_prof.done(PN("ppq::k_pair_closure_p"), s, 0.0, 2.0 * (NN - N) * (17792.0 + PPQ_PR_N + PPQ_PL_N));
-  ppq::k_r1<R><<<dim3(N, kR1Split), 256, 0, s>>>(N, hs, pc0, cl, pg, w->r1part);
+  size_t T36 = (size_t)NN * PPQ_NS36;
+  ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
+  g_prof.done(PN("ppq::k_transpose_g"), s);
+  ppq::k_r1<R><<<dim3(N, kR1Split), 256, sizeof(R) * ppq::kR1Ld * N, s>>>(N, hs, pc0, cl, (const R*)w->gT,
+                                                                        w->r1part);
   ppq::k_r1_reduce<R><<<(3 * N + 127) / 128, 128, 0, s>>>(N, kR1Split, hs, w->r1part, w->r);
   g_prof.done(PN("ppq::k_r1, k_r1_reduce"), s, 0.0, 2.0 * N * ((N - 1) * PPQ_NT3 + (double)(N - 1) * (N - 2) * PPQ_NT8));
-  size_t T36 = (size_t)NN * PPQ_NS36;
   ppq::k_transpose_cl<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, cl_ld(N), cl, (R*)w->clT);
   g_prof.done(PN("ppq::k_transpose_cl"), s);
   {
@@ -771,7 +779,20 @@ int residual(Workspace* w, int N, cudaStream_t s) {
     if ((rc = launch_t7_gemm<R>(w, N, mt, s))) return rc;
   }
   g_prof.done(PN("ppq::k_t7_gemm"), s, 0.0, 2.0 * PPQ_NK7 * (double)N * N * N);
-  ppq::k_r2<R><<<NN, 256, 0, s>>>(N, hs, pc0, (const R*)w->m7, pg, cl, t2, w->dir, w->abuf);
+  {
+    // staged rows of the T4 sum: 2 kR1Ld + 3 values per X (78.8 KB in FP64 at N = 128)
+    static std::once_flag attr[64][2];
+    int dev;
+    CK(cudaGetDevice(&dev));
+    cudaError_t e = cudaSuccess;
+    std::call_once(attr[dev & 63][sizeof(R) == 8], [&] {
+      e = cudaFuncSetAttribute(ppq::k_r2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(R) * 128 * (2 * ppq::kR1Ld + 3)));
+    });
+    if (e != cudaSuccess) return fail(-100, "k_r2 attribute: %s", cudaGetErrorString(e));
+    ppq::k_r2<R><<<NN, 256, sizeof(R) * N * (2 * ppq::kR1Ld + 3), s>>>(N, hs, pc0, (const R*)w->m7, pg, cl, t2,
+                                                                       w->dir, w->abuf);
+  }
   g_prof.done(PN("ppq::k_r2"), s, 0.0, 2.0 * ((NN - N) / 2.0 * (N - 2) * PPQ_NT4 + (NN - N) * (double)(PPQ_NT2 + PPQ_NT7 + PPQ_NSOP)));
   // quartic term
   if (std::is_same<R, float>::value && w->tc_N == N) {
@@ -787,6 +808,7 @@ int residual(Workspace* w, int N, cudaStream_t s) {
     ppq::k_t9_reduce<float><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc_nslot, w->tc_part,
                                                                                    w->t9);
     g_prof.done(PN("ppq::k_t9_reduce"), s);
+    w->n_launches += 3;
   } else if (std::is_same<R, double>::value && w->tc64_N == N) {
     // tensor cores, exact splitting: split B operands, then the MMA + W-contraction kernel
     ppq::tc::k_t9_bprep64<<<PPQ_NS36, 128, 0, s>>>(
@@ -801,22 +823,22 @@ int residual(Workspace* w, int N, cudaStream_t s) {
     ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->tc64_nslot,
                                                                                     w->tc64_part, w->t9);
     g_prof.done(PN("ppq::k_t9_reduce"), s);
+    w->n_launches += 4;
   } else {
-    // SIMT: transposed operands, GEMM, W-contraction
-    ppq::k_transpose_g<R><<<(unsigned)((T36 + 255) / 256), 256, 0, s>>>(N, pg, (R*)w->gT);
-    g_prof.done(PN("ppq::k_transpose_g"), s);
+    // SIMT: GEMM over the transposed operands, W-contraction
     if (w->profile) CK(cudaEventRecord(w->evq0, s));
     if ((rc = launch_t9_mt_rt<R>(w, N, w->mt[std::is_same<R, float>::value ? 1 : 0], s))) return rc;
     if (w->profile) CK(cudaEventRecord(w->evq1, s));
     g_prof.done("ppq::k_t9_gemm (quartic, SIMT)", s, 0.0, quartic_flops(N));
     ppq::k_t9_reduce<double><<<(unsigned)((NN * PPQ_NA2 + 255) / 256), 256, 0, s>>>(N, w->n_work9, w->t9part,
                                                                                     w->t9);
+    w->n_launches += 2;
   }
   size_t L2 = (size_t)NN * PPQ_NA2;
   ppq::k_assemble<<<(unsigned)((L2 + 255) / 256), 256, 0, s>>>(N, w->dir, w->abuf, w->t9, w->r + 3 * N);
   g_prof.done(PN("ppq::k_t9_reduce, k_assemble"), s);
   CK(cudaGetLastError());
-  w->n_launches += 12;
+  w->n_launches += 10;   // the launches common to the three quartic forms
   return 0;
 #undef PN
 }
@@ -849,10 +871,11 @@ int run_residual(Workspace* w, int N, int precision, cudaStream_t s) {
     cudaGraphDestroy(g);
     w->graph_N[p] = N;
     w->graph_profile[p] = (int)w->profile;
+    w->graph_launches[p] = w->n_launches - nl;
     w->n_launches = nl;
   }
   CK(cudaGraphLaunch(w->graph[p], s));
-  w->n_launches += 12;
+  w->n_launches += w->graph_launches[p];
   return 0;
 }
 
@@ -1154,7 +1177,9 @@ __global__ void k_axpy_to(size_t L, const double* __restrict__ a, const double* 
 // from dots[1..m]; the bordered system [B -1; -1 0][c; l] = [0; -1] over the
 // active slots (order[0..m), newest last) is solved in FP64 by one warp (a
 // lane per row, partial pivoting; back-substitution by lane 0), the error
-// block scaled by its largest diagonal, which leaves c unchanged;
+// block scaled by the power of two at or above its largest diagonal (exact;
+// c unchanged).  Divisions are few (FP64 division is long on this part): one
+// reciprocal of the pivot per column and one of each diagonal;
 // coef = c, or the newest iterate alone if the system is singular or
 // extrapolation is off.
 __global__ void __launch_bounds__(32) k_diis_solve(int m, const int* __restrict__ order, int inew,
@@ -1178,9 +1203,11 @@ __global__ void __launch_bounds__(32) k_diis_solve(int m, const int* __restrict_
   const int nn = m + 1;
   double dd = lane < m ? fabs(B[ord[lane] * ldb + ord[lane]]) : 0.0;
   for (int o = 16; o > 0; o >>= 1) dd = fmax(dd, __shfl_xor_sync(0xffffffffu, dd, o));
-  const double sc = dd > 0.0 ? dd : 1.0;
+  int ex = 0;
+  if (dd > 0.0) frexp(dd, &ex);
+  const double isc = ldexp(1.0, -ex);
   if (lane < nn) {
-    for (int j = 0; j < m; ++j) A[lane][j] = lane < m ? B[ord[lane] * ldb + ord[j]] / sc : -1.0;
+    for (int j = 0; j < m; ++j) A[lane][j] = lane < m ? B[ord[lane] * ldb + ord[j]] * isc : -1.0;
     A[lane][m] = lane < m ? -1.0 : 0.0;
     A[lane][nn] = lane < m ? 0.0 : -1.0;
   }
@@ -1201,18 +1228,22 @@ __global__ void __launch_bounds__(32) k_diis_solve(int m, const int* __restrict_
       A[idx][lane] = x;
     }
     __syncwarp();
+    const double ip = 1.0 / A[col][col];
     if (lane > col && lane < nn) {
-      double f = A[lane][col] / A[col][col];
+      double f = A[lane][col] * ip;
       for (int q = col; q <= nn; ++q) A[lane][q] -= f * A[col][q];
     }
     __syncwarp();
   }
+  __shared__ double idg[17];
+  if (lane < nn) idg[lane] = 1.0 / A[lane][lane];
+  __syncwarp();
   if (lane == 0) {
     double x[17];
     for (int r2 = nn - 1; r2 >= 0; --r2) {
       double s = A[r2][nn];
       for (int q = r2 + 1; q < nn; ++q) s -= A[r2][q] * x[q];
-      x[r2] = s / A[r2][r2];
+      x[r2] = s * idg[r2];
     }
     bool finite = true;
     for (int j = 0; j < m; ++j) finite = finite && isfinite(x[j]);
@@ -1265,7 +1296,7 @@ struct Solver {
     CK(cudaEventRecord(w->ev1, s));
     dim3 g(kRedBlocks, 1);
     k_multidot<<<g, 256, 0, s>>>(L, N, w->r, 0, w->slot_e, L, w->order, 0, w->part);
-    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+    k_rowsum<<<2, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
     CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(w->host + 60, w->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     g_prof.done("solver: norm, energy, device-to-host", s, 8.0 * L);
@@ -1314,7 +1345,7 @@ struct Solver {
     CK(cudaMemcpyAsync(w->order, w->host + 48, sizeof(int) * m, cudaMemcpyHostToDevice, s));
     dim3 g(kRedBlocks, 1 + m);
     k_multidot<<<g, 256, 0, s>>>(L, N, res, m, w->slot_e, L, w->order, slot, w->part);
-    k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
+    k_rowsum<<<m + 2, 256, 0, s>>>(kRedBlocks, 1 + m, w->part, N, w->esite, w->epair, w->scal);
     d.ring = act;
     // bordered least squares and extrapolation on the device (no host round trip)
     int extrap = o.diis_dim > 0 && it >= o.diis_start && m > 1;
@@ -1361,7 +1392,7 @@ struct Solver {
       if ((rc = lagrangian_gradient(w, N, w->lam, s))) return rc;
       dim3 g(kRedBlocks, 1);
       k_multidot<<<g, 256, 0, s>>>(L, N, w->gu, 0, w->slot_e, L, w->order, 0, w->part);
-      k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+      k_rowsum<<<2, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
       CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       res = sqrt(w->host[0]);
@@ -1414,7 +1445,7 @@ struct Solver {
       // weighted norm of rho
       dim3 g(kRedBlocks, 1);
       k_multidot<<<g, 256, 0, s>>>(L, N, rho, 0, w->slot_e, L, w->order, 0, w->part);
-      k_rowsum<<<1, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
+      k_rowsum<<<2, 256, 0, s>>>(kRedBlocks, 1, w->part, N, w->esite, w->epair, w->scal);
       CK(cudaMemcpyAsync(w->host, w->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       w->n_launches += 2;

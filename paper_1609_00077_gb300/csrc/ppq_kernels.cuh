@@ -114,15 +114,10 @@ __global__ void k_links(int N, const double* __restrict__ t2, R* __restrict__ cl
 #pragma unroll
   for (int c = 0; c < PPQ_NS36; ++c) v[c] = R(0);
   if (X != Y) {
+    // generated straight-line operator sequence (ppq_link_apply): constant
+    // indices keep v in registers
     v[0] = R(1);
-    const double* t = t2 + (size_t)XY * PPQ_NA2;
-    for (int k = 0; k < PPQ_NA2; ++k) {
-      R tk = R(t[k]);
-      for (int e = ppq_sop_ptr[k]; e < ppq_sop_ptr[k + 1]; ++e) {
-        int32_t w = ppq_sop[e];
-        v[unpack_t(w)] += tk * unpack_sign<R>(w) * v[unpack_s(w)];
-      }
-    }
+    ppq_link_apply(t2 + (size_t)XY * PPQ_NA2, v);
   }
   R* o = cl + (size_t)XY * PPQ_NS36;
 #pragma unroll
@@ -294,35 +289,41 @@ __device__ __forceinline__ R block_sum(R v, R* red) {
 
 // r1[Y]: topologies T1 (Ht_Y), T6 (pair pieces on Y,W), T3 (one-site piece on
 // X linked to Y), T8 (pair piece on X,W, both linked to Y)
+constexpr int kR1Ld = PPQ_NS36 + 1;   // row stride of the staged Cl column in k_r1
 template <typename R>
 __global__ void k_r1(int N, const R* __restrict__ hs, const R* __restrict__ pc0,
-                     const R* __restrict__ cl, const R* __restrict__ pg, double* __restrict__ part) {
+                     const R* __restrict__ cl, const R* __restrict__ gT, double* __restrict__ part) {
   // block (Y, split): the T3 / column-0 part in split 0, the T8 sum over
-  // XW = split, split + nsplit, ... ; partial sums to part[split][Y][3]
+  // XW = split, split + nsplit, ... ; partial sums to part[split][Y][3].
+  // Every link coefficient the block reads is one of Cl[., Y]: the column is
+  // staged in shared memory as rows cY[X][c] of kR1Ld (odd) words, so that
+  // lanes with consecutive W hit distinct banks; G[X,W][g] comes from the
+  // transposed gT[g][X][W] (lanes read consecutive words); the T8 entries
+  // are generated straight-line code (ppq_r1_t8), no table reads.
+  extern __shared__ __align__(16) unsigned char r1_smem[];
+  R* cY = reinterpret_cast<R*>(r1_smem);
   __shared__ R red[32];
-  int Y = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+  const int Y = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+  for (int i = threadIdx.x; i < N * PPQ_NS36; i += blockDim.x) {
+    const int X = i / PPQ_NS36, c = i % PPQ_NS36;
+    cY[X * kR1Ld + c] = cl[((size_t)X * N + Y) * PPQ_NS36 + c];
+  }
+  __syncthreads();
   R acc[3] = {R(0), R(0), R(0)};
   for (int X = threadIdx.x; sp == 0 && X < N; X += blockDim.x) {
     if (X == Y) continue;
-    const R* c = cl + ((size_t)X * N + Y) * PPQ_NS36;
     const R* h0 = hs + (size_t)X * 256;  // row 0 of Ht_X
     for (int k = 0; k < 3; ++k)
       for (int e = ppq_t3p[k]; e < ppq_t3p[k + 1]; ++e)
-        acc[k] += h0[ppq_t3[3 * e + 1]] * c[ppq_t3[3 * e]];
+        acc[k] += h0[ppq_t3[3 * e + 1]] * cY[X * kR1Ld + ppq_t3[3 * e]];
     const R* p0 = pc0 + ((size_t)Y * N + X) * PPQ_NCOL0;
     for (int k = 0; k < 3; ++k) acc[k] += p0[29 + k];
   }
+  const size_t NN = (size_t)N * N;
   for (int XW = sp * blockDim.x + threadIdx.x; XW < N * N; XW += nsp * blockDim.x) {
     int X = XW / N, W = XW % N;
     if (X == W || X == Y || W == Y) continue;
-    const R* cx = cl + ((size_t)X * N + Y) * PPQ_NS36;
-    const R* cw = cl + ((size_t)W * N + Y) * PPQ_NS36;
-    const R* g = pg + (size_t)XW * PPQ_NS36;
-    for (int k = 0; k < 3; ++k)
-      for (int e = ppq_t8p[k]; e < ppq_t8p[k + 1]; ++e) {
-        const int16_t* q = ppq_t8 + 5 * e;
-        acc[k] += R(0.5) * R(q[4]) * cx[q[0]] * cw[q[1]] * g[q[2]];
-      }
+    ppq_r1_t8(cY + X * kR1Ld, cY + W * kR1Ld, gT + XW, NN, acc);
   }
   for (int k = 0; k < 3; ++k) {
     R s = block_sum(acc[k], red);
@@ -361,24 +362,37 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
     return;
   }
   const R* clYZ = cl + (size_t)YZ * PPQ_NS36;
-  constexpr int S4 = 8, S7 = 7;
-  __shared__ R part4[PPQ_NA2][S4];
+  constexpr int S7 = 7;
   __shared__ R part7[PPQ_NS36][S7];
-  // T4 (direct term, needed for Y < Z only): thread (o, s) sums X = s, s + S4, ...
-  if (Y < Z && threadIdx.x < PPQ_NA2 * S4) {
-    int o = threadIdx.x / S4, sl = threadIdx.x % S4;
-    R acc = R(0);
-    for (int X = sl; X < N; X += S4) {
-      if (X == Y || X == Z) continue;
-      const R* cy = cl + ((size_t)X * N + Y) * PPQ_NS36;
-      const R* cz = cl + ((size_t)X * N + Z) * PPQ_NS36;
-      const R* h0 = hs + (size_t)X * 256;
-      for (int e = ppq_t4p[o]; e < ppq_t4p[o + 1]; ++e) {
-        const int16_t* q = ppq_t4 + 5 * e;
-        acc += R(q[4]) * cy[q[0]] * cz[q[1]] * h0[q[2]];
-      }
+  // T4 (direct term, needed for Y < Z only): the rows Cl[X,Y][.], Cl[X,Z][.]
+  // and Ht_X[0, 5 / 10 / 15] of every X are staged in shared memory (rows of
+  // kR1Ld words, lanes on consecutive X hit distinct banks); thread (X, half)
+  // runs the generated entries of outputs 0-14 or 15-28 (a warp per half
+  // and 32 X), and the per-X sums go to p4[o][X] (over the staged rows) for
+  // a fixed-order sum over X
+  extern __shared__ __align__(16) unsigned char r2_smem[];
+  R* cY = reinterpret_cast<R*>(r2_smem);          // [N][kR1Ld]
+  R* cZ = cY + (size_t)N * kR1Ld;                  // [N][kR1Ld]
+  R* hx = cZ + (size_t)N * kR1Ld;                  // [N][3]
+  R* p4 = cY;                                      // [29][N], after the T4 sums
+  if (Y < Z) {
+    for (int i = threadIdx.x; i < N * PPQ_NS36; i += blockDim.x) {
+      const int X = i / PPQ_NS36, c = i % PPQ_NS36;
+      cY[X * kR1Ld + c] = cl[((size_t)X * N + Y) * PPQ_NS36 + c];
+      cZ[X * kR1Ld + c] = cl[((size_t)X * N + Z) * PPQ_NS36 + c];
     }
-    part4[o][sl] = acc;
+    for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) hx[i] = hs[(size_t)(i / 3) * 256 + 5 * (i % 3 + 1)];
+  }
+  __syncthreads();
+  const int X4 = ((threadIdx.x >> 6) << 5) | (threadIdx.x & 31), h4 = (threadIdx.x >> 5) & 1;
+  const bool do4 = Y < Z && X4 < N;
+  static_assert(PPQ_NA2 == 29, "two halves of at most 15 outputs");
+  R a4[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) a4[i] = R(0);
+  if (do4 && X4 != Y && X4 != Z) {
+    if (h4 == 0) ppq_r2_t4_0(cY + X4 * kR1Ld, cZ + X4 * kR1Ld, hx + 3 * X4, a4);
+    else ppq_r2_t4_1(cY + X4 * kR1Ld, cZ + X4 * kR1Ld, hx + 3 * X4, a4);
   }
   // T7 from the GEMM products M7[Y,Z][k] = sum_W pt7[Y,W][e] Cl[W,Z][c2]
   // (W = Y and W = Z contribute zero: Cl[Z,Z] = 0, pt7[Y,Y] = 0)
@@ -392,13 +406,20 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
     }
     part7[nu][sl] = acc;
   }
+  __syncthreads();   // the staged rows are read; p4 reuses them
+  if (do4) {
+    const int o0 = 15 * h4, no = h4 ? PPQ_NA2 - 15 : 15;
+#pragma unroll
+    for (int i = 0; i < 15; ++i)
+      if (i < no) p4[(o0 + i) * N + X4] = a4[i];
+  }
   __syncthreads();
   if (threadIdx.x < PPQ_NA2) {
     int o = threadIdx.x;
     R acc = R(0);
     if (Y < Z) {
       acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
-      for (int sl = 0; sl < S4; ++sl) acc += part4[o][sl];
+      for (int X = 0; X < N; ++X) acc += p4[o * N + X];
     }
     outs[o] = acc;
   }

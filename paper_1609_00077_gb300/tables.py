@@ -573,6 +573,66 @@ def site_transform_lists(T):
             np.array(left, dtype=np.int64), np.array(lptr, dtype=np.int64))
 
 
+def r1_t8_code(t8, t8p):
+    """C++ source of the T8 sum of r1 as straight-line code: for output k the
+    entries (c1, c2, g, k, s) of the channel table in table order, each
+    acc[k] += (s/2) cx[c1] cw[c2] g[g NN], where cx, cw are the rows
+    Cl[X,Y][.], Cl[W,Y][.] and g points at G[X,W][0] in the transposed
+    (channel-major) G; the factor order is that of the table-driven form."""
+    out = ["template <typename R>",
+           "__device__ __forceinline__ void ppq_r1_t8(const R* __restrict__ cx, const R* __restrict__ cw, "
+           "const R* __restrict__ g, size_t NN, R* __restrict__ acc) {"]
+    for k in range(3):
+        for e in range(t8p[k], t8p[k + 1]):
+            c1, c2, gi, kk, sg = (int(x) for x in t8[e])
+            assert kk == k and sg in (-1, 1)
+            h = "R(0.5)" if sg > 0 else "R(-0.5)"
+            out.append(f"  acc[{k}] += {h} * cx[{c1}] * cw[{c2}] * g[{gi} * NN];")
+    out.append("}")
+    return "\n".join(out)
+
+
+def r2_t4_code(t4, t4p):
+    """C++ source of the T4 sum of r2 as straight-line code, for one X: the
+    outputs split in two halves (ppq_r2_t4_0: outputs 0-14, ppq_r2_t4_1:
+    15-28), each entry (c1, c2, m, o, s) of the table in table order as
+    acc[o - o0] += s cy[c1] cz[c2] hx[j], with cy, cz the rows Cl[X,Y][.],
+    Cl[X,Z][.] and hx[j] = Ht_X[0, m] for m = 5, 10, 15 (j = 0, 1, 2)."""
+    hm = {5: 0, 10: 1, 15: 2}
+    out = []
+    for half, (o0, o1) in enumerate(((0, 15), (15, 29))):
+        out += ["template <typename R>",
+                f"__device__ __forceinline__ void ppq_r2_t4_{half}(const R* __restrict__ cy, const R* __restrict__ cz, "
+                "const R* __restrict__ hx, R* __restrict__ acc) {"]
+        for o in range(o0, o1):
+            for e in range(t4p[o], t4p[o + 1]):
+                c1, c2, m, oo, sg = (int(x) for x in t4[e])
+                assert oo == o and sg in (-1, 1) and m in hm
+                out.append(f"  acc[{o - o0}] += R({sg}) * cy[{c1}] * cz[{c2}] * hx[{hm[m]}];")
+        out.append("}")
+    return "\n".join(out)
+
+
+def link_code(sop):
+    """C++ source of the link coefficients exp(T_XY)|ref> on the 36-state
+    sector as straight-line code over a register array: the factors
+    (1 + t_k O_k) in order k = 0..28, each operator entry (k, s, d, sign) of
+    the table in table order as v[d] += t_k sign v[s]."""
+    out = ["template <typename R>",
+           "__device__ __forceinline__ void ppq_link_apply(const double* __restrict__ t, R* __restrict__ v) {"]
+    for k in range(29):
+        rows = sop[sop[:, 0] == k]
+        if not len(rows):
+            continue
+        out.append(f"  {{ const R tk = R(t[{k}]);")
+        for _, src, dst, g in rows:
+            sg = "R(-1)" if g < 0 else "R(1)"
+            out.append(f"    v[{int(dst)}] += tk * {sg} * v[{int(src)}];")
+        out.append("  }")
+    out.append("}")
+    return "\n".join(out)
+
+
 def pair_sweep_code(T, L):
     """C++ source of the pair closure's per-sector sweeps with one thread's row
     (right, exp(I)) or column (left, exp(-I)) held in registers: for every
@@ -781,6 +841,7 @@ def emit_header(path):
     out += [f"#define PPQ_NSOP {len(sop)}",
             _c_array("ppq_sop", "int32_t", [_pack(d, s, g) for _, s, d, g in sop]),
             _c_array("ppq_sop_ptr", "int16_t", sptr)]
+    out.append(link_code(sop))
     # topology channel lists
     def by_out(arr, col, nout):
         arr = np.asarray(arr)
@@ -796,6 +857,8 @@ def emit_header(path):
             f"#define PPQ_NT3 {len(t3)}", _c_array("ppq_t3", "int16_t", t3), _c_array("ppq_t3p", "int16_t", t3p),
             f"#define PPQ_NT4 {len(t4)}", _c_array("ppq_t4", "int16_t", t4), _c_array("ppq_t4p", "int16_t", t4p),
             f"#define PPQ_NT8 {len(t8)}", _c_array("ppq_t8", "int16_t", t8), _c_array("ppq_t8p", "int16_t", t8p)]
+    out.append(r1_t8_code(t8, t8p))
+    out.append(r2_t4_code(t4, t4p))
     t7c, t7p = by_out(np.array([(c1, c2, t7e[(int(r), int(c))], nu, s) for c1, c2, r, c, nu, s in t7]), 3, 36)
     out += [f"#define PPQ_NT7 {len(t7c)}", _c_array("ppq_t7", "int16_t", t7c), _c_array("ppq_t7p", "int16_t", t7p)]
     # GEMM form of T7: M7[k][Y][Z] = sum_W pt7[Y,W][e] Cl[W,Z][c2] for each

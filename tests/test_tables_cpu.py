@@ -17,6 +17,8 @@ kernels rely on (no GPU needed).
   2^23, and the recombined product is within 3e-12 of row-max x column-max x K;
   the slicing on bit patterns (integer operations only) rounds to the nearest
   integer, ties away from zero, and its digits recombine exactly.
+* The FP64 epilogue groups keep each output of a (c1, c2, g) in one group.
+* The generated straight-line T8 code of r1 holds the table's entries in order.
 """
 import numpy as np
 import pytest
@@ -298,3 +300,29 @@ def test_fp64_epilogue_groups_keep_outputs_whole_and_balance():
         worst += load.max()
         fixed += np.bincount(o & 3, minlength=4).max()
     assert worst < 0.85 * fixed          # the busiest group does less than with outputs mod 4
+
+
+def test_generated_r1_t8_code_reproduces_the_table():
+    import re
+    t8 = T.t8_channels(T.Tables())
+    order = np.argsort(t8[:, 3], kind="stable")
+    ref = [tuple(int(x) for x in t8[i]) for i in order]
+    import os, tempfile
+    fd, path = tempfile.mkstemp(suffix=".h")
+    os.close(fd)
+    try:
+        T.emit_header(path)
+        text = open(path).read()
+    finally:
+        os.remove(path)
+    body = text[text.index("void ppq_r1_t8("):]
+    body = body[:body.index("\n}")]
+    lines = [l for l in body.splitlines() if l.strip().startswith("acc[")]
+    pat = re.compile(r"acc\[(\d)\] \+= R\((-?0\.5)\) \* cx\[(\d+)\] \* cw\[(\d+)\] \* g\[(\d+) \* NN\];")
+    got = []
+    for l in lines:
+        m = pat.fullmatch(l.strip())
+        assert m, l
+        k, h, c1, c2, g = m.groups()
+        got.append((int(c1), int(c2), int(g), int(k), 1 if float(h) > 0 else -1))
+    assert got == ref
