@@ -414,14 +414,19 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
       if (i < no) p4[(o0 + i) * N + X4] = a4[i];
   }
   __syncthreads();
-  if (threadIdx.x < PPQ_NA2) {
-    int o = threadIdx.x;
-    R acc = R(0);
-    if (Y < Z) {
-      acc = pc0[(size_t)YZ * PPQ_NCOL0 + o];
-      for (int X = 0; X < N; ++X) acc += p4[o * N + X];
+  // outputs: warp w sums outputs o = w, w + 8, ... over X (lane X = ln, ln + 32, ..., then a shuffle tree)
+  {
+    const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    for (int o = wp; o < PPQ_NA2; o += blockDim.x >> 5) {
+      R acc = R(0);
+      if (Y < Z) {
+        for (int X = ln; X < N; X += 32) acc += p4[o * N + X];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        acc += pc0[(size_t)YZ * PPQ_NCOL0 + o];
+      }
+      if (ln == 0) outs[o] = acc;
     }
-    outs[o] = acc;
   }
   if (threadIdx.x >= 64 && threadIdx.x < 64 + PPQ_NS36) {
     int nu = threadIdx.x - 64;
@@ -435,21 +440,17 @@ __global__ void __launch_bounds__(256) k_r2(int N, const R* __restrict__ hs, con
     U[nu] = acc;
   }
   __syncthreads();
-  // exp(-T_YZ) on U (sequential over the commuting factors)
-  const double* t = t2 + (size_t)YZ * PPQ_NA2;
-  for (int k = 0; k < PPQ_NA2; ++k) {
-    R tk = R(t[k]);
-    int e = ppq_sop_ptr[k] + threadIdx.x;
-    if (e < ppq_sop_ptr[k + 1]) {
-      int32_t w = ppq_sop[e];
-      U[unpack_t(w)] -= tk * unpack_sign<R>(w) * U[unpack_s(w)];
-    }
-    __syncthreads();
+  // exp(-T_YZ) on U by one thread, as generated straight-line code over
+  // registers (ppq_link_unapply), then the transformed elements to abuf
+  if (threadIdx.x == 0) {
+    R u[PPQ_NS36];
+#pragma unroll
+    for (int c = 0; c < PPQ_NS36; ++c) u[c] = U[c];
+    ppq_link_unapply(t2 + (size_t)YZ * PPQ_NA2, u);
+#pragma unroll
+    for (int k = 0; k < PPQ_NA2; ++k) abuf[(size_t)YZ * PPQ_NA2 + k] = double(u[1 + k]);
   }
-  for (int k = threadIdx.x; k < PPQ_NA2; k += blockDim.x) {
-    dir[(size_t)YZ * PPQ_NA2 + k] = double(outs[k]);
-    abuf[(size_t)YZ * PPQ_NA2 + k] = double(U[1 + k]);
-  }
+  for (int k = threadIdx.x; k < PPQ_NA2; k += blockDim.x) dir[(size_t)YZ * PPQ_NA2 + k] = double(outs[k]);
 }
 
 // r2[Y,Z] = dir[Y,Z] + abuf[Y,Z] + mirror(abuf[Z,Y]).  Both stored

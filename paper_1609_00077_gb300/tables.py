@@ -617,19 +617,23 @@ def link_code(sop):
     """C++ source of the link coefficients exp(T_XY)|ref> on the 36-state
     sector as straight-line code over a register array: the factors
     (1 + t_k O_k) in order k = 0..28, each operator entry (k, s, d, sign) of
-    the table in table order as v[d] += t_k sign v[s]."""
-    out = ["template <typename R>",
-           "__device__ __forceinline__ void ppq_link_apply(const double* __restrict__ t, R* __restrict__ v) {"]
-    for k in range(29):
-        rows = sop[sop[:, 0] == k]
-        if not len(rows):
-            continue
-        out.append(f"  {{ const R tk = R(t[{k}]);")
-        for _, src, dst, g in rows:
-            sg = "R(-1)" if g < 0 else "R(1)"
-            out.append(f"    v[{int(dst)}] += tk * {sg} * v[{int(src)}];")
-        out.append("  }")
-    out.append("}")
+    the table in table order as v[d] += t_k sign v[s] (ppq_link_apply); and
+    exp(-T_XY) the same way with v[d] -= t_k sign v[s] (ppq_link_unapply:
+    O_k^2 = 0, so 1 - t_k O_k is the inverse factor)."""
+    out = []
+    for name, op in (("ppq_link_apply", "+="), ("ppq_link_unapply", "-=")):
+        out += ["template <typename R>",
+                f"__device__ __forceinline__ void {name}(const double* __restrict__ t, R* __restrict__ v) {{"]
+        for k in range(29):
+            rows = sop[sop[:, 0] == k]
+            if not len(rows):
+                continue
+            out.append(f"  {{ const R tk = R(t[{k}]);")
+            for _, src, dst, g in rows:
+                sg = "R(-1)" if g < 0 else "R(1)"
+                out.append(f"    v[{int(dst)}] {op} tk * {sg} * v[{int(src)}];")
+            out.append("  }")
+        out.append("}")
     return "\n".join(out)
 
 

@@ -326,3 +326,52 @@ def test_generated_r1_t8_code_reproduces_the_table():
         k, h, c1, c2, g = m.groups()
         got.append((int(c1), int(c2), int(g), int(k), 1 if float(h) > 0 else -1))
     assert got == ref
+
+
+def _generated_function(name):
+    import os, re, tempfile
+    fd, path = tempfile.mkstemp(suffix=".h")
+    os.close(fd)
+    try:
+        T.emit_header(path)
+        text = open(path).read()
+    finally:
+        os.remove(path)
+    body = text[text.index(f"void {name}("):]
+    return body[:body.index("\n}")]
+
+
+def test_generated_link_code_follows_the_operator_table_and_inverts():
+    import re
+    sop = T.sector_pair_ops(T.Tables())
+    rng = np.random.default_rng(2)
+    t = rng.uniform(-0.3, 0.3, 29)
+    progs = {}
+    for name, sgn in (("ppq_link_apply", 1.0), ("ppq_link_unapply", -1.0)):
+        body = _generated_function(name)
+        k = None
+        prog = []
+        for l in body.splitlines():
+            m = re.fullmatch(r"\s*\{ const R tk = R\(t\[(\d+)\]\);", l)
+            if m:
+                k = int(m.group(1))
+                continue
+            m = re.fullmatch(r"\s*v\[(\d+)\] ([+-])= tk \* R\((-?1)\) \* v\[(\d+)\];", l)
+            if m:
+                d, op, g, src = int(m.group(1)), m.group(2), int(m.group(3)), int(m.group(4))
+                assert (op == "+") == (sgn > 0)
+                prog.append((k, src, d, g))
+        assert prog == [tuple(int(x) for x in r) for r in sop]
+        progs[name] = (prog, sgn)
+
+    def run(name, v):
+        prog, sgn = progs[name]
+        v = v.copy()
+        for k, src, d, g in prog:
+            v[d] += sgn * t[k] * g * v[src]
+        return v
+
+    v0 = np.zeros(36); v0[0] = 1.0
+    v1 = run("ppq_link_apply", v0)
+    assert np.abs(v1 - v0).max() > 1e-2
+    assert np.abs(run("ppq_link_unapply", v1) - v0).max() < 1e-14   # exp(-T) exp(T) |ref> = |ref>
