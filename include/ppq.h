@@ -39,7 +39,9 @@
  *     exactly once;
  *   - h (n_orb^2) and eri (n_orb^4, chemists' notation (pq|rs), 8-fold
  *     symmetric, row-major) are FP64 and may be host or device pointers
- *     (detected); they are read, never written, and stay caller-owned;
+ *     (detected); they are read, never written, and stay caller-owned.  A
+ *     pinned (page-locked, device-mapped) host eri is read in place by the
+ *     kernels over the host link; pageable host memory is copied first;
  *   - amplitude / residual buffers are FP64 and may be host or device
  *     pointers (detected);
  *   - work runs on `stream` (a cudaStream_t, 0 = legacy default stream); the

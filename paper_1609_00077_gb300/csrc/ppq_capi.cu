@@ -919,8 +919,14 @@ int prepare_ws(Workspace* w, int N, const int* occ, const int* vir, const double
     CK(cudaMemcpyAsync(w->h, h, sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
     P->h = w->h;
   }
+  void* mapped = nullptr;
   if (is_device_ptr(eri)) P->eri = eri;
-  else {
+  else if (cudaHostGetDevicePointer(&mapped, const_cast<double*>(eri), 0) == cudaSuccess && mapped) {
+    // pinned host integrals mapped into the device address space: the screen
+    // and the staging kernels read them over the host link, no n^4 copy
+    P->eri = (const double*)mapped;
+  } else {
+    cudaGetLastError();   // pageable host memory: copy it
     if (w->eri_cap < n4) {
       if (w->eri) cudaFree(w->eri);
       w->eri = nullptr;

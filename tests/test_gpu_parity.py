@@ -86,6 +86,15 @@ def test_residual_host_and_device_inputs_agree():
     r_host, e_host = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, np.ascontiguousarray(H.h),
                                      np.ascontiguousarray(H.eri), t)
     assert np.array_equal(r_dev.cpu().numpy(), r_host) and e_dev == e_host
+    # pinned (page-locked) host integrals are read in place over the host link
+    h_pin = torch.from_numpy(np.ascontiguousarray(H.h)).pin_memory()
+    eri_pin = torch.from_numpy(np.ascontiguousarray(H.eri)).pin_memory()
+    r_pin, e_pin = ppq.pq_residual(H.occ_of_pair, H.vir_of_pair, h_pin.numpy(), eri_pin.numpy(), t)
+    assert np.array_equal(r_dev.cpu().numpy(), r_pin) and e_dev == e_pin
+    rc, et_dev, _, _ = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, dev(H.h), dev(H.eri), H.e_const, precision=1)
+    rc2, et_pin, _, _ = ppq.pq_solve(H.occ_of_pair, H.vir_of_pair, h_pin.numpy(), eri_pin.numpy(), H.e_const,
+                                     precision=1)
+    assert rc == 0 and rc2 == 0 and et_dev == et_pin
 
 
 def test_zero_amplitudes_residual_is_mp2_like_first_order():
