@@ -76,7 +76,9 @@ typedef struct {
                       /*     takes 2, ph_solve 2 or 3                           */
   int precision;      /* 0 = FP64 throughout; 1 = mixed: FP32 residual until   */
                       /*     ||R|| <= switch_tol or stagnation, then FP64      */
-  double switch_tol;  /* 1e-5                                                  */
+  double switch_tol;  /* 0 = the solver's default: 1e-4 for the dense PQ      */
+                      /*     solver, 1e-5 for the label-subset solver (PH,     */
+                      /*     K_H = -1); > 0 as given; < 0 is rejected          */
   double r_tol;       /* converged when ||R||_2 <= r_tol ...  (1e-10)           */
   double e_tol;       /* ... and |dE| <= e_tol (1e-10): dE between successive   */
                       /*     FP64 iterates, or (defect-correction polish) the   */

@@ -1262,7 +1262,7 @@ int subset_solve(int K, int KH, int n_pairs, const int* occ_of_pair, const int* 
       // steps below 1e-4: the FP32 noise floor)
       size_t k = hist.size();
       bool stagnant = k >= 4 && res < 1e-4 && hist[k - 1] > 0.9 * hist[k - 4];
-      if (res <= o.switch_tol || stagnant) {
+      if (res <= (o.switch_tol > 0.0 ? o.switch_tol : 1e-5) || stagnant) {
         prec = 0;
         switched_at = it;
         have_old = false;

@@ -1477,7 +1477,7 @@ extern "C" {
 int ppq_default_opts(ppq_opts* o) {
   if (!o) return fail(-2, "null opts");
   o->K = 2; o->K_H = 0; o->precision = 0;
-  o->switch_tol = 1e-5; o->r_tol = 1e-10; o->e_tol = 1e-10;
+  o->switch_tol = 0.0; o->r_tol = 1e-10; o->e_tol = 1e-10;   // switch_tol 0: the solver's own default
   o->max_iter = 200; o->diis_dim = 8; o->diis_start = 3;
   o->level_shift = 0.0; o->guess = 0; o->profile = 0; o->polish = 1; o->max_rank = 0;
   return 0;
@@ -1599,6 +1599,7 @@ int validate_opts(const ppq_opts& o, bool allow_full = false) {
   if (o.max_iter < 1 || o.diis_dim < 0 || o.diis_dim > kDiisMax)
     return fail(-4, "max_iter >= 1 and 0 <= diis_dim <= %d required", kDiisMax);
   if (o.max_rank < 0 || o.max_rank > 6) return fail(-4, "max_rank must be 0 (every rank) or 1..6");
+  if (!(o.switch_tol >= 0.0)) return fail(-4, "switch_tol must be >= 0 (0: the solver's default)");
   if (o.max_rank != 0 && o.K_H != -1)
     return fail(-4, "max_rank needs the label-subset solver (ph_solve, or pq_solve with K_H = -1)");
   return 0;
@@ -1694,7 +1695,10 @@ int solve_core(Workspace* w, const Problem& P, double e_const, const ppq_opts& o
     if (prec == 1) {
       size_t k = hist.size();
       bool stagnant = k >= 4 && res < 1e-3 && hist[k - 1] > 0.9 * hist[k - 4];
-      if (res <= o.switch_tol || stagnant) {
+      // default switch at 1e-4: the defect-correction polish takes the same three
+      // FP64 steps from there as from 1e-5 on the C140H142 workload, with fewer
+      // FP32 iterations before it (41 instead of 46 evaluations in all)
+      if (res <= (o.switch_tol > 0.0 ? o.switch_tol : 1e-4) || stagnant) {
         prec = 0;
         switched_at = it;
         have_old = false;
