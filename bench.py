@@ -11,7 +11,7 @@ chain does not converge); dense FP64 MO integrals (pq|rs) of 140^4 entries
 
 A step is one complete mixed-precision PQ solve (FP32 residual until
 ||R|| <= 1e-4 (the PQ default) or stagnation, then FP64 polish to ||R|| <= 1e-10 and
-|dE| <= 1e-12): integral staging, every residual evaluation, energy, Jacobi
+|dE| <= 1e-10): integral staging, every residual evaluation, energy, Jacobi
 update and DIIS.  `value` is the time to solution in seconds (device time,
 CUDA events, inputs resident in HBM).  The FP64-only solve is timed beside it
 and |dE| between the two is reported.  `e2e` repeats the mixed solve through
