@@ -301,7 +301,7 @@ def cpu_baseline(sites, seconds, iters, seed=0, all_cores=True):
 # residual evaluations of the GPU mixed solve of PPP C140H142 (the value the
 # GPU arm reports live as iters; the reference arm scales its oracle sample by
 # the same count)
-SOLVE_EVALS = 47
+SOLVE_EVALS = 41
 
 
 METRIC = "PQ time to solution, PPP C140H142 (70 pairs), mixed FP32/FP64"
