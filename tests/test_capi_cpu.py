@@ -63,6 +63,8 @@ def test_ph_entry_points_reject_bad_arguments_without_gpu():
         ppq.ph_solve([2, 2, 0], [3, 4, 5], h, eri)
     with pytest.raises(ppq.PPQError, match=r"pq_solve failed \(-4\).*max_rank"):
         ppq.pq_solve([2, 1, 0], [3, 4, 5], h, eri, max_rank=2)
+    with pytest.raises(ppq.PPQError, match=r"pq_solve failed \(-4\).*switch_tol"):
+        ppq.pq_solve([2, 1, 0], [3, 4, 5], h, eri, switch_tol=-1e-5)
     with pytest.raises(ppq.PPQError, match=r"ph_solve failed \(-4\).*max_rank"):
         ppq.ph_solve([2, 1, 0], [3, 4, 5], h, eri, max_rank=7)
     t = np.zeros(ppq.amp_count(3, 3))
