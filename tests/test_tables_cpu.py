@@ -19,6 +19,11 @@ kernels rely on (no GPU needed).
   integer, ties away from zero, and its digits recombine exactly.
 * The FP64 epilogue groups keep each output of a (c1, c2, g) in one group.
 * The generated straight-line T8 code of r1 holds the table's entries in order.
+* The FP64 epilogue's double-float W contraction, run in emulated FP32
+  operations, stays within 2^-43 of the sum of |terms| of the exact value
+  (a variant that kept the lower limbs of D in plain FP32 accumulators, an
+  earlier draft, fails it), and the float pair of an integer below 2^58 is
+  exact to 2^-48.
 """
 import numpy as np
 import pytest
@@ -375,3 +380,67 @@ def test_generated_link_code_follows_the_operator_table_and_inverts():
     v1 = run("ppq_link_apply", v0)
     assert np.abs(v1 - v0).max() > 1e-2
     assert np.abs(run("ppq_link_unapply", v1) - v0).max() < 1e-14   # exp(-T) exp(T) |ref> = |ref>
+
+
+def _fma32(a, b, c):
+    """fmaf on float32 values: the product is exact in FP64 (48 bits), the
+    sum rounded once to FP64 and then to FP32 (a double rounding that can
+    differ from a fused operation in the last bit, which the bound below
+    absorbs)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _dpair(d):
+    d2, d1, d0 = d >> 46, (d >> 23) & 0x7FFFFF, d & 0x7FFFFF
+    f2 = np.float32(d2) * np.float32(2.0 ** 46)
+    f1 = np.float32(d1) * np.float32(2.0 ** 23)
+    f0 = np.float32(d0)
+    x = np.float32(f2 + f1)
+    e1 = np.float32(f1 - np.float32(x - f2))
+    dh = np.float32(x + f0)
+    e2 = np.float32(f0 - np.float32(dh - x))
+    return dh, np.float32(e1 + e2)
+
+
+def _epilogue_sum(D, A, B):
+    """The FP64 quartic epilogue's W contraction as the kernel runs it in
+    FP32 operations: float pairs for the link coefficients, a two-product,
+    the float pair of the exact integer D, a two-sum accumulator."""
+    vh = vl = np.float32(0.0)
+    for d, a, b in zip(D, A, B):
+        ax, ay = np.float32(a), np.float32(a - np.float64(np.float32(a)))
+        bx, by = np.float32(b), np.float32(b - np.float64(np.float32(b)))
+        dh, dl = _dpair(int(d))
+        p = np.float32(ax * bx)
+        pe = _fma32(ax, bx, -p)
+        pe = _fma32(ax, by, pe)
+        pe = _fma32(ay, bx, pe)
+        hp = np.float32(dh * p)
+        he = _fma32(dh, p, -hp)
+        he = _fma32(dh, pe, he)
+        he = _fma32(dl, p, he)
+        s = np.float32(vh + hp)
+        bb = np.float32(s - vh)
+        t = np.float32(np.float32(vh - np.float32(s - bb)) + np.float32(hp - bb))
+        vl = np.float32(vl + np.float32(t + he))
+        vh = s
+    return np.float64(vh) + np.float64(vl)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_double_float_epilogue_is_accurate_to_2e_minus_43(seed):
+    from fractions import Fraction
+    rng = np.random.default_rng(seed)
+    W = 80
+    # exact slice combinations of every magnitude below 2^58, both signs
+    D = [int(rng.integers(0, 2 ** int(rng.integers(1, 58)))) * (1 if rng.random() < 0.5 else -1) for _ in range(W)]
+    A = rng.standard_normal(W) * np.exp(rng.standard_normal(W))
+    B = rng.standard_normal(W) * np.exp(rng.standard_normal(W))
+    got = _epilogue_sum(D, A, B)
+    exact = sum(Fraction(d) * Fraction(float(a)) * Fraction(float(b)) for d, a, b in zip(D, A, B))
+    scale = sum(abs(Fraction(d) * Fraction(float(a)) * Fraction(float(b))) for d, a, b in zip(D, A, B))
+    assert abs(Fraction(float(got)) - exact) <= Fraction(2) ** -43 * scale
+    # the integer split alone is exact to 2^-48
+    for d in D:
+        dh, dl = _dpair(d)
+        assert abs(Fraction(float(dh)) + Fraction(float(dl)) - d) <= Fraction(2) ** -48 * abs(d)
