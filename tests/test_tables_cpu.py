@@ -18,7 +18,8 @@ kernels rely on (no GPU needed).
   the slicing on bit patterns (integer operations only) rounds to the nearest
   integer, ties away from zero, and its digits recombine exactly.
 * The FP64 epilogue groups keep each output of a (c1, c2, g) in one group.
-* The generated straight-line T8 code of r1 holds the table's entries in order.
+* The generated straight-line T8 code of r1 and T4 code of r2 hold their
+  tables' entries in order.
 * The FP64 epilogue's double-float W contraction, run in emulated FP32
   operations, stays within 2^-43 of the sum of |terms| of the exact value
   (a variant that kept the lower limbs of D in plain FP32 accumulators, an
@@ -444,3 +445,24 @@ def test_double_float_epilogue_is_accurate_to_2e_minus_43(seed):
     for d in D:
         dh, dl = _dpair(d)
         assert abs(Fraction(float(dh)) + Fraction(float(dl)) - d) <= Fraction(2) ** -48 * abs(d)
+
+
+def test_generated_r2_t4_code_reproduces_the_table():
+    import re
+    t4 = T.t4_channels(T.Tables())
+    order = np.argsort(t4[:, 3], kind="stable")
+    ref = [tuple(int(x) for x in t4[i]) for i in order]
+    hm = {0: 5, 1: 10, 2: 15}
+    pat = re.compile(r"acc\[(\d+)\] \+= R\((-?1)\) \* cy\[(\d+)\] \* cz\[(\d+)\] \* hx\[(\d)\];")
+    got = []
+    for half, o0 in ((0, 0), (1, 15)):
+        body = _generated_function(f"ppq_r2_t4_{half}")
+        for l in body.splitlines():
+            if not l.strip().startswith("acc["):
+                continue
+            m = pat.fullmatch(l.strip())
+            assert m, l
+            k, sg, c1, c2, j = (int(x) for x in m.groups())
+            assert 0 <= k < (15 if half == 0 else 14)
+            got.append((c1, c2, hm[j], o0 + k, sg))
+    assert got == ref
