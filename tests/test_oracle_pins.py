@@ -352,3 +352,31 @@ def test_fci_lanczos_branch():
     AB = _direct_sum(A, B)
     e_ab = fci_energy(AB.h, AB.eri, 4, AB.e_const)
     assert abs(e_ab - (fci_energy(A.h, A.eri, 2, A.e_const) + fci_energy(B.h, B.eri, 2, B.e_const))) < 1e-9
+
+
+@pytest.mark.parametrize("sites,K", [(6, 2), (6, 3), (8, 2)])
+def test_residual_is_spin_flip_symmetric_for_closed_shell_hamiltonians(sites, K):
+    """A spin-free Hamiltonian in RHF orbitals commutes with the spin flip
+    (alpha <-> beta on every orbital), which maps the reference to itself up
+    to a global sign and each excitation (a_holes, a_parts, b_holes,
+    b_parts) to (b_holes, b_parts, a_holes, a_parts) with no sign (both
+    spin strings hold an even number of operators).  So amplitudes equal on
+    spin-flip partners give residuals equal on them, for every residual
+    element and for K = 2 and 3; a spin-asymmetric perturbation breaks it."""
+    H = build_ppp('polyene', sites)
+    P = Problem(H.h, H.eri, H.occ_of_pair, H.vir_of_pair, K=K)
+    man = P.cc.manifold
+    idx = {m: i for i, m in enumerate(man)}
+    flip = np.array([idx[(bh, bp, ah, ap)] for ah, ap, bh, bp in man])
+    assert (flip != np.arange(len(man))).sum() > len(man) // 2 and (flip[flip] == np.arange(len(man))).all()
+    rng = np.random.default_rng(sites + 10 * K)
+    t = rng.uniform(-0.1, 0.1, len(man))
+    t = 0.5 * (t + t[flip])
+    R, e = P.residual(t)
+    assert np.abs(R).max() > 1e-2
+    assert np.abs(R - R[flip]).max() < 1e-13
+    j = int(np.nonzero(flip != np.arange(len(man)))[0][0])
+    t2 = t.copy()
+    t2[j] += 0.05
+    R2, _ = P.residual(t2)
+    assert np.abs(R2 - R2[flip]).max() > 1e-6
