@@ -310,6 +310,27 @@ class Tables:
 
 
 # ---------------------------------------------------------------- sector / channel lists
+def spin_flip_channels(T):
+    """The spin flip (alpha <-> beta on every orbital of a site: bits 0 <-> 1
+    and 2 <-> 3 of a monomial) on the amplitude channels.  The flip unitary
+    maps E^m to sigma(m) E^flip(m), sigma(m) = (-1)^(b0 b1 + b2 b3) (the two
+    creators and the two annihilators of a site swap places), site order
+    unchanged; so a closed-shell T (invariant under the flip) has
+    t[flip(k)] = sigma(k) t[k].  Returns (flip1, sign1) over A1 and (flip2,
+    sign2) over A2, index arrays into the same channel list."""
+    def fl(m):
+        return ((m & 1) << 1) | ((m >> 1) & 1) | ((m & 4) << 1) | ((m >> 1) & 4)
+
+    def sg(m):
+        return -1 if (((m & 3) == 3) + ((m & 12) == 12)) % 2 else 1
+
+    flip1 = np.array([T.a1_index[fl(m)] for m in T.A1])
+    sign1 = np.array([sg(m) for m in T.A1])
+    flip2 = np.array([T.a2_index[(fl(a), fl(b))] for a, b in T.A2])
+    sign2 = np.array([sg(a) * sg(b) for a, b in T.A2])
+    return flip1, sign1, flip2, sign2
+
+
 def sector36(A1, A2):
     """The 36 two-site states with zero total charge and S_z change, in the
     order: ref, A2 (29), (A1, ref) (3), (ref, A1) (3).  Index c; the link

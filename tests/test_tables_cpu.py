@@ -25,6 +25,8 @@ kernels rely on (no GPU needed).
   (a variant that kept the lower limbs of D in plain FP32 accumulators, an
   earlier draft, fails it), and the float pair of an integer below 2^58 is
   exact to 2^-48.
+* The spin-flip map of the amplitude channels (spin_flip_channels) and its
+  signs hold for closed-shell amplitudes of the oracle mapped to the layout.
 """
 import numpy as np
 import pytest
@@ -466,3 +468,34 @@ def test_generated_r2_t4_code_reproduces_the_table():
             assert 0 <= k < (15 if half == 0 else 14)
             got.append((c1, c2, hm[j], o0 + k, sg))
     assert got == ref
+
+
+@pytest.mark.parametrize("sites", [6, 8])
+def test_spin_flip_channel_map_matches_the_oracle(sites):
+    """Closed-shell amplitudes in the oracle's convention (equal on the
+    alpha <-> beta exchange of every excitation, the symmetry the oracle pin
+    test_residual_is_spin_flip_symmetric_for_closed_shell_hamiltonians
+    fixes) satisfy t[flip(k)] = sigma(k) t[k] per pair and per ordered pair
+    in the C-ABI layout, with the flip and signs of spin_flip_channels."""
+    import paper_1609_00077_gb300 as ppq
+    from workloads import build_ppp
+    from oracle.detcc import enumerate_manifold
+    from tests.layout import LayoutMap
+    H = build_ppp('polyene', sites)
+    N = H.n_pairs
+    man = enumerate_manifold(H.occ_of_pair, H.vir_of_pair, 2)
+    idx = {m: i for i, m in enumerate(man)}
+    flip = np.array([idx[(bh, bp, ah, ap)] for ah, ap, bh, bp in man])
+    t = np.random.default_rng(sites).uniform(-0.1, 0.1, len(man))
+    t = 0.5 * (t + t[flip])
+    lm = LayoutMap(man, H.occ_of_pair, H.vir_of_pair, H.n_orb, ppq.amp_layout(2))
+    v = lm.to_layout(t)
+    f1, s1, f2, s2 = T.spin_flip_channels(T.Tables())
+    t1 = v[:3 * N].reshape(N, 3)
+    t2 = v[3 * N:].reshape(N, N, 29)
+    assert np.abs(t1).max() > 1e-3 and np.abs(t2).max() > 1e-3
+    assert np.abs(t1[:, f1] - s1 * t1).max() < 1e-15
+    assert np.abs(t2[:, :, f2] - s2 * t2).max() < 1e-15
+    # and the map is an involution with consistent signs
+    assert (f1[f1] == np.arange(3)).all() and (f2[f2] == np.arange(29)).all()
+    assert (s2[f2] == s2).all() and (s1[f1] == s1).all()
