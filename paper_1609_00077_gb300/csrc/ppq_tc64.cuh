@@ -19,6 +19,11 @@
 // runs in double-float arithmetic on the FP32 pipe (about 2^-46 relative per
 // term), with the power of two applied once per row and channel in FP64.
 //
+// The four groups of four epilogue warps split the channels of a chunk's
+// (c1, c2, g) by output: all channels of one output go to one group (so the
+// group owns that output's row sums), the outputs spread over the groups by
+// channel count (ppq_c9grp, generated).
+//
 // Same pipeline as k_t9_tc (producers, one MMA thread, 16 epilogue warps,
 // bounded waits): chunks hold one g each (six accumulator groups of Npad
 // columns fill TMEM, so the accumulator is single-buffered), the Cl slices are
